@@ -1,0 +1,978 @@
+// FP64 CPU oracle for Kalman-filter track fitting and combinatorial track finding.
+//
+// TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the benchmark's CPU
+// baseline leg may load this library. It shares no code with the CUDA path.
+//
+// What it follows. The paper (Sec. 1, Sec. 2) adapts the traditional Kalman filter to track
+// fitting and combinatorial track finding, propagates layer to layer (Sec. 3.1), accounts for
+// multiple scattering from the detector material (Sec. 3.1), uses a constant 3.8 T field
+// (Sec. 4), selects hits through per-layer search windows and scores candidates (Sec. 4),
+// and processes seeds in parallel without marking used hits (Sec. 3.2). It prints no formulas,
+// so every formula below is the textbook one, written out plainly:
+//   * helix motion in a uniform field Bz, state (x, y, z, kappa = q/pT, phi, theta), transverse
+//     arc length s as the path parameter, signed curvature omega = -k*Bz*kappa;
+//   * crossing of a cylinder by circle-circle intersection, of a disk by z = z0 + s*cot(theta);
+//   * Jacobian of the fixed-s map, projected onto the surface (I - t g^T / g^T t);
+//   * covariance transport C' = J C J^T + Q, Q from the Highland formula (PDG, beta = 1);
+//   * extended Kalman update with 2D hits (barrel: r*phi and z; disk: r*phi and r);
+//   * hit binning with the FP32 rounding rule below; beam search keeping K candidates.
+// Full 6x6 matrices in FP64; nothing is blocked, fused or reordered.
+//
+// Parity unpinned (the paper prints no numbers): the prior widths, the candidate ranking key,
+// the barrel half-lengths and disk extents, and the efficiency definition are readings of the
+// text, not values it gives.
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kCurv = 0.00299792458;  // GeV/(T cm)
+
+// ------------------------------------------------------------------------------------------
+// Geometry as the oracle sees it (FP32 numbers are the canonical geometry, upcast here).
+// ------------------------------------------------------------------------------------------
+}  // namespace
+
+extern "C" {
+struct OrSurface {
+  int type;  // 0 barrel cylinder radius r_or_z, z in [lo, hi]; 1 disk at z = r_or_z, r in [lo, hi]
+  float r_or_z, lo, hi, x_over_x0;
+  int n_phi, n_2nd;
+};
+struct OrGeom {
+  float bz;
+  int n_surf;
+  const OrSurface* surf;
+  float sigma_rphi, sigma_2nd;
+  float prior[5];  // sd of u, second coordinate, kappa, phi, theta at the first hit
+};
+struct OrFindParams {
+  float chi2_cut;
+  int k_max;
+  int max_miss;
+  int brute_force;  // 1: scan every hit on the surface instead of the binned window
+};
+}
+
+namespace {
+
+using Vec6 = double[6];
+using Mat6 = double[6][6];
+
+struct State {
+  double p[6];     // x, y, z, kappa, phi, theta
+  double C[6][6];  // covariance
+};
+
+inline double wrap_angle(double a) {
+  a = std::fmod(a, 2.0 * kPi);
+  if (a > kPi) a -= 2.0 * kPi;
+  if (a <= -kPi) a += 2.0 * kPi;
+  return a;
+}
+
+inline double omega_of(const OrGeom& g, double kappa) { return -kCurv * static_cast<double>(g.bz) * kappa; }
+
+// ---- helix at fixed transverse path s -------------------------------------------------------
+// f1 = sin(D)/D, f2 = (1-cos D)/D with D = omega*s; position change
+//   dx = s*(cos(phi) f1 - sin(phi) f2),  dy = s*(sin(phi) f1 + cos(phi) f2).
+inline void helix_f(double D, double& f1, double& f2) {
+  if (D == 0.0) {
+    f1 = 1.0;
+    f2 = 0.0;
+  } else {
+    const double h = std::sin(0.5 * D);
+    f1 = std::sin(D) / D;
+    f2 = 2.0 * h * h / D;
+  }
+}
+// derivatives df1/dD, df2/dD
+inline void helix_df(double D, double& d1, double& d2) {
+  if (std::fabs(D) < 1e-3) {
+    const double D2 = D * D;
+    d1 = -D / 3.0 + D * D2 / 30.0 - D * D2 * D2 / 840.0;
+    d2 = 0.5 - D2 / 8.0 + D2 * D2 / 144.0;
+  } else {
+    const double h = std::sin(0.5 * D);
+    d1 = (D * std::cos(D) - std::sin(D)) / (D * D);
+    d2 = (D * std::sin(D) - 2.0 * h * h) / (D * D);
+  }
+}
+
+void helix_at(const OrGeom& g, const double* p0, double s, double* p1) {
+  const double w = omega_of(g, p0[3]);
+  double f1, f2;
+  helix_f(w * s, f1, f2);
+  const double c = std::cos(p0[4]), sn = std::sin(p0[4]);
+  p1[0] = p0[0] + s * (c * f1 - sn * f2);
+  p1[1] = p0[1] + s * (sn * f1 + c * f2);
+  p1[2] = p0[2] + s * std::cos(p0[5]) / std::sin(p0[5]);
+  p1[3] = p0[3];
+  p1[4] = wrap_angle(p0[4] + w * s);
+  p1[5] = p0[5];
+}
+
+// Smallest s > 0 at which the helix reaches radius R; false when it does not.
+bool path_to_cylinder(const OrGeom& g, const double* p0, double R, double& s_out) {
+  const double x = p0[0], y = p0[1], phi = p0[4];
+  const double w = omega_of(g, p0[3]);
+  const double c = std::cos(phi), sn = std::sin(phi);
+  if (std::fabs(w) < 1e-9) {  // straight line
+    const double a = x * c + y * sn;
+    const double disc = a * a + R * R - (x * x + y * y);
+    if (disc < 0.0) return false;
+    const double s = -a + std::sqrt(disc);
+    if (!(s > 1e-9)) return false;
+    s_out = s;
+    return true;
+  }
+  // Circle of the helix: centre (x - sin(phi)/w, y + cos(phi)/w), radius 1/|w|.
+  const double cx = x - sn / w, cy = y + c / w;
+  const double rc = 1.0 / std::fabs(w);
+  const double d = std::hypot(cx, cy);
+  if (d == 0.0) return false;
+  const double a = (R * R - rc * rc + d * d) / (2.0 * d);
+  const double h2 = R * R - a * a;
+  if (h2 < 0.0) return false;
+  const double hh = std::sqrt(h2);
+  const double ux = cx / d, uy = cy / d;
+  double best = -1.0;
+  for (int sgn = -1; sgn <= 1; sgn += 2) {
+    const double px = a * ux - sgn * hh * uy;
+    const double py = a * uy + sgn * hh * ux;
+    // On the helix, (p - centre) = (sin(psi), -cos(psi)) / w with psi = phi + w*s.
+    const double psi = std::atan2(w * (px - cx), -w * (py - cy));
+    double dpsi = std::fmod(psi - phi, 2.0 * kPi);
+    if (w > 0) {
+      if (dpsi <= 0) dpsi += 2.0 * kPi;
+    } else {
+      if (dpsi >= 0) dpsi -= 2.0 * kPi;
+    }
+    const double s = dpsi / w;
+    if (s > 1e-9 && (best < 0 || s < best)) best = s;
+  }
+  if (best < 0) return false;
+  s_out = best;
+  return true;
+}
+
+bool path_to_disk(const double* p0, double Z, double& s_out) {
+  const double cot = std::cos(p0[5]) / std::sin(p0[5]);
+  if (cot == 0.0) return false;
+  const double s = (Z - p0[2]) / cot;
+  if (!(s > 1e-9)) return false;
+  s_out = s;
+  return true;
+}
+
+// Jacobian d(state at s)/d(state at 0) at fixed s.
+void jacobian_fixed_s(const OrGeom& g, const double* p0, double s, Mat6 J) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) J[i][j] = (i == j) ? 1.0 : 0.0;
+  const double dwdk = -kCurv * static_cast<double>(g.bz);
+  const double w = dwdk * p0[3];
+  const double D = w * s;
+  double f1, f2, d1, d2;
+  helix_f(D, f1, f2);
+  helix_df(D, d1, d2);
+  const double c = std::cos(p0[4]), sn = std::sin(p0[4]);
+  const double dx = s * (c * f1 - sn * f2), dy = s * (sn * f1 + c * f2);
+  J[0][4] = -dy;
+  J[1][4] = dx;
+  J[0][3] = dwdk * s * s * (c * d1 - sn * d2);
+  J[1][3] = dwdk * s * s * (sn * d1 + c * d2);
+  const double st = std::sin(p0[5]);
+  J[2][5] = -s / (st * st);
+  J[4][3] = dwdk * s;
+}
+
+void matmul(const Mat6 A, const Mat6 B, Mat6 out) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += A[i][k] * B[k][j];
+      out[i][j] = acc;
+    }
+}
+
+void transpose(const Mat6 A, Mat6 out) {
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) out[i][j] = A[j][i];
+}
+
+double highland(double p, double x_over_x0) {
+  return 0.0136 / p * std::sqrt(x_over_x0) * (1.0 + 0.038 * std::log(x_over_x0));
+}
+
+// Propagate to surface `si`: state moves along the helix, covariance by J C J^T with J
+// projected onto the surface, plus multiple-scattering noise of the surface's material.
+bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_out = nullptr,
+               double* s_used = nullptr) {
+  const OrSurface& S = g.surf[si];
+  double s;
+  const bool ok = (S.type == 0) ? path_to_cylinder(g, in.p, S.r_or_z, s) : path_to_disk(in.p, S.r_or_z, s);
+  if (!ok) return false;
+  helix_at(g, in.p, s, out.p);
+  Mat6 Js, J;
+  jacobian_fixed_s(g, in.p, s, Js);
+  // Direction of motion along s at the crossing and the surface gradient.
+  const double w = omega_of(g, in.p[3]);
+  const double t[6] = {std::cos(out.p[4]), std::sin(out.p[4]), std::cos(out.p[5]) / std::sin(out.p[5]), 0.0, w, 0.0};
+  double gr[6] = {0, 0, 0, 0, 0, 0};
+  if (S.type == 0) {
+    gr[0] = out.p[0];
+    gr[1] = out.p[1];
+  } else {
+    gr[2] = 1.0;
+  }
+  double gt = 0.0;
+  for (int i = 0; i < 6; ++i) gt += gr[i] * t[i];
+  if (gt == 0.0) return false;
+  Mat6 P;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) P[i][j] = (i == j ? 1.0 : 0.0) - t[i] * gr[j] / gt;
+  matmul(P, Js, J);
+  Mat6 JC, Jt;
+  matmul(J, in.C, JC);
+  transpose(J, Jt);
+  matmul(JC, Jt, out.C);
+  // Thin-layer multiple scattering at the crossing.
+  if (S.x_over_x0 > 0.0f) {
+    const double kap = out.p[3], th = out.p[5];
+    const double sth = std::sin(th), cth = std::cos(th);
+    double cos_a;
+    if (S.type == 0) {
+      const double r = std::hypot(out.p[0], out.p[1]);
+      cos_a = sth * (out.p[0] * std::cos(out.p[4]) + out.p[1] * std::sin(out.p[4])) / r;
+    } else {
+      cos_a = cth;
+    }
+    const double p = 1.0 / (std::fabs(kap) * sth);
+    const double t0 = highland(p, static_cast<double>(S.x_over_x0) / std::fabs(cos_a));
+    const double v = t0 * t0;
+    const double cot = cth / sth;
+    out.C[5][5] += v;
+    out.C[4][4] += v / (sth * sth);
+    out.C[3][5] += -kap * cot * v;
+    out.C[5][3] += -kap * cot * v;
+    out.C[3][3] += kap * kap * cot * cot * v;
+  }
+  if (jac_out)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) (*jac_out)[i][j] = J[i][j];
+  if (s_used) *s_used = s;
+  return true;
+}
+
+// ---- measurement ----------------------------------------------------------------------------
+struct Meas {
+  double r[2];     // residual
+  double H[2][6];  // measurement Jacobian
+  double V[2];     // hit variances
+};
+
+void measure(const OrGeom& g, int si, const double* p, float hphi, float hsecond, Meas& m) {
+  const OrSurface& S = g.surf[si];
+  const double x = p[0], y = p[1];
+  const double rho2 = x * x + y * y, rho = std::sqrt(rho2);
+  const double phip = std::atan2(y, x);
+  const double dphi = wrap_angle(static_cast<double>(hphi) - phip);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 6; ++j) m.H[i][j] = 0.0;
+  m.V[0] = static_cast<double>(g.sigma_rphi) * g.sigma_rphi;
+  m.V[1] = static_cast<double>(g.sigma_2nd) * g.sigma_2nd;
+  if (S.type == 0) {
+    const double R = S.r_or_z;
+    m.r[0] = R * dphi;
+    m.r[1] = static_cast<double>(hsecond) - p[2];
+    m.H[0][0] = -R * y / rho2;
+    m.H[0][1] = R * x / rho2;
+    m.H[1][2] = 1.0;
+  } else {
+    m.r[0] = rho * dphi;
+    m.r[1] = static_cast<double>(hsecond) - rho;
+    m.H[0][0] = -y / rho;
+    m.H[0][1] = x / rho;
+    m.H[1][0] = x / rho;
+    m.H[1][1] = y / rho;
+  }
+}
+
+// S = H C H^T + V; returns chi2 = r^T S^-1 r and fills S.
+double chi2_of(const Meas& m, const Mat6 C, double Sm[2][2]) {
+  double HC[2][6];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += m.H[i][k] * C[k][j];
+      HC[i][j] = acc;
+    }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += HC[i][k] * m.H[j][k];
+      Sm[i][j] = acc;
+    }
+  Sm[0][0] += m.V[0];
+  Sm[1][1] += m.V[1];
+  const double det = Sm[0][0] * Sm[1][1] - Sm[0][1] * Sm[1][0];
+  const double i00 = Sm[1][1] / det, i01 = -Sm[0][1] / det, i11 = Sm[0][0] / det;
+  return m.r[0] * (i00 * m.r[0] + i01 * m.r[1]) + m.r[1] * (i01 * m.r[0] + i11 * m.r[1]);
+}
+
+// Kalman update: K = C H^T S^-1, p += K r, C -= K H C. Returns the predicted chi2.
+double kf_update(const Meas& m, State& st) {
+  double Sm[2][2];
+  const double chi2 = chi2_of(m, st.C, Sm);
+  const double det = Sm[0][0] * Sm[1][1] - Sm[0][1] * Sm[1][0];
+  const double Si[2][2] = {{Sm[1][1] / det, -Sm[0][1] / det}, {-Sm[1][0] / det, Sm[0][0] / det}};
+  double CHt[6][2];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 2; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += st.C[i][k] * m.H[j][k];
+      CHt[i][j] = acc;
+    }
+  double K[6][2];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 2; ++j) K[i][j] = CHt[i][0] * Si[0][j] + CHt[i][1] * Si[1][j];
+  for (int i = 0; i < 6; ++i) st.p[i] += K[i][0] * m.r[0] + K[i][1] * m.r[1];
+  st.p[4] = wrap_angle(st.p[4]);
+  double HC[2][6];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += m.H[i][k] * st.C[k][j];
+      HC[i][j] = acc;
+    }
+  Mat6 Cn;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) Cn[i][j] = st.C[i][j] - (K[i][0] * HC[0][j] + K[i][1] * HC[1][j]);
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) st.C[i][j] = 0.5 * (Cn[i][j] + Cn[j][i]);
+  return chi2;
+}
+
+// ---- hits -------------------------------------------------------------------------------------
+void hit_position(const OrGeom& g, int si, float hphi, float hsecond, double* xyz) {
+  const OrSurface& S = g.surf[si];
+  const double ph = hphi;
+  if (S.type == 0) {
+    xyz[0] = S.r_or_z * std::cos(ph);
+    xyz[1] = S.r_or_z * std::sin(ph);
+    xyz[2] = hsecond;
+  } else {
+    xyz[0] = static_cast<double>(hsecond) * std::cos(ph);
+    xyz[1] = static_cast<double>(hsecond) * std::sin(ph);
+    xyz[2] = S.r_or_z;
+  }
+}
+
+// Seed state at hit 1 from the circle through three hits (transverse plane) and the
+// straight line in (arc length, z); prior covariance on the tangent space of hit 1's surface.
+bool seed_state(const OrGeom& g, const float* hits, const int* hsurf, const int* ids, State& st) {
+  double P[3][3];
+  for (int i = 0; i < 3; ++i) hit_position(g, hsurf[ids[i]], hits[2 * ids[i]], hits[2 * ids[i] + 1], P[i]);
+  const double x1 = P[0][0], y1 = P[0][1], x2 = P[1][0], y2 = P[1][1], x3 = P[2][0], y3 = P[2][1];
+  const double D = 2.0 * (x1 * (y2 - y3) + x2 * (y3 - y1) + x3 * (y1 - y2));
+  const double cross = (x2 - x1) * (y3 - y2) - (y2 - y1) * (x3 - x2);
+  double w = 0.0, phi, s13;
+  const double scale = std::max({std::fabs(x1), std::fabs(y1), std::fabs(x3), std::fabs(y3), 1.0});
+  if (std::fabs(D) > 1e-12 * scale * scale) {
+    const double a1 = x1 * x1 + y1 * y1, a2 = x2 * x2 + y2 * y2, a3 = x3 * x3 + y3 * y3;
+    const double cx = (a1 * (y2 - y3) + a2 * (y3 - y1) + a3 * (y1 - y2)) / D;
+    const double cy = (a1 * (x3 - x2) + a2 * (x1 - x3) + a3 * (x2 - x1)) / D;
+    const double rc = std::hypot(x1 - cx, y1 - cy);
+    w = (cross > 0 ? 1.0 : -1.0) / rc;
+    // Direction of motion at hit 1: (cos phi, sin phi) = w * (-(y1 - cy), x1 - cx).
+    phi = std::atan2(w * (x1 - cx), -w * (y1 - cy));
+    const double ax = x1 - cx, ay = y1 - cy, bx = x3 - cx, by = y3 - cy;
+    const double swept = std::atan2(ax * by - ay * bx, ax * bx + ay * by);
+    s13 = swept / w;
+    if (s13 <= 0) s13 += 2.0 * kPi / std::fabs(w);
+  } else {
+    phi = std::atan2(y3 - y1, x3 - x1);
+    s13 = std::hypot(x3 - x1, y3 - y1);
+  }
+  if (!(s13 > 0)) return false;
+  const double theta = std::atan2(s13, P[2][2] - P[0][2]);
+  st.p[0] = x1;
+  st.p[1] = y1;
+  st.p[2] = P[0][2];
+  st.p[3] = -w / (kCurv * static_cast<double>(g.bz));
+  st.p[4] = phi;
+  st.p[5] = theta;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) st.C[i][j] = 0.0;
+  const OrSurface& S = g.surf[hsurf[ids[0]]];
+  const double pp = std::atan2(y1, x1);
+  const double eu[3] = {-std::sin(pp), std::cos(pp), 0.0};
+  const double su = g.prior[0], s2 = g.prior[1];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) st.C[i][j] += su * su * eu[i] * eu[j];
+  if (S.type == 0) {
+    st.C[2][2] += s2 * s2;
+  } else {
+    const double er[3] = {std::cos(pp), std::sin(pp), 0.0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) st.C[i][j] += s2 * s2 * er[i] * er[j];
+  }
+  st.C[3][3] = static_cast<double>(g.prior[2]) * g.prior[2];
+  st.C[4][4] = static_cast<double>(g.prior[3]) * g.prior[3];
+  st.C[5][5] = static_cast<double>(g.prior[4]) * g.prior[4];
+  return true;
+}
+
+void pack_cov(const Mat6 C, float* out21, double* out21d) {
+  int k = 0;
+  for (int i = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j, ++k) {
+      if (out21) out21[k] = static_cast<float>(C[i][j]);
+      if (out21d) out21d[k] = C[i][j];
+    }
+}
+
+template <class F>
+void parallel_for(long long n, int n_threads, F&& f) {
+  int nt = n_threads > 0 ? n_threads : static_cast<int>(std::thread::hardware_concurrency());
+  nt = static_cast<int>(std::max<long long>(1, std::min<long long>(nt, n)));
+  if (nt <= 1) {
+    for (long long i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<long long> next(0);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&]() {
+      for (;;) {
+        const long long i0 = next.fetch_add(64);
+        if (i0 >= n) break;
+        const long long i1 = std::min(n, i0 + 64);
+        for (long long i = i0; i < i1; ++i) f(i);
+      }
+    });
+  for (auto& th : pool) th.join();
+}
+
+// ---- hit binning: FP32, every operation rounded to nearest, no contraction -----------------
+// phi-bin = clamp(floor((phi + pi_f) * sphi), 0, n_phi - 1) with sphi = (float)(n_phi / 2pi);
+// 2nd-bin = clamp(floor((v - lo_f) * s2), 0, n_2nd - 1) with s2 = (float)(n_2nd / (hi_f - lo_f)).
+// The build flags forbid FMA contraction so each float operation rounds on its own.
+struct BinRule {
+  float pi_f, sphi, lo, s2;
+  int n_phi, n_2nd;
+  explicit BinRule(const OrSurface& S) {
+    pi_f = static_cast<float>(kPi);
+    sphi = static_cast<float>(static_cast<double>(S.n_phi) / (2.0 * kPi));
+    lo = S.lo;
+    s2 = static_cast<float>(static_cast<double>(S.n_2nd) / (static_cast<double>(S.hi) - static_cast<double>(S.lo)));
+    n_phi = S.n_phi;
+    n_2nd = S.n_2nd;
+  }
+  int phi_bin(float phi) const {
+    const float a = phi + pi_f;
+    const float b = a * sphi;
+    const float f = std::floor(b);
+    const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
+    return std::min(std::max(k, 0), n_phi - 1);
+  }
+  int second_bin(float v) const {
+    const float a = v - lo;
+    const float b = a * s2;
+    const float f = std::floor(b);
+    const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
+    return std::min(std::max(k, 0), n_2nd - 1);
+  }
+};
+
+int max_bins(const OrGeom& g) {
+  int m = 0;
+  for (int s = 0; s < g.n_surf; ++s) m = std::max(m, g.surf[s].n_phi * g.surf[s].n_2nd);
+  return m;
+}
+
+struct Index {
+  int nb = 0;                   // bins per slab (max over surfaces)
+  std::vector<long long> off;   // [(e*n_surf+s)*(nb+1) + b]: global position of bin b's first hit
+  std::vector<float> sorted;    // [n_hits][2]
+  std::vector<int> ids;         // [n_hits] original hit id
+};
+
+// Counting sort per (event, surface) slab: bin = phi_bin * n_2nd + second_bin; within a bin,
+// ascending hit id. Slabs keep their position in the hit array.
+void build_index(const OrGeom& g, const float* hits, const long long* slab_off, int n_events, Index& ix) {
+  ix.nb = max_bins(g);
+  const long long n_slabs = static_cast<long long>(n_events) * g.n_surf;
+  const long long n_hits = slab_off[n_slabs];
+  ix.off.assign(n_slabs * (ix.nb + 1), 0);
+  ix.sorted.assign(2 * n_hits, 0.0f);
+  ix.ids.assign(n_hits, 0);
+  for (long long sl = 0; sl < n_slabs; ++sl) {
+    const int si = static_cast<int>(sl % g.n_surf);
+    const OrSurface& S = g.surf[si];
+    const BinRule br(S);
+    const long long h0 = slab_off[sl], h1 = slab_off[sl + 1];
+    std::vector<long long> count(ix.nb + 1, 0);
+    std::vector<int> bin(h1 - h0);
+    for (long long h = h0; h < h1; ++h) {
+      const int b = br.phi_bin(hits[2 * h]) * S.n_2nd + br.second_bin(hits[2 * h + 1]);
+      bin[h - h0] = b;
+      count[b + 1]++;
+    }
+    long long* o = &ix.off[sl * (ix.nb + 1)];
+    o[0] = h0;
+    for (int b = 0; b < ix.nb; ++b) o[b + 1] = o[b] + count[b + 1];
+    std::vector<long long> cursor(o, o + ix.nb);
+    for (long long h = h0; h < h1; ++h) {  // ascending id keeps equal bins in id order
+      const long long pos = cursor[bin[h - h0]]++;
+      ix.sorted[2 * pos] = hits[2 * h];
+      ix.sorted[2 * pos + 1] = hits[2 * h + 1];
+      ix.ids[pos] = static_cast<int>(h);
+    }
+  }
+}
+
+// ---- finding ----------------------------------------------------------------------------------
+struct Cand {
+  State st;
+  int n_hits = 0, n_miss = 0;
+  double chi2 = 0.0;
+  int surf = -1;
+  bool stopped = false;
+  std::vector<int> hits;  // hit id per step, -1 = miss
+};
+
+// Next surface outward from a candidate: the next barrel layer beyond its radius (accepted if
+// the crossing lies within the layer's z extent) and the next disk beyond |z| in the direction
+// of motion (accepted if the crossing radius is within the disk); the nearer accepted one wins.
+int next_surface(const OrGeom& g, const State& st, double* s_next) {
+  const double rho = std::hypot(st.p[0], st.p[1]);
+  const double z = st.p[2];
+  const double cot = std::cos(st.p[5]) / std::sin(st.p[5]);
+  int best = -1;
+  double best_s = 0.0;
+  int nb = -1;
+  for (int s = 0; s < g.n_surf; ++s) {
+    const OrSurface& S = g.surf[s];
+    if (S.type == 0 && S.r_or_z > rho + 0.01 && (nb < 0 || S.r_or_z < g.surf[nb].r_or_z)) nb = s;
+  }
+  if (nb >= 0) {
+    double s;
+    if (path_to_cylinder(g, st.p, g.surf[nb].r_or_z, s)) {
+      double q[6];
+      helix_at(g, st.p, s, q);
+      if (q[2] >= g.surf[nb].lo && q[2] <= g.surf[nb].hi) {
+        best = nb;
+        best_s = s;
+      }
+    }
+  }
+  int nd = -1;
+  for (int s = 0; s < g.n_surf; ++s) {
+    const OrSurface& S = g.surf[s];
+    if (S.type != 1) continue;
+    if ((cot > 0 && S.r_or_z > z + 0.01) || (cot < 0 && S.r_or_z < z - 0.01)) {
+      if (nd < 0 || std::fabs(S.r_or_z) < std::fabs(g.surf[nd].r_or_z)) nd = s;
+    }
+  }
+  if (nd >= 0) {
+    double s;
+    if (path_to_disk(st.p, g.surf[nd].r_or_z, s)) {
+      double q[6];
+      helix_at(g, st.p, s, q);
+      const double r = std::hypot(q[0], q[1]);
+      if (r >= g.surf[nd].lo && r <= g.surf[nd].hi && (best < 0 || s < best_s)) {
+        best = nd;
+        best_s = s;
+      }
+    }
+  }
+  if (s_next) *s_next = best_s;
+  return best;
+}
+
+struct Found {
+  int hit;
+  double chi2;
+};
+
+struct Ctx {
+  const OrGeom* g;
+  const float* hits;
+  const int* hsurf;
+  const long long* slab_off;
+  const Index* ix;
+  OrFindParams prm;
+};
+
+// All hits of surface si in event ev whose chi2 against the predicted state is below the cut.
+// Binned: the window is the bounding box of the chi2 ellipse, padded, turned into bin ranges by
+// the same FP32 rule as the index; brute force: every hit of the surface.
+void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<Found>& out) {
+  out.clear();
+  const OrGeom& g = *cx.g;
+  const OrSurface& S = g.surf[si];
+  const long long sl = static_cast<long long>(ev) * g.n_surf + si;
+  const double cut = cx.prm.chi2_cut;
+  auto try_hit = [&](float hphi, float h2, int id) {
+    Meas m;
+    measure(g, si, pred.p, hphi, h2, m);
+    double Sm[2][2];
+    const double c2 = chi2_of(m, pred.C, Sm);
+    if (c2 < cut) out.push_back({id, c2});
+  };
+  if (cx.prm.brute_force) {
+    for (long long h = cx.slab_off[sl]; h < cx.slab_off[sl + 1]; ++h) try_hit(cx.hits[2 * h], cx.hits[2 * h + 1], static_cast<int>(h));
+    return;
+  }
+  // Window half-widths from the diagonal of S.
+  Meas m0;
+  measure(g, si, pred.p, 0.0f, 0.0f, m0);
+  double Sm[2][2];
+  chi2_of(m0, pred.C, Sm);
+  const double x = pred.p[0], y = pred.p[1];
+  const double rho = std::hypot(x, y);
+  const double rref = (S.type == 0) ? static_cast<double>(S.r_or_z) : rho;
+  double dphi = std::sqrt(cut * Sm[0][0]) / rref;
+  dphi = dphi * (1.0 + 1e-4) + 1e-5;
+  double d2 = std::sqrt(cut * Sm[1][1]);
+  d2 = d2 * (1.0 + 1e-4) + 1e-4;
+  const double phip = std::atan2(y, x);
+  const double c2 = (S.type == 0) ? pred.p[2] : rho;
+  const BinRule br(S);
+  int pb0, npb;
+  if (!(dphi < kPi * (1.0 - 2.0 / S.n_phi))) {
+    pb0 = 0;
+    npb = S.n_phi;
+  } else {
+    pb0 = br.phi_bin(static_cast<float>(wrap_angle(phip - dphi)));
+    const int pb1 = br.phi_bin(static_cast<float>(wrap_angle(phip + dphi)));
+    npb = ((pb1 - pb0) % S.n_phi + S.n_phi) % S.n_phi + 1;
+  }
+  const int zb0 = br.second_bin(static_cast<float>(std::max(c2 - d2, -1e30)));
+  const int zb1 = br.second_bin(static_cast<float>(std::min(c2 + d2, 1e30)));
+  const long long* o = &cx.ix->off[sl * (cx.ix->nb + 1)];
+  for (int k = 0; k < npb; ++k) {
+    const int pb = (pb0 + k) % S.n_phi;
+    const long long a = o[pb * S.n_2nd + zb0], b = o[pb * S.n_2nd + zb1 + 1];
+    for (long long q = a; q < b; ++q) try_hit(cx.ix->sorted[2 * q], cx.ix->sorted[2 * q + 1], cx.ix->ids[q]);
+  }
+}
+
+struct Child {
+  int parent;
+  int hit;       // -1: miss child or carried candidate
+  int kind;      // 0 hit child, 1 miss child, 2 carried
+  int n_hits;
+  double chi2;   // total
+  double chi2_hit;
+};
+
+bool child_less(const Child& a, const Child& b) {
+  if (a.n_hits != b.n_hits) return a.n_hits > b.n_hits;
+  if (a.chi2 != b.chi2) return a.chi2 < b.chi2;
+  if (a.parent != b.parent) return a.parent < b.parent;
+  if (a.kind != b.kind) return a.kind < b.kind;
+  return a.hit < b.hit;
+}
+
+struct Counters {
+  long long n_prop = 0, n_chi2 = 0, n_upd = 0;
+};
+
+// Beam search for one seed. Returns false if the seed could not be formed.
+bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, Counters& cnt) {
+  const OrGeom& g = *cx.g;
+  Cand c0;
+  if (!seed_state(g, cx.hits, cx.hsurf, seed_ids, c0.st)) return false;
+  // Fit the seed hits: update with hit 1, then propagate + update through hits 2, 3.
+  for (int k = 0; k < 3; ++k) {
+    const int id = seed_ids[k];
+    const int si = cx.hsurf[id];
+    if (k > 0) {
+      State pr;
+      if (!propagate(g, c0.st, si, pr)) return false;
+      c0.st = pr;
+      cnt.n_prop++;
+    }
+    Meas m;
+    measure(g, si, c0.st.p, cx.hits[2 * id], cx.hits[2 * id + 1], m);
+    c0.chi2 += kf_update(m, c0.st);
+    cnt.n_chi2++;
+    cnt.n_upd++;
+    c0.hits.push_back(id);
+    c0.surf = si;
+  }
+  c0.n_hits = 3;
+  std::vector<Cand> cands{c0};
+  std::vector<Found> found;
+  std::vector<Child> pool;
+  std::vector<State> pred;
+  for (int step = 3; step < lmax; ++step) {
+    bool any_active = false;
+    for (const Cand& c : cands) any_active |= !c.stopped;
+    if (!any_active) break;
+    pool.clear();
+    pred.assign(cands.size(), State());
+    std::vector<int> pred_surf(cands.size(), -1);
+    for (int ci = 0; ci < static_cast<int>(cands.size()); ++ci) {
+      const Cand& c = cands[ci];
+      if (c.stopped) {
+        pool.push_back({ci, -1, 2, c.n_hits, c.chi2, 0.0});
+        continue;
+      }
+      const int si = next_surface(g, c.st, nullptr);
+      if (si < 0 || !propagate(g, c.st, si, pred[ci])) {
+        pool.push_back({ci, -1, 2, c.n_hits, c.chi2, 0.0});
+        continue;
+      }
+      cnt.n_prop++;
+      pred_surf[ci] = si;
+      search_hits(cx, ev, si, pred[ci], found);
+      cnt.n_chi2 += static_cast<long long>(found.size());
+      if (!found.empty()) {
+        for (const Found& f : found) pool.push_back({ci, f.hit, 0, c.n_hits + 1, c.chi2 + f.chi2, f.chi2});
+      } else if (c.n_miss < cx.prm.max_miss) {
+        pool.push_back({ci, -1, 1, c.n_hits, c.chi2, 0.0});
+      } else {
+        pool.push_back({ci, -1, 2, c.n_hits, c.chi2, 0.0});
+      }
+    }
+    std::sort(pool.begin(), pool.end(), child_less);
+    if (static_cast<int>(pool.size()) > cx.prm.k_max) pool.resize(cx.prm.k_max);
+    std::vector<Cand> next;
+    next.reserve(pool.size());
+    for (const Child& ch : pool) {
+      const Cand& par = cands[ch.parent];
+      Cand n = par;
+      if (ch.kind == 2) {
+        n.stopped = true;
+      } else {
+        n.st = pred[ch.parent];
+        n.surf = pred_surf[ch.parent];
+        if (ch.kind == 0) {
+          Meas m;
+          measure(g, n.surf, n.st.p, cx.hits[2 * ch.hit], cx.hits[2 * ch.hit + 1], m);
+          kf_update(m, n.st);
+          cnt.n_upd++;
+          n.n_hits += 1;
+          n.chi2 = ch.chi2;
+          n.hits.push_back(ch.hit);
+        } else {
+          n.n_miss += 1;
+          n.hits.push_back(-1);
+        }
+      }
+      next.push_back(std::move(n));
+    }
+    cands.swap(next);
+  }
+  best = cands.front();
+  return true;
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+int or_version() { return 1; }
+
+// Propagate one state (p[6], full C[36] row-major) to surface `surf`. Outputs the new state,
+// covariance, the projected Jacobian J[36] and the path s. Returns 0, or -1 if not reached.
+int or_propagate(const OrGeom* g, const double* p, const double* C, int surf, double* p_out, double* C_out,
+                 double* J_out, double* s_out) {
+  State in, out;
+  for (int i = 0; i < 6; ++i) in.p[i] = p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) in.C[i][j] = C ? C[6 * i + j] : 0.0;
+  Mat6 J;
+  double s;
+  if (!propagate(*g, in, surf, out, &J, &s)) return -1;
+  for (int i = 0; i < 6; ++i) p_out[i] = out.p[i];
+  if (C_out)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) C_out[6 * i + j] = out.C[i][j];
+  if (J_out)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) J_out[6 * i + j] = J[i][j];
+  if (s_out) *s_out = s;
+  return 0;
+}
+
+// Position of the helix at fixed transverse path s (no surface), for finite-difference tests.
+void or_helix_at(const OrGeom* g, const double* p, double s, double* p_out) { helix_at(*g, p, s, p_out); }
+
+// Seed state + prior from three hit ids.
+int or_seed(const OrGeom* g, const float* hits, const int* hsurf, const int* ids, double* p_out, double* C_out) {
+  State st;
+  if (!seed_state(*g, hits, hsurf, ids, st)) return -1;
+  for (int i = 0; i < 6; ++i) p_out[i] = st.p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C_out[6 * i + j] = st.C[i][j];
+  return 0;
+}
+
+// Fit tracks over known hit sequences. track_hits is [n][lmax] row-major, -1 padded (the
+// first -1 ends the track). Outputs per track: p[6], C packed upper-triangle [21] (row-major
+// i<=j), chi2 total, ndof = 2N-5, status (0 ok, 1 seed failed, 2 propagation failed, 3 < 3 hits).
+// Optional per-hit outputs [n][lmax]: predicted chi2 and the two normalised predicted residuals.
+void or_fit(const OrGeom* g, const float* hits, const int* hsurf, const int* track_hits, long long n, int lmax,
+            int n_threads, double* p_out, double* C_out, double* chi2_out, int* ndof_out, int* status_out,
+            double* hit_chi2, double* hit_pull) {
+  parallel_for(n, n_threads, [&](long long t) {
+    const int* th = track_hits + t * lmax;
+    int nh = 0;
+    while (nh < lmax && th[nh] >= 0) ++nh;
+    if (hit_chi2)
+      for (int k = 0; k < lmax; ++k) hit_chi2[t * lmax + k] = -1.0;
+    State st{};
+    int status = 0;
+    double chi2 = 0.0;
+    if (nh < 3) {
+      status = 3;
+    } else if (!seed_state(*g, hits, hsurf, th, st)) {
+      status = 1;
+    } else {
+      for (int k = 0; k < nh; ++k) {
+        const int id = th[k];
+        const int si = hsurf[id];
+        if (k > 0) {
+          State pr;
+          if (!propagate(*g, st, si, pr)) {
+            status = 2;
+            break;
+          }
+          st = pr;
+        }
+        Meas m;
+        measure(*g, si, st.p, hits[2 * id], hits[2 * id + 1], m);
+        if (hit_pull) {
+          double Sm[2][2];
+          chi2_of(m, st.C, Sm);
+          hit_pull[(t * lmax + k) * 2 + 0] = m.r[0] / std::sqrt(Sm[0][0]);
+          hit_pull[(t * lmax + k) * 2 + 1] = m.r[1] / std::sqrt(Sm[1][1]);
+        }
+        const double c2 = kf_update(m, st);
+        if (hit_chi2) hit_chi2[t * lmax + k] = c2;
+        chi2 += c2;
+      }
+    }
+    for (int i = 0; i < 6; ++i) p_out[6 * t + i] = status == 0 ? st.p[i] : NAN;
+    pack_cov(st.C, nullptr, C_out + 21 * t);
+    if (status != 0)
+      for (int i = 0; i < 21; ++i) C_out[21 * t + i] = NAN;
+    chi2_out[t] = status == 0 ? chi2 : NAN;
+    ndof_out[t] = 2 * nh - 5;
+    status_out[t] = status;
+  });
+}
+
+// Hit index. bin_off is [n_events*n_surf][nb+1] (nb = max n_phi*n_2nd), absolute positions
+// into sorted_hits[n_hits][2] / sorted_ids[n_hits].
+int or_index_bins(const OrGeom* g) { return max_bins(*g); }
+
+void or_build_index(const OrGeom* g, const float* hits, const long long* slab_off, int n_events, long long* bin_off,
+                    float* sorted_hits, int* sorted_ids) {
+  Index ix;
+  build_index(*g, hits, slab_off, n_events, ix);
+  std::memcpy(bin_off, ix.off.data(), sizeof(long long) * ix.off.size());
+  std::memcpy(sorted_hits, ix.sorted.data(), sizeof(float) * ix.sorted.size());
+  std::memcpy(sorted_ids, ix.ids.data(), sizeof(int) * ix.ids.size());
+}
+
+// Bin of one value by the FP32 rule (tests compare it with the index).
+void or_bin_of(const OrGeom* g, int surf, float phi, float second, int* phi_bin, int* second_bin) {
+  const BinRule br(g->surf[surf]);
+  *phi_bin = br.phi_bin(phi);
+  *second_bin = br.second_bin(second);
+}
+
+// Hits passing the chi2 cut on surface `surf` of event `ev` for a predicted state (p, full C),
+// by the binned window (brute=0) or by scanning every hit (brute=1). Returns the count written
+// (at most cap), ids and chi2 in scan order.
+int or_search(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
+              const double* p, const double* C, int ev, int surf, float chi2_cut, int brute, int cap, int* ids_out,
+              double* chi2_out) {
+  Index ix;
+  if (!brute) build_index(*g, hits, slab_off, n_events, ix);
+  Ctx cx{g, hits, hsurf, slab_off, &ix, {chi2_cut, 1, 0, brute}};
+  State st;
+  for (int i = 0; i < 6; ++i) st.p[i] = p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) st.C[i][j] = C[6 * i + j];
+  std::vector<Found> found;
+  search_hits(cx, ev, surf, st, found);
+  const int n = std::min(cap, static_cast<int>(found.size()));
+  for (int i = 0; i < n; ++i) {
+    ids_out[i] = found[i].hit;
+    chi2_out[i] = found[i].chi2;
+  }
+  return static_cast<int>(found.size());
+}
+
+// Kalman update of one state (p[6], full C[36]) with hit (phi, second) on surface `surf`.
+// Writes the updated state and covariance; returns the predicted chi2.
+double or_update(const OrGeom* g, const double* p, const double* C, int surf, float hphi, float hsecond,
+                 double* p_out, double* C_out) {
+  State st;
+  for (int i = 0; i < 6; ++i) st.p[i] = p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) st.C[i][j] = C[6 * i + j];
+  Meas m;
+  measure(*g, surf, st.p, hphi, hsecond, m);
+  const double chi2 = kf_update(m, st);
+  for (int i = 0; i < 6; ++i) p_out[i] = st.p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) C_out[6 * i + j] = st.C[i][j];
+  return chi2;
+}
+
+// Next surface rule, for tests.
+int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
+  State st;
+  for (int i = 0; i < 6; ++i) st.p[i] = p[i];
+  return next_surface(*g, st, s_out);
+}
+
+// Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. Outputs per
+// seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
+// status (0 ok, 1 seed failed). counters[3] += propagations, chi2 evaluations that passed the
+// cut, Kalman updates.
+void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
+             const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
+             int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
+             long long* counters) {
+  Index ix;
+  if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm};
+  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0);
+  parallel_for(n, n_threads, [&](long long i) {
+    Cand best;
+    Counters cnt;
+    const bool ok = find_one(cx, seeds + 3 * i, seed_event[i], lmax, best, cnt);
+    for (int k = 0; k < lmax; ++k) hits_out[i * lmax + k] = (ok && k < static_cast<int>(best.hits.size())) ? best.hits[k] : -1;
+    nhits_out[i] = ok ? best.n_hits : 0;
+    chi2_out[i] = ok ? best.chi2 : NAN;
+    for (int k = 0; k < 6; ++k) p_out[6 * i + k] = ok ? best.st.p[k] : NAN;
+    pack_cov(best.st.C, nullptr, C_out + 21 * i);
+    status_out[i] = ok ? 0 : 1;
+    c_prop += cnt.n_prop;
+    c_chi2 += cnt.n_chi2;
+    c_upd += cnt.n_upd;
+  });
+  if (counters) {
+    counters[0] += c_prop.load();
+    counters[1] += c_chi2.load();
+    counters[2] += c_upd.load();
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+"""Pins of the oracle's combinatorial finder (CPU only).
+
+The beam search is checked against plain search loops written here from the oracle's single-step
+primitives (propagate, brute-force hit search, update): K = 1 is the greedy best-chi2 walk, and a
+K larger than the number of branches is exhaustive enumeration. On clean sparse events every true
+hit must be found. The binned and brute-force search modes give identical tracks.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _seed_fit(g, b, ids):
+    """Seed state at hit 1, then update with hit 1 and propagate + update through hits 2, 3."""
+    p, C = oracle.seed(g, b.hits, b.hit_surface, ids)
+    chi2 = 0.0
+    for k, h in enumerate(ids):
+        s = int(b.hit_surface[h])
+        if k > 0:
+            p, C, _, _ = oracle.propagate(g, p, C, s)
+        p, C, c2 = oracle.update(g, p, C, s, b.hits[h])
+        chi2 += c2
+    return p, C, chi2
+
+
+def _expand(g, b, wl, ev, p, C):
+    """One step: next surface, prediction, and every passing hit (id, chi2), or None."""
+    surf, _ = oracle.next_surface(g, p)
+    if surf < 0:
+        return None
+    r = oracle.propagate(g, p, C, surf)
+    if r is None:
+        return None
+    pp, CC = r[0], r[1]
+    ids, c2 = oracle.search(g, b, pp, CC, ev, surf, wl.chi2_cut, brute=True)
+    return surf, pp, CC, ids, c2
+
+
+def _greedy(g, b, wl, seed_ids, ev, lmax):
+    p, C, chi2 = _seed_fit(g, b, seed_ids)
+    hits = list(seed_ids)
+    n_miss = 0
+    while len(hits) < lmax:
+        e = _expand(g, b, wl, ev, p, C)
+        if e is None:
+            break
+        surf, pp, CC, ids, c2 = e
+        if len(ids):
+            j = min(range(len(ids)), key=lambda i: (c2[i], ids[i]))
+            p, C, _ = oracle.update(g, pp, CC, surf, b.hits[ids[j]])
+            chi2 += c2[j]
+            hits.append(int(ids[j]))
+        elif n_miss < wl.max_miss:
+            p, C = pp, CC
+            n_miss += 1
+            hits.append(-1)
+        else:
+            break
+    return hits + [-1] * (lmax - len(hits))
+
+
+def _enumerate(g, b, wl, seed_ids, ev, lmax):
+    """Every branch of the search tree; best by (most hits, lowest chi2)."""
+    p, C, chi2 = _seed_fit(g, b, seed_ids)
+    leaves = []
+
+    def rec(p, C, chi2, hits, n_miss, n_hits):
+        if len(hits) >= lmax:
+            leaves.append((-n_hits, chi2, hits))
+            return
+        e = _expand(g, b, wl, ev, p, C)
+        if e is None:
+            leaves.append((-n_hits, chi2, hits))
+            return
+        surf, pp, CC, ids, c2 = e
+        if len(ids):
+            for i in range(len(ids)):
+                pn, Cn, _ = oracle.update(g, pp, CC, surf, b.hits[ids[i]])
+                rec(pn, Cn, chi2 + c2[i], hits + [int(ids[i])], n_miss, n_hits + 1)
+        elif n_miss < wl.max_miss:
+            rec(pp, CC, chi2, hits + [-1], n_miss + 1, n_hits)
+        else:
+            leaves.append((-n_hits, chi2, hits))
+
+    rec(p, C, chi2, list(seed_ids), 0, 3)
+    leaves.sort(key=lambda x: (x[0], x[1]))
+    best = leaves[0][2]
+    return best + [-1] * (lmax - len(best)), len(leaves), leaves
+
+
+def _tiny(wl_name, n_tracks, noise, seed):
+    wl = synth.workload(wl_name, n_events=2, tracks_lo=n_tracks, tracks_hi=n_tracks, noise_frac=noise, seed=seed)
+    return wl, oracle.Geometry(wl), synth.generate(wl)
+
+
+@pytest.mark.parametrize("wl_name", ["find", "hi_occ"])
+def test_k1_is_greedy_best_chi2(wl_name):
+    wl, g, b = _tiny(wl_name, 25, 3.0, 21)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    f = oracle.find(g, b, sh, ev, k_max=1)
+    for i in range(len(st)):
+        ref = _greedy(g, b, wl, sh[i], ev[i], wl.lmax)
+        assert f["hits"][i].tolist() == ref, i
+
+
+def test_large_k_is_exhaustive_enumeration():
+    """Dense noise (100 noise hits per signal hit) makes branches; with K above the number of
+    leaves the beam search keeps everything and must return the enumeration's best."""
+    wl, g, b = _tiny("find", 12, 100.0, 22)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    f = oracle.find(g, b, sh, ev, k_max=400)
+    branched = 0
+    for i in range(len(st)):
+        best, n_leaves, _ = _enumerate(g, b, wl, sh[i], ev[i], wl.lmax)
+        if n_leaves > 400:
+            continue
+        branched += n_leaves > 1
+        assert f["hits"][i].tolist() == best, i
+    assert branched >= 3
+
+
+@pytest.mark.parametrize("wl_name", ["find", "hi_occ"])
+def test_clean_sparse_events_find_every_true_hit(wl_name):
+    """No noise, few tracks: every seed's best track is its own sim track, hit for hit."""
+    wl = synth.workload(wl_name, n_events=3, tracks_lo=40, tracks_hi=40, noise_frac=0.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    f = oracle.find(g, b, sh, b.track_event[st])
+    assert np.array_equal(f["hits"], b.track_hits[st])
+    assert np.array_equal(f["n_hits"], b.track_nhits[st])
+
+
+@pytest.mark.parametrize("wl_name", ["find", "hi_occ"])
+def test_binned_and_brute_force_finding_agree(wl_name):
+    wl = synth.workload(wl_name, n_events=2, tracks_lo=60, tracks_hi=60, noise_frac=2.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    a = oracle.find(g, b, sh, ev)
+    c = oracle.find(g, b, sh, ev, brute_force=True)
+    for k in ("hits", "n_hits", "status"):
+        assert np.array_equal(a[k], c[k])
+    assert np.array_equal(a["chi2"], c["chi2"])

@@ -1,0 +1,157 @@
+"""Pins of the oracle's helix propagation and covariance transport (CPU only).
+
+The propagator is checked against things other than itself: the generator's independent
+root-finding crossing solver (a different helix parametrisation), central finite differences
+for the Jacobian, the straight-line limit and geometric invariants of the helix.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _wrap(a):
+    return (a + np.pi) % (2 * np.pi) - np.pi
+
+
+@pytest.mark.parametrize("wl_name", ["fit_small", "hi_occ"])
+def test_propagation_reproduces_generator_crossings(wl_name):
+    """No smearing, no scattering: from the true state at crossing k, the oracle's closed-form
+    propagation lands on the generator's root-found crossing k+1 to 1e-9 cm."""
+    wl = synth.workload(wl_name, n_events=1, tracks_lo=300, tracks_hi=300, ms_on=False)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl, smear=False, record_truth=True)
+    worst_pos, worst_ang, n_checked = 0.0, 0.0, 0
+    for t in range(b.n_tracks):
+        nh = b.track_nhits[t]
+        for k in range(nh - 1):
+            r = oracle.propagate(g, b.truth_in[t, k], None, b.track_surf[t, k + 1])
+            assert r is not None
+            p, _, _, _ = r
+            ref = b.truth_in[t, k + 1]
+            worst_pos = max(worst_pos, np.abs(p[:3] - ref[:3]).max())
+            worst_ang = max(worst_ang, abs(_wrap(p[4] - ref[4])), abs(p[5] - ref[5]), abs(p[3] - ref[3]))
+            n_checked += 1
+    assert n_checked > 2000
+    assert worst_pos < 1e-9
+    assert worst_ang < 1e-11
+
+
+def _central(g, p0, surf, j, h):
+    dp = np.zeros(6)
+    dp[j] = h
+    a = oracle.propagate(g, p0 + dp, None, surf)[0]
+    b = oracle.propagate(g, p0 - dp, None, surf)[0]
+    d = a - b
+    d[4] = _wrap(d[4])
+    return d / (2 * h)
+
+
+def _fd_jacobian(g, p0, surf, h):
+    """Central differences with one Richardson step (truncation error O(h^4))."""
+    J = np.empty((6, 6))
+    for j in range(6):
+        J[:, j] = (4 * _central(g, p0, surf, j, h[j] / 2) - _central(g, p0, surf, j, h[j])) / 3
+    return J
+
+
+@pytest.mark.parametrize("wl_name", ["fit_batched", "hi_occ"])
+def test_jacobian_matches_central_differences(wl_name):
+    """The analytic, surface-projected Jacobian equals central finite differences of the full
+    propagate-to-surface map (path length re-solved for every perturbation)."""
+    wl = synth.workload(wl_name, n_events=1, tracks_lo=60, tracks_hi=60, ms_on=False)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl, smear=False, record_truth=True)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for t in range(b.n_tracks):
+        nh = b.track_nhits[t]
+        k = rng.integers(0, nh - 1)
+        p0 = b.truth_in[t, k].copy()
+        surf = b.track_surf[t, k + 1]
+        J = oracle.propagate(g, p0, None, surf)[2]
+        h = np.array([1e-3, 1e-3, 1e-3, 1e-4, 1e-5, 1e-5])
+        Jfd = _fd_jacobian(g, p0, surf, h)
+        scale = np.maximum(np.abs(J), 1e-2)
+        assert np.all(np.abs(J - Jfd) / scale < 1e-6), (t, k, J, Jfd)
+        checked += 1
+    assert checked == b.n_tracks
+
+
+def _surface_gradient(wl, surf, p):
+    s = wl.surfaces[surf]
+    g = np.zeros(6)
+    if s.type == synth.BARREL:
+        g[0], g[1] = p[0], p[1]
+    else:
+        g[2] = 1.0
+    return g
+
+
+def test_transported_covariance_stays_on_tangent_space():
+    """C' = J C J^T + Q is symmetric, annihilates the surface normal (C n = 0) and is positive
+    definite on the 5D tangent space."""
+    wl = synth.workload("hi_occ", n_events=1, tracks_lo=80, tracks_hi=80)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl, record_truth=True)
+    rng = np.random.default_rng(3)
+    for t in range(b.n_tracks):
+        nh = b.track_nhits[t]
+        k = rng.integers(0, nh - 1)
+        A = rng.normal(size=(6, 6))
+        C0 = A @ A.T * 1e-3 + np.diag([1e-4, 1e-4, 1e-2, 1e-3, 1e-5, 1e-5])
+        p, C, J, s = oracle.propagate(g, b.truth_out[t, k], C0, b.track_surf[t, k + 1])
+        assert np.allclose(C, C.T, rtol=0, atol=1e-15 * np.abs(C).max())
+        n = _surface_gradient(wl, b.track_surf[t, k + 1], p)
+        n /= np.linalg.norm(n)
+        assert np.linalg.norm(C @ n) <= 1e-12 * np.linalg.norm(C)
+        # basis of the tangent space: orthogonal complement of n
+        q, _ = np.linalg.qr(np.column_stack([n, np.eye(6)]))
+        T = q[:, 1:6]
+        ev = np.linalg.eigvalsh(T.T @ C @ T)
+        assert ev.min() > 0
+
+
+def test_straight_line_limit():
+    """kappa -> 0: the crossing is the straight-line intersection with the cylinder."""
+    wl = synth.workload("fit_small")
+    g = oracle.Geometry(wl)
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        phi = rng.uniform(-np.pi, np.pi)
+        th = rng.uniform(0.6, 2.5)
+        p0 = np.array([rng.normal() * 0.5, rng.normal() * 0.5, rng.normal(), 1e-12, phi, th])
+        R = 20.0
+        p = oracle.propagate(g, p0, None, 4)[0]  # layer at r = 20
+        a = p0[0] * np.cos(phi) + p0[1] * np.sin(phi)
+        s = -a + np.sqrt(a * a + R * R - p0[0] ** 2 - p0[1] ** 2)
+        ref = np.array([p0[0] + s * np.cos(phi), p0[1] + s * np.sin(phi), p0[2] + s / np.tan(th)])
+        assert np.abs(p[:3] - ref).max() < 1e-9
+
+
+def test_helix_invariants():
+    """Crossing lies on the cylinder, on the helix's transverse circle (radius 1/|omega|), with
+    phi advanced by omega*s and z by s*cot(theta)."""
+    wl = synth.workload("fit_batched")
+    g = oracle.Geometry(wl)
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        kap = rng.choice([-1, 1]) * rng.uniform(0.1, 2.0)
+        p0 = np.array([4 * np.cos(0.3), 4 * np.sin(0.3), rng.normal(), kap, rng.uniform(-np.pi, np.pi),
+                       rng.uniform(0.8, 2.3)])
+        if np.cos(p0[4] - 0.3) < 0.3:  # moving outward
+            continue
+        surf = int(rng.integers(1, 17))
+        r = oracle.propagate(g, p0, None, surf)
+        if r is None:
+            continue
+        p, _, _, s = r
+        R = wl.surfaces[surf].r_or_z
+        w = -oracle.K_CURV * float(np.float32(wl.bz)) * kap  # geometry values are FP32
+        assert abs(np.hypot(p[0], p[1]) - R) < 1e-9
+        c0 = np.array([p0[0] - np.sin(p0[4]) / w, p0[1] + np.cos(p0[4]) / w])
+        assert abs(np.hypot(p[0] - c0[0], p[1] - c0[1]) - 1 / abs(w)) < 1e-8
+        assert abs(_wrap(p[4] - p0[4] - w * s)) < 1e-12
+        assert abs(p[2] - p0[2] - s / np.tan(p0[5])) < 1e-9
+        assert s > 0
