@@ -1,0 +1,399 @@
+"""Benchmark: Kalman-filter track reconstruction throughput on one GB300 (or N, weak scaling).
+
+One step is one pass of the whole hot path over one batch of synthetic events: build the hit
+index of every event, find tracks from every seed (beam search, K candidates), and fit every found
+track, all through the C ABI, captured once in a CUDA graph and replayed. The workload is the
+batched uneven-event configuration: 100 events with 2,000-20,000 tracks each (about 1.07 M seeds),
+17 barrel layers at r = 4..68 cm with 0.02 X0 each, 3.8 T, pT 0.5-10 GeV, |eta| < 1, hit
+resolution 0.01 cm (r phi) and 0.1 cm (z); finding with chi2 < 30, K = 6, one miss allowed.
+The metric is seeds per second through the step (every seed is found and its track fitted).
+
+The FP64 oracle runs only in the CPU baseline leg (and as the whole reference arm, --impl
+reference), on a bounded sample of the same workload, on the host cores.
+
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KF finding seeds/s & fitting tracks/s on 1 GB300; learned vs plain at <=0.5% eff loss"
+UNIT = "seeds/s"
+WORKLOAD = "fit_batched"
+
+# Algorithmic FP32 operation counts per unit of work, counted from the formulas the path
+# evaluates (fused multiply-add = 2 flops, special functions and divisions not counted):
+#   propagation to the next surface incl. path search (3 Newton steps) ...... 150
+#   covariance transport J C J^T, projection onto the surface, scattering ... 320
+#   Kalman update (measurement, S = H C H^T + V, gain, state, covariance) .... 260
+#   chi2 of one hit in a search window ...................................... 20
+#   seed from three hits ..................................................... 80
+FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
+# Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z), write 8 B sorted + 4 B id) plus
+# the bin offsets written per (event, surface).
+INDEX_BYTES_PER_HIT = 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+# ------------------------------------------------------------------------------------------------
+# Oracle legs (host cores only)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(wl, batch, n_seeds_max: int):
+    """Run the FP64 oracle (index + find + fit of the found tracks) on the first seeds of the batch,
+    all host cores. Returns (seconds, n_seeds, counters, threads)."""
+    import numpy as np
+    import oracle
+
+    g = oracle.Geometry(wl)
+    seeds, st = batch.seeds()
+    ev = batch.track_event[st]
+    n = min(n_seeds_max, len(st))
+    last_ev = int(ev[n - 1])
+    sub = np.nonzero(ev <= last_ev)[0][:n]
+    t0 = time.perf_counter()
+    f = oracle.find(g, batch, seeds[sub], ev[sub])
+    oracle.fit(g, batch.hits, batch.hit_surface, f["hits"])
+    dt = time.perf_counter() - t0
+    return dt, len(sub), f["counters"], os.cpu_count() or 1
+
+
+def run_reference(args, wl, batch):
+    """The reference arm: the oracle as it stands, on the host cores, one bounded sample per step."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    per_step = args.ref_seeds
+    for _ in range(args.warmup):
+        oracle_sample(wl, batch, min(per_step, 2000))
+    times, n = [], 0
+    for _ in range(args.steps):
+        dt, n, _, cores = oracle_sample(wl, batch, per_step)
+        times.append(dt)
+    value = n / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": wl.name, "sample": f"first {n} seeds of the batch (index, find, fit)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} seeds per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def run_gpu(args, wl, batch):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1906_02253_gb300 as kf
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kf.load_library()
+    g = kf.Geometry(wl)
+    host = kf.to_device_event_batch(batch, device="cpu")
+    n_seeds = host["seed_hits"].shape[1]
+    n_hits = batch.n_hits
+    lmax = wl.lmax
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm)
+
+    # Device inputs and preallocated outputs.
+    d = {k: v.to(dev) for k, v in host.items() if isinstance(v, torch.Tensor)}
+    idx = kf.HitIndex(g, batch.n_events, n_hits, dev)
+    fout = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32, device=dev),
+                nhits=torch.empty(n_seeds, dtype=torch.int32, device=dev),
+                chi2=torch.empty(n_seeds, dtype=torch.float32, device=dev),
+                state=torch.empty((6, n_seeds), dtype=torch.float32, device=dev),
+                cov=torch.empty((21, n_seeds), dtype=torch.float32, device=dev),
+                status=torch.empty(n_seeds, dtype=torch.int32, device=dev))
+    fit_out = dict(state=torch.empty((6, n_seeds), dtype=torch.float32, device=dev),
+                   cov=torch.empty((21, n_seeds), dtype=torch.float32, device=dev),
+                   chi2=torch.empty(n_seeds, dtype=torch.float32, device=dev),
+                   ndof=torch.empty(n_seeds, dtype=torch.int32, device=dev),
+                   status=torch.empty(n_seeds, dtype=torch.int32, device=dev))
+    wsb = torch.empty(max(kf.find_workspace_size(n_seeds, prm), 256), dtype=torch.uint8, device=dev)
+    max_slab = host["max_slab_hits"]
+    stream = torch.cuda.Stream(device=dev)
+    launches = {"index": 0, "find": 0, "fit": 0}
+
+    def step(s, events=None):
+        if events:
+            events[0].record(s)
+        kf.build_hit_index(g, d["hits"], d["slab_offsets"], batch.n_events, max_slab, index=idx, stream=s)
+        if events:
+            events[1].record(s)
+        kf.find_tracks(g, idx, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], prm, out=fout,
+                       workspace=wsb, stream=s)
+        if events:
+            events[2].record(s)
+        kf.fit_tracks(g, d["hits"], d["hit_surface"], fout["hits"], out=fit_out, stream=s)
+        if events:
+            events[3].record(s)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+    torch.cuda.synchronize()
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step(stream)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 126 MB L2
+
+    def timed_steps(k, fn):
+        times = []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            times.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_steps = timed_steps(args.steps, graph.replay)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms_step = statistics.mean(t_steps)
+    if ws > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    launches_per_step = 3  # index, find, fit kernels (plus one memset node)
+
+    # Per-kernel durations: the same three launches eager, events on the launching stream.
+    kern = {"index": [], "find": [], "fit": []}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            step(stream, ev)
+        torch.cuda.synchronize()
+        kern["index"].append(ev[0].elapsed_time(ev[1]))
+        kern["find"].append(ev[1].elapsed_time(ev[2]))
+        kern["fit"].append(ev[2].elapsed_time(ev[3]))
+    kern_ms = {k: statistics.mean(v) for k, v in kern.items()}
+
+    # End to end through the public API with host buffers: H2D of the step's inputs from pinned
+    # memory, the three calls, D2H of the step's result (found hit lists, fitted states, chi2).
+    pinned = {k: host[k].pin_memory() for k in ("hits", "hit_surface", "slab_offsets", "seed_hits", "seed_event")}
+    res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory(),
+                    state=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
+                    chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory())
+    h2d = sum(t.numel() * t.element_size() for t in pinned.values())
+    d2h = sum(t.numel() * t.element_size() for t in res_host.values())
+
+    def e2e_step():
+        for k, t in pinned.items():
+            d[k].copy_(t, non_blocking=True)
+        step(stream)
+        res_host["hits"].copy_(fout["hits"], non_blocking=True)
+        res_host["state"].copy_(fit_out["state"], non_blocking=True)
+        res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
+
+    t_e2e = timed_steps(args.steps, e2e_step)
+    ms_e2e = statistics.mean(t_e2e)
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    # Result sanity on the last step (efficiency of the found tracks, host logic only).
+    from paper_1906_02253_gb300 import metrics
+    eff, fake = metrics.efficiency(batch, host["seed_track"], res_host["hits"].numpy().T,
+                                   fout["nhits"].cpu().numpy())
+    fit_ok = float((fit_out["status"] == 0).float().mean().item())
+
+    value = ws * n_seeds / (ms_step / 1000.0)
+    e2e_value = ws * n_seeds / (ms_e2e / 1000.0)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, no datasets)",
+           "config": {"workload": wl.name, "events": batch.n_events, "seeds": n_seeds, "hits": n_hits,
+                      "layers": len(wl.surfaces), "k_max": wl.k_max, "chi2_cut": wl.chi2_cut,
+                      "step": "hit index + find + fit, one CUDA graph", "l2": "flushed between steps (256 MB write)",
+                      "parallelism": f"events sharded over {ws} GPU(s), no collective"},
+           "gpu_launches": launches_per_step * args.steps,
+           "kernel_ms": kern_ms, "efficiency": eff, "fake_rate": fake, "fit_ok_fraction": fit_ok,
+           "fit_tracks_per_s": ws * n_seeds / (kern_ms["fit"] / 1000.0),
+           "find_seeds_per_s": ws * n_seeds / (kern_ms["find"] / 1000.0),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": ms_e2e}}
+    out["clocks"] = clk.summary()
+
+    # CPU baseline (oracle on a bounded sample) and the finder's algorithmic work per seed.
+    counters = None
+    if rank == 0 and not args.no_cpu_baseline:
+        dt, n, counters, cores = oracle_sample(wl, batch, args.cpu_seeds)
+        out["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {n} seeds of the batch: index, find, fit of the found tracks "
+                                         f"(FP64, {dt:.1f} s)"}
+        counters = np.asarray(counters, np.float64) / n
+    out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
+    """Roofline of the dominant kernel. The finder and the fit are FP32-ALU bound (no dense
+    contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM clock. The index is HBM bound."""
+    import torch
+    peaks = _peaks()
+    dom = max(kern_ms, key=kern_ms.get)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if dom == "index":
+        nbytes = INDEX_BYTES_PER_HIT * n_hits + 4 * batch.n_events * len(batch.wl.surfaces) * (2048 + 1)
+        ach = nbytes / (kern_ms["index"] / 1000.0) / 1e9
+        return {"kernel": "k_build_hit_index", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None}
+    if dom == "fit":
+        n_steps = float((batch.track_nhits - 1).sum())
+        flops = len(batch.track_nhits) * (FLOP_SEED + FLOP_UPDATE) + n_steps * (FLOP_PROP + FLOP_TRANSPORT + FLOP_UPDATE)
+        ach = flops / (kern_ms["fit"] / 1000.0) / 1e12
+        return {"kernel": "k_fit_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz"}
+    if counters is None:
+        return {"kernel": "k_find_tracks", "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+    n_prop, n_pass, n_upd, n_scan = counters
+    per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_scan * FLOP_CHI2
+    ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
+    return {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz",
+            "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_scan, "flop": per_seed}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kfgb", choices=["kfgb", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--events", type=int, default=None, help="override the number of events")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--cpu-seeds", type=int, default=10 ** 9, help="oracle sample for the CPU baseline")
+    ap.add_argument("--ref-seeds", type=int, default=200000, help="oracle sample per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = _dist()
+    if args.impl == "reference" and rank != 0:
+        return  # the reference arm runs on rank 0 only
+    if ws > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synth
+    over = {"n_events": args.events} if args.events else {}
+    # weak scaling: every rank processes its own events (different seed), no data exchange
+    wl = synth.workload(args.workload, seed=synth.WORKLOADS[args.workload].seed + 1000 * rank, **over)
+    batch = synth.generate(wl)
+    if args.impl == "reference":
+        run_reference(args, wl, batch)
+        return
+    run_gpu(args, wl, batch)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * kfgb: Kalman-filter track fitting and combinatorial track finding on the GPU (sm_103a).
+ *
+ * C ABI over caller-owned device buffers. Every entry point is asynchronous on the given CUDA
+ * stream, allocates nothing, synchronises nothing and returns a status code at launch time:
+ *   KF_OK (0) launched; KF_ERR_ARG invalid argument (nothing launched); KF_ERR_CAPACITY a size
+ *   above a compiled limit (nothing launched); KF_ERR_CUDA a CUDA launch error.
+ * Conditions found on the device (propagation failures, capacity overflow inside a kernel) are
+ * written to per-track status arrays and to an optional device status word (see each call); no
+ * kernel traps or asserts. All float data are IEEE FP32.
+ *
+ * Method. The paper (arXiv:1906.02253, Sec. 1-2) adapts the traditional Kalman filter to track
+ * fitting and to combinatorial track finding: tracks are propagated layer to layer (Sec. 3.1) in
+ * a constant 3.8 T field (Sec. 4), multiple scattering from the detector material enters the
+ * prediction (Sec. 3.1), hits are selected through per-layer search windows and candidates are
+ * scored and kept per seed (Sec. 4), and seeds are processed in parallel without marking used
+ * hits (Sec. 3.2). The formulas are the textbook ones; the state is (x, y, z, kappa = q/pT, phi,
+ * theta) in cm, 1/GeV and rad, with a 6x6 covariance stored as its upper triangle, row-major:
+ * element (i, j), i <= j, at index i*(11-i)/2 + j ("packed 21").
+ */
+#ifndef KFGB_H
+#define KFGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* kf_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+#define KF_OK 0
+#define KF_ERR_ARG (-1)
+#define KF_ERR_CAPACITY (-2)
+#define KF_ERR_CUDA (-3)
+#define KF_ERR_TIMEOUT (-4)
+
+#define KF_BARREL 0
+#define KF_DISK 1
+
+#define KF_MAX_SURF 64       /* surfaces per geometry */
+#define KF_MAX_LMAX 31       /* entries per track hit list */
+#define KF_MAX_K 16          /* candidates kept per seed */
+#define KF_MAX_SLAB_HITS 32768 /* hits per (event, surface) in the hit index */
+
+/* One detection surface (the paper's per-layer description, Sec. 3.1, reduced to what the
+ * fit and the search use). Barrel: cylinder of radius r_or_z, hits (phi, z) with z in [lo, hi].
+ * Disk: plane z = r_or_z, hits (phi, r) with r in [lo, hi]. x_over_x0 is the material thickness
+ * at normal incidence in radiation lengths (0: no scattering). n_phi x n_2nd index bins. */
+typedef struct {
+  int type;
+  float r_or_z, lo, hi;
+  float x_over_x0;
+  int n_phi, n_2nd;
+} KfSurface;
+
+/* Geometry and resolution. surf is a HOST array of n_surf entries, read during the call only.
+ * prior: standard deviations of the seed prior at the first hit: transverse position (cm),
+ * second coordinate z or r (cm), kappa (1/GeV), phi (rad), theta (rad). */
+typedef struct {
+  float bz;
+  int n_surf;
+  const KfSurface* surf;
+  float sigma_rphi, sigma_2nd;
+  float prior[5];
+} KfGeometry;
+
+/* Hit index: per (event, surface) slab, hits sorted by bin (phi-bin * n_2nd + second-bin) and,
+ * within a bin, by ascending hit id. All pointers are caller-owned device memory:
+ *   bin_off     int [n_events * n_surf][n_bins + 1]: absolute position in sorted_* of the first
+ *               hit of each bin; entry n_bins (and every bin beyond the surface's own count) is
+ *               the slab end. n_bins = max over surfaces of n_phi * n_2nd.
+ *   sorted_hits float [n_hits][2] and sorted_ids int [n_hits]: same slab ranges as the input. */
+typedef struct {
+  int n_events;
+  int n_bins;
+  int* bin_off;
+  float* sorted_hits;
+  int* sorted_ids;
+} KfHitIndex;
+
+/* Finder settings. chi2_cut: hits with predicted chi2 below it make children; k_max: candidates
+ * kept per seed (<= KF_MAX_K); max_miss: surfaces a candidate may cross without a hit; lmax:
+ * length of each output hit list (3 seed hits + at most lmax-3 steps, <= KF_MAX_LMAX);
+ * block_threads: threads per block (0 = default 128; a multiple of 32, <= 128);
+ * blocks_per_sm: resident blocks per SM for the persistent grid (0 = occupancy maximum). */
+typedef struct {
+  float chi2_cut;
+  int k_max;
+  int max_miss;
+  int lmax;
+  int block_threads;
+  int blocks_per_sm;
+} KfFindParams;
+
+/* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,
+ * and the hit-data reuse of Sec. 3.2).
+ *   hits          device float [n_hits][2]: (phi, z) on barrels, (phi, r) on disks; phi in
+ *                 [-pi, pi]. Hits of one event are contiguous and grouped by surface.
+ *   slab_offsets  device int [n_events * n_surf + 1]: first hit id of slab (event e, surface s)
+ *                 at index e * n_surf + s; non-decreasing; the last entry is n_hits.
+ *   max_slab_hits host int: an upper bound of the largest slab (sets shared memory); must be
+ *                 <= KF_MAX_SLAB_HITS, else KF_ERR_CAPACITY.
+ *   index         host struct whose device arrays receive the result (index->n_events and
+ *                 index->n_bins must match the geometry; kf_index_bins gives n_bins).
+ *   d_status      optional device int, OR-ed with 1 if a slab exceeded max_slab_hits (its
+ *                 bins are then left empty).
+ * Bins follow the FP32 rule: phi-bin = clamp(floor((phi + pi_f) * sphi), 0, n_phi - 1) with
+ * pi_f = (float)pi and sphi = (float)(n_phi / (2 pi)); second-bin = clamp(floor((v - lo) * s2),
+ * 0, n_2nd - 1) with s2 = (float)(n_2nd / ((double)hi - (double)lo)); each FP32 operation rounds
+ * to nearest on its own (no fused multiply-add); NaN goes to bin 0. */
+int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* slab_offsets, int n_events,
+                       int max_slab_hits, const KfHitIndex* index, int* d_status, kf_stream_t stream);
+
+/* Bins per slab of the index for this geometry (max n_phi * n_2nd), or KF_ERR_ARG. */
+int kf_index_bins(const KfGeometry* geom);
+
+/* Fit tracks over known hit sequences (Kalman-filter track fitting, Sec. 2).
+ *   hits, hit_surface  device float [n_hits][2] and int [n_hits] (surface of each hit).
+ *   track_hits         device int [lmax][n_tracks] (structure of arrays: entry k of track t at
+ *                      k * n_tracks + t): hit ids in path order; -1 entries are skipped (misses);
+ *                      the first three must be hits, they seed the fit.
+ * The seed state comes from the circle through the first three hits (transverse plane) and the
+ * line through the first and third in (arc length, z), with the prior of the geometry on the
+ * first hit's surface; the filter updates with hit 1, then propagates and updates through the
+ * rest. Outputs (device, caller-owned), at the last hit:
+ *   state_out float [6][n_tracks], cov_out float [21][n_tracks] (packed 21), chi2_out float
+ *   [n_tracks] (sum of predicted chi2), ndof_out int [n_tracks] (2 * hits - 5), status_out int
+ *   [n_tracks]: 0 ok, 1 seed failed, 2 a surface was not reached, 3 fewer than three seed hits.
+ * block_threads: 0 for the default (128), else a multiple of 32 up to 256. */
+int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* track_hits,
+                  int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
+                  int* status_out, int block_threads, kf_stream_t stream);
+
+/* Device workspace (bytes) kf_find_tracks needs for these parameters on the current device. */
+size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params);
+
+/* Combinatorial track finding (Sec. 2 and Sec. 4): from each seed's three hits, fit the seed,
+ * then step outward surface by surface. The next surface is the nearer of the next barrel layer
+ * beyond the candidate's radius (if crossed inside its z extent) and the next disk beyond |z| in
+ * the direction of motion (if crossed inside its r extent). At each step every candidate is
+ * propagated (covariance with scattering noise), every hit in its search window with chi2 below
+ * the cut becomes a child (updated); a candidate with no such hit becomes one miss child while
+ * it has misses left, else it stops and is carried unchanged. The k_max best of all children and
+ * carried candidates of the seed survive, ordered by more hits, then lower total chi2, then
+ * parent rank, then child kind (hit, miss, carried), then hit id. Seeds run in parallel with no
+ * hit marking across seeds (Sec. 3.2).
+ *   hits, hit_surface  as for the fit (original hit ids); index built by kf_build_hit_index.
+ *   seed_hits          device int [3][n_seeds] (structure of arrays), seed_event int [n_seeds].
+ *   workspace          device memory of kf_find_workspace_size bytes, 256-byte aligned.
+ * Outputs (device): hits_out int [lmax][n_seeds] (best candidate's hit ids in path order, -1 for
+ * a miss or no further step), nhits_out int, chi2_out float, state_out float [6][n_seeds],
+ * cov_out float [21][n_seeds], status_out int (0 ok, 1 seed failed). */
+int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                   const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
+                   int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
+                   int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
+
+/* Human-readable name of a status code. */
+const char* kf_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFGB_H */

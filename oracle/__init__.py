@@ -226,7 +226,8 @@ def next_surface(geom: Geometry, p):
 def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=None, max_miss=None,
          brute_force: bool = False, n_threads: int = 0):
     """Combinatorial finding from seeds. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
-    status and counters (propagations, passing chi2 evaluations, updates)."""
+    status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
+    evaluated in a window)."""
     lib = _load()
     wl = geom.wl
     prm = OrFindParams(wl.chi2_cut if chi2_cut is None else chi2_cut, wl.k_max if k_max is None else k_max,
@@ -240,7 +241,7 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     lmax = wl.lmax
     out = dict(hits=np.empty((n, lmax), np.int32), n_hits=np.empty(n, np.int32), chi2=np.empty(n),
                p=np.empty((n, 6)), cov=np.empty((n, 21)), status=np.empty(n, np.int32))
-    counters = np.zeros(3, np.int64)
+    counters = np.zeros(4, np.int64)
     lib.or_find(geom.ref, hits.ctypes.data, hs.ctypes.data, so.ctypes.data, batch.n_events, sh.ctypes.data,
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,

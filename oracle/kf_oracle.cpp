@@ -615,7 +615,8 @@ struct Ctx {
 // All hits of surface si in event ev whose chi2 against the predicted state is below the cut.
 // Binned: the window is the bounding box of the chi2 ellipse, padded, turned into bin ranges by
 // the same FP32 rule as the index; brute force: every hit of the surface.
-void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<Found>& out) {
+void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<Found>& out,
+                 long long* scanned = nullptr) {
   out.clear();
   const OrGeom& g = *cx.g;
   const OrSurface& S = g.surf[si];
@@ -626,6 +627,7 @@ void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<F
     measure(g, si, pred.p, hphi, h2, m);
     double Sm[2][2];
     const double c2 = chi2_of(m, pred.C, Sm);
+    if (scanned) ++*scanned;
     if (c2 < cut) out.push_back({id, c2});
   };
   if (cx.prm.brute_force) {
@@ -684,7 +686,7 @@ bool child_less(const Child& a, const Child& b) {
 }
 
 struct Counters {
-  long long n_prop = 0, n_chi2 = 0, n_upd = 0;
+  long long n_prop = 0, n_chi2 = 0, n_upd = 0, n_scan = 0;
 };
 
 // Beam search for one seed. Returns false if the seed could not be formed.
@@ -735,7 +737,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       }
       cnt.n_prop++;
       pred_surf[ci] = si;
-      search_hits(cx, ev, si, pred[ci], found);
+      search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan);
       cnt.n_chi2 += static_cast<long long>(found.size());
       if (!found.empty()) {
         for (const Found& f : found) pool.push_back({ci, f.hit, 0, c.n_hits + 1, c.chi2 + f.chi2, f.chi2});
@@ -821,7 +823,8 @@ int or_seed(const OrGeom* g, const float* hits, const int* hsurf, const int* ids
 }
 
 // Fit tracks over known hit sequences. track_hits is [n][lmax] row-major, -1 padded (the
-// first -1 ends the track). Outputs per track: p[6], C packed upper-triangle [21] (row-major
+// entries equal to -1 are skipped, e.g. misses of a found track; the first three entries are
+// the seed hits). Outputs per track: p[6], C packed upper-triangle [21] (row-major
 // i<=j), chi2 total, ndof = 2N-5, status (0 ok, 1 seed failed, 2 propagation failed, 3 < 3 hits).
 // Optional per-hit outputs [n][lmax]: predicted chi2 and the two normalised predicted residuals.
 void or_fit(const OrGeom* g, const float* hits, const int* hsurf, const int* track_hits, long long n, int lmax,
@@ -830,19 +833,20 @@ void or_fit(const OrGeom* g, const float* hits, const int* hsurf, const int* tra
   parallel_for(n, n_threads, [&](long long t) {
     const int* th = track_hits + t * lmax;
     int nh = 0;
-    while (nh < lmax && th[nh] >= 0) ++nh;
+    for (int k = 0; k < lmax; ++k) nh += th[k] >= 0;
     if (hit_chi2)
       for (int k = 0; k < lmax; ++k) hit_chi2[t * lmax + k] = -1.0;
     State st{};
     int status = 0;
     double chi2 = 0.0;
-    if (nh < 3) {
+    if (nh < 3 || th[0] < 0 || th[1] < 0 || th[2] < 0) {
       status = 3;
     } else if (!seed_state(*g, hits, hsurf, th, st)) {
       status = 1;
     } else {
-      for (int k = 0; k < nh; ++k) {
+      for (int k = 0; k < lmax; ++k) {
         const int id = th[k];
+        if (id < 0) continue;
         const int si = hsurf[id];
         if (k > 0) {
           State pr;
@@ -944,8 +948,8 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 
 // Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
-// status (0 ok, 1 seed failed). counters[3] += propagations, chi2 evaluations that passed the
-// cut, Kalman updates.
+// status (0 ok, 1 seed failed). counters[4] += propagations, chi2 evaluations that passed the
+// cut, Kalman updates, hits whose chi2 was evaluated (window scans).
 void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
@@ -953,7 +957,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
   Ctx cx{g, hits, hsurf, slab_off, &ix, *prm};
-  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0);
+  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;
     Counters cnt;
@@ -966,12 +970,14 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     status_out[i] = ok ? 0 : 1;
     c_prop += cnt.n_prop;
     c_chi2 += cnt.n_chi2;
+    c_scan += cnt.n_scan;
     c_upd += cnt.n_upd;
   });
   if (counters) {
     counters[0] += c_prop.load();
     counters[1] += c_chi2.load();
     counters[2] += c_upd.load();
+    counters[3] += c_scan.load();
   }
 }
 

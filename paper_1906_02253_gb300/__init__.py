@@ -1,0 +1,234 @@
+"""kfgb: Kalman-filter track fitting and combinatorial track finding on GB300 (sm_103a).
+
+Thin binding over the C ABI in ``include/kfgb.h`` (``_build/libkfgb.so``): each function takes
+PyTorch CUDA tensors, passes their device pointers and the current stream, and returns the
+output tensors. No arithmetic happens here and there is no fallback: if the CUDA library is not
+built or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkfgb.so")
+_lib = None
+_lock = threading.Lock()
+
+KF_OK, KF_ERR_ARG, KF_ERR_CAPACITY, KF_ERR_CUDA, KF_ERR_TIMEOUT = 0, -1, -2, -3, -4
+KF_BARREL, KF_DISK = 0, 1
+KF_MAX_SURF, KF_MAX_LMAX, KF_MAX_K, KF_MAX_SLAB_HITS = 64, 31, 16, 32768
+
+
+class KfError(RuntimeError):
+    pass
+
+
+class KfSurface(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("r_or_z", ctypes.c_float), ("lo", ctypes.c_float), ("hi", ctypes.c_float),
+                ("x_over_x0", ctypes.c_float), ("n_phi", ctypes.c_int), ("n_2nd", ctypes.c_int)]
+
+
+class KfGeometry(ctypes.Structure):
+    _fields_ = [("bz", ctypes.c_float), ("n_surf", ctypes.c_int), ("surf", ctypes.POINTER(KfSurface)),
+                ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5)]
+
+
+class KfHitIndex(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_int), ("n_bins", ctypes.c_int), ("bin_off", ctypes.c_void_p),
+                ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p)]
+
+
+class KfFindParams(ctypes.Structure):
+    _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
+                ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+
+EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
+           "kf_status_string")
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libkfgb.so`` (raises if it is missing: there is no CPU path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise KfError(f"{path} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+            lib = ctypes.CDLL(path)
+            P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+            G = ctypes.POINTER(KfGeometry)
+            lib.kf_build_hit_index.restype = I
+            lib.kf_build_hit_index.argtypes = [G, P, P, I, I, ctypes.POINTER(KfHitIndex), P, P]
+            lib.kf_index_bins.restype = I
+            lib.kf_index_bins.argtypes = [G]
+            lib.kf_fit_tracks.restype = I
+            lib.kf_fit_tracks.argtypes = [G, P, P, P, I, I, P, P, P, P, P, I, P]
+            lib.kf_find_workspace_size.restype = S
+            lib.kf_find_workspace_size.argtypes = [I, ctypes.POINTER(KfFindParams)]
+            lib.kf_find_tracks.restype = I
+            lib.kf_find_tracks.argtypes = [G, ctypes.POINTER(KfHitIndex), P, P, P, P, I, ctypes.POINTER(KfFindParams),
+                                           P, P, P, P, P, P, P, S, P]
+            lib.kf_status_string.restype = ctypes.c_char_p
+            lib.kf_status_string.argtypes = [I]
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != KF_OK:
+        msg = load_library().kf_status_string(rc).decode()
+        raise KfError(f"{what} failed: {msg} ({rc})")
+
+
+class Geometry:
+    """C-ABI geometry built from any object with ``surfaces`` (type, r_or_z, lo, hi, x_over_x0,
+    n_phi, n_2nd), ``bz``, ``sigma_rphi``, ``sigma_2nd``, ``prior`` and ``ms_on``."""
+
+    def __init__(self, wl):
+        self.wl = wl
+        n = len(wl.surfaces)
+        self._surf = (KfSurface * n)()
+        ms = getattr(wl, "ms_on", True)
+        for i, s in enumerate(wl.surfaces):
+            self._surf[i] = KfSurface(s.type, s.r_or_z, s.lo, s.hi, s.x_over_x0 if ms else 0.0, s.n_phi, s.n_2nd)
+        self.g = KfGeometry(wl.bz, n, ctypes.cast(self._surf, ctypes.POINTER(KfSurface)), wl.sigma_rphi, wl.sigma_2nd,
+                            (ctypes.c_float * 5)(*wl.prior))
+        self.n_surf = n
+        self.n_bins = load_library().kf_index_bins(ctypes.byref(self.g))
+        if self.n_bins < 0:
+            _check(self.n_bins, "geometry")
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.g)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _cuda(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise KfError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise KfError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise KfError(f"{name} must be contiguous")
+    return t
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class HitIndex:
+    """Device buffers of a hit index (caller-owned tensors)."""
+
+    def __init__(self, geom: Geometry, n_events: int, n_hits: int, device="cuda"):
+        self.n_events = n_events
+        self.n_bins = geom.n_bins
+        self.bin_off = torch.empty((n_events * geom.n_surf, geom.n_bins + 1), dtype=torch.int32, device=device)
+        self.sorted_hits = torch.empty((n_hits, 2), dtype=torch.float32, device=device)
+        self.sorted_ids = torch.empty(n_hits, dtype=torch.int32, device=device)
+        self.c = KfHitIndex(n_events, self.n_bins, self.bin_off.data_ptr(), self.sorted_hits.data_ptr(),
+                            self.sorted_ids.data_ptr())
+
+
+def build_hit_index(geom: Geometry, hits, slab_offsets, n_events: int, max_slab_hits: int, index: HitIndex = None,
+                    status=None, stream=None) -> HitIndex:
+    """kf_build_hit_index: hits [n,2] f32, slab_offsets [n_events*n_surf+1] i32 (device)."""
+    lib = load_library()
+    _cuda(hits, torch.float32, "hits")
+    _cuda(slab_offsets, torch.int32, "slab_offsets")
+    if index is None:
+        index = HitIndex(geom, n_events, hits.shape[0], hits.device)
+    rc = lib.kf_build_hit_index(geom.ref, _ptr(hits), _ptr(slab_offsets), n_events, int(max_slab_hits),
+                                ctypes.byref(index.c), _ptr(status), _stream(stream))
+    _check(rc, "kf_build_hit_index")
+    return index
+
+
+def fit_tracks(geom: Geometry, hits, hit_surface, track_hits, out: dict = None, block_threads: int = 0,
+               stream=None) -> dict:
+    """kf_fit_tracks: track_hits [lmax, n] i32 (structure of arrays). Returns state [6,n],
+    cov [21,n], chi2 [n], ndof [n], status [n]."""
+    lib = load_library()
+    _cuda(hits, torch.float32, "hits")
+    _cuda(hit_surface, torch.int32, "hit_surface")
+    _cuda(track_hits, torch.int32, "track_hits")
+    lmax, n = track_hits.shape
+    dev = hits.device
+    if out is None:
+        out = dict(state=torch.empty((6, n), dtype=torch.float32, device=dev),
+                   cov=torch.empty((21, n), dtype=torch.float32, device=dev),
+                   chi2=torch.empty(n, dtype=torch.float32, device=dev),
+                   ndof=torch.empty(n, dtype=torch.int32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    rc = lib.kf_fit_tracks(geom.ref, _ptr(hits), _ptr(hit_surface), _ptr(track_hits), n, lmax, _ptr(out["state"]),
+                           _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["ndof"]), _ptr(out["status"]),
+                           int(block_threads), _stream(stream))
+    _check(rc, "kf_fit_tracks")
+    return out
+
+
+def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
+                blocks_per_sm: int = 0) -> KfFindParams:
+    return KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm)
+
+
+def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:
+    return int(load_library().kf_find_workspace_size(n_seeds, ctypes.byref(params)))
+
+
+def find_tracks(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits, seed_event, params: KfFindParams,
+                out: dict = None, workspace=None, stream=None) -> dict:
+    """kf_find_tracks: seed_hits [3, n] i32 (structure of arrays), seed_event [n] i32. Returns
+    hits [lmax, n], nhits, chi2, state [6,n], cov [21,n], status."""
+    lib = load_library()
+    _cuda(hits, torch.float32, "hits")
+    _cuda(hit_surface, torch.int32, "hit_surface")
+    _cuda(seed_hits, torch.int32, "seed_hits")
+    _cuda(seed_event, torch.int32, "seed_event")
+    n = seed_hits.shape[1]
+    dev = hits.device
+    lmax = params.lmax
+    if out is None:
+        out = dict(hits=torch.empty((lmax, n), dtype=torch.int32, device=dev),
+                   nhits=torch.empty(n, dtype=torch.int32, device=dev),
+                   chi2=torch.empty(n, dtype=torch.float32, device=dev),
+                   state=torch.empty((6, n), dtype=torch.float32, device=dev),
+                   cov=torch.empty((21, n), dtype=torch.float32, device=dev),
+                   status=torch.empty(n, dtype=torch.int32, device=dev))
+    ws_bytes = find_workspace_size(n, params)
+    if ws_bytes == 0 and n > 0:
+        raise KfError("kf_find_workspace_size rejected the parameters")
+    if workspace is None or workspace.numel() < ws_bytes:
+        workspace = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=dev)
+    rc = lib.kf_find_tracks(geom.ref, ctypes.byref(index.c), _ptr(hits), _ptr(hit_surface), _ptr(seed_hits),
+                            _ptr(seed_event), n, ctypes.byref(params), _ptr(out["hits"]), _ptr(out["nhits"]),
+                            _ptr(out["chi2"]), _ptr(out["state"]), _ptr(out["cov"]), _ptr(out["status"]),
+                            _ptr(workspace), workspace.numel(), _stream(stream))
+    _check(rc, "kf_find_tracks")
+    out["workspace"] = workspace
+    return out
+
+
+def to_device_event_batch(batch, device="cuda") -> dict:
+    """Move a generated event batch's inputs to the device in the layouts the ABI takes."""
+    seeds, st = batch.seeds()
+    return dict(
+        hits=torch.from_numpy(np.ascontiguousarray(batch.hits)).to(device),
+        hit_surface=torch.from_numpy(np.ascontiguousarray(batch.hit_surface)).to(device),
+        slab_offsets=torch.from_numpy(batch.slab_offsets.astype(np.int32)).to(device),
+        track_hits=torch.from_numpy(np.ascontiguousarray(batch.track_hits.T)).to(device),
+        seed_hits=torch.from_numpy(np.ascontiguousarray(seeds.T)).to(device),
+        seed_event=torch.from_numpy(batch.track_event[st].astype(np.int32)).to(device),
+        seed_track=st,
+        max_slab_hits=int(np.diff(batch.slab_offsets).max()) if batch.slab_offsets.size > 1 else 0,
+    )

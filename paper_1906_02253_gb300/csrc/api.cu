@@ -1,0 +1,206 @@
+// C ABI of the library (declared in include/kfgb.h): argument checks, geometry packing into the
+// kernels' by-value struct, launch configuration. Nothing here allocates device memory or
+// synchronises; every launch goes to the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "../../include/kfgb.h"
+#include "kf_math.cuh"
+
+namespace kfgb {
+
+__global__ void k_build_hit_index(DevGeom G, const float2* hits, const int* slab_off, int n_slabs, int cap,
+                                  int* bin_off, float2* sorted_hits, int* sorted_ids, int* d_status);
+__global__ void k_fit_tracks(DevGeom G, const float2* hits, const int* hit_surface, const int* track_hits,
+                             int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
+                             int* status_out);
+
+}  // namespace kfgb
+
+#include "find_launch.cuh"
+
+namespace kfgb {
+
+static int pack_geometry(const KfGeometry* g, DevGeom* d) {
+  if (!g || !g->surf || g->n_surf <= 0 || g->n_surf > kMaxSurf) return KF_ERR_ARG;
+  if (!(std::isfinite(g->bz)) || g->bz == 0.f) return KF_ERR_ARG;
+  if (!(g->sigma_rphi > 0.f) || !(g->sigma_2nd > 0.f)) return KF_ERR_ARG;
+  std::memset(d, 0, sizeof(*d));
+  d->bz = g->bz;
+  d->sigma_rphi = g->sigma_rphi;
+  d->sigma_2nd = g->sigma_2nd;
+  for (int i = 0; i < 5; ++i) {
+    if (!(g->prior[i] > 0.f)) return KF_ERR_ARG;
+    d->prior[i] = g->prior[i];
+  }
+  d->n_surf = g->n_surf;
+  int nb = 0;
+  for (int s = 0; s < g->n_surf; ++s) {
+    const KfSurface& S = g->surf[s];
+    if (S.type != KF_BARREL && S.type != KF_DISK) return KF_ERR_ARG;
+    if (S.n_phi < 1 || S.n_2nd < 1 || S.n_phi * S.n_2nd > 65536) return KF_ERR_ARG;
+    if (!(S.hi > S.lo) || !(S.x_over_x0 >= 0.f)) return KF_ERR_ARG;
+    if (S.type == KF_BARREL && !(S.r_or_z > 0.f)) return KF_ERR_ARG;
+    d->type[s] = S.type;
+    d->r_or_z[s] = S.r_or_z;
+    d->lo[s] = S.lo;
+    d->hi[s] = S.hi;
+    d->x0[s] = S.x_over_x0;
+    d->n_phi[s] = S.n_phi;
+    d->n_2nd[s] = S.n_2nd;
+    d->sphi[s] = static_cast<float>(static_cast<double>(S.n_phi) / (2.0 * 3.14159265358979323846));
+    d->s2[s] = static_cast<float>(static_cast<double>(S.n_2nd) / (static_cast<double>(S.hi) - static_cast<double>(S.lo)));
+    nb = std::max(nb, S.n_phi * S.n_2nd);
+  }
+  d->n_bins = nb;
+  int ib = 0, ip = 0, in = 0;
+  signed char idx[kMaxSurf];
+  for (int s = 0; s < g->n_surf; ++s) idx[s] = static_cast<signed char>(s);
+  std::sort(idx, idx + g->n_surf, [&](signed char a, signed char b) { return g->surf[a].r_or_z < g->surf[b].r_or_z; });
+  for (int k = 0; k < g->n_surf; ++k) {
+    const int s = idx[k];
+    if (g->surf[s].type == KF_BARREL) d->barrel_order[ib++] = static_cast<signed char>(s);
+    else if (g->surf[s].r_or_z > 0.f) d->dpos_order[ip++] = static_cast<signed char>(s);
+  }
+  for (int k = g->n_surf - 1; k >= 0; --k) {
+    const int s = idx[k];
+    if (g->surf[s].type == KF_DISK && g->surf[s].r_or_z < 0.f) d->dneg_order[in++] = static_cast<signed char>(s);
+  }
+  d->n_barrel = ib;
+  d->n_dpos = ip;
+  d->n_dneg = in;
+  return KF_OK;
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+static int launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KF_OK : KF_ERR_CUDA;
+}
+
+}  // namespace kfgb
+
+using namespace kfgb;
+
+extern "C" {
+
+int kf_index_bins(const KfGeometry* geom) {
+  DevGeom G;
+  const int rc = pack_geometry(geom, &G);
+  return rc == KF_OK ? G.n_bins : rc;
+}
+
+int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* slab_offsets, int n_events,
+                       int max_slab_hits, const KfHitIndex* index, int* d_status, kf_stream_t stream) {
+  DevGeom G;
+  int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  if (!slab_offsets || !index || n_events < 0 || max_slab_hits < 0) return KF_ERR_ARG;
+  if (max_slab_hits > KF_MAX_SLAB_HITS) return KF_ERR_CAPACITY;
+  if (index->n_events != n_events || index->n_bins != G.n_bins) return KF_ERR_ARG;
+  if (n_events == 0) return KF_OK;
+  if (!index->bin_off || !index->sorted_hits || !index->sorted_ids || (!hits && max_slab_hits > 0)) return KF_ERR_ARG;
+  const int n_slabs = n_events * G.n_surf;
+  const int cap = std::max(2, (max_slab_hits + 1) & ~1);
+  const size_t smem = static_cast<size_t>(G.n_bins + 1) * sizeof(int) + 2 * static_cast<size_t>(cap) * sizeof(unsigned short);
+  // Raise the kernel's dynamic shared memory limit once per device (and only when a larger slab
+  // needs it), so later calls, e.g. inside a stream capture, make no attribute call.
+  static int smem_set[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KF_ERR_CUDA;
+  if (static_cast<int>(smem) > smem_set[dev]) {
+    if (cudaFuncSetAttribute(k_build_hit_index, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return KF_ERR_CUDA;
+    smem_set[dev] = static_cast<int>(smem);
+  }
+  k_build_hit_index<<<n_slabs, 512, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
+      G, reinterpret_cast<const float2*>(hits), slab_offsets, n_slabs, cap, index->bin_off,
+      reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, d_status);
+  return launch_status();
+}
+
+int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* track_hits,
+                  int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
+                  int* status_out, int block_threads, kf_stream_t stream) {
+  DevGeom G;
+  int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  if (n_tracks < 0 || lmax < 3 || lmax > KF_MAX_LMAX) return KF_ERR_ARG;
+  if (block_threads == 0) block_threads = 128;
+  if (block_threads < 32 || block_threads > 256 || block_threads % 32) return KF_ERR_ARG;
+  if (n_tracks == 0) return KF_OK;
+  if (!hits || !hit_surface || !track_hits || !state_out || !cov_out || !chi2_out || !ndof_out || !status_out)
+    return KF_ERR_ARG;
+  const int grid = (n_tracks + block_threads - 1) / block_threads;
+  k_fit_tracks<<<grid, block_threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      G, reinterpret_cast<const float2*>(hits), hit_surface, track_hits, n_tracks, lmax, state_out, cov_out, chi2_out,
+      ndof_out, status_out);
+  return launch_status();
+}
+
+size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params) {
+  FindPlan plan;
+  if (plan_find(n_seeds, params, sm_count(), &plan) != KF_OK) return 0;
+  return plan.ws_bytes;
+}
+
+int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                   const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
+                   int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
+                   int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream) {
+  DevGeom G;
+  int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
+  FindPlan plan;
+  rc = plan_find(n_seeds, params, sm_count(), &plan);
+  if (rc != KF_OK) return rc;
+  if (n_seeds == 0) return KF_OK;
+  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids) return KF_ERR_ARG;
+  if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
+      !cov_out || !status_out)
+    return KF_ERR_ARG;
+  if (!workspace || workspace_bytes < plan.ws_bytes || (reinterpret_cast<size_t>(workspace) & 255)) return KF_ERR_ARG;
+  FindArgs A;
+  A.bin_off = index->bin_off;
+  A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
+  A.sorted_ids = index->sorted_ids;
+  A.hits = reinterpret_cast<const float2*>(hits);
+  A.hit_surface = hit_surface;
+  A.seed_hits = seed_hits;
+  A.seed_event = seed_event;
+  A.n_seeds = n_seeds;
+  A.n_events = index->n_events;
+  A.chi2_cut = params->chi2_cut;
+  A.k_max = params->k_max;
+  A.max_miss = params->max_miss;
+  A.lmax = params->lmax;
+  A.hits_out = hits_out;
+  A.nhits_out = nhits_out;
+  A.chi2_out = chi2_out;
+  A.state_out = state_out;
+  A.cov_out = cov_out;
+  A.status_out = status_out;
+  return launch_find(G, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+const char* kf_status_string(int status) {
+  switch (status) {
+    case KF_OK: return "ok";
+    case KF_ERR_ARG: return "invalid argument";
+    case KF_ERR_CAPACITY: return "size above a compiled capacity";
+    case KF_ERR_CUDA: return "CUDA launch error";
+    case KF_ERR_TIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

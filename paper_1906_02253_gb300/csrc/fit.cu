@@ -1,0 +1,87 @@
+// Kalman-filter track fit over known hit sequences (paper Sec. 2: track fitting as the first
+// vectorised use of the filter). One thread per track; the state (6) and the packed covariance
+// (21) stay in registers through all surfaces; track hit ids are read as structure-of-arrays
+// (coalesced), hits are gathered by id.
+#include "kf_math.cuh"
+
+namespace kfgb {
+
+__global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __restrict__ hits,
+                                                    const int* __restrict__ hit_surface,
+                                                    const int* __restrict__ track_hits, int n_tracks, int lmax,
+                                                    float* __restrict__ state_out, float* __restrict__ cov_out,
+                                                    float* __restrict__ chi2_out, int* __restrict__ ndof_out,
+                                                    int* __restrict__ status_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tracks) return;
+  float p[6], C[21];
+  int status = 0;
+  float chi2 = 0.f;
+  int nh = 0;
+  int id[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) id[k] = track_hits[static_cast<size_t>(k) * n_tracks + t];
+  if (id[0] < 0 || id[1] < 0 || id[2] < 0) {
+    status = 3;
+  } else {
+    float xs[3], ys[3], zs[3];
+    int s1 = 0;
+    bool surf_ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 h = hits[id[k]];
+      const int si = hit_surface[id[k]];
+      surf_ok &= si >= 0 && si < G.n_surf;
+      if (k == 0) s1 = si;
+      if (surf_ok) hit_xyz(G, si, h.x, h.y, xs[k], ys[k], zs[k]);
+    }
+    if (!surf_ok || !seed_from_hits(G, xs, ys, zs, s1, p, C)) {
+      status = 1;
+    } else {
+      for (int k = 0; k < lmax; ++k) {
+        const int hid = k < 3 ? id[k] : track_hits[static_cast<size_t>(k) * n_tracks + t];
+        if (hid < 0) continue;
+        const float2 h = hits[hid];
+        const int si = hit_surface[hid];
+        if (si < 0 || si >= G.n_surf) {
+          status = 2;
+          break;
+        }
+        if (k > 0) {
+          const float w = -kCurvF * G.bz * p[3];
+          Prop pr;
+          const bool ok = G.type[si] == 0 ? path_to_cylinder(p, w, G.r_or_z[si], pr)
+                                          : path_to_disk(p, w, G.r_or_z[si], pr);
+          if (!ok || !apply_propagation(G, si, p, C, pr)) {
+            status = 2;
+            break;
+          }
+        }
+        Meas m;
+        float rho;
+        meas_setup(G, si, p, m, rho);
+        meas_residual(G, si, p, rho, h.x, h.y, m);
+        Innov in;
+        innovation(G, C, m, in);
+        chi2 += kalman_update(p, C, in, m.r0, m.r1);
+        ++nh;
+      }
+    }
+  }
+  const float nanf_ = __int_as_float(0x7fc00000);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) state_out[static_cast<size_t>(i) * n_tracks + t] = status == 0 ? p[i] : nanf_;
+#pragma unroll
+  for (int i = 0; i < 21; ++i) cov_out[static_cast<size_t>(i) * n_tracks + t] = status == 0 ? C[i] : nanf_;
+  chi2_out[t] = status == 0 ? chi2 : nanf_;
+  // ndof counts every valid entry of the list, as the oracle does.
+  int nvalid = nh;
+  if (status != 0) {
+    nvalid = 0;
+    for (int k = 0; k < lmax; ++k) nvalid += track_hits[static_cast<size_t>(k) * n_tracks + t] >= 0;
+  }
+  ndof_out[t] = 2 * nvalid - 5;
+  status_out[t] = status;
+}
+
+}  // namespace kfgb

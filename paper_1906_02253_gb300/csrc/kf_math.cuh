@@ -1,0 +1,424 @@
+// FP32 device math of the Kalman-filter hot path: helix propagation to a barrel cylinder or an
+// endcap disk, surface-projected Jacobian and covariance transport C' = J C J^T + Q with
+// thin-layer multiple scattering, 2D hit measurement and the Kalman update, seed from three hits.
+//
+// The paper (arXiv:1906.02253, Sec. 1-2) names the traditional Kalman filter and prints no
+// formulas; these are the textbook ones for a helix in a uniform field Bz (Sec. 4: 3.8 T) with
+// state (x, y, z, kappa = q/pT, phi, theta) and transverse arc length s as path parameter,
+// signed curvature omega = -k Bz kappa. Written for FP32 accuracy: positions advance by small
+// increments computed from half-angle sines, the crossing is found by Newton steps on a
+// residual assembled from small terms, the small-angle derivatives use series.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kfgb {
+
+constexpr int kMaxSurf = 64;
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+constexpr float kCurvF = 0.00299792458f;  // GeV / (T cm)
+
+// Geometry as the kernels see it: passed by value, so it lives in the constant bank.
+struct DevGeom {
+  float bz, sigma_rphi, sigma_2nd;
+  float prior[5];
+  int n_surf, n_barrel, n_dpos, n_dneg;
+  int n_bins;
+  int type[kMaxSurf];
+  float r_or_z[kMaxSurf], lo[kMaxSurf], hi[kMaxSurf], x0[kMaxSurf];
+  int n_phi[kMaxSurf], n_2nd[kMaxSurf];
+  float sphi[kMaxSurf], s2[kMaxSurf];        // FP32 bin scales, rounded once from FP64 on the host
+  signed char barrel_order[kMaxSurf];        // barrel surfaces by increasing radius
+  signed char dpos_order[kMaxSurf];          // disks at z > 0 by increasing z
+  signed char dneg_order[kMaxSurf];          // disks at z < 0 by decreasing z
+};
+
+// Packed symmetric 6x6 index, i <= j (upper triangle, row-major).
+__host__ __device__ constexpr int ci(int i, int j) { return i <= j ? i * (11 - i) / 2 + j : j * (11 - j) / 2 + i; }
+
+__device__ __forceinline__ float wrap_pi(float a) {
+  if (a > kPiF) a -= kTwoPiF;
+  if (a <= -kPiF) a += kTwoPiF;
+  return a;
+}
+
+// sin(D/2), cos(D/2) and q = sin(D/2)/(D/2); then f1 = sin(D)/D = q cos(D/2) and
+// f2 = (1 - cos D)/D = q sin(D/2).
+__device__ __forceinline__ void half_angle(float D, float& q, float& sh, float& ch) {
+  const float h = 0.5f * D;
+  sincosf(h, &sh, &ch);
+  if (fabsf(h) < 0.05f) {
+    const float h2 = h * h;
+    q = 1.f - h2 * (1.f / 6.f) + h2 * h2 * (1.f / 120.f);
+  } else {
+    q = sh / h;
+  }
+}
+
+// Derivatives d f1/dD and d f2/dD (series below |D| = 0.5, where the closed forms cancel).
+__device__ __forceinline__ void helix_dfd(float D, float f1, float q, float cosD, float& d1, float& d2) {
+  if (fabsf(D) < 0.5f) {
+    const float D2 = D * D;
+    d1 = D * (-1.f / 3.f + D2 * (1.f / 30.f + D2 * (-1.f / 840.f + D2 * (1.f / 45360.f))));
+    d2 = 0.5f + D2 * (-1.f / 8.f + D2 * (1.f / 144.f + D2 * (-1.f / 5760.f)));
+  } else {
+    d1 = (cosD - f1) / D;
+    d2 = f1 - 0.5f * q * q;
+  }
+}
+
+struct Prop {
+  float s;        // transverse path to the surface
+  float f1, f2;   // helix functions at D = omega s
+  float q, sh, ch;
+  float c0, s0;   // cos, sin of phi at the start
+};
+
+__device__ __forceinline__ void prop_eval(Prop& pr, float w) {
+  half_angle(w * pr.s, pr.q, pr.sh, pr.ch);
+  pr.f1 = pr.q * pr.ch;
+  pr.f2 = pr.q * pr.sh;
+}
+
+// Smallest s > 0 reaching radius R from state p, by Newton steps from the straight-line
+// estimate on g(s) = (rho0^2 - R^2) + 2 p0.dp(s) + |dp(s)|^2.
+__device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float R, Prop& pr) {
+  sincosf(p[4], &pr.s0, &pr.c0);
+  const float x0 = p[0], y0 = p[1];
+  const float rho0 = sqrtf(x0 * x0 + y0 * y0);
+  const float d0 = (rho0 - R) * (rho0 + R);
+  const float A = x0 * pr.c0 + y0 * pr.s0;
+  const float disc = A * A - d0;
+  if (!(disc >= 0.f)) return false;
+  const float den = A + sqrtf(disc);
+  if (!(den > 0.f)) return false;
+  pr.s = -d0 / den;
+  if (!(pr.s > 0.f)) return false;
+  for (int it = 0; it < 12; ++it) {
+    prop_eval(pr, w);
+    const float dx = pr.s * (pr.c0 * pr.f1 - pr.s0 * pr.f2);
+    const float dy = pr.s * (pr.s0 * pr.f1 + pr.c0 * pr.f2);
+    const float g = d0 + 2.f * (x0 * dx + y0 * dy) + (dx * dx + dy * dy);
+    const float cD = 1.f - 2.f * pr.sh * pr.sh, sD = 2.f * pr.sh * pr.ch;
+    const float tx = pr.c0 * cD - pr.s0 * sD, ty = pr.s0 * cD + pr.c0 * sD;
+    const float gp = 2.f * ((x0 + dx) * tx + (y0 + dy) * ty);
+    if (!(gp > 0.f)) return false;
+    const float ds = g / gp;
+    pr.s -= ds;
+    if (fabsf(ds) <= 2e-7f * pr.s) break;
+  }
+  if (!(pr.s > 0.f)) return false;
+  prop_eval(pr, w);
+  return true;
+}
+
+__device__ __forceinline__ bool path_to_disk(const float* p, float w, float Z, Prop& pr) {
+  float st, ct;
+  sincosf(p[5], &st, &ct);
+  if (ct == 0.f) return false;
+  pr.s = (Z - p[2]) * st / ct;
+  if (!(pr.s > 0.f)) return false;
+  sincosf(p[4], &pr.s0, &pr.c0);
+  prop_eval(pr, w);
+  return true;
+}
+
+// Position reached after path s (used to test a crossing against the surface extent).
+__device__ __forceinline__ void prop_position(const float* p, const Prop& pr, float cot, float& x, float& y,
+                                              float& z) {
+  x = p[0] + pr.s * (pr.c0 * pr.f1 - pr.s0 * pr.f2);
+  y = p[1] + pr.s * (pr.s0 * pr.f1 + pr.c0 * pr.f2);
+  z = p[2] + pr.s * cot;
+}
+
+__device__ __forceinline__ float highland_var(float p, float x_over_x0) {
+  const float t0 = 0.0136f / p * sqrtf(x_over_x0) * (1.f + 0.038f * logf(x_over_x0));
+  return t0 * t0;
+}
+
+// Move state p and covariance C along the helix by pr.s onto surface `si`; C' = J C J^T + Q where
+// J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface.
+__device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, float* p, float* C, const Prop& pr) {
+  const float a = -kCurvF * G.bz;  // d omega / d kappa
+  const float w = a * p[3];
+  const float s = pr.s;
+  const float D = w * s;
+  float st, ct;
+  sincosf(p[5], &st, &ct);
+  const float cot = ct / st;
+  const float dx = s * (pr.c0 * pr.f1 - pr.s0 * pr.f2);
+  const float dy = s * (pr.s0 * pr.f1 + pr.c0 * pr.f2);
+  const float cD = 1.f - 2.f * pr.sh * pr.sh, sD = 2.f * pr.sh * pr.ch;
+  float d1, d2;
+  helix_dfd(D, pr.f1, pr.q, cD, d1, d2);
+  // Jacobian at fixed s.
+  const float Jxp = -dy, Jyp = dx;
+  const float Jxk = a * s * s * (pr.c0 * d1 - pr.s0 * d2);
+  const float Jyk = a * s * s * (pr.s0 * d1 + pr.c0 * d2);
+  const float Jzt = -s / (st * st);
+  const float Jpk = a * s;
+  // New state.
+  p[0] += dx;
+  p[1] += dy;
+  p[2] += s * cot;
+  p[4] = wrap_pi(p[4] + D);
+  const float tx = pr.c0 * cD - pr.s0 * sD, ty = pr.s0 * cD + pr.c0 * sD;
+  // Rows of J_s C for the changed rows 0, 1, 2, 4.
+  float R0[6], R1[6], R2[6], R4[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    R0[k] = C[ci(0, k)] + Jxk * C[ci(3, k)] + Jxp * C[ci(4, k)];
+    R1[k] = C[ci(1, k)] + Jyk * C[ci(3, k)] + Jyp * C[ci(4, k)];
+    R2[k] = C[ci(2, k)] + Jzt * C[ci(5, k)];
+    R4[k] = C[ci(4, k)] + Jpk * C[ci(3, k)];
+  }
+  const float c33 = C[ci(3, 3)], c34 = C[ci(3, 4)], c35 = C[ci(3, 5)], c55 = C[ci(5, 5)];
+  // C1 = (J_s C) J_s^T, upper triangle.
+  C[ci(0, 0)] = R0[0] + Jxk * R0[3] + Jxp * R0[4];
+  C[ci(0, 1)] = R0[1] + Jyk * R0[3] + Jyp * R0[4];
+  C[ci(0, 2)] = R0[2] + Jzt * R0[5];
+  C[ci(0, 3)] = R0[3];
+  C[ci(0, 4)] = R0[4] + Jpk * R0[3];
+  C[ci(0, 5)] = R0[5];
+  C[ci(1, 1)] = R1[1] + Jyk * R1[3] + Jyp * R1[4];
+  C[ci(1, 2)] = R1[2] + Jzt * R1[5];
+  C[ci(1, 3)] = R1[3];
+  C[ci(1, 4)] = R1[4] + Jpk * R1[3];
+  C[ci(1, 5)] = R1[5];
+  C[ci(2, 2)] = R2[2] + Jzt * R2[5];
+  C[ci(2, 3)] = R2[3];
+  C[ci(2, 4)] = R2[4] + Jpk * R2[3];
+  C[ci(2, 5)] = R2[5];
+  C[ci(3, 4)] = c34 + Jpk * c33;
+  C[ci(4, 4)] = R4[4] + Jpk * R4[3];
+  C[ci(4, 5)] = R4[5];
+  (void)c35;
+  (void)c55;
+  // Projection onto the surface: with gh = g / (g.t), v = C1 gh, alpha = gh.v,
+  // C' = C1 - t v^T - v t^T + alpha t t^T  (t3 = t5 = 0).
+  const float t[6] = {tx, ty, cot, 0.f, w, 0.f};
+  float g0, g1, g2;
+  if (G.type[si] == 0) {
+    const float gt = p[0] * tx + p[1] * ty;
+    if (!(gt != 0.f)) return false;
+    g0 = p[0] / gt;
+    g1 = p[1] / gt;
+    g2 = 0.f;
+  } else {
+    if (!(cot != 0.f)) return false;
+    g0 = 0.f;
+    g1 = 0.f;
+    g2 = 1.f / cot;
+  }
+  float v[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) v[i] = C[ci(i, 0)] * g0 + C[ci(i, 1)] * g1 + C[ci(i, 2)] * g2;
+  const float alpha = g0 * v[0] + g1 * v[1] + g2 * v[2];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i; j < 6; ++j) {
+      if (i == 3 || i == 5) {
+        if (j == 3 || j == 5) continue;
+      }
+      C[ci(i, j)] += -t[i] * v[j] - v[i] * t[j] + alpha * t[i] * t[j];
+    }
+  }
+  // Thin-layer multiple scattering (Highland, beta = 1) in (kappa, phi, theta).
+  const float xx0 = G.x0[si];
+  if (xx0 > 0.f) {
+    float cos_a;
+    if (G.type[si] == 0) {
+      const float r = sqrtf(p[0] * p[0] + p[1] * p[1]);
+      cos_a = st * (p[0] * tx + p[1] * ty) / r;
+    } else {
+      cos_a = ct;
+    }
+    const float kap = p[3];
+    const float pm = 1.f / (fabsf(kap) * st);
+    const float var = highland_var(pm, xx0 / fabsf(cos_a));
+    C[ci(5, 5)] += var;
+    C[ci(4, 4)] += var / (st * st);
+    C[ci(3, 5)] += -kap * cot * var;
+    C[ci(3, 3)] += kap * kap * cot * cot * var;
+  }
+  return true;
+}
+
+// Measurement model of one hit on surface si for state p: residuals r0 (transverse, cm), r1
+// (z or r), and the two rows of H restricted to (x, y, z).
+struct Meas {
+  float r0, r1;
+  float h0[3], h1[3];
+};
+
+// Predicted position azimuth and the H rows; residuals are filled by meas_residual.
+__device__ __forceinline__ void meas_setup(const DevGeom& G, int si, const float* p, Meas& m, float& rho) {
+  const float x = p[0], y = p[1];
+  const float rho2 = x * x + y * y;
+  rho = sqrtf(rho2);
+  if (G.type[si] == 0) {
+    const float R = G.r_or_z[si];
+    m.h0[0] = -R * y / rho2;
+    m.h0[1] = R * x / rho2;
+    m.h0[2] = 0.f;
+    m.h1[0] = 0.f;
+    m.h1[1] = 0.f;
+    m.h1[2] = 1.f;
+  } else {
+    m.h0[0] = -y / rho;
+    m.h0[1] = x / rho;
+    m.h0[2] = 0.f;
+    m.h1[0] = x / rho;
+    m.h1[1] = y / rho;
+    m.h1[2] = 0.f;
+  }
+}
+
+// Residual of hit (phi_h, v): the angle phi_h - phi_pred comes from the hit direction rotated
+// into the predicted position's frame, which avoids subtracting two rounded azimuths.
+__device__ __forceinline__ void meas_residual(const DevGeom& G, int si, const float* p, float rho, float phi_h,
+                                              float v, Meas& m) {
+  float sh, ch;
+  sincosf(phi_h, &sh, &ch);
+  const float x = p[0], y = p[1];
+  const float dphi = atan2f(x * sh - y * ch, x * ch + y * sh);
+  if (G.type[si] == 0) {
+    m.r0 = G.r_or_z[si] * dphi;
+    m.r1 = v - p[2];
+  } else {
+    m.r0 = rho * dphi;
+    m.r1 = v - rho;
+  }
+}
+
+// Innovation covariance S = H C H^T + V (2x2) and the columns C H^T.
+struct Innov {
+  float ch0[6], ch1[6];
+  float s00, s01, s11;
+};
+
+__device__ __forceinline__ void innovation(const DevGeom& G, const float* C, const Meas& m, Innov& in) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    in.ch0[i] = C[ci(i, 0)] * m.h0[0] + C[ci(i, 1)] * m.h0[1] + C[ci(i, 2)] * m.h0[2];
+    in.ch1[i] = C[ci(i, 0)] * m.h1[0] + C[ci(i, 1)] * m.h1[1] + C[ci(i, 2)] * m.h1[2];
+  }
+  in.s00 = m.h0[0] * in.ch0[0] + m.h0[1] * in.ch0[1] + m.h0[2] * in.ch0[2] + G.sigma_rphi * G.sigma_rphi;
+  in.s01 = m.h0[0] * in.ch1[0] + m.h0[1] * in.ch1[1] + m.h0[2] * in.ch1[2];
+  in.s11 = m.h1[0] * in.ch1[0] + m.h1[1] * in.ch1[1] + m.h1[2] * in.ch1[2] + G.sigma_2nd * G.sigma_2nd;
+}
+
+__device__ __forceinline__ float chi2_of(const Innov& in, float r0, float r1) {
+  const float det = in.s00 * in.s11 - in.s01 * in.s01;
+  return (in.s11 * r0 * r0 - 2.f * in.s01 * r0 * r1 + in.s00 * r1 * r1) / det;
+}
+
+// Kalman update: K = C H^T S^-1, p += K r, C -= K (H C). Returns the predicted chi2.
+__device__ __forceinline__ float kalman_update(float* p, float* C, const Innov& in, float r0, float r1) {
+  const float det = in.s00 * in.s11 - in.s01 * in.s01;
+  const float inv = 1.f / det;
+  const float i00 = in.s11 * inv, i01 = -in.s01 * inv, i11 = in.s00 * inv;
+  const float chi2 = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
+  float k0[6], k1[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    k0[i] = in.ch0[i] * i00 + in.ch1[i] * i01;
+    k1[i] = in.ch0[i] * i01 + in.ch1[i] * i11;
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) p[i] += k0[i] * r0 + k1[i] * r1;
+  p[4] = wrap_pi(p[4]);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+#pragma unroll
+    for (int j = i; j < 6; ++j) C[ci(i, j)] -= k0[i] * in.ch0[j] + k1[i] * in.ch1[j];
+  }
+  return chi2;
+}
+
+// Hit position in space.
+__device__ __forceinline__ void hit_xyz(const DevGeom& G, int si, float phi_h, float v, float& x, float& y,
+                                        float& z) {
+  float sh, ch;
+  sincosf(phi_h, &sh, &ch);
+  if (G.type[si] == 0) {
+    const float R = G.r_or_z[si];
+    x = R * ch;
+    y = R * sh;
+    z = v;
+  } else {
+    x = v * ch;
+    y = v * sh;
+    z = G.r_or_z[si];
+  }
+}
+
+// Seed from three hits: curvature of the circle through them (4 * area / product of sides,
+// signed by the turning direction), azimuth at hit 1 = chord direction 1->3 minus half the turning
+// angle, arc length 1->3 from the chord, cot(theta) from z over that arc. The prior sits on the
+// tangent space of hit 1's surface.
+__device__ __forceinline__ bool seed_from_hits(const DevGeom& G, const float* xs, const float* ys, const float* zs,
+                                               int si1, float* p, float* C) {
+  const float ax = xs[1] - xs[0], ay = ys[1] - ys[0];
+  const float bx = xs[2] - xs[0], by = ys[2] - ys[0];
+  const float cx = xs[2] - xs[1], cy = ys[2] - ys[1];
+  const float la = sqrtf(ax * ax + ay * ay), lb = sqrtf(bx * bx + by * by), lc = sqrtf(cx * cx + cy * cy);
+  const float cross = ax * by - ay * bx;  // twice the signed area; > 0 turning left
+  if (!(la > 0.f && lb > 0.f && lc > 0.f)) return false;
+  const float w = 2.f * cross / (la * lb * lc);
+  // Turning angle between hits 1 and 3 and arc length.
+  const float hw = 0.5f * lb * w;
+  if (!(fabsf(hw) < 1.f)) return false;
+  const float half = asinf(hw);                 // half the turning angle
+  float s13;
+  if (fabsf(hw) < 1e-3f) s13 = lb * (1.f + hw * hw * (1.f / 6.f));
+  else s13 = 2.f * half / w;
+  const float phi = wrap_pi(atan2f(by, bx) - half);
+  const float theta = atan2f(s13, zs[2] - zs[0]);
+  p[0] = xs[0];
+  p[1] = ys[0];
+  p[2] = zs[0];
+  p[3] = -w / (kCurvF * G.bz);
+  p[4] = phi;
+  p[5] = theta;
+#pragma unroll
+  for (int i = 0; i < 21; ++i) C[i] = 0.f;
+  const float rho = sqrtf(xs[0] * xs[0] + ys[0] * ys[0]);
+  const float ux = -ys[0] / rho, uy = xs[0] / rho;  // transverse direction along the surface
+  const float su2 = G.prior[0] * G.prior[0], s22 = G.prior[1] * G.prior[1];
+  C[ci(0, 0)] = su2 * ux * ux;
+  C[ci(0, 1)] = su2 * ux * uy;
+  C[ci(1, 1)] = su2 * uy * uy;
+  if (G.type[si1] == 0) {
+    C[ci(2, 2)] = s22;
+  } else {
+    const float rx = xs[0] / rho, ry = ys[0] / rho;
+    C[ci(0, 0)] += s22 * rx * rx;
+    C[ci(0, 1)] += s22 * rx * ry;
+    C[ci(1, 1)] += s22 * ry * ry;
+  }
+  C[ci(3, 3)] = G.prior[2] * G.prior[2];
+  C[ci(4, 4)] = G.prior[3] * G.prior[3];
+  C[ci(5, 5)] = G.prior[4] * G.prior[4];
+  return true;
+}
+
+// Hit-index bins by the FP32 rule, every operation separately rounded.
+__device__ __forceinline__ int phi_bin(const DevGeom& G, int si, float phi) {
+  const float a = __fmul_rn(__fadd_rn(phi, kPiF), G.sphi[si]);
+  const float f = floorf(a);
+  const int k = (f >= 0.f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;
+  return min(max(k, 0), G.n_phi[si] - 1);
+}
+
+__device__ __forceinline__ int second_bin(const DevGeom& G, int si, float v) {
+  const float a = __fmul_rn(__fsub_rn(v, G.lo[si]), G.s2[si]);
+  const float f = floorf(a);
+  const int k = (f >= 0.f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;
+  return min(max(k, 0), G.n_2nd[si] - 1);
+}
+
+}  // namespace kfgb

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Bars: hit index and bin lookup bit-exact; fitted parameters within 1e-4 relative and chi2 within
+1e-3 relative; finding hit assignments identical on >= 99.9% of seeds with efficiency equal within
+0.1%. Relative tolerances use a floor scale per quantity (1 cm for positions, 0.1/GeV for kappa,
+1 rad for angles, 1 for chi2) so values near zero are compared on the scale of the quantity.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FLOOR = np.array([1.0, 1.0, 1.0, 0.1, 1.0, 1.0])
+
+
+@pytest.fixture(scope="module")
+def kf():
+    import __graft_entry__ as ge
+    ge.build_library()
+    import paper_1906_02253_gb300 as k
+    k.load_library()
+    return k
+
+
+def _wrap(a):
+    return (a + np.pi) % (2 * np.pi) - np.pi
+
+
+def _state_rel_err(p_gpu, p_ora):
+    d = p_gpu.astype(np.float64) - p_ora
+    d[:, 4] = _wrap(d[:, 4])
+    return np.abs(d) / np.maximum(np.abs(p_ora), FLOOR)
+
+
+def _index_both(kf, wl, b):
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    torch.cuda.synchronize()
+    off, sh, si = oracle.build_index(oracle.Geometry(wl), b.hits, b.slab_offsets, b.n_events)
+    return idx, (off, sh, si), dev, g
+
+
+@pytest.mark.parametrize("wl_name,n_ev,nt", [("find", 3, 2500), ("hi_occ", 2, 1500), ("fit_batched", 2, 20000)])
+def test_hit_index_bit_exact(kf, wl_name, n_ev, nt):
+    wl = synth.workload(wl_name, n_events=n_ev, tracks_lo=nt // 2, tracks_hi=nt)
+    b = synth.generate(wl)
+    idx, (off, sh, si), _, _ = _index_both(kf, wl, b)
+    assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
+    assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
+    assert np.array_equal(idx.sorted_hits.cpu().numpy().view(np.uint32), sh.view(np.uint32))
+
+
+def test_hit_index_edge_cases(kf):
+    """Empty slabs, a single hit, hits on bin edges, at +-pi and outside the z extent."""
+    wl = synth.workload("find", n_events=2, tracks_lo=3, tracks_hi=3)
+    b = synth.generate(wl)
+    # keep only surface 0 hits of event 0 plus edge values, everything else empty
+    s0 = wl.surfaces[0]
+    edge = np.array([[-np.pi, s0.lo], [np.float32(np.pi), s0.hi], [0.0, 0.0], [np.nextafter(np.float32(np.pi), 0), -1e3],
+                     [-np.float32(np.pi), 1e3], [0.5, s0.lo + (s0.hi - s0.lo) / 32]], np.float32)
+    hits = np.concatenate([b.hits[b.slab_offsets[0]:b.slab_offsets[1]], edge]).astype(np.float32)
+    n = hits.shape[0]
+    slab = np.full(b.n_events * b.n_surf + 1, n, np.int64)
+    slab[0] = 0
+    b.hits, b.slab_offsets = hits, slab
+    b.hit_surface = np.zeros(n, np.int32)
+    idx, (off, sh, si), _, _ = _index_both(kf, wl, b)
+    assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
+    assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
+
+
+def test_hit_index_empty_event(kf):
+    wl = synth.workload("find", n_events=1, tracks_lo=0, tracks_hi=0)
+    b = synth.generate(wl)
+    assert b.n_hits == 0
+    g = kf.Geometry(wl)
+    hits = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
+    slab = torch.zeros(b.n_surf + 1, dtype=torch.int32, device="cuda")
+    idx = kf.HitIndex(g, 1, 1)
+    kf.build_hit_index(g, hits, slab, 1, 0, index=idx)
+    assert int(idx.bin_off.abs().sum()) == 0
+
+
+def _fit_both(kf, wl, b, tracks=None):
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    th = b.track_hits if tracks is None else tracks
+    out = kf.fit_tracks(g, dev["hits"], dev["hit_surface"], torch.from_numpy(np.ascontiguousarray(th.T)).cuda())
+    torch.cuda.synchronize()
+    r = oracle.fit(oracle.Geometry(wl), b.hits, b.hit_surface, th)
+    # surface type at each track's last hit (the covariance's null direction depends on it)
+    last = np.array([row[row >= 0][-1] if (row >= 0).any() else 0 for row in th])
+    r["surf_type"] = np.array([wl.surfaces[s].type == synth.DISK for s in b.hit_surface[last]])
+    return {k: v.cpu().numpy() for k, v in out.items()}, r
+
+
+def _assert_fit_parity(gpu, ora):
+    assert np.array_equal(gpu["status"], ora["status"])
+    assert np.array_equal(gpu["ndof"], ora["ndof"])
+    ok = ora["status"] == 0
+    rel = _state_rel_err(gpu["state"].T[ok], ora["p"][ok])
+    assert rel.max() < 1e-4, rel.max(axis=0)
+    c2r = np.abs(gpu["chi2"][ok] - ora["chi2"][ok]) / np.maximum(ora["chi2"][ok], 1.0)
+    assert c2r.max() < 1e-3, c2r.max()
+    _assert_cov_parity(gpu["cov"].T[ok], ora["cov"][ok], ora["p"][ok], ora["surf_type"][ok])
+
+
+def _tangent_basis(p, disk):
+    """Orthonormal basis of the 5D tangent space: complement of the surface normal (the
+    covariance is singular along the normal by construction)."""
+    n = np.zeros(6)
+    if disk:
+        n[2] = 1.0
+    else:
+        n[:2] = p[:2] / np.hypot(p[0], p[1])
+    q, _ = np.linalg.qr(np.column_stack([n, np.eye(6)]))
+    return q[:, 1:6]
+
+
+def _assert_cov_parity(cov_gpu, cov_ora, p_ora, disk=None, tol=1e-3):
+    """Tangent-space covariance elements agree within tol of sqrt(A_ii A_jj)."""
+    C = oracle.unpack_cov(cov_ora)
+    Cg = oracle.unpack_cov(cov_gpu.astype(np.float64))
+    worst = 0.0
+    for t in range(C.shape[0]):
+        T = _tangent_basis(p_ora[t], bool(disk[t]) if disk is not None else False)
+        A, Ag = T.T @ C[t] @ T, T.T @ Cg[t] @ T
+        d = np.sqrt(np.diag(A))
+        worst = max(worst, (np.abs(Ag - A) / np.outer(d, d)).max())
+    assert worst < tol, worst
+
+
+def test_fit_parity_small(kf):
+    """1000 tracks, 10 layers, no scattering (the small fitting workload)."""
+    wl = synth.workload("fit_small")
+    b = synth.generate(wl)
+    gpu, ora = _fit_both(kf, wl, b)
+    _assert_fit_parity(gpu, ora)
+
+
+def test_fit_parity_scattering_and_disks(kf):
+    for name in ("fit_batched", "hi_occ"):
+        wl = synth.workload(name, n_events=2, tracks_lo=1500, tracks_hi=3000)
+        b = synth.generate(wl)
+        gpu, ora = _fit_both(kf, wl, b)
+        _assert_fit_parity(gpu, ora)
+
+
+def test_fit_with_misses_and_short_tracks(kf):
+    """-1 entries inside a list are skipped; lists with fewer than three seed hits are rejected."""
+    wl = synth.workload("fit_batched", n_events=1, tracks_lo=700, tracks_hi=700)
+    b = synth.generate(wl)
+    th = b.track_hits.copy()
+    rng = np.random.default_rng(0)
+    for t in range(th.shape[0]):
+        k = rng.integers(3, th.shape[1], size=2)
+        th[t, k] = -1
+    th[:5, 1] = -1
+    gpu, ora = _fit_both(kf, wl, b, th)
+    assert np.all(ora["status"][:5] == 3)
+    _assert_fit_parity(gpu, ora)
+
+
+def _find_both(kf, wl, b, **kw):
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(kw.get("chi2_cut", wl.chi2_cut), kw.get("k_max", wl.k_max), kw.get("max_miss", wl.max_miss),
+                         wl.lmax)
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    torch.cuda.synchronize()
+    sh, st = b.seeds()
+    r = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], **kw)
+    gpu = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    return gpu, r, st
+
+
+def _assert_find_parity(b, gpu, ora, st):
+    same = (gpu["hits"].T == ora["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    assert np.array_equal(gpu["status"], ora["status"])
+    e_g = oracle.efficiency(b, st, gpu["hits"].T, gpu["nhits"])[0]
+    e_o = oracle.efficiency(b, st, ora["hits"], ora["n_hits"])[0]
+    assert abs(e_g - e_o) <= 0.001
+    # identical tracks carry the same fit
+    ok = same & (ora["status"] == 0)
+    rel = _state_rel_err(gpu["state"].T[ok], ora["p"][ok])
+    assert np.quantile(rel.max(axis=1), 0.999) < 1e-4
+    c2r = np.abs(gpu["chi2"][ok] - ora["chi2"][ok]) / np.maximum(ora["chi2"][ok], 1.0)
+    assert np.quantile(c2r, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("wl_name,n_ev,nt,k", [("find", 2, 2500, 6), ("find", 2, 2500, 1), ("hi_occ", 2, 1500, 8),
+                                              ("learned", 2, 3000, 16)])
+def test_find_parity(kf, wl_name, n_ev, nt, k):
+    wl = synth.workload(wl_name, n_events=n_ev, tracks_lo=nt // 2, tracks_hi=nt)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b, k_max=k)
+    _assert_find_parity(b, gpu, ora, st)
+
+
+def test_find_parity_dense_noise(kf):
+    """Many branches per seed: 5 noise hits per signal hit."""
+    wl = synth.workload("find", n_events=1, tracks_lo=1200, tracks_hi=1200, noise_frac=5.0)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b)
+    _assert_find_parity(b, gpu, ora, st)

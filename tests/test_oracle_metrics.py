@@ -59,3 +59,17 @@ def test_clean_events_are_fully_efficient():
     f = oracle.find(g, b, sh, b.track_event[st])
     eff, fake, _ = oracle.efficiency(b, st, f["hits"], f["n_hits"])
     assert eff == 1.0 and fake == 0.0
+
+
+def test_package_efficiency_matches_oracle_definition():
+    """The package's vectorised efficiency (used by the benchmark) equals the oracle's loop."""
+    from paper_1906_02253_gb300 import metrics
+    wl = synth.workload("find", n_events=2, tracks_lo=300, tracks_hi=300, noise_frac=3.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    f = oracle.find(g, b, sh, b.track_event[st], k_max=1)
+    e1, f1, _ = oracle.efficiency(b, st, f["hits"], f["n_hits"])
+    e2, f2 = metrics.efficiency(b, st, f["hits"], f["n_hits"])
+    assert e1 == e2 and f1 == f2
+    assert 0.9 < e1 <= 1.0
