@@ -253,7 +253,7 @@ def run_gpu(args, wl, batch):
         t = torch.tensor([ms_step], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-    launches_per_step = 3  # index, find, fit kernels (plus one memset node)
+    launches_per_step = 4  # index, seed states, find, fit kernels (plus one memset node)
 
     # Per-kernel durations: the same three launches eager, events on the launching stream.
     kern = {"index": [], "find": [], "fit": []}

@@ -70,19 +70,22 @@ typedef struct {
  *   bin_off     int [n_events * n_surf][n_bins + 1]: absolute position in sorted_* of the first
  *               hit of each bin; entry n_bins (and every bin beyond the surface's own count) is
  *               the slab end. n_bins = max over surfaces of n_phi * n_2nd.
- *   sorted_hits float [n_hits][2] and sorted_ids int [n_hits]: same slab ranges as the input. */
+ *   sorted_hits float [n_hits][2] and sorted_ids int [n_hits]: same slab ranges as the input.
+ *   sorted_dir  float [n_hits][2]: (cos phi, sin phi) of each sorted hit. Optional for
+ *               kf_build_hit_index (NULL: not written); required by kf_find_tracks. */
 typedef struct {
   int n_events;
   int n_bins;
   int* bin_off;
   float* sorted_hits;
   int* sorted_ids;
+  float* sorted_dir;
 } KfHitIndex;
 
 /* Finder settings. chi2_cut: hits with predicted chi2 below it make children; k_max: candidates
  * kept per seed (<= KF_MAX_K); max_miss: surfaces a candidate may cross without a hit; lmax:
- * length of each output hit list (3 seed hits + at most lmax-3 steps, <= KF_MAX_LMAX);
- * block_threads: threads per block (0 = default 128; a multiple of 32, <= 128);
+ * length of each output hit list (3 seed hits + at most lmax-3 steps; 4 <= lmax <= KF_MAX_LMAX);
+ * block_threads: threads per block (0 = default 256; a multiple of 32, <= 256);
  * blocks_per_sm: resident blocks per SM for the persistent grid (0 = occupancy maximum). */
 typedef struct {
   float chi2_cut;

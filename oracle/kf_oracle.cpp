@@ -163,11 +163,15 @@ bool path_to_cylinder(const OrGeom& g, const double* p0, double R, double& s_out
   return true;
 }
 
-bool path_to_disk(const double* p0, double Z, double& s_out) {
+// Path to the plane z = Z. A track is followed for at most half a turn in the transverse plane
+// (|omega s| < pi), as the generator follows particles: beyond that it would be coming back
+// inward, and the disk is not reached.
+bool path_to_disk(const OrGeom& g, const double* p0, double Z, double& s_out) {
   const double cot = std::cos(p0[5]) / std::sin(p0[5]);
   if (cot == 0.0) return false;
   const double s = (Z - p0[2]) / cot;
   if (!(s > 1e-9)) return false;
+  if (!(std::fabs(omega_of(g, p0[3]) * s) < kPi)) return false;
   s_out = s;
   return true;
 }
@@ -217,7 +221,7 @@ bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_o
                double* s_used = nullptr) {
   const OrSurface& S = g.surf[si];
   double s;
-  const bool ok = (S.type == 0) ? path_to_cylinder(g, in.p, S.r_or_z, s) : path_to_disk(in.p, S.r_or_z, s);
+  const bool ok = (S.type == 0) ? path_to_cylinder(g, in.p, S.r_or_z, s) : path_to_disk(g, in.p, S.r_or_z, s);
   if (!ok) return false;
   helix_at(g, in.p, s, out.p);
   Mat6 Js, J;
@@ -323,6 +327,7 @@ double chi2_of(const Meas& m, const Mat6 C, double Sm[2][2]) {
   Sm[0][0] += m.V[0];
   Sm[1][1] += m.V[1];
   const double det = Sm[0][0] * Sm[1][1] - Sm[0][1] * Sm[1][0];
+  if (!(det > 0.0) || !(Sm[0][0] > 0.0)) return HUGE_VAL;  // not a covariance: no hit is compatible
   const double i00 = Sm[1][1] / det, i01 = -Sm[0][1] / det, i11 = Sm[0][0] / det;
   return m.r[0] * (i00 * m.r[0] + i01 * m.r[1]) + m.r[1] * (i01 * m.r[0] + i11 * m.r[1]);
 }
@@ -584,7 +589,7 @@ int next_surface(const OrGeom& g, const State& st, double* s_next) {
   }
   if (nd >= 0) {
     double s;
-    if (path_to_disk(st.p, g.surf[nd].r_or_z, s)) {
+    if (path_to_disk(g, st.p, g.surf[nd].r_or_z, s)) {
       double q[6];
       helix_at(g, st.p, s, q);
       const double r = std::hypot(q[0], q[1]);

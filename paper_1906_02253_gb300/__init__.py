@@ -40,7 +40,7 @@ class KfGeometry(ctypes.Structure):
 
 class KfHitIndex(ctypes.Structure):
     _fields_ = [("n_events", ctypes.c_int), ("n_bins", ctypes.c_int), ("bin_off", ctypes.c_void_p),
-                ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p)]
+                ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p), ("sorted_dir", ctypes.c_void_p)]
 
 
 class KfFindParams(ctypes.Structure):
@@ -136,8 +136,9 @@ class HitIndex:
         self.bin_off = torch.empty((n_events * geom.n_surf, geom.n_bins + 1), dtype=torch.int32, device=device)
         self.sorted_hits = torch.empty((n_hits, 2), dtype=torch.float32, device=device)
         self.sorted_ids = torch.empty(n_hits, dtype=torch.int32, device=device)
+        self.sorted_dir = torch.empty((n_hits, 2), dtype=torch.float32, device=device)
         self.c = KfHitIndex(n_events, self.n_bins, self.bin_off.data_ptr(), self.sorted_hits.data_ptr(),
-                            self.sorted_ids.data_ptr())
+                            self.sorted_ids.data_ptr(), self.sorted_dir.data_ptr())
 
 
 def build_hit_index(geom: Geometry, hits, slab_offsets, n_events: int, max_slab_hits: int, index: HitIndex = None,

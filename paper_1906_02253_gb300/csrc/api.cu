@@ -11,7 +11,8 @@
 namespace kfgb {
 
 __global__ void k_build_hit_index(DevGeom G, const float2* hits, const int* slab_off, int n_slabs, int cap,
-                                  int* bin_off, float2* sorted_hits, int* sorted_ids, int* d_status);
+                                  int* bin_off, float2* sorted_hits, int* sorted_ids, float2* sorted_dir,
+                                  int* d_status);
 __global__ void k_fit_tracks(DevGeom G, const float2* hits, const int* hit_surface, const int* track_hits,
                              int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
                              int* status_out);
@@ -123,7 +124,8 @@ int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* sla
   }
   k_build_hit_index<<<n_slabs, 512, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
       G, reinterpret_cast<const float2*>(hits), slab_offsets, n_slabs, cap, index->bin_off,
-      reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, d_status);
+      reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, reinterpret_cast<float2*>(index->sorted_dir),
+      d_status);
   return launch_status();
 }
 
@@ -164,7 +166,9 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   rc = plan_find(n_seeds, params, sm_count(), &plan);
   if (rc != KF_OK) return rc;
   if (n_seeds == 0) return KF_OK;
-  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids) return KF_ERR_ARG;
+  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
+      !index->sorted_dir)
+    return KF_ERR_ARG;
   if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
       !cov_out || !status_out)
     return KF_ERR_ARG;
@@ -173,6 +177,7 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   A.bin_off = index->bin_off;
   A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
   A.sorted_ids = index->sorted_ids;
+  A.sorted_dir = index->sorted_dir;
   A.hits = reinterpret_cast<const float2*>(hits);
   A.hit_surface = hit_surface;
   A.seed_hits = seed_hits;

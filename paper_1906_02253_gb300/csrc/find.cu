@@ -3,120 +3,51 @@
 // through binned search windows. Seeds run in parallel with no hit marking between them
 // (Sec. 3.2).
 //
-// Design. One thread per seed in a persistent grid: each warp takes 32 consecutive seeds from an
-// atomic work counter (seeds of one event and nearby direction sit next to each other, so a
-// warp's windows touch neighbouring bins and reuse cached hits). A thread keeps its seed's
-// candidates in a structure-of-arrays workspace (two buffers, current and next, 32 words per
-// candidate, word-major so a warp's accesses to the same word coalesce) and the ranking keys
-// of the next step in registers. Each parent is propagated once; its passing hits are kept as a
-// sorted top-k list; children are updated only when they enter the next step's top k, in
-// ranking order, so a parent's remaining children are skipped once one is rejected. A per-step
-// trace (parent slot, hit id) is backtracked at the end for the best candidate's hit list.
+// Design: a warp owns floor(32 / KC) seeds with KC candidate slots each, one lane per slot, and
+// keeps the candidates in shared memory. One step of all its seeds:
+//  1. every lane with a live candidate picks the next surface and propagates it (state and
+//     covariance in registers), then sets up its search window: the inverse innovation covariance
+//     and up to kRows runs [a, b) of sorted hit positions (one run per phi bin of the window);
+//  2. the hits of all the warp's windows are flattened with a warp prefix sum and every lane
+//     evaluates chi2 for every 32nd of them (full SIMT width whatever the window sizes); hits
+//     below the cut are buffered and each owner lane keeps its k_max best in a sorted list;
+//  3. per seed, the k_max best of all children (hit children, miss child, carried candidate) are
+//     selected by a group arg-min over the seed's lanes with shuffles; lane j materialises the
+//     j-th winner (Kalman update for a hit child) from its parent's record;
+//  4. a seed whose candidates have all stopped writes its best track (backtracking a per-step
+//     trace of parent slot and hit) and its lanes take the next seed from an atomic queue.
+// Seeds are consumed in order (one event after another, neighbouring directions together), so the
+// warps of an SM read neighbouring bins of the same event's index through L1/L2.
 #include <algorithm>
 
 #include "find_launch.cuh"
 
 namespace kfgb {
 
-constexpr int kWords = 32;
-constexpr int kHitBits = 27;  // trace entry: parent slot << 27 | (hit id + 1)
-
-// Ranking key: more hits first, then lower total chi2, then parent rank, then kind (0 hit child,
-// 1 miss child, 2 carried), then hit id.
-struct Key {
-  int nh;
-  float c2;
-  int pk;   // parent rank << 2 | kind
-  int hit;
-};
-
-__device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
-  if (a.nh != b.nh) return a.nh > b.nh;
-  if (a.c2 != b.c2) return a.c2 < b.c2;
-  if (a.pk != b.pk) return a.pk < b.pk;
-  return a.hit < b.hit;
-}
+constexpr int kWords = 32;      // candidate record: p[6], C[21], chi2, nh, nm, stopped, surf
+constexpr int kHitBits = 27;    // trace entry: parent slot << 27 | (hit id + 1)
+constexpr int kRows = 4;        // window runs per lane scanned cooperatively
+constexpr int kPList = 128;     // buffered passing (candidate, hit) pairs per warp
+constexpr unsigned kFull = 0xffffffffu;
 
 template <int KC>
-struct NextList {
-  Key k[KC];
-  int slot[KC];
-  int n;
-};
-
-// Would `e` enter a list of capacity cap holding n entries?
-template <int KC>
-__device__ __forceinline__ bool next_accepts(const NextList<KC>& L, int cap, const Key& e) {
-  if (L.n < cap) return true;
-  bool acc = false;
-#pragma unroll
-  for (int i = 0; i < KC; ++i)
-    if (i == cap - 1) acc = key_less(e, L.k[i]);
-  return acc;
-}
-
-// Storage slot the accepted entry will occupy: a fresh one, or the evicted worst's.
-template <int KC>
-__device__ __forceinline__ int next_slot_for(const NextList<KC>& L, int cap) {
-  if (L.n < cap) return L.n;
-  int s = 0;
-#pragma unroll
-  for (int i = 0; i < KC; ++i)
-    if (i == cap - 1) s = L.slot[i];
-  return s;
-}
-
-template <int KC>
-__device__ __forceinline__ void next_insert(NextList<KC>& L, int cap, const Key& e, int slot) {
-  const int p0 = L.n < cap ? L.n : cap - 1;
-  if (L.n < cap) ++L.n;
-  bool placed = false;
-#pragma unroll
-  for (int i = KC - 1; i >= 0; --i) {
-    if (i > p0 || placed) continue;
-    if (i > 0 && key_less(e, L.k[i - 1])) {
-      L.k[i] = L.k[i - 1];
-      L.slot[i] = L.slot[i - 1];
-    } else {
-      L.k[i] = e;
-      L.slot[i] = slot;
-      placed = true;
-    }
-  }
-}
-
-// A parent's passing hits, sorted by (chi2, hit id), at most cap of them.
-template <int KC>
-struct HitList {
-  float c2[KC];
-  int hit[KC];
-  int n;
+struct WarpSmem {
+  float cand[kWords][32];  // candidate records, one column per lane
+  float win[8][32];        // window of each lane: x, y, centre of 2nd coord, transverse scale, S^-1
+  int rowa[kRows][32];
+  int rowb[kRows][32];
+  float hl_c2[KC][32];     // per lane: best passing hits, sorted by (chi2, hit id)
+  int hl_id[KC][32];
+  int hl_pos[KC][32];
+  float pl_c2[kPList];
+  int pl_id[kPList];
+  int pl_pos[kPList];
+  int pl_own[kPList];
 };
 
 template <int KC>
-__device__ __forceinline__ void hits_insert(HitList<KC>& L, int cap, float c2, int hit) {
-  if (L.n == cap) {
-    bool better = false;
-#pragma unroll
-    for (int i = 0; i < KC; ++i)
-      if (i == cap - 1) better = (c2 < L.c2[i]) || (c2 == L.c2[i] && hit < L.hit[i]);
-    if (!better) return;
-  }
-  const int p0 = L.n < cap ? L.n : cap - 1;
-  if (L.n < cap) ++L.n;
-  bool placed = false;
-#pragma unroll
-  for (int i = KC - 1; i >= 0; --i) {
-    if (i > p0 || placed) continue;
-    if (i > 0 && ((c2 < L.c2[i - 1]) || (c2 == L.c2[i - 1] && hit < L.hit[i - 1]))) {
-      L.c2[i] = L.c2[i - 1];
-      L.hit[i] = L.hit[i - 1];
-    } else {
-      L.c2[i] = c2;
-      L.hit[i] = hit;
-      placed = true;
-    }
-  }
+__host__ __device__ size_t warp_smem_bytes(int lmax) {
+  return (sizeof(WarpSmem<KC>) + static_cast<size_t>(lmax - 3) * 32 * sizeof(int) + 15) / 16 * 16;
 }
 
 struct Cand {
@@ -126,37 +57,99 @@ struct Cand {
   int nh, nm, stopped, surf;
 };
 
-__device__ __forceinline__ float* rec(float* cand, int KC, int buf, int slot, int nt, int tid) {
-  return cand + (static_cast<size_t>(buf * KC + slot) * kWords) * nt + tid;
+template <int KC>
+__device__ __forceinline__ void load_cand(const WarpSmem<KC>& W, int col, Cand& c) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) c.p[i] = W.cand[i][col];
+#pragma unroll
+  for (int i = 0; i < 21; ++i) c.C[i] = W.cand[6 + i][col];
+  c.chi2 = W.cand[27][col];
+  c.nh = __float_as_int(W.cand[28][col]);
+  c.nm = __float_as_int(W.cand[29][col]);
+  c.stopped = __float_as_int(W.cand[30][col]);
+  c.surf = __float_as_int(W.cand[31][col]);
 }
 
-__device__ __forceinline__ void store_cand(float* r, int nt, const Cand& c) {
+template <int KC>
+__device__ __forceinline__ void store_cand(WarpSmem<KC>& W, int col, const Cand& c) {
 #pragma unroll
-  for (int i = 0; i < 6; ++i) r[static_cast<size_t>(i) * nt] = c.p[i];
+  for (int i = 0; i < 6; ++i) W.cand[i][col] = c.p[i];
 #pragma unroll
-  for (int i = 0; i < 21; ++i) r[static_cast<size_t>(6 + i) * nt] = c.C[i];
-  r[static_cast<size_t>(27) * nt] = c.chi2;
-  r[static_cast<size_t>(28) * nt] = __int_as_float(c.nh);
-  r[static_cast<size_t>(29) * nt] = __int_as_float(c.nm);
-  r[static_cast<size_t>(30) * nt] = __int_as_float(c.stopped);
-  r[static_cast<size_t>(31) * nt] = __int_as_float(c.surf);
+  for (int i = 0; i < 21; ++i) W.cand[6 + i][col] = c.C[i];
+  W.cand[27][col] = c.chi2;
+  W.cand[28][col] = __int_as_float(c.nh);
+  W.cand[29][col] = __int_as_float(c.nm);
+  W.cand[30][col] = __int_as_float(c.stopped);
+  W.cand[31][col] = __int_as_float(c.surf);
 }
 
-__device__ __forceinline__ void load_cand(const float* r, int nt, Cand& c) {
-#pragma unroll
-  for (int i = 0; i < 6; ++i) c.p[i] = r[static_cast<size_t>(i) * nt];
-#pragma unroll
-  for (int i = 0; i < 21; ++i) c.C[i] = r[static_cast<size_t>(6 + i) * nt];
-  c.chi2 = r[static_cast<size_t>(27) * nt];
-  c.nh = __float_as_int(r[static_cast<size_t>(28) * nt]);
-  c.nm = __float_as_int(r[static_cast<size_t>(29) * nt]);
-  c.stopped = __float_as_int(r[static_cast<size_t>(30) * nt]);
-  c.surf = __float_as_int(r[static_cast<size_t>(31) * nt]);
+// Residual angle phi_hit - phi_pred from the hit direction (c, s) rotated into the frame of the
+// predicted position (x, y); series of atan for the small angles of a search window.
+__device__ __forceinline__ float resid_angle(float x, float y, float c, float s) {
+  const float a = x * s - y * c, b = x * c + y * s;
+  if (b > 0.f && fabsf(a) < 0.05f * b) {
+    const float t = a / b, t2 = t * t;
+    return t * (1.f + t2 * (-1.f / 3.f + t2 * (1.f / 5.f + t2 * (-1.f / 7.f))));
+  }
+  return atan2f(a, b);
+}
+
+// Kalman update of candidate c on surface si with the hit (phi, v) of direction d.
+__device__ __forceinline__ void update_with(const DevGeom& G, int si, Cand& c, float2 h, float2 d) {
+  Meas m;
+  float rho;
+  meas_setup(G, si, c.p, m, rho);
+  const float dphi = resid_angle(c.p[0], c.p[1], d.x, d.y);
+  if (G.type[si] == 0) {
+    m.r0 = G.r_or_z[si] * dphi;
+    m.r1 = h.y - c.p[2];
+  } else {
+    m.r0 = rho * dphi;
+    m.r1 = h.y - rho;
+  }
+  Innov in;
+  innovation(G, c.C, m, in);
+  kalman_update(c.p, c.C, in, m.r0, m.r1);
+}
+
+__device__ __forceinline__ float update_exact(const DevGeom& G, int si, Cand& c, float phi_h, float v) {
+  Meas m;
+  float rho;
+  meas_setup(G, si, c.p, m, rho);
+  meas_residual(G, si, c.p, rho, phi_h, v, m);
+  Innov in;
+  innovation(G, c.C, m, in);
+  return kalman_update(c.p, c.C, in, m.r0, m.r1);
+}
+
+// Insert (c2, id, pos) into lane's sorted list of capacity cap (holding n entries).
+template <int KC>
+__device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int cap, float c2, int id, int pos) {
+  if (n == cap) {
+    const float lc = W.hl_c2[cap - 1][lane];
+    const int li = W.hl_id[cap - 1][lane];
+    if (!(c2 < lc || (c2 == lc && id < li))) return;
+    n = cap - 1;
+  }
+  int i = n;
+  while (i > 0) {
+    const float pc = W.hl_c2[i - 1][lane];
+    const int pi = W.hl_id[i - 1][lane];
+    if (!(c2 < pc || (c2 == pc && id < pi))) break;
+    W.hl_c2[i][lane] = pc;
+    W.hl_id[i][lane] = pi;
+    W.hl_pos[i][lane] = W.hl_pos[i - 1][lane];
+    --i;
+  }
+  W.hl_c2[i][lane] = c2;
+  W.hl_id[i][lane] = id;
+  W.hl_pos[i][lane] = pos;
+  ++n;
 }
 
 // Next surface outward and the path to it: the next barrel layer beyond the candidate's radius
 // (accepted if crossed within its z extent) and the next disk beyond |z| in the direction of
-// motion (accepted if crossed within its r extent); the nearer accepted one. -1 if none.
+// motion (accepted if crossed within its r extent and half a turn); the nearer one. -1 if none.
 __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, Prop& best) {
   const float w = -kCurvF * G.bz * p[3];
   const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
@@ -199,303 +192,522 @@ __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, Pr
   return sel;
 }
 
-// Every hit of surface si in event ev with chi2 below the cut for the predicted state (p, C),
-// through the padded bounding box of the chi2 ellipse turned into bin ranges.
-template <int KC>
-__device__ __forceinline__ void search_window(const DevGeom& G, const FindArgs& A, int ev, int si, const float* p,
-                                              const float* C, int cap, HitList<KC>& out) {
-  out.n = 0;
-  Meas m;
-  float rho;
-  meas_setup(G, si, p, m, rho);
-  Innov in;
-  innovation(G, C, m, in);
-  const float cut = A.chi2_cut;
-  const float rref = G.type[si] == 0 ? G.r_or_z[si] : rho;
-  const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
-  const float d2 = sqrtf(cut * in.s11) * (1.f + 1e-4f) + 1e-4f;
-  const float phip = atan2f(p[1], p[0]);
-  const float c2 = G.type[si] == 0 ? p[2] : rho;
-  const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
-  int pb0, npb;
-  if (!(dphi < kPiF * (1.f - 2.f / nphi))) {
-    pb0 = 0;
-    npb = nphi;
+// Seed states, one thread per seed: the circle seed of the three hits and the filter over them
+// (update with hit 1, propagate and update through hits 2 and 3). Written structure-of-arrays
+// as kSeedWords words per seed (p[6], C[21], chi2; chi2 < 0 marks a failed seed, whose outputs
+// are written here).
+constexpr int kSeedWords = 28;
+
+__global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
+  const int seed = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = A.n_seeds;
+  if (seed >= n) return;
+  int ids[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ids[k] = A.seed_hits[static_cast<size_t>(k) * n + seed];
+  const int ev = A.seed_event[seed];
+  bool ok = ids[0] >= 0 && ids[1] >= 0 && ids[2] >= 0 && ev >= 0 && ev < A.n_events;
+  Cand c;
+  int ss[3] = {0, 0, 0};
+  if (ok) {
+    float xs[3], ys[3], zs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 h = A.hits[ids[k]];
+      ss[k] = A.hit_surface[ids[k]];
+      ok = ok && ss[k] >= 0 && ss[k] < G.n_surf;
+      if (ok) hit_xyz(G, ss[k], h.x, h.y, xs[k], ys[k], zs[k]);
+    }
+    ok = ok && seed_from_hits(G, xs, ys, zs, ss[0], c.p, c.C);
+  }
+  c.chi2 = 0.f;
+  for (int k = 0; k < 3 && ok; ++k) {
+    if (k > 0) {
+      const float w = -kCurvF * G.bz * c.p[3];
+      Prop pr;
+      ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
+                              : path_to_disk(c.p, w, G.r_or_z[ss[k]], pr);
+      ok = ok && apply_propagation(G, ss[k], c.p, c.C, pr);
+      if (!ok) break;
+    }
+    const float2 h = A.hits[ids[k]];
+    c.chi2 += update_exact(G, ss[k], c, h.x, h.y);
+  }
+  float* out = A.seed_state + seed;
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[static_cast<size_t>(i) * n] = c.p[i];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) out[static_cast<size_t>(6 + i) * n] = c.C[i];
+    out[static_cast<size_t>(27) * n] = c.chi2;
+    A.seed_surf[seed] = ss[2];
   } else {
-    pb0 = phi_bin(G, si, wrap_pi(phip - dphi));
-    const int pb1 = phi_bin(G, si, wrap_pi(phip + dphi));
-    npb = ((pb1 - pb0) % nphi + nphi) % nphi + 1;
-  }
-  const int zb0 = second_bin(G, si, c2 - d2);
-  const int zb1 = second_bin(G, si, c2 + d2);
-  const float det = in.s00 * in.s11 - in.s01 * in.s01;
-  const float inv = 1.f / det;
-  const float i00 = in.s11 * inv, i01 = -in.s01 * inv, i11 = in.s00 * inv;
-  const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
-  for (int k = 0; k < npb; ++k) {
-    int pb = pb0 + k;
-    if (pb >= nphi) pb -= nphi;
-    const int a = __ldg(off + pb * n2 + zb0);
-    const int b = __ldg(off + pb * n2 + zb1 + 1);
-    for (int q = a; q < b; ++q) {
-      const float2 h = __ldg(A.sorted_hits + q);
-      meas_residual(G, si, p, rho, h.x, h.y, m);
-      const float c = m.r0 * (i00 * m.r0 + i01 * m.r1) + m.r1 * (i01 * m.r0 + i11 * m.r1);
-      if (c < cut) hits_insert<KC>(out, cap, c, __ldg(A.sorted_ids + q));
-    }
+    out[static_cast<size_t>(27) * n] = -1.f;
+    const float nanf_ = __int_as_float(0x7fc00000);
+    for (int k = 0; k < A.lmax; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
+    A.nhits_out[seed] = 0;
+    A.chi2_out[seed] = nanf_;
+    for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = nanf_;
+    for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = nanf_;
+    A.status_out[seed] = 1;
   }
 }
 
-__device__ __forceinline__ float kf_step_update(const DevGeom& G, int si, Cand& c, float phi_h, float v) {
-  Meas m;
-  float rho;
-  meas_setup(G, si, c.p, m, rho);
-  meas_residual(G, si, c.p, rho, phi_h, v, m);
-  Innov in;
-  innovation(G, c.C, m, in);
-  return kalman_update(c.p, c.C, in, m.r0, m.r1);
+// Packed ranking key: (63 - hits) << 58 | chi2 bits << 26 | (parent slot << 2 | kind) << 20.
+// chi2 >= 0, so its IEEE bits order like its value; the hit id breaks remaining ties.
+__device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk) {
+  return (static_cast<unsigned long long>(63 - nh) << 58) |
+         (static_cast<unsigned long long>(__float_as_uint(c2)) << 26) | (static_cast<unsigned long long>(pk) << 20);
 }
 
 template <int KC>
-__device__ __forceinline__ void find_one_seed(const DevGeom& G, const FindArgs& A, int seed, int tid) {
-    const int nt = A.nt;
-    const int cap = A.k_max;
-    const float nanf_ = __int_as_float(0x7fc00000);
-    const int n = A.n_seeds;
-    // ---- seed fit ------------------------------------------------------------------------
-    int ids[3];
+__global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NS = 32 / KC;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const size_t wbytes = warp_smem_bytes<KC>(A.lmax);
+  WarpSmem<KC>& W = *reinterpret_cast<WarpSmem<KC>*>(smem + wid * wbytes);
+  int* trace = reinterpret_cast<int*>(smem + wid * wbytes + sizeof(WarpSmem<KC>));  // [step][32]
+  const int grp = lane / KC, slot = lane % KC;
+  const bool in_grp = grp < NS;
+  const int gbase = in_grp ? grp * KC : lane;
+  const unsigned gmask = in_grp ? (((KC >= 32) ? kFull : ((1u << KC) - 1u)) << gbase) : (1u << lane);
+  const int cap = A.k_max;
+  const int n = A.n_seeds;
+  const int max_steps = A.lmax - 3;
+  const float cut = A.chi2_cut;
+  const float nanf_ = __int_as_float(0x7fc00000);
+
+  int seed = -1, ev = 0, step = 0;
+  bool exhausted = !in_grp;
+  bool valid = false;
+
+  for (;;) {
+    // ---- refill: a group without a seed takes the next one --------------------------------
+    const bool want = !exhausted && seed < 0;
+    int s = -1;
+    if (want && slot == 0) s = atomicAdd(A.counter, 1);
+    s = __shfl_sync(kFull, s, gbase);
+    bool fresh = false;
+    if (want) {
+      if (s >= n) {
+        exhausted = true;
+      } else {
+        seed = s;
+        step = 0;
+        valid = false;
+        fresh = true;
+        ev = A.seed_event[seed];
+      }
+    }
+    if (!__any_sync(kFull, seed >= 0)) break;
+
+    // ---- a fresh group loads its seed state into slot 0 ------------------------------------
+    int failed = 0;
+    if (fresh && slot == 0) {
+      const float* in = A.seed_state + seed;
+      const float chi2 = in[static_cast<size_t>(27) * n];
+      if (chi2 >= 0.f) {
+        Cand c;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) ids[k] = A.seed_hits[static_cast<size_t>(k) * n + seed];
-    const int ev = A.seed_event[seed];
+        for (int i = 0; i < 6; ++i) c.p[i] = in[static_cast<size_t>(i) * n];
+#pragma unroll
+        for (int i = 0; i < 21; ++i) c.C[i] = in[static_cast<size_t>(6 + i) * n];
+        c.chi2 = chi2;
+        c.nh = 3;
+        c.nm = 0;
+        c.stopped = 0;
+        c.surf = A.seed_surf[seed];
+        store_cand(W, lane, c);
+        valid = true;
+      } else {
+        failed = 1;  // outputs already written by the seed-state kernel
+      }
+    }
+    failed = __shfl_sync(kFull, failed, gbase);
+    if (fresh && failed) {
+      seed = -1;
+      valid = false;
+    }
+    const bool on = seed >= 0;
+
+    // ---- 1. propagation and window set-up -------------------------------------------------
     Cand c;
-    bool ok = ids[0] >= 0 && ids[1] >= 0 && ids[2] >= 0 && ev >= 0 && ev < A.n_events;
-    if (ok) {
-      float xs[3], ys[3], zs[3];
-      int ss[3];
+    int kind = 3;  // 0 hit children, 1 miss child, 2 carried, 3 empty slot
+    int si = -1, T = 0, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, hl_n = 0;
+    bool wide = false;
+    if (on && valid) {
+      load_cand(W, lane, c);
+      kind = 2;
+      if (!c.stopped) {
+        Prop pr;
+        si = next_surface(G, c.p, pr);
+        if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr)) {
+          kind = 1;
+          Meas m;
+          float rho;
+          meas_setup(G, si, c.p, m, rho);
+          Innov in;
+          innovation(G, c.C, m, in);
+          if (innovation_ok(in)) {
+            const float det = in.s00 * in.s11 - in.s01 * in.s01;
+            const float inv = 1.f / det;
+            const bool barrel = G.type[si] == 0;
+            const float rref = barrel ? G.r_or_z[si] : rho;
+            const float cz = barrel ? c.p[2] : rho;
+            W.win[0][lane] = c.p[0];
+            W.win[1][lane] = c.p[1];
+            W.win[2][lane] = cz;
+            W.win[3][lane] = rref;
+            W.win[4][lane] = in.s11 * inv;
+            W.win[5][lane] = -in.s01 * inv;
+            W.win[6][lane] = in.s00 * inv;
+            const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
+            const float d2 = sqrtf(cut * in.s11) * (1.f + 1e-4f) + 1e-4f;
+            const int nphi = G.n_phi[si];
+            if (!(dphi < kPiF * (1.f - 2.f / nphi))) {
+              pb0 = 0;
+              npb = nphi;
+            } else {
+              const float phip = atan2f(c.p[1], c.p[0]);
+              pb0 = phi_bin(G, si, wrap_pi(phip - dphi));
+              const int pb1 = phi_bin(G, si, wrap_pi(phip + dphi));
+              npb = ((pb1 - pb0) % nphi + nphi) % nphi + 1;
+            }
+            zb0 = second_bin(G, si, cz - d2);
+            zb1 = second_bin(G, si, cz + d2);
+            wide = npb > kRows;
+            if (!wide) {
+              const int n2 = G.n_2nd[si];
+              const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float2 h = A.hits[ids[k]];
-        ss[k] = A.hit_surface[ids[k]];
-        ok &= ss[k] >= 0 && ss[k] < G.n_surf;
-        if (ok) hit_xyz(G, ss[k], h.x, h.y, xs[k], ys[k], zs[k]);
-      }
-      ok = ok && seed_from_hits(G, xs, ys, zs, ss[0], c.p, c.C);
-      c.chi2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (!ok) break;
-        if (k > 0) {
-          const float w = -kCurvF * G.bz * c.p[3];
-          Prop pr;
-          ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
-                                  : path_to_disk(c.p, w, G.r_or_z[ss[k]], pr);
-          if (ok) ok = apply_propagation(G, ss[k], c.p, c.C, pr);
-          if (!ok) break;
-        }
-        const float2 h = A.hits[ids[k]];
-        c.chi2 += kf_step_update(G, ss[k], c, h.x, h.y);
-      }
-      c.surf = ss[2];
-    }
-    if (!ok) {
-      for (int k = 0; k < A.lmax; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
-      A.nhits_out[seed] = 0;
-      A.chi2_out[seed] = nanf_;
-      for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = nanf_;
-      for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = nanf_;
-      A.status_out[seed] = 1;
-      return;
-    }
-    c.nh = 3;
-    c.nm = 0;
-    c.stopped = 0;
-    store_cand(rec(A.cand, KC, 0, 0, nt, tid), nt, c);
-    int ncur = 1;
-    unsigned long long cur_slots = 0ull;  // storage slot of rank r in bits [4r, 4r+4)
-    int cur = 0;
-    int nsteps = 0;
-    bool any_active = true;
-    // ---- steps ---------------------------------------------------------------------------
-    for (int step = 0; step < A.lmax - 3 && any_active; ++step) {
-      NextList<KC> L;
-      L.n = 0;
-      const int nxt = cur ^ 1;
-      int* trace_step = A.trace + static_cast<size_t>(step) * KC * nt + tid;
-      for (int r = 0; r < ncur; ++r) {
-        const int pslot = static_cast<int>((cur_slots >> (4 * r)) & 0xFull);
-        float* prec = rec(A.cand, KC, cur, pslot, nt, tid);
-        load_cand(prec, nt, c);
-        int kind = 2;  // carried unless a child is produced
-        HitList<KC> H;
-        H.n = 0;
-        int si = -1;
-        if (!c.stopped) {
-          Prop pr;
-          si = next_surface(G, c.p, pr);
-          if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr)) {
-            search_window<KC>(G, A, ev, si, c.p, c.C, cap, H);
-            kind = H.n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
-          } else {
-            si = -1;
-          }
-        }
-        if (kind == 0) {
-          if (H.n > 1) store_cand(prec, nt, c);  // the prediction, for the other children
-          const float parent_chi2 = c.chi2;
-          const int parent_nh = c.nh;
-#pragma unroll
-          for (int j = 0; j < KC; ++j) {
-            if (j >= H.n) break;
-            const Key e{parent_nh + 1, parent_chi2 + H.c2[j], (r << 2) | 0, H.hit[j]};
-            if (!next_accepts<KC>(L, cap, e)) break;
-            if (j > 0) load_cand(prec, nt, c);
-            const int hid = H.hit[j];
-            const float2 h = __ldg(A.hits + hid);
-            kf_step_update(G, si, c, h.x, h.y);
-            c.chi2 = e.c2;
-            c.nh = parent_nh + 1;
-            c.surf = si;
-            const int ns = next_slot_for<KC>(L, cap);
-            store_cand(rec(A.cand, KC, nxt, ns, nt, tid), nt, c);
-            trace_step[static_cast<size_t>(ns) * nt] = (pslot << kHitBits) | (hid + 1);
-            next_insert<KC>(L, cap, e, ns);
+              for (int r = 0; r < kRows; ++r) {
+                int a = 0, b = 0;
+                if (r < npb) {
+                  int pb = pb0 + r;
+                  if (pb >= nphi) pb -= nphi;
+                  a = __ldg(off + pb * n2 + zb0);
+                  b = __ldg(off + pb * n2 + zb1 + 1);
+                }
+                W.rowa[r][lane] = a;
+                W.rowb[r][lane] = b;
+                T += b - a;
+              }
+            }
           }
         } else {
-          const Key e{c.nh, c.chi2, (r << 2) | kind, -1};
-          if (next_accepts<KC>(L, cap, e)) {
-            if (kind == 1) {
-              c.nm += 1;
-              c.surf = si;
-            } else {
-              if (!c.stopped) load_cand(prec, nt, c);  // undo the prediction
-              c.stopped = 1;
-            }
-            const int ns = next_slot_for<KC>(L, cap);
-            store_cand(rec(A.cand, KC, nxt, ns, nt, tid), nt, c);
-            trace_step[static_cast<size_t>(ns) * nt] = pslot << kHitBits;
-            next_insert<KC>(L, cap, e, ns);
-          }
+          si = -1;
         }
       }
-      // Promote the next list.
-      ncur = L.n;
-      cur_slots = 0ull;
-      any_active = false;
-#pragma unroll
-      for (int i = 0; i < KC; ++i) {
-        if (i < L.n) {
-          cur_slots |= static_cast<unsigned long long>(L.slot[i]) << (4 * i);
-          any_active |= (L.k[i].pk & 3) != 2;
-        }
-      }
-      cur ^= 1;
-      nsteps = step + 1;
     }
-    // ---- output: best candidate, hit list by backtracking ----------------------------------
-    int slot = static_cast<int>(cur_slots & 0xFull);
-    load_cand(rec(A.cand, KC, cur, slot, nt, tid), nt, c);
-    for (int k = A.lmax - 1; k >= 3 + nsteps; --k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
-    for (int step = nsteps - 1; step >= 0; --step) {
-      const int e = A.trace[(static_cast<size_t>(step) * KC + slot) * nt + tid];
-      const int hit = (e & ((1 << kHitBits) - 1)) - 1;
-      A.hits_out[static_cast<size_t>(3 + step) * n + seed] = hit;
-      slot = e >> kHitBits;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = ids[k];
-    A.nhits_out[seed] = c.nh;
-    A.chi2_out[seed] = c.chi2;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = c.p[i];
-#pragma unroll
-    for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = c.C[i];
-    A.status_out[seed] = 0;
-}
 
-template <int KC>
-__global__ void __launch_bounds__(128) k_find_tracks(DevGeom G, FindArgs A) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(A.counter, 32);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= A.n_seeds) break;
-    const int seed = base + lane;
-    if (seed < A.n_seeds) find_one_seed<KC>(G, A, seed, tid);
+    // ---- 2. cooperative chi2 over every window hit of the warp ------------------------------
+    int incl = T;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - T;
+    int np = 0;
     __syncwarp();
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      int owner = 0;
+#pragma unroll
+      for (int bit = 16; bit > 0; bit >>= 1) {
+        const int v = __shfl_sync(kFull, incl, owner + bit - 1);
+        if (v <= q) owner += bit;
+      }
+      owner = min(owner, 31);
+      const int obase = __shfl_sync(kFull, excl, owner);
+      bool pass = false;
+      float c2v = 0.f;
+      int pos = 0, hid = 0;
+      if (q < total) {
+        int o = q - obase;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const int ra = W.rowa[r][owner];
+          const int len = W.rowb[r][owner] - ra;
+          if (o >= 0 && o < len) pos = ra + o;
+          o -= len;
+        }
+        const float2 h = __ldg(A.sorted_hits + pos);
+        const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
+        const float dphi = resid_angle(W.win[0][owner], W.win[1][owner], d.x, d.y);
+        const float r0 = W.win[3][owner] * dphi, r1 = h.y - W.win[2][owner];
+        c2v = r0 * (W.win[4][owner] * r0 + W.win[5][owner] * r1) + r1 * (W.win[5][owner] * r0 + W.win[6][owner] * r1);
+        pass = c2v < cut;
+        if (pass) hid = __ldg(A.sorted_ids + pos);
+      }
+      const unsigned m = __ballot_sync(kFull, pass);
+      if (pass) {
+        const int k = np + __popc(m & ((1u << lane) - 1u));
+        W.pl_c2[k] = c2v;
+        W.pl_id[k] = hid;
+        W.pl_pos[k] = pos;
+        W.pl_own[k] = owner;
+      }
+      np += __popc(m);
+      if (np > kPList - 32) {
+        __syncwarp();
+        for (int k = 0; k < np; ++k)
+          if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, cap, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+        np = 0;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    for (int k = 0; k < np; ++k)
+      if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, cap, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+    // Windows wider than kRows phi bins: the owner scans them alone.
+    if (wide) {
+      const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
+      const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
+      const float w0 = W.win[0][lane], w1 = W.win[1][lane], w2 = W.win[2][lane], w3 = W.win[3][lane];
+      const float i00 = W.win[4][lane], i01 = W.win[5][lane], i11 = W.win[6][lane];
+      for (int r = 0; r < npb; ++r) {
+        int pb = pb0 + r;
+        if (pb >= nphi) pb -= nphi;
+        const int a = __ldg(off + pb * n2 + zb0), b = __ldg(off + pb * n2 + zb1 + 1);
+        for (int pos = a; pos < b; ++pos) {
+          const float2 h = __ldg(A.sorted_hits + pos);
+          const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
+          const float dphi = resid_angle(w0, w1, d.x, d.y);
+          const float r0 = w3 * dphi, r1 = h.y - w2;
+          const float c2v = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
+          if (c2v < cut) hl_insert(W, lane, hl_n, cap, c2v, __ldg(A.sorted_ids + pos), pos);
+        }
+      }
+    }
+    // Outcome of each propagated candidate; keep the prediction for its children.
+    if (kind == 1) {
+      kind = hl_n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
+      if (kind != 2) {
+        c.surf = si;
+        store_cand(W, lane, c);
+      }
+    }
+    __syncwarp();
+
+    // ---- 3. selection of the k_max best children of each seed -----------------------------
+    // Each lane offers the head of its list; a butterfly over the group's lanes (partners outside
+    // the group read themselves) leaves the group minimum in the group's first lane, which then
+    // broadcasts it. Lane j of the group keeps the j-th winner; the winner's lane pops its head.
+    int head = 0;
+    int w_par = 0, w_kind = 3, w_id = -1, w_pos = 0, w_nh = 0;
+    float w_c2 = 0.f;
+    for (int w = 0; w < cap; ++w) {
+      unsigned long long key = ~0ull;
+      int hk = 0x7fffffff, kpos = 0;
+      if (on && kind != 3) {
+        if (kind == 0) {
+          if (head < hl_n) {
+            key = pack_key(c.nh + 1, c.chi2 + W.hl_c2[head][lane], slot << 2);
+            hk = W.hl_id[head][lane];
+            kpos = W.hl_pos[head][lane];
+          }
+        } else if (head == 0) {
+          key = pack_key(c.nh, c.chi2, (slot << 2) | kind);
+          hk = -1;
+        }
+      }
+      if (!__any_sync(kFull, key != ~0ull)) break;
+      unsigned long long mk = key;
+      int mh = hk;
+#pragma unroll
+      for (int off = 1; off < KC; off <<= 1) {
+        const int partner = slot ^ off;
+        const int src = (in_grp && partner < KC) ? gbase + partner : lane;
+        const unsigned long long ok = __shfl_sync(kFull, mk, src);
+        const int oh = __shfl_sync(kFull, mh, src);
+        if (ok < mk || (ok == mk && oh < mh)) {
+          mk = ok;
+          mh = oh;
+        }
+      }
+      mk = __shfl_sync(kFull, mk, gbase);
+      mh = __shfl_sync(kFull, mh, gbase);
+      const int pk = static_cast<int>((mk >> 20) & 63ull);
+      const int wslot = pk >> 2;
+      const int wpos = __shfl_sync(kFull, kpos, in_grp ? gbase + wslot : lane);
+      if (on && mk != ~0ull) {
+        if (slot == w) {
+          w_par = wslot;
+          w_kind = pk & 3;
+          w_id = mh;
+          w_pos = wpos;
+          w_nh = 63 - static_cast<int>(mk >> 58);
+          w_c2 = __uint_as_float(static_cast<unsigned>((mk >> 26) & 0xffffffffull));
+        }
+        if (wslot == slot) ++head;
+      }
+    }
+
+    // ---- materialise: lane j takes the j-th winner ----------------------------------------
+    Cand nc;
+    const bool won = on && w_kind != 3;
+    if (won) {
+      load_cand(W, gbase + w_par, nc);
+      if (w_kind == 0) {
+        const float2 h = __ldg(A.sorted_hits + w_pos);
+        const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + w_pos);
+        update_with(G, nc.surf, nc, h, d);
+        nc.chi2 = w_c2;
+        nc.nh = w_nh;
+      } else if (w_kind == 1) {
+        nc.nm += 1;
+      } else {
+        nc.stopped = 1;
+      }
+    }
+    __syncwarp();
+    if (won) {
+      store_cand(W, lane, nc);
+      trace[step * 32 + lane] = (w_par << kHitBits) | (w_kind == 0 ? w_id + 1 : 0);
+    }
+    if (on) valid = won;
+    __syncwarp();
+
+    // ---- 4. finished seeds write their best track -----------------------------------------
+    if (on) ++step;
+    const unsigned live = __ballot_sync(kFull, on && won && !nc.stopped);
+    const bool done = on && (((live & gmask) == 0u) || step >= max_steps);
+    if (done && slot == 0) {
+      Cand b;
+      load_cand(W, gbase, b);
+      int sl = 0;
+      for (int st = step - 1; st >= 0; --st) {
+        const int e = trace[st * 32 + gbase + sl];
+        A.hits_out[static_cast<size_t>(3 + st) * n + seed] = (e & ((1 << kHitBits) - 1)) - 1;
+        sl = e >> kHitBits;
+      }
+      for (int k = 3 + step; k < A.lmax; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        A.hits_out[static_cast<size_t>(k) * n + seed] = A.seed_hits[static_cast<size_t>(k) * n + seed];
+      A.nhits_out[seed] = b.nh;
+      A.chi2_out[seed] = b.chi2;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = b.p[i];
+#pragma unroll
+      for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = b.C[i];
+      A.status_out[seed] = 0;
+    }
+    __syncwarp();
+    if (done) {
+      seed = -1;
+      valid = false;
+    }
   }
 }
 
 template __global__ void k_find_tracks<1>(DevGeom, FindArgs);
 template __global__ void k_find_tracks<2>(DevGeom, FindArgs);
 template __global__ void k_find_tracks<4>(DevGeom, FindArgs);
+template __global__ void k_find_tracks<6>(DevGeom, FindArgs);
 template __global__ void k_find_tracks<8>(DevGeom, FindArgs);
 template __global__ void k_find_tracks<16>(DevGeom, FindArgs);
 
-}  // namespace kfgb
+// ------------------------------------------------------------------------------------------------
 
-namespace kfgb {
+template <int KC>
+static int kc_occupancy(int block, size_t smem, int* bps) {
+  static int attr_set[16] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_CUDA;
+  if (static_cast<int>(smem) > attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_find_tracks<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return KF_ERR_CUDA;
+    attr_set[dev] = static_cast<int>(smem);
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC>, block, smem) != cudaSuccess) return KF_ERR_CUDA;
+  return KF_OK;
+}
+
+static int pick_kc(int k_max, int kc_hint) {
+  static const int caps[] = {1, 2, 4, 6, 8, 16};
+  for (int c : caps)
+    if (c >= k_max && c >= kc_hint) return c;
+  return -1;
+}
 
 int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   if (!p || n_seeds < 0 || sms <= 0) return KF_ERR_ARG;
-  if (p->k_max < 1 || p->k_max > KF_MAX_K || p->max_miss < 0 || p->lmax < 3 || p->lmax > KF_MAX_LMAX) return KF_ERR_ARG;
+  if (p->k_max < 1 || p->k_max > KF_MAX_K || p->max_miss < 0 || p->lmax < 4 || p->lmax > KF_MAX_LMAX) return KF_ERR_ARG;
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
-  const int block = p->block_threads == 0 ? 128 : p->block_threads;
-  if (block < 32 || block > 128 || block % 32) return KF_ERR_ARG;
-  int kc = 1;
-  while (kc < p->k_max) kc *= 2;
-  int bps = p->blocks_per_sm;
-  if (bps < 0) return KF_ERR_ARG;
-  // Occupancy per (device, capacity, block size), queried once so later calls (for instance
-  // inside a stream capture) only launch.
-  static int occ_cache[16][5][5] = {};
+  const int block = p->block_threads == 0 ? 256 : p->block_threads;
+  if (block < 32 || block > 256 || block % 32) return KF_ERR_ARG;
+  if (p->blocks_per_sm < 0) return KF_ERR_ARG;
+  const int kc = pick_kc(p->k_max, 0);
+  if (kc < 0) return KF_ERR_ARG;
+  size_t wb = 0;
+  switch (kc) {
+    case 1: wb = warp_smem_bytes<1>(p->lmax); break;
+    case 2: wb = warp_smem_bytes<2>(p->lmax); break;
+    case 4: wb = warp_smem_bytes<4>(p->lmax); break;
+    case 6: wb = warp_smem_bytes<6>(p->lmax); break;
+    case 8: wb = warp_smem_bytes<8>(p->lmax); break;
+    default: wb = warp_smem_bytes<16>(p->lmax); break;
+  }
+  const size_t smem = wb * (block / 32);
+  if (smem > 227 * 1024) return KF_ERR_CAPACITY;
+  // Occupancy per (device, capacity, block size, lmax), queried once so later calls (for
+  // instance inside a stream capture) only launch.
+  static int occ_cache[16][6][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
-  const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 8 ? 3 : 4;
+  const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
   const int bi = block / 32 - 1;
-  if (bps == 0 && occ_cache[dev][ki][bi] > 0) bps = occ_cache[dev][ki][bi];
-  if (bps == 0) {
-    cudaError_t e = cudaSuccess;
+  int bps = p->blocks_per_sm;
+  int occ = occ_cache[dev][ki][bi][p->lmax];
+  if (occ == 0) {
+    int rc = KF_OK;
     switch (kc) {
-      case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_find_tracks<1>, block, 0); break;
-      case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_find_tracks<2>, block, 0); break;
-      case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_find_tracks<4>, block, 0); break;
-      case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_find_tracks<8>, block, 0); break;
-      default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_find_tracks<16>, block, 0); break;
+      case 1: rc = kc_occupancy<1>(block, smem, &occ); break;
+      case 2: rc = kc_occupancy<2>(block, smem, &occ); break;
+      case 4: rc = kc_occupancy<4>(block, smem, &occ); break;
+      case 6: rc = kc_occupancy<6>(block, smem, &occ); break;
+      case 8: rc = kc_occupancy<8>(block, smem, &occ); break;
+      default: rc = kc_occupancy<16>(block, smem, &occ); break;
     }
-    if (e != cudaSuccess || bps < 1) bps = 1;
-    occ_cache[dev][ki][bi] = bps;
+    if (rc != KF_OK) return rc;
+    if (occ < 1) return KF_ERR_CAPACITY;
+    occ_cache[dev][ki][bi][p->lmax] = occ;
   }
-  const long long want = (static_cast<long long>(n_seeds) + block - 1) / block;
-  const int grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
+  if (bps == 0 || bps > occ) bps = occ;
+  const int warps = block / 32;
+  const long long groups_per_block = static_cast<long long>(warps) * (32 / kc);
+  const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
   plan->kc = kc;
   plan->block = block;
-  plan->grid = grid;
-  plan->nt = grid * block;
-  const size_t align = 256;
-  auto up = [&](size_t v) { return (v + align - 1) / align * align; };
-  plan->off_cand = align;
-  const size_t cand_bytes = 2ull * kc * kWords * plan->nt * sizeof(float);
-  plan->off_trace = up(plan->off_cand + cand_bytes);
-  const size_t trace_bytes = static_cast<size_t>(p->lmax) * kc * plan->nt * sizeof(int);
-  plan->ws_bytes = up(plan->off_trace + trace_bytes);
+  plan->grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
+  plan->smem = smem;
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  plan->off_state = 256;  // after the work counter
+  plan->off_surf = up(plan->off_state + static_cast<size_t>(kSeedWords) * n_seeds * sizeof(float));
+  plan->ws_bytes = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
   return KF_OK;
 }
 
 int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream) {
   char* base = static_cast<char*>(ws);
   A.counter = reinterpret_cast<int*>(base);
-  A.cand = reinterpret_cast<float*>(base + plan.off_cand);
-  A.trace = reinterpret_cast<int*>(base + plan.off_trace);
-  A.nt = plan.nt;
+  A.seed_state = reinterpret_cast<float*>(base + plan.off_state);
+  A.seed_surf = reinterpret_cast<int*>(base + plan.off_surf);
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
+  k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, A);
   switch (plan.kc) {
-    case 1: k_find_tracks<1><<<plan.grid, plan.block, 0, stream>>>(G, A); break;
-    case 2: k_find_tracks<2><<<plan.grid, plan.block, 0, stream>>>(G, A); break;
-    case 4: k_find_tracks<4><<<plan.grid, plan.block, 0, stream>>>(G, A); break;
-    case 8: k_find_tracks<8><<<plan.grid, plan.block, 0, stream>>>(G, A); break;
-    default: k_find_tracks<16><<<plan.grid, plan.block, 0, stream>>>(G, A); break;
+    case 1: k_find_tracks<1><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
+    case 2: k_find_tracks<2><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
+    case 4: k_find_tracks<4><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
+    case 6: k_find_tracks<6><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
+    case 8: k_find_tracks<8><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
+    default: k_find_tracks<16><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
   }
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;
 }

@@ -12,6 +12,7 @@ struct FindArgs {
   const int* bin_off;
   const float2* sorted_hits;
   const int* sorted_ids;
+  const float* sorted_dir;  // (cos phi, sin phi) per sorted hit
   const float2* hits;
   const int* hit_surface;
   const int* seed_hits;
@@ -26,16 +27,18 @@ struct FindArgs {
   float* state_out;
   float* cov_out;
   int* status_out;
-  int* counter;  // work counter, zeroed before each launch
-  float* cand;   // [2][KC][32][nt] candidate records, word-major
-  int* trace;    // [lmax][KC][nt] parent slot and hit per step
-  int nt;        // threads in the grid
+  // Workspace: the work counter (zeroed before each launch) and the fitted seed states.
+  int* counter;
+  float* seed_state;  // [28][n_seeds]: p[6], C[21], chi2 (< 0: failed seed)
+  int* seed_surf;     // [n_seeds]: surface of the third seed hit
 };
 
-// Template capacity kc (power of two >= k_max), persistent grid, workspace layout.
+// Candidate capacity kc (smallest compiled capacity >= k_max), persistent grid, shared memory,
+// workspace layout.
 struct FindPlan {
-  int kc, block, grid, nt;
-  size_t off_cand, off_trace, ws_bytes;
+  int kc, block, grid;
+  size_t smem;
+  size_t off_state, off_surf, ws_bytes;
 };
 
 int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan);

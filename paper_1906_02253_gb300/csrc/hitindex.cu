@@ -6,8 +6,10 @@
 // One CTA per slab, everything staged in shared memory: the bin of each hit (u16), the bin
 // histogram and its exclusive scan, then an unstable scatter of local hit numbers by shared
 // atomics, then a per-bin insertion sort that restores ascending id (bins hold a handful of
-// hits), then a coalesced gather-write of the sorted hits and ids. Global traffic per hit: one
-// 8-byte read (plus an L2 re-read in the gather) and a 12-byte write.
+// hits), then a coalesced gather-write of the sorted hits and ids and, when asked for, of each
+// hit's direction (cos phi, sin phi) so that the search computes residual angles without trig.
+// Global traffic per hit: one 8-byte read (plus an L2 re-read in the gather) and a 12-byte write
+// (20 bytes with directions).
 #include "kf_math.cuh"
 
 namespace kfgb {
@@ -16,7 +18,8 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
                                                          const int* __restrict__ slab_off, int n_slabs,
                                                          int cap, int* __restrict__ bin_off,
                                                          float2* __restrict__ sorted_hits,
-                                                         int* __restrict__ sorted_ids, int* __restrict__ d_status) {
+                                                         int* __restrict__ sorted_ids, float2* __restrict__ sorted_dir,
+                                                         int* __restrict__ d_status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = G.n_bins;
   int* hist = reinterpret_cast<int*>(smem_raw);                       // [nb + 1]
@@ -103,8 +106,14 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
     __syncthreads();
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
       const int i = order[p];
-      sorted_hits[h0 + p] = hits[h0 + i];
+      const float2 h = hits[h0 + i];
+      sorted_hits[h0 + p] = h;
       sorted_ids[h0 + p] = h0 + i;
+      if (sorted_dir) {
+        float s, c;
+        sincosf(h.x, &s, &c);
+        sorted_dir[h0 + p] = make_float2(c, s);
+      }
     }
     __syncthreads();
   }

@@ -46,13 +46,18 @@ __device__ __forceinline__ float wrap_pi(float a) {
 
 // sin(D/2), cos(D/2) and q = sin(D/2)/(D/2); then f1 = sin(D)/D = q cos(D/2) and
 // f2 = (1 - cos D)/D = q sin(D/2).
+// Below |D/2| = 0.1 (every step of a track above ~0.1 GeV over a few cm) the Taylor series are
+// exact to FP32 (next terms < 3e-11 relative) and cost a few FMAs instead of a range-reduced
+// sincos.
 __device__ __forceinline__ void half_angle(float D, float& q, float& sh, float& ch) {
   const float h = 0.5f * D;
-  sincosf(h, &sh, &ch);
-  if (fabsf(h) < 0.05f) {
+  if (fabsf(h) < 0.1f) {
     const float h2 = h * h;
-    q = 1.f - h2 * (1.f / 6.f) + h2 * h2 * (1.f / 120.f);
+    q = 1.f + h2 * (-1.f / 6.f + h2 * (1.f / 120.f + h2 * (-1.f / 5040.f)));
+    sh = h * q;
+    ch = 1.f + h2 * (-0.5f + h2 * (1.f / 24.f + h2 * (-1.f / 720.f)));
   } else {
+    sincosf(h, &sh, &ch);
     q = sh / h;
   }
 }
@@ -114,12 +119,15 @@ __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float 
   return true;
 }
 
+// Path to the plane z = Z; reached only within half a turn in the transverse plane
+// (|omega s| < pi): beyond that the particle would be coming back inward.
 __device__ __forceinline__ bool path_to_disk(const float* p, float w, float Z, Prop& pr) {
   float st, ct;
   sincosf(p[5], &st, &ct);
   if (ct == 0.f) return false;
   pr.s = (Z - p[2]) * st / ct;
   if (!(pr.s > 0.f)) return false;
+  if (!(fabsf(w * pr.s) < kPiF)) return false;
   sincosf(p[4], &pr.s0, &pr.c0);
   prop_eval(pr, w);
   return true;
@@ -311,9 +319,10 @@ __device__ __forceinline__ void innovation(const DevGeom& G, const float* C, con
   in.s11 = m.h1[0] * in.ch1[0] + m.h1[1] * in.ch1[1] + m.h1[2] * in.ch1[2] + G.sigma_2nd * G.sigma_2nd;
 }
 
-__device__ __forceinline__ float chi2_of(const Innov& in, float r0, float r1) {
+// True when S is a covariance (positive definite); otherwise no hit can be compatible.
+__device__ __forceinline__ bool innovation_ok(const Innov& in) {
   const float det = in.s00 * in.s11 - in.s01 * in.s01;
-  return (in.s11 * r0 * r0 - 2.f * in.s01 * r0 * r1 + in.s00 * r1 * r1) / det;
+  return det > 0.f && in.s00 > 0.f;
 }
 
 // Kalman update: K = C H^T S^-1, p += K r, C -= K (H C). Returns the predicted chi2.

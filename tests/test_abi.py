@@ -51,7 +51,7 @@ def test_host_side_argument_checks(kf):
     # bad geometry: n_surf = 0
     bad = kf.KfGeometry(3.8, 0, None, 0.01, 0.1, (ctypes.c_float * 5)(*wl.prior))
     assert lib.kf_index_bins(ctypes.byref(bad)) == kf.KF_ERR_ARG
-    idx = kf.KfHitIndex(1, g.n_bins, None, None, None)
+    idx = kf.KfHitIndex(1, g.n_bins, None, None, None, None)
     rc = lib.kf_build_hit_index(ctypes.byref(bad), None, None, 1, 10, ctypes.byref(idx), None, None)
     assert rc == kf.KF_ERR_ARG
     # slab above the compiled capacity: rejected before any launch

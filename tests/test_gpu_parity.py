@@ -53,6 +53,10 @@ def test_hit_index_bit_exact(kf, wl_name, n_ev, nt):
     assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
     assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
     assert np.array_equal(idx.sorted_hits.cpu().numpy().view(np.uint32), sh.view(np.uint32))
+    # hit directions: (cos phi, sin phi) of the sorted hits, to FP32 accuracy
+    d = idx.sorted_dir.cpu().numpy().astype(np.float64)
+    ph = sh[:, 0].astype(np.float64)
+    assert np.abs(d[:, 0] - np.cos(ph)).max() < 3e-7 and np.abs(d[:, 1] - np.sin(ph)).max() < 3e-7
 
 
 def test_hit_index_edge_cases(kf):

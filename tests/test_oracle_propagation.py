@@ -155,3 +155,21 @@ def test_helix_invariants():
         assert abs(_wrap(p[4] - p0[4] - w * s)) < 1e-12
         assert abs(p[2] - p0[2] - s / np.tan(p0[5])) < 1e-9
         assert s > 0
+
+
+def test_next_surface_rule_follows_generator_paths():
+    """Without scattering, the finder's next-surface rule (next barrel layer outward vs next disk in
+    the direction of motion, nearer accepted one, at most half a turn) reproduces the surface
+    sequence the generator finds by searching every surface, and ends where the generator ends."""
+    wl = synth.workload("hi_occ", n_events=1, tracks_lo=600, tracks_hi=600, ms_on=False)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl, smear=False, record_truth=True)
+    n_checked = 0
+    for t in range(b.n_tracks):
+        nh = b.track_nhits[t]
+        for k in range(nh):
+            nxt, _ = oracle.next_surface(g, b.truth_in[t, k])
+            want = b.track_surf[t, k + 1] if k + 1 < nh else -1
+            assert nxt == want, (t, k, nxt, want)
+            n_checked += 1
+    assert n_checked > 5000
