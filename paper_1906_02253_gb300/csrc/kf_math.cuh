@@ -87,19 +87,28 @@ __device__ __forceinline__ void prop_eval(Prop& pr, float w) {
   pr.f2 = pr.q * pr.sh;
 }
 
-// Smallest s > 0 reaching radius R from state p, by Newton steps from the straight-line
-// estimate on g(s) = (rho0^2 - R^2) + 2 p0.dp(s) + |dp(s)|^2.
+// Smallest s > 0 reaching radius R from state p, by Newton steps on
+// g(s) = (rho0^2 - R^2) + 2 p0.dp(s) + |dp(s)|^2, started from the root of its second-order
+// expansion dp = s t0 + (omega s^2 / 2) n0: (1 + omega B) s^2 + 2 A s + (rho0^2 - R^2) = 0 with
+// A = p0.t0, B = p0.n0 (t0, n0 the unit direction and its left normal).
 __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float R, Prop& pr) {
   sincosf(p[4], &pr.s0, &pr.c0);
   const float x0 = p[0], y0 = p[1];
   const float rho0 = sqrtf(x0 * x0 + y0 * y0);
   const float d0 = (rho0 - R) * (rho0 + R);
   const float A = x0 * pr.c0 + y0 * pr.s0;
-  const float disc = A * A - d0;
-  if (!(disc >= 0.f)) return false;
-  const float den = A + sqrtf(disc);
-  if (!(den > 0.f)) return false;
-  pr.s = -d0 / den;
+  const float B = y0 * pr.c0 - x0 * pr.s0;
+  const float disc2 = A * A - (1.f + w * B) * d0;
+  const float den2 = disc2 >= 0.f ? A + sqrtf(disc2) : -1.f;
+  if (den2 > 0.f) {
+    pr.s = -d0 / den2;  // near root of the second-order expansion (also when 1 + omega B <= 0)
+  } else {
+    const float disc = A * A - d0;  // straight line
+    if (!(disc >= 0.f)) return false;
+    const float den = A + sqrtf(disc);
+    if (!(den > 0.f)) return false;
+    pr.s = -d0 / den;
+  }
   if (!(pr.s > 0.f)) return false;
   for (int it = 0; it < 12; ++it) {
     prop_eval(pr, w);
