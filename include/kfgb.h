@@ -159,6 +159,29 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
                    int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
                    int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
 
+/* Allocation-free track finding. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory while they reconstruct events, for example an
+ * online trigger process that reserves all of its GPU memory at start-up and forbids any
+ * allocation during event processing (to keep latency bounded and memory unfragmented), or a
+ * plug-in running inside a host framework that owns the device memory pool. Such callers cannot
+ * provide the workspace kf_find_tracks takes.
+ *
+ * Same arguments and results as kf_find_tracks, without workspace. The scratch (work counter and
+ * seed states) is a fixed array inside the library of KF_STATIC_SCRATCH_BYTES (about 7.3 MiB),
+ * held on every GPU that loads the library until the process exits. At most KF_STATIC_MAX_SEEDS
+ * seeds per call: more returns KF_ERR_CAPACITY and launches nothing (split the seeds into
+ * chunks). The call allocates nothing and calls no allocating routine.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture. Every call uses the same
+ * array and leaves its contents behind: calls whose kernels can overlap on the GPU (several
+ * streams, several host threads) race and corrupt each other's results, so serialise them. */
+#define KF_STATIC_MAX_SEEDS 65536
+#define KF_STATIC_SCRATCH_BYTES 7602432
+int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const float* hits,
+                          const int* hit_surface, const int* seed_hits, const int* seed_event, int n_seeds,
+                          const KfFindParams* params, int* hits_out, int* nhits_out, float* chi2_out,
+                          float* state_out, float* cov_out, int* status_out, kf_stream_t stream);
+
 /* Human-readable name of a status code. */
 const char* kf_status_string(int status);
 

@@ -197,6 +197,54 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   return launch_find(G, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// Allocation-free finding: the library's fixed scratch array replaces the caller's workspace.
+int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const float* hits,
+                          const int* hit_surface, const int* seed_hits, const int* seed_event, int n_seeds,
+                          const KfFindParams* params, int* hits_out, int* nhits_out, float* chi2_out,
+                          float* state_out, float* cov_out, int* status_out, kf_stream_t stream) {
+  DevGeom G;
+  int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
+  if (n_seeds > KF_STATIC_MAX_SEEDS) return KF_ERR_CAPACITY;
+  FindPlan plan;
+  rc = plan_find(n_seeds, params, sm_count(), &plan);
+  if (rc != KF_OK) return rc;
+  if (plan.ws_bytes > KF_STATIC_SCRATCH_BYTES) return KF_ERR_CAPACITY;
+  if (n_seeds == 0) return KF_OK;
+  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
+      !index->sorted_dir)
+    return KF_ERR_ARG;
+  if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
+      !cov_out || !status_out)
+    return KF_ERR_ARG;
+  void* scratch = nullptr;
+  rc = static_scratch(&scratch);
+  if (rc != KF_OK) return rc;
+  FindArgs A;
+  A.bin_off = index->bin_off;
+  A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
+  A.sorted_ids = index->sorted_ids;
+  A.sorted_dir = index->sorted_dir;
+  A.hits = reinterpret_cast<const float2*>(hits);
+  A.hit_surface = hit_surface;
+  A.seed_hits = seed_hits;
+  A.seed_event = seed_event;
+  A.n_seeds = n_seeds;
+  A.n_events = index->n_events;
+  A.chi2_cut = params->chi2_cut;
+  A.k_max = params->k_max;
+  A.max_miss = params->max_miss;
+  A.lmax = params->lmax;
+  A.hits_out = hits_out;
+  A.nhits_out = nhits_out;
+  A.chi2_out = chi2_out;
+  A.state_out = state_out;
+  A.cov_out = cov_out;
+  A.status_out = status_out;
+  return launch_find(G, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
+}
+
 const char* kf_status_string(int status) {
   switch (status) {
     case KF_OK: return "ok";

@@ -694,6 +694,33 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   return KF_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Scratch of the allocation-free entry point (kf_find_tracks_static): the work counter and the
+// seed states for at most KF_STATIC_MAX_SEEDS seeds, laid out as plan_find lays out a caller's
+// workspace. A fixed array in the library: every GPU that loads the library holds it until the
+// process exits. In host code g_find_scratch only names the array; its device address comes from
+// cudaGetSymbolAddress, looked up once per device.
+constexpr size_t static_scratch_bytes() {
+  return ((256 + static_cast<size_t>(kSeedWords) * KF_STATIC_MAX_SEEDS * sizeof(float) + 255) / 256 * 256 +
+          static_cast<size_t>(KF_STATIC_MAX_SEEDS) * sizeof(int) + 255) /
+         256 * 256;
+}
+static_assert(static_scratch_bytes() == KF_STATIC_SCRATCH_BYTES, "header and library disagree on the scratch size");
+static __device__ __align__(256) unsigned char g_find_scratch[static_scratch_bytes()];
+
+int static_scratch(void** ptr) {
+  static void* addr[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KF_ERR_CUDA;
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_find_scratch) != cudaSuccess || p == nullptr) return KF_ERR_CUDA;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return KF_OK;
+}
+
 int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream) {
   char* base = static_cast<char*>(ws);
   A.counter = reinterpret_cast<int*>(base);
