@@ -40,9 +40,9 @@ WORKLOAD = "fit_batched"
 #   chi2 of one hit in a search window ...................................... 20
 #   seed from three hits ..................................................... 80
 FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
-# Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z), write 8 B sorted + 4 B id) plus
+# Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 8 B direction) plus
 # the bin offsets written per (event, surface).
-INDEX_BYTES_PER_HIT = 20
+INDEX_BYTES_PER_HIT = 28
 
 
 def _dist():
