@@ -86,7 +86,19 @@ def _load():
             lib.or_next_surface.restype = ctypes.c_int
             lib.or_next_surface.argtypes = [G, _P, _P]
             lib.or_find.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_longlong, ctypes.c_int,
-                                    ctypes.POINTER(OrFindParams), ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
+                                    ctypes.POINTER(OrFindParams), ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                    _P, _P, _P, ctypes.c_int]
+            lib.or_mlp_nparams.restype = ctypes.c_int
+            lib.or_find_pairs.restype = ctypes.c_longlong
+            lib.or_find_pairs.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_longlong,
+                                          ctypes.c_int, ctypes.POINTER(OrFindParams), ctypes.c_int,
+                                          ctypes.c_longlong, _P, _P]
+            lib.or_mlp_forward.argtypes = [_P, _P, ctypes.c_longlong, _P]
+            lib.or_pair_features.argtypes = [G, ctypes.c_int, _P, _P, ctypes.c_float, ctypes.c_float, _P]
+            lib.or_mlp_loss_grad.restype = ctypes.c_double
+            lib.or_mlp_loss_grad.argtypes = [_P, _P, _P, ctypes.c_longlong, _P]
+            lib.or_adam.argtypes = [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -224,8 +236,9 @@ def next_surface(geom: Geometry, p):
 
 
 def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=None, max_miss=None,
-         brute_force: bool = False, n_threads: int = 0):
-    """Combinatorial finding from seeds. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
+         brute_force: bool = False, n_threads: int = 0, mlp=None, top_n: int = 0):
+    """Combinatorial finding from seeds; with ``mlp`` = (weights, mean, sd) and top_n > 0 the
+    learned proposal keeps the top_n passing hits by score. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
     evaluated in a window)."""
     lib = _load()
@@ -245,9 +258,79 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     lib.or_find(geom.ref, hits.ctypes.data, hs.ctypes.data, so.ctypes.data, batch.n_events, sh.ctypes.data,
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,
-                out["status"].ctypes.data, counters.ctypes.data)
+                out["status"].ctypes.data, counters.ctypes.data, *_mlp_ptrs(mlp), int(top_n))
     out["counters"] = counters
     return out
+
+
+MLP_NPARAMS = 14 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def _mlp_ptrs(mlp):
+    if mlp is None:
+        return None, None, None
+    w, mean, sd = (np.ascontiguousarray(a, np.float64) for a in mlp)
+    _mlp_ptrs.keep = (w, mean, sd)  # alive for the duration of the call
+    return w.ctypes.data, mean.ctypes.data, sd.ctypes.data
+
+
+def find_pairs(geom: Geometry, batch, seed_hits, seed_event, seed_track, *, cap: int = 10_000_000,
+               n_threads: int = 0):
+    """Training pairs of the learned proposal: every passing (candidate, hit) pair of the plain
+    finding from these seeds. Returns (features [n,14] float32, labels [n] float32)."""
+    lib = _load()
+    wl = geom.wl
+    prm = OrFindParams(wl.chi2_cut, wl.k_max, wl.max_miss, 0)
+    sh = _c(seed_hits, np.int32)
+    se = _c(seed_event, np.int32)
+    stk = _c(seed_track, np.int32)
+    feats = np.empty((cap, 14), np.float32)
+    labels = np.empty(cap, np.float32)
+    n = lib.or_find_pairs(geom.ref, _c(batch.hits, np.float32).ctypes.data, _c(batch.hit_surface, np.int32).ctypes.data,
+                          _c(batch.slab_offsets, np.int64).ctypes.data, batch.n_events, sh.ctypes.data, se.ctypes.data,
+                          stk.ctypes.data, _c(batch.hit_sim, np.int32).ctypes.data, sh.shape[0], wl.lmax,
+                          ctypes.byref(prm), n_threads, cap, feats.ctypes.data, labels.ctypes.data)
+    n = min(n, cap)
+    return feats[:n].copy(), labels[:n].copy()
+
+
+def pair_features(geom: Geometry, surf: int, p, C, hit):
+    """The learned proposal's 14 features of a predicted state (p, C) and a hit (phi, v)."""
+    lib = _load()
+    p = _c(p, np.float64)
+    C = _c(C, np.float64)
+    f = np.empty(14)
+    lib.or_pair_features(geom.ref, int(surf), p.ctypes.data, C.ctypes.data, float(hit[0]), float(hit[1]), f.ctypes.data)
+    return f
+
+
+def mlp_forward(w, xs):
+    """Logits of the MLP for standardised features xs [n,14] (FP64)."""
+    lib = _load()
+    w = _c(w, np.float64)
+    xs = _c(xs, np.float64)
+    out = np.empty(xs.shape[0])
+    lib.or_mlp_forward(w.ctypes.data, xs.ctypes.data, xs.shape[0], out.ctypes.data)
+    return out
+
+
+def mlp_loss_grad(w, xs, y):
+    """Mean BCE-with-logits loss over the batch and its gradient (FP64)."""
+    lib = _load()
+    w = _c(w, np.float64)
+    xs = _c(xs, np.float64)
+    y = _c(y, np.float64)
+    g = np.empty(MLP_NPARAMS)
+    loss = lib.or_mlp_loss_grad(w.ctypes.data, xs.ctypes.data, y.ctypes.data, xs.shape[0], g.ctypes.data)
+    return loss, g
+
+
+def adam(w, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in place on (w, m, v) (FP64 arrays)."""
+    lib = _load()
+    for a in (w, grad, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib.or_adam(w.ctypes.data, grad.ctypes.data, m.ctypes.data, v.ctypes.data, int(t), lr, b1, b2, eps)
 
 
 def unpack_cov(c21):

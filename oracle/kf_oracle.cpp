@@ -608,6 +608,94 @@ struct Found {
   double chi2;
 };
 
+// ---- learned hit proposal: MLP 14 -> 64 -> 64 -> 1 (ReLU), FP64 -------------------------------
+// Weight layout (shared with the CUDA path as data only): W1[64][14], b1[64], W2[64][64], b2[64],
+// W3[64], b3; features are standardised by (x - mean) / sd before the first layer.
+constexpr int kIn = 14, kHid = 64;
+constexpr int kW1 = 0, kB1 = kW1 + kHid * kIn, kW2 = kB1 + kHid, kB2 = kW2 + kHid * kHid, kW3 = kB2 + kHid,
+              kB3 = kW3 + kHid, kNParam = kB3 + 1;
+
+struct Mlp {
+  const double* w = nullptr;   // kNParam weights
+  const double* mean = nullptr;
+  const double* sd = nullptr;
+  int top_n = 0;               // 0: plain finding
+};
+
+double mlp_forward(const double* w, const double* xs, double* h1 = nullptr, double* h2 = nullptr) {
+  double a1[kHid], a2[kHid];
+  for (int j = 0; j < kHid; ++j) {
+    double z = w[kB1 + j];
+    for (int i = 0; i < kIn; ++i) z += w[kW1 + j * kIn + i] * xs[i];
+    a1[j] = z > 0.0 ? z : 0.0;
+  }
+  for (int j = 0; j < kHid; ++j) {
+    double z = w[kB2 + j];
+    for (int i = 0; i < kHid; ++i) z += w[kW2 + j * kHid + i] * a1[i];
+    a2[j] = z > 0.0 ? z : 0.0;
+  }
+  double out = w[kB3];
+  for (int j = 0; j < kHid; ++j) out += w[kW3 + j] * a2[j];
+  if (h1) std::memcpy(h1, a1, sizeof(a1));
+  if (h2) std::memcpy(h2, a2, sizeof(a2));
+  return out;
+}
+
+// Binary cross-entropy with logits of one sample; adds its gradient (scaled by `scale`) to g.
+double mlp_loss_grad(const double* w, const double* xs, double y, double scale, double* g) {
+  double h1[kHid], h2[kHid];
+  const double z = mlp_forward(w, xs, h1, h2);
+  const double loss = std::max(z, 0.0) - z * y + std::log1p(std::exp(-std::fabs(z)));
+  const double dz = (1.0 / (1.0 + std::exp(-z)) - y) * scale;
+  g[kB3] += dz;
+  double d2[kHid];
+  for (int j = 0; j < kHid; ++j) {
+    g[kW3 + j] += dz * h2[j];
+    d2[j] = h2[j] > 0.0 ? dz * w[kW3 + j] : 0.0;
+  }
+  double d1[kHid];
+  for (int i = 0; i < kHid; ++i) d1[i] = 0.0;
+  for (int j = 0; j < kHid; ++j) {
+    g[kB2 + j] += d2[j];
+    for (int i = 0; i < kHid; ++i) {
+      g[kW2 + j * kHid + i] += d2[j] * h1[i];
+      d1[i] += d2[j] * w[kW2 + j * kHid + i];
+    }
+  }
+  for (int j = 0; j < kHid; ++j) {
+    const double dj = h1[j] > 0.0 ? d1[j] : 0.0;
+    g[kB1 + j] += dj;
+    for (int i = 0; i < kIn; ++i) g[kW1 + j * kIn + i] += dj * xs[i];
+  }
+  return loss;
+}
+
+// Features of a (predicted candidate, hit) pair: the predicted state, log of the covariance
+// diagonal, and the two residuals over the square roots of the innovation variances.
+void pair_features(const OrGeom& g, int si, const State& pred, float hphi, float h2, double* f) {
+  Meas m;
+  measure(g, si, pred.p, hphi, h2, m);
+  double Sm[2][2];
+  chi2_of(m, pred.C, Sm);
+  for (int i = 0; i < 6; ++i) f[i] = pred.p[i];
+  for (int i = 0; i < 6; ++i) f[6 + i] = std::log(pred.C[i][i] + 1e-12);
+  f[12] = m.r[0] / std::sqrt(Sm[0][0]);
+  f[13] = m.r[1] / std::sqrt(Sm[1][1]);
+}
+
+double mlp_score(const Mlp& mlp, const double* f) {
+  double xs[kIn];
+  for (int i = 0; i < kIn; ++i) xs[i] = (f[i] - mlp.mean[i]) / mlp.sd[i];
+  return mlp_forward(mlp.w, xs);
+}
+
+struct PairSink {
+  const int* hit_sim = nullptr;
+  int seed_track = -1;
+  std::vector<float> features;  // [n][14]
+  std::vector<float> labels;
+};
+
 struct Ctx {
   const OrGeom* g;
   const float* hits;
@@ -615,6 +703,7 @@ struct Ctx {
   const long long* slab_off;
   const Index* ix;
   OrFindParams prm;
+  Mlp mlp;
 };
 
 // All hits of surface si in event ev whose chi2 against the predicted state is below the cut.
@@ -695,7 +784,8 @@ struct Counters {
 };
 
 // Beam search for one seed. Returns false if the seed could not be formed.
-bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, Counters& cnt) {
+bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, Counters& cnt,
+              PairSink* sink = nullptr) {
   const OrGeom& g = *cx.g;
   Cand c0;
   if (!seed_state(g, cx.hits, cx.hsurf, seed_ids, c0.st)) return false;
@@ -744,6 +834,31 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       pred_surf[ci] = si;
       search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan);
       cnt.n_chi2 += static_cast<long long>(found.size());
+      if (sink) {  // training pairs: every passing (candidate, hit) pair, labelled by truth
+        double f[kIn];
+        for (const Found& fd : found) {
+          pair_features(g, si, pred[ci], cx.hits[2 * fd.hit], cx.hits[2 * fd.hit + 1], f);
+          for (int i = 0; i < kIn; ++i) sink->features.push_back(static_cast<float>(f[i]));
+          sink->labels.push_back(sink->hit_sim[fd.hit] == sink->seed_track ? 1.f : 0.f);
+        }
+      }
+      if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > cx.mlp.top_n) {
+        // Learned proposal: keep the top_n passing hits by MLP score (ties: lower hit id).
+        std::vector<std::pair<double, int>> sc;
+        double f[kIn];
+        for (const Found& fd : found) {
+          pair_features(g, si, pred[ci], cx.hits[2 * fd.hit], cx.hits[2 * fd.hit + 1], f);
+          sc.push_back({mlp_score(cx.mlp, f), fd.hit});
+        }
+        std::sort(sc.begin(), sc.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+          return a.first != b.first ? a.first > b.first : a.second < b.second;
+        });
+        std::vector<Found> kept;
+        for (int k = 0; k < cx.mlp.top_n; ++k)
+          for (const Found& fd : found)
+            if (fd.hit == sc[k].second) kept.push_back(fd);
+        found.swap(kept);
+      }
       if (!found.empty()) {
         for (const Found& f : found) pool.push_back({ci, f.hit, 0, c.n_hits + 1, c.chi2 + f.chi2, f.chi2});
       } else if (c.n_miss < cx.prm.max_miss) {
@@ -951,17 +1066,19 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
   return next_surface(*g, st, s_out);
 }
 
-// Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. Outputs per
+// Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. With mlp_w set and
+// top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
+// that has more. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
 // status (0 ok, 1 seed failed). counters[4] += propagations, chi2 evaluations that passed the
 // cut, Kalman updates, hits whose chi2 was evaluated (window scans).
 void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
-             long long* counters) {
+             long long* counters, const double* mlp_w, const double* mlp_mean, const double* mlp_sd, int top_n) {
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
-  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm};
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}};
   std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;
@@ -983,6 +1100,70 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     counters[1] += c_chi2.load();
     counters[2] += c_upd.load();
     counters[3] += c_scan.load();
+  }
+}
+
+// ---- learned proposal: training pairs and the FP64 MLP ----------------------------------------
+int or_mlp_nparams() { return kNParam; }
+
+// Plain finding over the given seeds, returning every passing (candidate, hit) pair seen: features
+// [n][14] (float) and label 1 if the hit belongs to the seed's simulated track. Returns the number
+// of pairs (at most cap are written).
+long long or_find_pairs(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
+                        const int* seeds, const int* seed_event, const int* seed_track, const int* hit_sim, long long n,
+                        int lmax, const OrFindParams* prm, int n_threads, long long cap, float* features, float* labels) {
+  Index ix;
+  build_index(*g, hits, slab_off, n_events, ix);
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{}};
+  std::vector<PairSink> sinks(n);
+  parallel_for(n, n_threads, [&](long long i) {
+    sinks[i].hit_sim = hit_sim;
+    sinks[i].seed_track = seed_track[i];
+    Cand best;
+    Counters cnt;
+    find_one(cx, seeds + 3 * i, seed_event[i], lmax, best, cnt, &sinks[i]);
+  });
+  long long k = 0;
+  for (long long i = 0; i < n; ++i) {
+    const long long m = static_cast<long long>(sinks[i].labels.size());
+    for (long long j = 0; j < m && k < cap; ++j, ++k) {
+      std::memcpy(features + kIn * k, sinks[i].features.data() + kIn * j, sizeof(float) * kIn);
+      labels[k] = sinks[i].labels[j];
+    }
+  }
+  return k;
+}
+
+// Features of one (predicted state p[6], covariance C[36] row-major, hit) pair, as the learned
+// proposal sees them: p, log(C_ii + 1e-12), residuals over sqrt(S_ii).
+void or_pair_features(const OrGeom* g, int surf, const double* p, const double* C, float hphi, float h2, double* f) {
+  State st;
+  for (int i = 0; i < 6; ++i) st.p[i] = p[i];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) st.C[i][j] = C[6 * i + j];
+  pair_features(*g, surf, st, hphi, h2, f);
+}
+
+// MLP on standardised features xs[n][14]: logits[n].
+void or_mlp_forward(const double* w, const double* xs, long long n, double* logits) {
+  for (long long i = 0; i < n; ++i) logits[i] = mlp_forward(w, xs + kIn * i);
+}
+
+// Mean binary cross-entropy with logits over the batch and its gradient grad[kNParam].
+double or_mlp_loss_grad(const double* w, const double* xs, const double* y, long long n, double* grad) {
+  for (int i = 0; i < kNParam; ++i) grad[i] = 0.0;
+  double loss = 0.0;
+  for (long long i = 0; i < n; ++i) loss += mlp_loss_grad(w, xs + kIn * i, y[i], 1.0 / n, grad);
+  return loss / n;
+}
+
+// One Adam step (Kingma and Ba): m, v moments; step t >= 1.
+void or_adam(double* w, const double* grad, double* m, double* v, int t, double lr, double b1, double b2, double eps) {
+  const double c1 = 1.0 - std::pow(b1, t), c2 = 1.0 - std::pow(b2, t);
+  for (int i = 0; i < kNParam; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
+    w[i] -= lr * (m[i] / c1) / (std::sqrt(v[i] / c2) + eps);
   }
 }
 

@@ -300,3 +300,15 @@ def cross(surface_type: int, r_or_z: float, bz: float, q: int, pos, mom):
     if rc != 0:
         return None
     return po, mo, psi.value
+
+
+def mlp_init(seed: int, n_in: int = 14, n_hid: int = 64) -> np.ndarray:
+    """He-initialised weights of the learned hit-proposal MLP (n_in -> n_hid -> n_hid -> 1) as
+    one float32 vector: W1[n_hid][n_in], b1, W2[n_hid][n_hid], b2, W3[n_hid], b3. Weights are
+    N(0, 2 / fan_in), biases 0, drawn from numpy's PCG64 stream of ``seed``. These random numbers
+    are an input of training, drawn here so that every consumer gets the same ones."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, np.sqrt(2.0 / n_in), n_hid * n_in), np.zeros(n_hid),
+             rng.normal(0.0, np.sqrt(2.0 / n_hid), n_hid * n_hid), np.zeros(n_hid),
+             rng.normal(0.0, np.sqrt(2.0 / n_hid), n_hid), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

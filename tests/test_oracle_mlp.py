@@ -1,0 +1,119 @@
+"""Pins of the oracle's learned hit proposal (CPU only): backpropagation against central finite
+differences, training that lowers the loss, and the pruning wired into the beam search checked
+against a plain loop over the oracle's single-step primitives."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _pairs(n_events=2, stride=10, seed=4):
+    wl = synth.workload("learned", n_events=n_events, tracks_lo=1500, tracks_hi=3000, seed=seed)
+    b = synth.generate(wl)
+    g = oracle.Geometry(wl)
+    sh, st = b.seeds()
+    sel = np.arange(0, len(st), stride)
+    F, L = oracle.find_pairs(g, b, sh[sel], b.track_event[st][sel], st[sel])
+    return F.astype(np.float64), L.astype(np.float64)
+
+
+def test_backprop_matches_finite_differences():
+    F, L = _pairs()
+    mean, sd = F.mean(0), F.std(0)
+    xs = (F[:64] - mean) / sd
+    y = L[:64]
+    w = synth.mlp_init(7).astype(np.float64)
+    loss, g = oracle.mlp_loss_grad(w, xs, y)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([rng.choice(np.arange(0, 896), 20), rng.choice(np.arange(960, 5056), 40),
+                          rng.choice(np.arange(5120, 5184), 10), [895, 900, 5100, 5184]])
+    h = 1e-5
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (oracle.mlp_loss_grad(wp, xs, y)[0] - oracle.mlp_loss_grad(wm, xs, y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3), (i, fd, g[i])
+    # the logit of one sample by an explicit matrix chain
+    W1, b1 = w[:896].reshape(64, 14), w[896:960]
+    W2, b2 = w[960:5056].reshape(64, 64), w[5056:5120]
+    W3, b3 = w[5120:5184], w[5184]
+    z = W3 @ np.maximum(W2 @ np.maximum(W1 @ xs[3] + b1, 0) + b2, 0) + b3
+    assert abs(oracle.mlp_forward(w, xs[3:4])[0] - z) < 1e-12
+
+
+def test_adam_training_lowers_the_loss():
+    F, L = _pairs(n_events=3, stride=8)
+    mean, sd = F.mean(0), F.std(0)
+    xs = (F - mean) / sd
+    w = synth.mlp_init(11).astype(np.float64)
+    m, v = np.zeros_like(w), np.zeros_like(w)
+    rng = np.random.default_rng(1)
+    first = oracle.mlp_loss_grad(w, xs, L)[0]
+    for t in range(1, 201):
+        b = rng.choice(len(L), 256, replace=False)
+        _, g = oracle.mlp_loss_grad(w, xs[b], L[b])
+        oracle.adam(w, g, m, v, t)
+    last = oracle.mlp_loss_grad(w, xs, L)[0]
+    assert last < 0.75 * first, (first, last)
+    # the trained network ranks true continuations above other hits (area under the ROC curve:
+    # the fraction of (true, other) pairs it orders correctly; 0.5 is chance)
+    s = oracle.mlp_forward(w, xs)
+    pos, neg = np.sort(s[L == 1]), s[L == 0]
+    auc = np.searchsorted(pos, neg, side="right").sum() / (len(pos) * len(neg))
+    auc = 1.0 - auc
+    assert auc > 0.7, auc
+
+
+def _mlp_for(F):
+    return synth.mlp_init(3).astype(np.float64), F.mean(0), F.std(0) + 1e-9
+
+
+def test_learned_with_large_top_n_is_plain_finding():
+    wl = synth.workload("find", n_events=2, tracks_lo=400, tracks_hi=400, noise_frac=3.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    F, _ = oracle.find_pairs(g, b, sh, b.track_event[st], st)
+    plain = oracle.find(g, b, sh, b.track_event[st])
+    learned = oracle.find(g, b, sh, b.track_event[st], mlp=_mlp_for(F), top_n=1000)
+    assert np.array_equal(plain["hits"], learned["hits"])
+
+
+def test_learned_top1_matches_a_plain_loop():
+    """K = 1, top_n = 1: at every step the kept hit is the passing hit of highest score."""
+    import test_oracle_find as tf
+    wl = synth.workload("find", n_events=2, tracks_lo=40, tracks_hi=40, noise_frac=80.0, seed=41)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    f = oracle.find(g, b, sh, ev, k_max=1, mlp=mlp, top_n=1)
+    pruned = 0
+    for i in range(len(st)):
+        p, C, _ = tf._seed_fit(g, b, sh[i])
+        hits, n_miss = list(sh[i]), 0
+        while len(hits) < wl.lmax:
+            e = tf._expand(g, b, wl, ev[i], p, C)
+            if e is None:
+                break
+            surf, pp, CC, ids, c2 = e
+            if len(ids) > 1:
+                feats = np.array([oracle.pair_features(g, surf, pp, CC, b.hits[h]) for h in ids])
+                sc = oracle.mlp_forward(mlp[0], (feats - mlp[1]) / mlp[2])
+                order = sorted(range(len(ids)), key=lambda k: (-sc[k], ids[k]))
+                ids, c2 = ids[order[:1]], c2[order[:1]]
+                pruned += 1
+            if len(ids):
+                p, C, _ = oracle.update(g, pp, CC, surf, b.hits[ids[0]])
+                hits.append(int(ids[0]))
+            elif n_miss < wl.max_miss:
+                p, C, n_miss = pp, CC, n_miss + 1
+                hits.append(-1)
+            else:
+                break
+        assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
+    assert pruned > 10
