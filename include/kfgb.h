@@ -94,6 +94,12 @@ typedef struct {
   int lmax;
   int block_threads;
   int blocks_per_sm;
+  /* Learned hit proposal (not in the paper): NULL for plain finding, else a device buffer of
+   * KF_MLP_BUFFER floats (see kf_mlp_forward). With top_n > 0, when more than top_n hits of a
+   * candidate's window pass the chi2 cut, only the top_n with the highest network score (ties:
+   * lower hit id) make children. */
+  const float* mlp;
+  int top_n;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,
@@ -158,6 +164,32 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
                    const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
                    int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
                    int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
+
+/* Learned hit proposal network (not in the paper): MLP 14 -> 64 -> 64 -> 1 with ReLU, scoring a
+ * (predicted candidate, hit) pair from 14 features: the predicted state (x, y, z, kappa, phi,
+ * theta), log(C_ii + 1e-12) of the six covariance diagonal terms, and the two residuals divided by
+ * the square roots of the innovation variances. Parameter buffer, FP32, KF_MLP_BUFFER floats:
+ * W1[64][14], b1[64], W2[64][64], b2[64], W3[64], b3 (KF_MLP_PARAMS weights), then the feature
+ * normaliser mean[14], sd[14] (x -> (x - mean) / sd before the first layer). All pointers are
+ * device memory. */
+#define KF_MLP_IN 14
+#define KF_MLP_HID 64
+#define KF_MLP_PARAMS 5185
+#define KF_MLP_BUFFER 5213
+
+/* Logits of n feature rows (features float [n][14], raw, standardised inside). */
+int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream);
+
+/* Mean binary cross-entropy with logits over n samples (labels 0 or 1) and its gradient with
+ * respect to the KF_MLP_PARAMS weights: grad float [KF_MLP_PARAMS] and loss float [1] are
+ * overwritten. */
+int kf_mlp_loss_grad(const float* params, const float* features, const float* labels, int n, float* grad,
+                     float* loss, kf_stream_t stream);
+
+/* One Adam step (Kingma and Ba) on the weights of params with gradient grad and moments m, v
+ * (float [KF_MLP_PARAMS] each, zero before step 1); step counts from 1. */
+int kf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1, float beta2,
+                float eps, kf_stream_t stream);
 
 /* Allocation-free track finding. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory while they reconstruct events, for example an

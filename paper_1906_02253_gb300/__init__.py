@@ -45,11 +45,13 @@ class KfHitIndex(ctypes.Structure):
 
 class KfFindParams(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
-                ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+                ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
-           "kf_status_string")
+           "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_status_string")
+MLP_PARAMS, MLP_BUFFER = 5185, 5213
 
 
 def load_library(path: str = LIB_PATH):
@@ -73,6 +75,13 @@ def load_library(path: str = LIB_PATH):
             lib.kf_find_tracks.restype = I
             lib.kf_find_tracks.argtypes = [G, ctypes.POINTER(KfHitIndex), P, P, P, P, I, ctypes.POINTER(KfFindParams),
                                            P, P, P, P, P, P, P, S, P]
+            lib.kf_mlp_forward.restype = I
+            lib.kf_mlp_forward.argtypes = [P, P, I, P, P]
+            lib.kf_mlp_loss_grad.restype = I
+            lib.kf_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
+            lib.kf_mlp_adam.restype = I
+            lib.kf_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -179,8 +188,16 @@ def fit_tracks(geom: Geometry, hits, hit_surface, track_hits, out: dict = None, 
 
 
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
-                blocks_per_sm: int = 0) -> KfFindParams:
-    return KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm)
+                blocks_per_sm: int = 0, mlp=None, top_n: int = 0) -> KfFindParams:
+    """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal)."""
+    if mlp is not None:
+        _cuda(mlp, torch.float32, "mlp")
+        if mlp.numel() != MLP_BUFFER:
+            raise KfError(f"mlp must hold {MLP_BUFFER} floats")
+    prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
+                       None if mlp is None else mlp.data_ptr(), int(top_n))
+    prm._mlp_ref = mlp  # keep the buffer alive with the parameters
+    return prm
 
 
 def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:
@@ -233,3 +250,73 @@ def to_device_event_batch(batch, device="cuda") -> dict:
         seed_track=st,
         max_slab_hits=int(np.diff(batch.slab_offsets).max()) if batch.slab_offsets.size > 1 else 0,
     )
+
+
+# ------------------------------------------------------------------------------------------------
+# Learned hit proposal: network buffer, inference and training through the C ABI
+# ------------------------------------------------------------------------------------------------
+
+def mlp_buffer(weights, mean, sd, device="cuda"):
+    """Device parameter buffer: KF_MLP_PARAMS weights, then the feature mean[14] and sd[14]."""
+    buf = np.concatenate([np.asarray(weights, np.float32).ravel(), np.asarray(mean, np.float32).ravel(),
+                          np.asarray(sd, np.float32).ravel()])
+    if buf.size != MLP_BUFFER:
+        raise KfError(f"expected {MLP_BUFFER} values, got {buf.size}")
+    return torch.from_numpy(buf).to(device)
+
+
+def mlp_forward(params, features, out=None, stream=None):
+    """Logits of raw feature rows [n, 14] (kf_mlp_forward)."""
+    _cuda(params, torch.float32, "params")
+    _cuda(features, torch.float32, "features")
+    n = features.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=features.device) if out is None else out
+    _check(load_library().kf_mlp_forward(_ptr(params), _ptr(features), n, _ptr(out), _stream(stream)), "kf_mlp_forward")
+    return out
+
+
+def mlp_loss_grad(params, features, labels, grad=None, loss=None, stream=None):
+    """Mean BCE-with-logits loss and its gradient over the weights (kf_mlp_loss_grad)."""
+    _cuda(params, torch.float32, "params")
+    _cuda(features, torch.float32, "features")
+    _cuda(labels, torch.float32, "labels")
+    dev = params.device
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=dev) if grad is None else grad
+    loss = torch.empty(1, dtype=torch.float32, device=dev) if loss is None else loss
+    _check(load_library().kf_mlp_loss_grad(_ptr(params), _ptr(features), _ptr(labels), features.shape[0], _ptr(grad),
+                                           _ptr(loss), _stream(stream)), "kf_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8, stream=None):
+    """One Adam step on the weights in params (kf_mlp_adam)."""
+    _check(load_library().kf_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), lr, beta1, beta2, eps,
+                                      _stream(stream)), "kf_mlp_adam")
+
+
+def mlp_train(params, features, labels, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+              log=None):
+    """Train the network in params on (features, labels) with minibatch Adam, all arithmetic in the
+    library's kernels (forward, backward, Adam); the host only picks the minibatches."""
+    dev = params.device
+    n = features.shape[0]
+    m = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+    v = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    step = 0
+    history = []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=gen).to(dev)
+        fx, fy = features[perm].contiguous(), labels[perm].contiguous()
+        for b0 in range(0, n - batch + 1, batch):
+            step += 1
+            mlp_loss_grad(params, fx[b0:b0 + batch], fy[b0:b0 + batch], grad, loss)
+            mlp_adam(params, grad, m, v, step, lr)
+        full, _ = mlp_loss_grad(params, features, labels, grad, loss)
+        history.append(float(full.item()))
+        if log:
+            log(f"epoch {ep}: loss {history[-1]:.4f}")
+    return history

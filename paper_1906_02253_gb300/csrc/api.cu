@@ -7,6 +7,7 @@
 
 #include "../../include/kfgb.h"
 #include "kf_math.cuh"
+#include "mlp.cuh"
 
 namespace kfgb {
 
@@ -194,7 +195,26 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   A.state_out = state_out;
   A.cov_out = cov_out;
   A.status_out = status_out;
+  A.mlp = params->mlp;
+  A.top_n = params->mlp ? params->top_n : 0;
   return launch_find(G, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream) {
+  if (n < 0 || (n > 0 && (!params || !features || !logits))) return KF_ERR_ARG;
+  return launch_mlp_forward(params, features, n, logits, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_mlp_loss_grad(const float* params, const float* features, const float* labels, int n, float* grad,
+                     float* loss, kf_stream_t stream) {
+  if (n < 0 || !params || !grad || !loss || (n > 0 && (!features || !labels))) return KF_ERR_ARG;
+  return launch_mlp_loss_grad(params, features, labels, n, grad, loss, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1, float beta2,
+                float eps, kf_stream_t stream) {
+  if (!params || !grad || !m || !v || step < 1 || !(lr > 0.f) || !(eps > 0.f)) return KF_ERR_ARG;
+  return launch_mlp_adam(params, grad, m, v, step, lr, beta1, beta2, eps, reinterpret_cast<cudaStream_t>(stream));
 }
 
 // Allocation-free finding: the library's fixed scratch array replaces the caller's workspace.
@@ -242,6 +262,8 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   A.state_out = state_out;
   A.cov_out = cov_out;
   A.status_out = status_out;
+  A.mlp = params->mlp;
+  A.top_n = params->mlp ? params->top_n : 0;
   return launch_find(G, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "find_launch.cuh"
+#include "mlp.cuh"
 
 namespace kfgb {
 
@@ -45,9 +46,76 @@ struct WarpSmem {
   int pl_own[kPList];
 };
 
+// Learned proposal, per warp: each lane's features (predicted state, log covariance diagonal,
+// sqrt of the two innovation variances), the residuals and scores of buffered passing pairs, and
+// the score of each kept hit.
 template <int KC>
+struct WarpLearned {
+  float feat[kMlpIn][32];
+  float pl_r0[kPList];
+  float pl_r1[kPList];
+  float pl_sc[kPList];
+  float hl_sc[KC][32];
+};
+
+template <int KC, bool LEARNED>
 __host__ __device__ size_t warp_smem_bytes(int lmax) {
-  return (sizeof(WarpSmem<KC>) + static_cast<size_t>(lmax - 3) * 32 * sizeof(int) + 15) / 16 * 16;
+  return (sizeof(WarpSmem<KC>) + static_cast<size_t>(lmax - 3) * 32 * sizeof(int) +
+          (LEARNED ? sizeof(WarpLearned<KC>) : 0) + 15) / 16 * 16;
+}
+
+// Block-level region before the warps: the network's parameters in learned mode.
+template <bool LEARNED>
+__host__ __device__ constexpr size_t block_smem_head() {
+  return LEARNED ? (sizeof(float) * kMlpParamsAll + 15) / 16 * 16 : 0;
+}
+
+// Insert into a lane's kept list ordered by (score descending, hit id ascending), capacity cap.
+template <int KC>
+__device__ __forceinline__ void hl_insert_scored(WarpSmem<KC>& W, WarpLearned<KC>& L, int lane, int& n, int cap,
+                                                 float sc, float c2, int id, int pos) {
+  if (n == cap) {
+    const float ls = L.hl_sc[cap - 1][lane];
+    const int li = W.hl_id[cap - 1][lane];
+    if (!(sc > ls || (sc == ls && id < li))) return;
+    n = cap - 1;
+  }
+  int i = n;
+  while (i > 0) {
+    const float ps = L.hl_sc[i - 1][lane];
+    const int pi = W.hl_id[i - 1][lane];
+    if (!(sc > ps || (sc == ps && id < pi))) break;
+    L.hl_sc[i][lane] = ps;
+    W.hl_c2[i][lane] = W.hl_c2[i - 1][lane];
+    W.hl_id[i][lane] = pi;
+    W.hl_pos[i][lane] = W.hl_pos[i - 1][lane];
+    --i;
+  }
+  L.hl_sc[i][lane] = sc;
+  W.hl_c2[i][lane] = c2;
+  W.hl_id[i][lane] = id;
+  W.hl_pos[i][lane] = pos;
+  ++n;
+}
+
+// Reorder a lane's kept list by (chi2, hit id) and keep at most cap entries.
+template <int KC>
+__device__ __forceinline__ void hl_sort_by_chi2(WarpSmem<KC>& W, int lane, int& n, int cap) {
+  for (int i = 1; i < n; ++i) {
+    const float c = W.hl_c2[i][lane];
+    const int id = W.hl_id[i][lane], pos = W.hl_pos[i][lane];
+    int j = i;
+    while (j > 0 && (c < W.hl_c2[j - 1][lane] || (c == W.hl_c2[j - 1][lane] && id < W.hl_id[j - 1][lane]))) {
+      W.hl_c2[j][lane] = W.hl_c2[j - 1][lane];
+      W.hl_id[j][lane] = W.hl_id[j - 1][lane];
+      W.hl_pos[j][lane] = W.hl_pos[j - 1][lane];
+      --j;
+    }
+    W.hl_c2[j][lane] = c;
+    W.hl_id[j][lane] = id;
+    W.hl_pos[j][lane] = pos;
+  }
+  if (n > cap) n = cap;
 }
 
 struct Cand {
@@ -260,15 +328,25 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
          (static_cast<unsigned long long>(__float_as_uint(c2)) << 26) | (static_cast<unsigned long long>(pk) << 20);
 }
 
-template <int KC>
-__global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
+template <int KC, bool LEARNED>
+__global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NS = 32 / KC;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  const size_t wbytes = warp_smem_bytes<KC>(A.lmax);
-  WarpSmem<KC>& W = *reinterpret_cast<WarpSmem<KC>*>(smem + wid * wbytes);
-  int* trace = reinterpret_cast<int*>(smem + wid * wbytes + sizeof(WarpSmem<KC>));  // [step][32]
+  const size_t wbytes = warp_smem_bytes<KC, LEARNED>(A.lmax);
+  unsigned char* wbase = smem + block_smem_head<LEARNED>() + wid * wbytes;
+  WarpSmem<KC>& W = *reinterpret_cast<WarpSmem<KC>*>(wbase);
+  int* trace = reinterpret_cast<int*>(wbase + sizeof(WarpSmem<KC>));  // [step][32]
+  WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
+                                                            static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
+  const float* wmlp = reinterpret_cast<const float*>(smem);
+  if (LEARNED) {
+    float* w = reinterpret_cast<float*>(smem);
+    for (int i = threadIdx.x; i < kMlpParamsAll; i += blockDim.x) w[i] = A.mlp[i];
+    __syncthreads();
+  }
+  const int keep = LEARNED ? A.top_n : A.k_max;  // capacity of a lane's list during the scan
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
   const int gbase = in_grp ? grp * KC : lane;
@@ -363,6 +441,14 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
             W.win[4][lane] = in.s11 * inv;
             W.win[5][lane] = -in.s01 * inv;
             W.win[6][lane] = in.s00 * inv;
+            if (LEARNED) {
+#pragma unroll
+              for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
+#pragma unroll
+              for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
+              WL.feat[12][lane] = sqrtf(in.s00);
+              WL.feat[13][lane] = sqrtf(in.s11);
+            }
             const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
             const float d2 = sqrtf(cut * in.s11) * (1.f + 1e-4f) + 1e-4f;
             const int nphi = G.n_phi[si];
@@ -412,6 +498,28 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - T;
     int np = 0;
+    // Buffered passing pairs go to their owner's list: the k_max best by chi2 (plain), or, with the
+    // learned proposal, the top_n best by network score, scored here by all lanes together.
+    auto flush = [&](int count) {
+      if (LEARNED) {
+        for (int k = lane; k < count; k += 32) {
+          const int o = W.pl_own[k];
+          float f[kMlpIn];
+#pragma unroll
+          for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][o];
+          f[12] = WL.pl_r0[k] / WL.feat[12][o];
+          f[13] = WL.pl_r1[k] / WL.feat[13][o];
+          WL.pl_sc[k] = mlp_logit(wmlp, f);
+        }
+        __syncwarp();
+        for (int k = 0; k < count; ++k)
+          if (W.pl_own[k] == lane)
+            hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+      } else {
+        for (int k = 0; k < count; ++k)
+          if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, keep, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+      }
+    };
     __syncwarp();
     for (int q0 = 0; q0 < total; q0 += 32) {
       const int q = q0 + lane;
@@ -424,7 +532,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
       owner = min(owner, 31);
       const int obase = __shfl_sync(kFull, excl, owner);
       bool pass = false;
-      float c2v = 0.f;
+      float c2v = 0.f, r0 = 0.f, r1 = 0.f;
       int pos = 0, hid = 0;
       if (q < total) {
         int o = q - obase;
@@ -438,7 +546,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
         const float2 h = __ldg(A.sorted_hits + pos);
         const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
         const float dphi = resid_angle(W.win[0][owner], W.win[1][owner], d.x, d.y);
-        const float r0 = W.win[3][owner] * dphi, r1 = h.y - W.win[2][owner];
+        r0 = W.win[3][owner] * dphi;
+        r1 = h.y - W.win[2][owner];
         c2v = r0 * (W.win[4][owner] * r0 + W.win[5][owner] * r1) + r1 * (W.win[5][owner] * r0 + W.win[6][owner] * r1);
         pass = c2v < cut;
         if (pass) hid = __ldg(A.sorted_ids + pos);
@@ -450,19 +559,21 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
         W.pl_id[k] = hid;
         W.pl_pos[k] = pos;
         W.pl_own[k] = owner;
+        if (LEARNED) {
+          WL.pl_r0[k] = r0;
+          WL.pl_r1[k] = r1;
+        }
       }
       np += __popc(m);
       if (np > kPList - 32) {
         __syncwarp();
-        for (int k = 0; k < np; ++k)
-          if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, cap, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+        flush(np);
         np = 0;
         __syncwarp();
       }
     }
     __syncwarp();
-    for (int k = 0; k < np; ++k)
-      if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, cap, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+    flush(np);
     // Windows wider than kRows phi bins: the owner scans them alone.
     if (wide) {
       const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
@@ -479,10 +590,23 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
           const float dphi = resid_angle(w0, w1, d.x, d.y);
           const float r0 = w3 * dphi, r1 = h.y - w2;
           const float c2v = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
-          if (c2v < cut) hl_insert(W, lane, hl_n, cap, c2v, __ldg(A.sorted_ids + pos), pos);
+          if (c2v < cut) {
+            if (LEARNED) {
+              float f[kMlpIn];
+#pragma unroll
+              for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][lane];
+              f[12] = r0 / WL.feat[12][lane];
+              f[13] = r1 / WL.feat[13][lane];
+              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_logit(wmlp, f), c2v, __ldg(A.sorted_ids + pos), pos);
+            } else {
+              hl_insert(W, lane, hl_n, keep, c2v, __ldg(A.sorted_ids + pos), pos);
+            }
+          }
         }
       }
     }
+    // With the learned proposal the kept hits are reordered by chi2 for the ranking below.
+    if (LEARNED && hl_n > 0) hl_sort_by_chi2(W, lane, hl_n, cap);
     // Outcome of each propagated candidate; keep the prediction for its children.
     if (kind == 1) {
       kind = hl_n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
@@ -605,34 +729,48 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
   }
 }
 
-template __global__ void k_find_tracks<1>(DevGeom, FindArgs);
-template __global__ void k_find_tracks<2>(DevGeom, FindArgs);
-template __global__ void k_find_tracks<4>(DevGeom, FindArgs);
-template __global__ void k_find_tracks<6>(DevGeom, FindArgs);
-template __global__ void k_find_tracks<8>(DevGeom, FindArgs);
-template __global__ void k_find_tracks<16>(DevGeom, FindArgs);
+// Compile-time choice of capacity and mode, dispatched from the runtime plan.
+template <int KC, bool L>
+struct FindKernel {
+  static constexpr int kc = KC;
+  static constexpr bool learned = L;
+};
+
+template <class F>
+static int dispatch_find(int kc, bool learned, F&& f) {
+  switch (kc) {
+    case 1: return learned ? f(FindKernel<1, true>{}) : f(FindKernel<1, false>{});
+    case 2: return learned ? f(FindKernel<2, true>{}) : f(FindKernel<2, false>{});
+    case 4: return learned ? f(FindKernel<4, true>{}) : f(FindKernel<4, false>{});
+    case 6: return learned ? f(FindKernel<6, true>{}) : f(FindKernel<6, false>{});
+    case 8: return learned ? f(FindKernel<8, true>{}) : f(FindKernel<8, false>{});
+    case 16: return learned ? f(FindKernel<16, true>{}) : f(FindKernel<16, false>{});
+    default: return KF_ERR_ARG;
+  }
+}
 
 // ------------------------------------------------------------------------------------------------
 
-template <int KC>
+template <int KC, bool L>
 static int kc_occupancy(int block, size_t smem, int* bps) {
   static int attr_set[16] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_CUDA;
   if (static_cast<int>(smem) > attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_find_tracks<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_find_tracks<KC, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
       return KF_ERR_CUDA;
     attr_set[dev] = static_cast<int>(smem);
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC>, block, smem) != cudaSuccess) return KF_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC, L>, block, smem) != cudaSuccess)
+    return KF_ERR_CUDA;
   return KF_OK;
 }
 
-static int pick_kc(int k_max, int kc_hint) {
+static int pick_kc(int need) {
   static const int caps[] = {1, 2, 4, 6, 8, 16};
   for (int c : caps)
-    if (c >= k_max && c >= kc_hint) return c;
+    if (c >= need) return c;
   return -1;
 }
 
@@ -640,50 +778,43 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   if (!p || n_seeds < 0 || sms <= 0) return KF_ERR_ARG;
   if (p->k_max < 1 || p->k_max > KF_MAX_K || p->max_miss < 0 || p->lmax < 4 || p->lmax > KF_MAX_LMAX) return KF_ERR_ARG;
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
+  const bool learned = p->mlp != nullptr && p->top_n > 0;
+  if (p->top_n < 0 || p->top_n > KF_MAX_K) return KF_ERR_ARG;
   const int block = p->block_threads == 0 ? 256 : p->block_threads;
   if (block < 32 || block > 256 || block % 32) return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;
-  const int kc = pick_kc(p->k_max, 0);
+  const int kc = pick_kc(learned ? std::max(p->k_max, p->top_n) : p->k_max);
   if (kc < 0) return KF_ERR_ARG;
-  size_t wb = 0;
-  switch (kc) {
-    case 1: wb = warp_smem_bytes<1>(p->lmax); break;
-    case 2: wb = warp_smem_bytes<2>(p->lmax); break;
-    case 4: wb = warp_smem_bytes<4>(p->lmax); break;
-    case 6: wb = warp_smem_bytes<6>(p->lmax); break;
-    case 8: wb = warp_smem_bytes<8>(p->lmax); break;
-    default: wb = warp_smem_bytes<16>(p->lmax); break;
-  }
-  const size_t smem = wb * (block / 32);
+  size_t smem = 0;
+  dispatch_find(kc, learned, [&](auto k) {
+    smem = decltype(k)::learned ? block_smem_head<true>() : 0;
+    smem += warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (block / 32);
+    return KF_OK;
+  });
   if (smem > 227 * 1024) return KF_ERR_CAPACITY;
-  // Occupancy per (device, capacity, block size, lmax), queried once so later calls (for
+  // Occupancy per (device, capacity, mode, block size, lmax), queried once so later calls (for
   // instance inside a stream capture) only launch.
-  static int occ_cache[16][6][8][32] = {};
+  static int occ_cache[16][6][2][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
   const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
   const int bi = block / 32 - 1;
   int bps = p->blocks_per_sm;
-  int occ = occ_cache[dev][ki][bi][p->lmax];
+  int occ = occ_cache[dev][ki][learned][bi][p->lmax];
   if (occ == 0) {
-    int rc = KF_OK;
-    switch (kc) {
-      case 1: rc = kc_occupancy<1>(block, smem, &occ); break;
-      case 2: rc = kc_occupancy<2>(block, smem, &occ); break;
-      case 4: rc = kc_occupancy<4>(block, smem, &occ); break;
-      case 6: rc = kc_occupancy<6>(block, smem, &occ); break;
-      case 8: rc = kc_occupancy<8>(block, smem, &occ); break;
-      default: rc = kc_occupancy<16>(block, smem, &occ); break;
-    }
+    const int rc = dispatch_find(kc, learned, [&](auto k) {
+      return kc_occupancy<decltype(k)::kc, decltype(k)::learned>(block, smem, &occ);
+    });
     if (rc != KF_OK) return rc;
     if (occ < 1) return KF_ERR_CAPACITY;
-    occ_cache[dev][ki][bi][p->lmax] = occ;
+    occ_cache[dev][ki][learned][bi][p->lmax] = occ;
   }
   if (bps == 0 || bps > occ) bps = occ;
   const int warps = block / 32;
   const long long groups_per_block = static_cast<long long>(warps) * (32 / kc);
   const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
   plan->kc = kc;
+  plan->learned = learned;
   plan->block = block;
   plan->grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
   plan->smem = smem;
@@ -728,14 +859,10 @@ int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, c
   A.seed_surf = reinterpret_cast<int*>(base + plan.off_surf);
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
   k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, A);
-  switch (plan.kc) {
-    case 1: k_find_tracks<1><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-    case 2: k_find_tracks<2><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-    case 4: k_find_tracks<4><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-    case 6: k_find_tracks<6><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-    case 8: k_find_tracks<8><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-    default: k_find_tracks<16><<<plan.grid, plan.block, plan.smem, stream>>>(G, A); break;
-  }
+  dispatch_find(plan.kc, plan.learned, [&](auto k) {
+    k_find_tracks<decltype(k)::kc, decltype(k)::learned><<<plan.grid, plan.block, plan.smem, stream>>>(G, A);
+    return KF_OK;
+  });
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;
 }
 

@@ -21,6 +21,8 @@ struct FindArgs {
   int n_events;  // events in the index; seeds naming another event fail (status 1)
   float chi2_cut;
   int k_max, max_miss, lmax;
+  const float* mlp;  // learned proposal parameters (KF_MLP_BUFFER floats) or null
+  int top_n;         // > 0 with mlp: keep the top_n passing hits by score
   int* hits_out;
   int* nhits_out;
   float* chi2_out;
@@ -37,6 +39,7 @@ struct FindArgs {
 // workspace layout.
 struct FindPlan {
   int kc, block, grid;
+  bool learned;
   size_t smem;
   size_t off_state, off_surf, ws_bytes;
 };
