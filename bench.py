@@ -196,6 +196,23 @@ def run_gpu(args, wl, batch):
     wsb = torch.empty(max(kf.find_workspace_size(n_seeds, prm), 256), dtype=torch.uint8, device=dev)
     max_slab = host["max_slab_hits"]
     stream = torch.cuda.Stream(device=dev)
+    # Autotune (block size, candidate capacity) of the finder and the fit's block size on a
+    # calibration subset: the seeds of the first events (outside the timed region).
+    tuning = {}
+    fit_block = 0
+    if not args.no_autotune:
+        with torch.cuda.stream(stream):
+            kf.build_hit_index(g, d["hits"], d["slab_offsets"], batch.n_events, max_slab, index=idx, stream=stream)
+            n_cal = int(np.searchsorted(host["seed_event"].numpy(), min(10, batch.n_events)))
+            cal_s = d["seed_hits"][:, :n_cal].contiguous()
+            cal_e = d["seed_event"][:n_cal].contiguous()
+            prm, ms_find = kf.autotune_find(g, idx, d["hits"], d["hit_surface"], cal_s, cal_e, prm, stream=stream)
+            cal = kf.find_tracks(g, idx, d["hits"], d["hit_surface"], cal_s, cal_e, prm, stream=stream)
+            fit_block, ms_fit = kf.autotune_fit(g, d["hits"], d["hit_surface"], cal["hits"], stream=stream)
+        torch.cuda.synchronize()
+        tuning = {"calibration_seeds": n_cal, "find_block_threads": prm.block_threads,
+                  "find_k_capacity": prm.k_capacity, "find_ms": ms_find, "fit_block_threads": fit_block,
+                  "fit_ms": ms_fit}
     launches = {"index": 0, "find": 0, "fit": 0}
 
     def step(s, events=None):
@@ -208,7 +225,7 @@ def run_gpu(args, wl, batch):
                        workspace=wsb, stream=s)
         if events:
             events[2].record(s)
-        kf.fit_tracks(g, d["hits"], d["hit_surface"], fout["hits"], out=fit_out, stream=s)
+        kf.fit_tracks(g, d["hits"], d["hit_surface"], fout["hits"], out=fit_out, block_threads=fit_block, stream=s)
         if events:
             events[3].record(s)
 
@@ -298,6 +315,10 @@ def run_gpu(args, wl, batch):
                                    fout["nhits"].cpu().numpy())
     fit_ok = float((fit_out["status"] == 0).float().mean().item())
 
+    learned = None
+    if not args.no_learned:
+        learned = compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff, fake, kern_ms["find"])
+
     value = ws * n_seeds / (ms_step / 1000.0)
     e2e_value = ws * n_seeds / (ms_e2e / 1000.0)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -307,13 +328,15 @@ def run_gpu(args, wl, batch):
                       "layers": len(wl.surfaces), "k_max": wl.k_max, "chi2_cut": wl.chi2_cut,
                       "step": "hit index + find + fit, one CUDA graph", "l2": "flushed between steps (256 MB write)",
                       "parallelism": f"events sharded over {ws} GPU(s), no collective"},
-           "gpu_launches": launches_per_step * args.steps,
+           "gpu_launches": launches_per_step * args.steps, "autotune": tuning,
            "kernel_ms": kern_ms, "efficiency": eff, "fake_rate": fake, "fit_ok_fraction": fit_ok,
            "fit_tracks_per_s": ws * n_seeds / (kern_ms["fit"] / 1000.0),
            "find_seeds_per_s": ws * n_seeds / (kern_ms["find"] / 1000.0),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": ms_e2e}}
     out["clocks"] = clk.summary()
+    if learned is not None:
+        out["learned_vs_plain"] = learned
 
     # CPU baseline (oracle on a bounded sample) and the finder's algorithmic work per seed.
     counters = None
@@ -326,6 +349,52 @@ def run_gpu(args, wl, batch):
     out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+MLP_FILE = os.path.join(ROOT, "paper_1906_02253_gb300", "data", "mlp_learned.npz")
+
+
+def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff_plain, fake_plain, ms_plain):
+    """Learned proposal vs the plain finder on the same batch and K: finder seeds/s (CUDA events on
+    the launching stream, L2 flushed between runs), efficiency and fake rate, for several top_n."""
+    import numpy as np
+    import torch
+    from paper_1906_02253_gb300 import metrics
+
+    if not os.path.exists(MLP_FILE):
+        return {"unavailable": "no trained network at paper_1906_02253_gb300/data/mlp_learned.npz"}
+    z = np.load(MLP_FILE)
+    buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device=d["hits"].device)
+    n = host["seed_hits"].shape[1]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=d["hits"].device)
+    res = {"network": json.loads(str(z["info"])), "k_max": prm.k_max,
+           "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain}}
+    best = None
+    for top_n in (1, 2, 4):
+        lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
+                            mlp=buf, top_n=top_n)
+        lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
+        times = []
+        for i in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                kf.find_tracks(g, idx, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], lp, out=fout,
+                               workspace=lw, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        e, f = metrics.efficiency(batch, host["seed_track"], fout["hits"].cpu().numpy().T, fout["nhits"].cpu().numpy())
+        r = {"find_seeds_per_s": n / (statistics.mean(times) / 1000.0), "efficiency": e, "fake_rate": f,
+             "efficiency_loss": eff_plain - e}
+        r["speedup_vs_plain"] = r["find_seeds_per_s"] / res["plain"]["find_seeds_per_s"]
+        res[f"top_n={top_n}"] = r
+        if r["efficiency_loss"] <= 0.005 and (best is None or r["find_seeds_per_s"] > res[best]["find_seeds_per_s"]):
+            best = f"top_n={top_n}"
+    res["best_within_0.5pct_eff_loss"] = best
+    return res
 
 
 def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
@@ -372,6 +441,8 @@ def main():
     ap.add_argument("--cpu-seeds", type=int, default=10 ** 9, help="oracle sample for the CPU baseline")
     ap.add_argument("--ref-seeds", type=int, default=200000, help="oracle sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch configuration")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -85,7 +85,8 @@ typedef struct {
 /* Finder settings. chi2_cut: hits with predicted chi2 below it make children; k_max: candidates
  * kept per seed (<= KF_MAX_K); max_miss: surfaces a candidate may cross without a hit; lmax:
  * length of each output hit list (3 seed hits + at most lmax-3 steps; 4 <= lmax <= KF_MAX_LMAX);
- * block_threads: threads per block (0 = default 256; a multiple of 32, <= 256);
+ * block_threads: threads per block (0 = the size keeping most warps resident; a multiple of 32,
+ * <= 256);
  * blocks_per_sm: resident blocks per SM for the persistent grid (0 = occupancy maximum). */
 typedef struct {
   float chi2_cut;
@@ -100,6 +101,9 @@ typedef struct {
    * lower hit id) make children. */
   const float* mlp;
   int top_n;
+  /* Candidate capacity of the compiled kernel (one of 1, 2, 4, 6, 8, 16, >= k_max and top_n);
+   * 0 picks the smallest that fits. A larger capacity gives the same results. */
+  int k_capacity;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,
@@ -136,6 +140,7 @@ int kf_index_bins(const KfGeometry* geom);
  *   state_out float [6][n_tracks], cov_out float [21][n_tracks] (packed 21), chi2_out float
  *   [n_tracks] (sum of predicted chi2), ndof_out int [n_tracks] (2 * hits - 5), status_out int
  *   [n_tracks]: 0 ok, 1 seed failed, 2 a surface was not reached, 3 fewer than three seed hits.
+ * The grid is persistent (a multiple of the SM count, each thread striding over tracks).
  * block_threads: 0 for the default (128), else a multiple of 32 up to 256. */
 int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* track_hits,
                   int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
@@ -213,6 +218,23 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
                           const int* hit_surface, const int* seed_hits, const int* seed_event, int n_seeds,
                           const KfFindParams* params, int* hits_out, int* nhits_out, float* chi2_out,
                           float* state_out, float* cov_out, int* status_out, kf_stream_t stream);
+
+/* Autotuner for the persistent finder (not in the paper): runs kf_find_tracks on the given seeds
+ * (a calibration subset of the workload) for every block size 64..256 (step 32) and for the
+ * smallest and the next compiled candidate capacity, times each run with CUDA events (the stream
+ * is synchronised: do not call it during a stream capture), and writes the fastest block size
+ * and capacity into params->block_threads and params->k_capacity; *best_ms receives its time.
+ * Every configuration gives the same results. Outputs and workspace as for kf_find_tracks. */
+int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                     const int* seed_hits, const int* seed_event, int n_seeds, KfFindParams* params, int* hits_out,
+                     int* nhits_out, float* chi2_out, float* state_out, float* cov_out, int* status_out,
+                     void* workspace, size_t workspace_bytes, float* best_ms, kf_stream_t stream);
+
+/* Autotuner for the fit: times kf_fit_tracks for block sizes 64..256 (step 32) on the given tracks
+ * and writes the fastest to *block_threads (synchronises the stream). */
+int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* track_hits,
+                    int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
+                    int* status_out, int* block_threads, float* best_ms, kf_stream_t stream);
 
 /* Human-readable name of a status code. */
 const char* kf_status_string(int status);

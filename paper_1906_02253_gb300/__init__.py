@@ -46,11 +46,12 @@ class KfHitIndex(ctypes.Structure):
 class KfFindParams(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
-           "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_status_string")
+           "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
+           "kf_autotune_fit", "kf_status_string")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 
 
@@ -82,6 +83,13 @@ def load_library(path: str = LIB_PATH):
             lib.kf_mlp_adam.restype = I
             lib.kf_mlp_adam.argtypes = [P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, P]
+            lib.kf_autotune_find.restype = I
+            lib.kf_autotune_find.argtypes = [G, ctypes.POINTER(KfHitIndex), P, P, P, P, I,
+                                             ctypes.POINTER(KfFindParams), P, P, P, P, P, P, P, S,
+                                             ctypes.POINTER(ctypes.c_float), P]
+            lib.kf_autotune_fit.restype = I
+            lib.kf_autotune_fit.argtypes = [G, P, P, P, I, I, P, P, P, P, P, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_float), P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -188,14 +196,14 @@ def fit_tracks(geom: Geometry, hits, hit_surface, track_hits, out: dict = None, 
 
 
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
-                blocks_per_sm: int = 0, mlp=None, top_n: int = 0) -> KfFindParams:
+                blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0) -> KfFindParams:
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal)."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
             raise KfError(f"mlp must hold {MLP_BUFFER} floats")
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
-                       None if mlp is None else mlp.data_ptr(), int(top_n))
+                       None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity))
     prm._mlp_ref = mlp  # keep the buffer alive with the parameters
     return prm
 
@@ -296,9 +304,10 @@ def mlp_adam(params, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9
 
 
 def mlp_train(params, features, labels, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
-              log=None):
+              log=None, lr_halving: int = 0):
     """Train the network in params on (features, labels) with minibatch Adam, all arithmetic in the
-    library's kernels (forward, backward, Adam); the host only picks the minibatches."""
+    library's kernels (forward, backward, Adam); the host only picks the minibatches. With
+    lr_halving > 0 the learning rate halves every lr_halving epochs."""
     dev = params.device
     n = features.shape[0]
     m = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=dev)
@@ -311,12 +320,59 @@ def mlp_train(params, features, labels, epochs: int = 3, batch: int = 4096, lr: 
     for ep in range(epochs):
         perm = torch.randperm(n, generator=gen).to(dev)
         fx, fy = features[perm].contiguous(), labels[perm].contiguous()
+        lr_ep = lr * (0.5 ** (ep // lr_halving) if lr_halving > 0 else 1.0)
         for b0 in range(0, n - batch + 1, batch):
             step += 1
             mlp_loss_grad(params, fx[b0:b0 + batch], fy[b0:b0 + batch], grad, loss)
-            mlp_adam(params, grad, m, v, step, lr)
+            mlp_adam(params, grad, m, v, step, lr_ep)
         full, _ = mlp_loss_grad(params, features, labels, grad, loss)
         history.append(float(full.item()))
         if log:
             log(f"epoch {ep}: loss {history[-1]:.4f}")
     return history
+
+
+# ------------------------------------------------------------------------------------------------
+# Autotuning (kf_autotune_find / kf_autotune_fit) and its cache
+# ------------------------------------------------------------------------------------------------
+
+def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits, seed_event, params: KfFindParams,
+                  stream=None):
+    """Time every block size and candidate capacity on these seeds (a calibration subset) and
+    return (tuned params, best ms). Synchronises the stream."""
+    out = find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, params, stream=stream)
+    ws = out["workspace"]
+    tuned = KfFindParams.from_buffer_copy(params)
+    tuned._mlp_ref = getattr(params, "_mlp_ref", None)
+    ms = ctypes.c_float()
+    rc = load_library().kf_autotune_find(geom.ref, ctypes.byref(index.c), _ptr(hits), _ptr(hit_surface),
+                                         _ptr(seed_hits), _ptr(seed_event), seed_hits.shape[1], ctypes.byref(tuned),
+                                         _ptr(out["hits"]), _ptr(out["nhits"]), _ptr(out["chi2"]), _ptr(out["state"]),
+                                         _ptr(out["cov"]), _ptr(out["status"]), _ptr(ws), ws.numel(),
+                                         ctypes.byref(ms), _stream(stream))
+    _check(rc, "kf_autotune_find")
+    return tuned, ms.value
+
+
+def autotune_fit(geom: Geometry, hits, hit_surface, track_hits, stream=None):
+    """Time every block size of the fit on these tracks; returns (block_threads, best ms)."""
+    out = fit_tracks(geom, hits, hit_surface, track_hits, stream=stream)
+    blk, ms = ctypes.c_int(), ctypes.c_float()
+    lmax, n = track_hits.shape
+    rc = load_library().kf_autotune_fit(geom.ref, _ptr(hits), _ptr(hit_surface), _ptr(track_hits), n, lmax,
+                                        _ptr(out["state"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out["ndof"]),
+                                        _ptr(out["status"]), ctypes.byref(blk), ctypes.byref(ms), _stream(stream))
+    _check(rc, "kf_autotune_fit")
+    return blk.value, ms.value
+
+
+def save_tuning(path: str, entry: dict):
+    """Append an autotuning result to a JSON cache keyed by workload name and device."""
+    import json
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[entry["key"]] = entry
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)

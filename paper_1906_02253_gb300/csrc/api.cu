@@ -89,6 +89,39 @@ static int launch_status() {
 
 }  // namespace kfgb
 
+namespace {
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+// Median of three timed runs after one untimed run; negative on a launch error.
+template <class F>
+float time_config(cudaStream_t st, F&& run) {
+  EventPair ev;
+  if (run() != KF_OK) return -1.f;
+  float t[3];
+  for (int i = 0; i < 3; ++i) {
+    cudaEventRecord(ev.a, st);
+    if (run() != KF_OK) return -1.f;
+    cudaEventRecord(ev.b, st);
+    if (cudaEventSynchronize(ev.b) != cudaSuccess) return -1.f;
+    cudaEventElapsedTime(&t[i], ev.a, ev.b);
+  }
+  std::sort(t, t + 3);
+  return t[1];
+}
+
+}  // namespace
+
 using namespace kfgb;
 
 extern "C" {
@@ -142,7 +175,17 @@ int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surf
   if (n_tracks == 0) return KF_OK;
   if (!hits || !hit_surface || !track_hits || !state_out || !cov_out || !chi2_out || !ndof_out || !status_out)
     return KF_ERR_ARG;
-  const int grid = (n_tracks + block_threads - 1) / block_threads;
+  // Persistent grid: as many blocks as stay resident, each thread striding over the tracks.
+  static int occ_cache[64][8] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return KF_ERR_CUDA;
+  int& occ = occ_cache[dev][block_threads / 32 - 1];
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit_tracks, block_threads, 0) != cudaSuccess || occ < 1)
+      occ = 1;
+  }
+  const long long want = (static_cast<long long>(n_tracks) + block_threads - 1) / block_threads;
+  const int grid = static_cast<int>(std::min<long long>(want, static_cast<long long>(sm_count()) * occ));
   k_fit_tracks<<<grid, block_threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       G, reinterpret_cast<const float2*>(hits), hit_surface, track_hits, n_tracks, lmax, state_out, cov_out, chi2_out,
       ndof_out, status_out);
@@ -265,6 +308,67 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   A.mlp = params->mlp;
   A.top_n = params->mlp ? params->top_n : 0;
   return launch_find(G, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---- autotuners: time each configuration with CUDA events on the caller's stream ---------------
+
+
+int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                     const int* seed_hits, const int* seed_event, int n_seeds, KfFindParams* params, int* hits_out,
+                     int* nhits_out, float* chi2_out, float* state_out, float* cov_out, int* status_out,
+                     void* workspace, size_t workspace_bytes, float* best_ms, kf_stream_t stream) {
+  if (!params || !best_ms || n_seeds <= 0) return KF_ERR_ARG;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int need = std::max(params->k_max, params->mlp ? params->top_n : 0);
+  static const int caps[] = {1, 2, 4, 6, 8, 16};
+  int cap_opts[2] = {0, 0}, n_cap = 0;
+  for (int c : caps)
+    if (c >= need && n_cap < 2) cap_opts[n_cap++] = c;
+  KfFindParams best = *params;
+  float best_t = -1.f;
+  for (int ci2 = 0; ci2 < n_cap; ++ci2) {
+    for (int blk = 64; blk <= 256; blk += 32) {
+      KfFindParams p = *params;
+      p.block_threads = blk;
+      p.k_capacity = cap_opts[ci2];
+      p.blocks_per_sm = 0;
+      const float t = time_config(st, [&]() {
+        return kf_find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, &p, hits_out, nhits_out,
+                              chi2_out, state_out, cov_out, status_out, workspace, workspace_bytes, stream);
+      });
+      if (t >= 0.f && (best_t < 0.f || t < best_t)) {
+        best_t = t;
+        best = p;
+      }
+    }
+  }
+  if (best_t < 0.f) return KF_ERR_CUDA;
+  *params = best;
+  *best_ms = best_t;
+  return KF_OK;
+}
+
+int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* track_hits,
+                    int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
+                    int* status_out, int* block_threads, float* best_ms, kf_stream_t stream) {
+  if (!block_threads || !best_ms || n_tracks <= 0) return KF_ERR_ARG;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  float best_t = -1.f;
+  int best_b = 0;
+  for (int blk = 64; blk <= 256; blk += 32) {
+    const float t = time_config(st, [&]() {
+      return kf_fit_tracks(geom, hits, hit_surface, track_hits, n_tracks, lmax, state_out, cov_out, chi2_out, ndof_out,
+                           status_out, blk, stream);
+    });
+    if (t >= 0.f && (best_t < 0.f || t < best_t)) {
+      best_t = t;
+      best_b = blk;
+    }
+  }
+  if (best_t < 0.f) return KF_ERR_CUDA;
+  *block_threads = best_b;
+  *best_ms = best_t;
+  return KF_OK;
 }
 
 const char* kf_status_string(int status) {

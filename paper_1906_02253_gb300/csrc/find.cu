@@ -47,13 +47,11 @@ struct WarpSmem {
 };
 
 // Learned proposal, per warp: each lane's features (predicted state, log covariance diagonal,
-// sqrt of the two innovation variances), the residuals and scores of buffered passing pairs, and
-// the score of each kept hit.
+// sqrt of the two innovation variances), the scores of buffered passing pairs, and the score of
+// each kept hit.
 template <int KC>
 struct WarpLearned {
   float feat[kMlpIn][32];
-  float pl_r0[kPList];
-  float pl_r1[kPList];
   float pl_sc[kPList];
   float hl_sc[KC][32];
 };
@@ -64,11 +62,6 @@ __host__ __device__ size_t warp_smem_bytes(int lmax) {
           (LEARNED ? sizeof(WarpLearned<KC>) : 0) + 15) / 16 * 16;
 }
 
-// Block-level region before the warps: the network's parameters in learned mode.
-template <bool LEARNED>
-__host__ __device__ constexpr size_t block_smem_head() {
-  return LEARNED ? (sizeof(float) * kMlpParamsAll + 15) / 16 * 16 : 0;
-}
 
 // Insert into a lane's kept list ordered by (score descending, hit id ascending), capacity cap.
 template <int KC>
@@ -328,24 +321,23 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
          (static_cast<unsigned long long>(__float_as_uint(c2)) << 26) | (static_cast<unsigned long long>(pk) << 20);
 }
 
+// Network score of a pair, out of line: scoring is rare (only windows with more passing hits
+// than top_n), so it does not set the finder's register budget.
+__device__ __noinline__ float mlp_score(const float* w, const float* f) { return mlp_logit(w, f); }
+
 template <int KC, bool LEARNED>
-__global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G, FindArgs A) {
+__global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NS = 32 / KC;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const size_t wbytes = warp_smem_bytes<KC, LEARNED>(A.lmax);
-  unsigned char* wbase = smem + block_smem_head<LEARNED>() + wid * wbytes;
+  unsigned char* wbase = smem + wid * wbytes;
   WarpSmem<KC>& W = *reinterpret_cast<WarpSmem<KC>*>(wbase);
   int* trace = reinterpret_cast<int*>(wbase + sizeof(WarpSmem<KC>));  // [step][32]
   WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
-  const float* wmlp = reinterpret_cast<const float*>(smem);
-  if (LEARNED) {
-    float* w = reinterpret_cast<float*>(smem);
-    for (int i = threadIdx.x; i < kMlpParamsAll; i += blockDim.x) w[i] = A.mlp[i];
-    __syncthreads();
-  }
+  const float* wmlp = A.mlp;  // read through L1/L2: scoring is rare
   const int keep = LEARNED ? A.top_n : A.k_max;  // capacity of a lane's list during the scan
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
@@ -414,6 +406,8 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
     Cand c;
     int kind = 3;  // 0 hit children, 1 miss child, 2 carried, 3 empty slot
     int si = -1, T = 0, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, hl_n = 0;
+    bool scored = false;  // learned: this lane's kept hits carry network scores
+    float s00v = 1.f, s11v = 1.f;  // innovation variances of this lane's window
     bool wide = false;
     if (on && valid) {
       load_cand(W, lane, c);
@@ -441,14 +435,8 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
             W.win[4][lane] = in.s11 * inv;
             W.win[5][lane] = -in.s01 * inv;
             W.win[6][lane] = in.s00 * inv;
-            if (LEARNED) {
-#pragma unroll
-              for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
-#pragma unroll
-              for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
-              WL.feat[12][lane] = sqrtf(in.s00);
-              WL.feat[13][lane] = sqrtf(in.s11);
-            }
+            s00v = in.s00;
+            s11v = in.s11;
             const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
             const float d2 = sqrtf(cut * in.s11) * (1.f + 1e-4f) + 1e-4f;
             const int nphi = G.n_phi[si];
@@ -500,21 +488,55 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
     int np = 0;
     // Buffered passing pairs go to their owner's list: the k_max best by chi2 (plain), or, with the
     // learned proposal, the top_n best by network score, scored here by all lanes together.
-    auto flush = [&](int count) {
+    // Buffered passing pairs go to their owner's list: the k_max best by chi2 (plain), or, with the
+    // learned proposal, the top_n best by network score. A pair is scored (by all lanes together)
+    // only when its owner has more passing hits than top_n; otherwise every hit is kept anyway.
+    // A flush in the middle of the scan (buffer nearly full) scores all its pairs.
+    auto flush = [&](int count, bool final_flush) {
       if (LEARNED) {
-        for (int k = lane; k < count; k += 32) {
-          const int o = W.pl_own[k];
-          float f[kMlpIn];
+        int cnt = 0;
+        for (int k = 0; k < count; ++k) cnt += W.pl_own[k] == lane;
+        const bool need = !final_flush || scored || hl_n + cnt > keep;
+        const unsigned needmask = __ballot_sync(kFull, need);
+        // Features of the owners that need scores, from their predictions still in registers.
+        if (need && cnt > 0 && !scored) {
 #pragma unroll
-          for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][o];
-          f[12] = WL.pl_r0[k] / WL.feat[12][o];
-          f[13] = WL.pl_r1[k] / WL.feat[13][o];
-          WL.pl_sc[k] = mlp_logit(wmlp, f);
+          for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
+          WL.feat[12][lane] = sqrtf(s00v);
+          WL.feat[13][lane] = sqrtf(s11v);
         }
         __syncwarp();
-        for (int k = 0; k < count; ++k)
-          if (W.pl_own[k] == lane)
+        for (int k = lane; k < count; k += 32) {
+          const int o = W.pl_own[k];
+          if ((needmask >> o) & 1u) {
+            float f[kMlpIn];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][o];
+            const int pos = W.pl_pos[k];
+            const float2 h = __ldg(A.sorted_hits + pos);
+            const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
+            const float r0 = W.win[3][o] * resid_angle(W.win[0][o], W.win[1][o], d.x, d.y);
+            const float r1 = h.y - W.win[2][o];
+            f[12] = r0 / WL.feat[12][o];
+            f[13] = r1 / WL.feat[13][o];
+            WL.pl_sc[k] = mlp_score(wmlp, f);
+          }
+        }
+        __syncwarp();
+        for (int k = 0; k < count; ++k) {
+          if (W.pl_own[k] != lane) continue;
+          if (need) {
             hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+          } else {  // kept unconditionally (at most top_n of them)
+            W.hl_c2[hl_n][lane] = W.pl_c2[k];
+            W.hl_id[hl_n][lane] = W.pl_id[k];
+            W.hl_pos[hl_n][lane] = W.pl_pos[k];
+            ++hl_n;
+          }
+        }
+        scored = scored || (need && cnt > 0);
       } else {
         for (int k = 0; k < count; ++k)
           if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, keep, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
@@ -532,7 +554,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
       owner = min(owner, 31);
       const int obase = __shfl_sync(kFull, excl, owner);
       bool pass = false;
-      float c2v = 0.f, r0 = 0.f, r1 = 0.f;
+      float c2v = 0.f;
       int pos = 0, hid = 0;
       if (q < total) {
         int o = q - obase;
@@ -546,8 +568,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
         const float2 h = __ldg(A.sorted_hits + pos);
         const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
         const float dphi = resid_angle(W.win[0][owner], W.win[1][owner], d.x, d.y);
-        r0 = W.win[3][owner] * dphi;
-        r1 = h.y - W.win[2][owner];
+        const float r0 = W.win[3][owner] * dphi, r1 = h.y - W.win[2][owner];
         c2v = r0 * (W.win[4][owner] * r0 + W.win[5][owner] * r1) + r1 * (W.win[5][owner] * r0 + W.win[6][owner] * r1);
         pass = c2v < cut;
         if (pass) hid = __ldg(A.sorted_ids + pos);
@@ -559,23 +580,27 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
         W.pl_id[k] = hid;
         W.pl_pos[k] = pos;
         W.pl_own[k] = owner;
-        if (LEARNED) {
-          WL.pl_r0[k] = r0;
-          WL.pl_r1[k] = r1;
-        }
       }
       np += __popc(m);
       if (np > kPList - 32) {
         __syncwarp();
-        flush(np);
+        flush(np, false);
         np = 0;
         __syncwarp();
       }
     }
     __syncwarp();
-    flush(np);
+    flush(np, true);
     // Windows wider than kRows phi bins: the owner scans them alone.
     if (wide) {
+      if (LEARNED) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
+        WL.feat[12][lane] = sqrtf(s00v);
+        WL.feat[13][lane] = sqrtf(s11v);
+      }
       const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
       const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
       const float w0 = W.win[0][lane], w1 = W.win[1][lane], w2 = W.win[2][lane], w3 = W.win[3][lane];
@@ -597,7 +622,7 @@ __global__ void __launch_bounds__(256, LEARNED ? 1 : 2) k_find_tracks(DevGeom G,
               for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][lane];
               f[12] = r0 / WL.feat[12][lane];
               f[13] = r1 / WL.feat[13][lane];
-              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_logit(wmlp, f), c2v, __ldg(A.sorted_ids + pos), pos);
+              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_score(wmlp, f), c2v, __ldg(A.sorted_ids + pos), pos);
             } else {
               hl_insert(W, lane, hl_n, keep, c2v, __ldg(A.sorted_ids + pos), pos);
             }
@@ -780,35 +805,63 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
   const bool learned = p->mlp != nullptr && p->top_n > 0;
   if (p->top_n < 0 || p->top_n > KF_MAX_K) return KF_ERR_ARG;
-  const int block = p->block_threads == 0 ? 256 : p->block_threads;
-  if (block < 32 || block > 256 || block % 32) return KF_ERR_ARG;
+  if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32))
+    return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;
-  const int kc = pick_kc(learned ? std::max(p->k_max, p->top_n) : p->k_max);
+  if (p->k_capacity < 0 || p->k_capacity > KF_MAX_K) return KF_ERR_ARG;
+  const int kc = pick_kc(std::max(learned ? std::max(p->k_max, p->top_n) : p->k_max, p->k_capacity));
   if (kc < 0) return KF_ERR_ARG;
-  size_t smem = 0;
-  dispatch_find(kc, learned, [&](auto k) {
-    smem = decltype(k)::learned ? block_smem_head<true>() : 0;
-    smem += warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (block / 32);
-    return KF_OK;
-  });
-  if (smem > 227 * 1024) return KF_ERR_CAPACITY;
-  // Occupancy per (device, capacity, mode, block size, lmax), queried once so later calls (for
-  // instance inside a stream capture) only launch.
+  // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
+  // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
   static int occ_cache[16][6][2][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
   const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
-  const int bi = block / 32 - 1;
-  int bps = p->blocks_per_sm;
-  int occ = occ_cache[dev][ki][learned][bi][p->lmax];
-  if (occ == 0) {
-    const int rc = dispatch_find(kc, learned, [&](auto k) {
-      return kc_occupancy<decltype(k)::kc, decltype(k)::learned>(block, smem, &occ);
+  auto occupancy = [&](int blk, size_t* smem_out, int* occ_out) {
+    size_t sm = 0;
+    dispatch_find(kc, learned, [&](auto k) {
+      sm = warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
+      return KF_OK;
     });
+    *smem_out = sm;
+    *occ_out = 0;
+    if (sm > 227 * 1024) return KF_OK;
+    int& cached = occ_cache[dev][ki][learned][blk / 32 - 1][p->lmax];
+    if (cached == 0) {
+      int o = 0;
+      const int rc = dispatch_find(kc, learned, [&](auto k) {
+        return kc_occupancy<decltype(k)::kc, decltype(k)::learned>(blk, sm, &o);
+      });
+      if (rc != KF_OK) return rc;
+      cached = o > 0 ? o : -1;
+    }
+    *occ_out = cached > 0 ? cached : 0;
+    return KF_OK;
+  };
+  // Block size: the caller's, or the one that keeps the most warps resident per SM.
+  int block = p->block_threads;
+  size_t smem = 0;
+  int occ = 0;
+  if (block != 0) {
+    const int rc = occupancy(block, &smem, &occ);
     if (rc != KF_OK) return rc;
-    if (occ < 1) return KF_ERR_CAPACITY;
-    occ_cache[dev][ki][learned][bi][p->lmax] = occ;
+  } else {
+    int best_warps = 0;
+    for (int blk = 256; blk >= 64; blk -= 32) {
+      size_t sm = 0;
+      int o = 0;
+      const int rc = occupancy(blk, &sm, &o);
+      if (rc != KF_OK) return rc;
+      if (o * blk / 32 > best_warps) {
+        best_warps = o * blk / 32;
+        block = blk;
+        smem = sm;
+        occ = o;
+      }
+    }
   }
+  if (occ < 1) return KF_ERR_CAPACITY;
+  int bps = p->blocks_per_sm;
   if (bps == 0 || bps > occ) bps = occ;
   const int warps = block / 32;
   const long long groups_per_block = static_cast<long long>(warps) * (32 / kc);

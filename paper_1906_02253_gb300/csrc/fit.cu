@@ -1,7 +1,7 @@
 // Kalman-filter track fit over known hit sequences (paper Sec. 2: track fitting as the first
-// vectorised use of the filter). One thread per track; the state (6) and the packed covariance
-// (21) stay in registers through all surfaces; track hit ids are read as structure-of-arrays
-// (coalesced), hits are gathered by id.
+// vectorised use of the filter). One thread per track in a persistent grid striding over all
+// tracks of all events; the state (6) and the packed covariance (21) stay in registers through
+// all surfaces; track hit ids are read as structure-of-arrays (coalesced), hits gathered by id.
 #include "kf_math.cuh"
 
 namespace kfgb {
@@ -12,8 +12,7 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __r
                                                     float* __restrict__ state_out, float* __restrict__ cov_out,
                                                     float* __restrict__ chi2_out, int* __restrict__ ndof_out,
                                                     int* __restrict__ status_out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_tracks) return;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tracks; t += gridDim.x * blockDim.x) {
   float p[6], C[21];
   int status = 0;
   float chi2 = 0.f;
@@ -82,6 +81,7 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __r
   }
   ndof_out[t] = 2 * nvalid - 5;
   status_out[t] = status;
+  }
 }
 
 }  // namespace kfgb

@@ -214,3 +214,27 @@ def test_find_parity_dense_noise(kf):
     b = synth.generate(wl)
     gpu, ora, st = _find_both(kf, wl, b)
     _assert_find_parity(b, gpu, ora, st)
+
+
+def test_autotuner_configurations_give_identical_results(kf):
+    """Block size and candidate capacity change the schedule, never the result: every configuration
+    the autotuner tries finds the same tracks, and it returns one of them."""
+    wl = synth.workload("find", n_events=2, tracks_lo=1500, tracks_hi=2500, noise_frac=1.0)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    ref = None
+    for blk in (64, 160, 256):
+        for cap in (6, 8, 16):
+            prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, block_threads=blk, k_capacity=cap)
+            out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+            hits = out["hits"].cpu().numpy()
+            if ref is None:
+                ref = hits
+            assert np.array_equal(hits, ref), (blk, cap)
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+    tuned, ms = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    assert tuned.block_threads in range(64, 257, 32) and tuned.k_capacity in (6, 8) and ms > 0
+    blk, ms = kf.autotune_fit(g, dev["hits"], dev["hit_surface"], dev["track_hits"])
+    assert blk in range(64, 257, 32) and ms > 0
