@@ -265,11 +265,8 @@ def run_gpu(args, wl, batch):
         torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    ms_step = statistics.mean(t_steps)
-    if ws > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    from paper_1906_02253_gb300 import shard
+    ms_step = shard.max_over_ranks(statistics.mean(t_steps), device=dev)
     launches_per_step = 4  # index, seed states, find, fit kernels (plus one memset node)
 
     # Per-kernel durations: the same three launches eager, events on the launching stream.
@@ -303,11 +300,7 @@ def run_gpu(args, wl, batch):
         res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
 
     t_e2e = timed_steps(args.steps, e2e_step)
-    ms_e2e = statistics.mean(t_e2e)
-    if ws > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = shard.max_over_ranks(statistics.mean(t_e2e), device=dev)
 
     # Result sanity on the last step (efficiency of the found tracks, host logic only).
     from paper_1906_02253_gb300 import metrics
@@ -455,7 +448,8 @@ def main():
     import synth
     over = {"n_events": args.events} if args.events else {}
     # weak scaling: every rank processes its own events (different seed), no data exchange
-    wl = synth.workload(args.workload, seed=synth.WORKLOADS[args.workload].seed + 1000 * rank, **over)
+    from paper_1906_02253_gb300 import shard
+    wl = synth.workload(args.workload, seed=shard.rank_seed(synth.WORKLOADS[args.workload].seed, rank), **over)
     batch = synth.generate(wl)
     if args.impl == "reference":
         run_reference(args, wl, batch)
