@@ -354,13 +354,16 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     import torch
     from paper_1906_02253_gb300 import metrics
 
-    if not os.path.exists(MLP_FILE):
-        return {"unavailable": "no trained network at paper_1906_02253_gb300/data/mlp_learned.npz"}
-    z = np.load(MLP_FILE)
+    path = os.path.join(ROOT, "paper_1906_02253_gb300", "data", f"mlp_{args.workload}.npz")
+    if not os.path.exists(path):
+        path = MLP_FILE  # the barrel-geometry network
+    if not os.path.exists(path):
+        return {"unavailable": "no trained network in paper_1906_02253_gb300/data"}
+    z = np.load(path)
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device=d["hits"].device)
     n = host["seed_hits"].shape[1]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=d["hits"].device)
-    res = {"network": json.loads(str(z["info"])), "k_max": prm.k_max,
+    res = {"network": json.loads(str(z["info"])), "network_file": os.path.basename(path), "k_max": prm.k_max,
            "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain}}
     best = None
     for top_n in (1, 2, 4):

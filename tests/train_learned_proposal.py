@@ -8,6 +8,8 @@ He initialisation and is trained by the library's kernels (kf_mlp_loss_grad, kf_
 host only shuffles minibatches. One pair in ten is held out to measure the ranking quality.
 
     python tests/train_learned_proposal.py [--out paper_1906_02253_gb300/data/mlp_learned.npz]
+    python tests/train_learned_proposal.py --workload hi_occ --stride 20 \
+        --out paper_1906_02253_gb300/data/mlp_hi_occ.npz
 """
 import argparse
 import json
@@ -33,6 +35,7 @@ def auc_of(scores, labels):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_1906_02253_gb300", "data", "mlp_learned.npz"))
+    ap.add_argument("--workload", default="learned", help="learned (barrel) or hi_occ (barrel + disks)")
     ap.add_argument("--events", type=int, default=200)
     ap.add_argument("--stride", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=12)
@@ -47,7 +50,7 @@ def main():
     import paper_1906_02253_gb300 as kf
 
     t0 = time.time()
-    wl = synth.workload("learned", n_events=args.events)
+    wl = synth.workload(args.workload, n_events=args.events)
     b = synth.generate(wl)
     g = oracle.Geometry(wl)
     sh, st = b.seeds()
@@ -68,7 +71,7 @@ def main():
     sc = kf.mlp_forward(params, torch.from_numpy(Fte).cuda()).cpu().numpy()
     auc = auc_of(sc, Lte)
     w = params.cpu().numpy()
-    info = dict(events=args.events, seed=wl.seed, seed_stride=args.stride, pairs=int(len(L)), lr_halving=args.lr_halving,
+    info = dict(workload=args.workload, events=args.events, seed=wl.seed, seed_stride=args.stride, pairs=int(len(L)), lr_halving=args.lr_halving,
                 positive_fraction=float(L.mean()), held_out=int(hold.sum()), held_out_auc=float(auc),
                 loss_per_epoch=hist, epochs=args.epochs, batch=args.batch, lr=args.lr, init_seed=args.init_seed,
                 seconds_pairs=t_pairs, seconds_train=t_train)
