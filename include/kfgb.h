@@ -66,20 +66,32 @@ typedef struct {
 } KfGeometry;
 
 /* Hit index: per (event, surface) slab, hits sorted by bin (phi-bin * n_2nd + second-bin) and,
- * within a bin, by ascending hit id. All pointers are caller-owned device memory:
+ * within a bin, by phi sub-bin and then ascending hit id. The phi sub-bin refines the phi bin
+ * into KF_PHI_SUB equal parts: fine = clamp(floor((phi + pi_f) * (float)(n_phi * KF_PHI_SUB /
+ * 2pi)), 0, n_phi * KF_PHI_SUB - 1) by the same FP32 rule as the bins, sub = clamp(fine -
+ * phi-bin * KF_PHI_SUB, 0, KF_PHI_SUB - 1). All pointers are caller-owned device memory:
  *   bin_off     int [n_events * n_surf][n_bins + 1]: absolute position in sorted_* of the first
  *               hit of each bin; entry n_bins (and every bin beyond the surface's own count) is
  *               the slab end. n_bins = max over surfaces of n_phi * n_2nd.
  *   sorted_hits float [n_hits][2] and sorted_ids int [n_hits]: same slab ranges as the input.
- *   sorted_dir  float [n_hits][2]: (cos phi, sin phi) of each sorted hit. Optional for
- *               kf_build_hit_index (NULL: not written); required by kf_find_tracks. */
+ *   sorted_rec  float [n_hits][4], 16-byte aligned: the search record of each sorted hit,
+ *               (cos phi, sin phi, second coordinate, hit id as int32 bits), so that a window scan
+ *               reads one 16-byte record per hit. Optional for kf_build_hit_index (NULL: not
+ *               written); required by kf_find_tracks.
+ *   sub_off     uint16 [n_events * n_surf][n_bins][KF_PHI_SUB]: entry j of a bin = number of the
+ *               bin's hits with sub-bin <= j (entry KF_PHI_SUB - 1 = the bin's count; zero for
+ *               bins beyond the surface's own count). Optional for kf_build_hit_index (NULL: not
+ *               written); required by kf_find_tracks, whose windows scan only the sub-bins their
+ *               phi range touches. */
+#define KF_PHI_SUB 8
 typedef struct {
   int n_events;
   int n_bins;
   int* bin_off;
   float* sorted_hits;
   int* sorted_ids;
-  float* sorted_dir;
+  float* sorted_rec;
+  unsigned short* sub_off;
 } KfHitIndex;
 
 /* Finder settings. chi2_cut: hits with predicted chi2 below it make children; k_max: candidates

@@ -76,7 +76,7 @@ def _load():
                                    _P, _P, _P, _P, _P, _P, _P]
             lib.or_index_bins.restype = ctypes.c_int
             lib.or_index_bins.argtypes = [G]
-            lib.or_build_index.argtypes = [G, _P, _P, ctypes.c_int, _P, _P, _P]
+            lib.or_build_index.argtypes = [G, _P, _P, ctypes.c_int, _P, _P, _P, _P]
             lib.or_bin_of.argtypes = [G, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P, _P]
             lib.or_search.restype = ctypes.c_int
             lib.or_search.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
@@ -178,8 +178,12 @@ def fit(geom: Geometry, hits, hit_surface, track_hits, n_threads: int = 0, per_h
     return out
 
 
-def build_index(geom: Geometry, hits, slab_offsets, n_events: int):
-    """Returns (bin_off [n_events*n_surf, nb+1] int64, sorted_hits [n,2] f32, sorted_ids [n] i32)."""
+PHI_SUB = 8  # phi sub-bins per phi bin
+
+
+def build_index(geom: Geometry, hits, slab_offsets, n_events: int, with_sub: bool = False):
+    """Returns (bin_off [n_events*n_surf, nb+1] int64, sorted_hits [n,2] f32, sorted_ids [n] i32),
+    plus sub_off [n_events*n_surf, nb, PHI_SUB] uint16 with ``with_sub``."""
     lib = _load()
     hits = _c(hits, np.float32)
     so = _c(slab_offsets, np.int64)
@@ -188,9 +192,10 @@ def build_index(geom: Geometry, hits, slab_offsets, n_events: int):
     off = np.empty((n_slabs, nb + 1), np.int64)
     sh = np.empty_like(hits)
     si = np.empty(hits.shape[0], np.int32)
+    sub = np.empty((n_slabs, nb, PHI_SUB), np.uint16)
     lib.or_build_index(geom.ref, hits.ctypes.data, so.ctypes.data, n_events, off.ctypes.data, sh.ctypes.data,
-                       si.ctypes.data)
-    return off, sh, si
+                       si.ctypes.data, sub.ctypes.data)
+    return (off, sh, si, sub) if with_sub else (off, sh, si)
 
 
 def bin_of(geom: Geometry, surf: int, phi: float, second: float):

@@ -470,12 +470,17 @@ void parallel_for(long long n, int n_threads, F&& f) {
 // phi-bin = clamp(floor((phi + pi_f) * sphi), 0, n_phi - 1) with sphi = (float)(n_phi / 2pi);
 // 2nd-bin = clamp(floor((v - lo_f) * s2), 0, n_2nd - 1) with s2 = (float)(n_2nd / (hi_f - lo_f)).
 // The build flags forbid FMA contraction so each float operation rounds on its own.
+// Phi sub-bins (kSub per phi bin): fine = clamp(floor((phi + pi_f) * sphi_sub), 0, n_phi*kSub - 1)
+// with sphi_sub = (float)(n_phi * kSub / 2pi), sub = clamp(fine - phi_bin * kSub, 0, kSub - 1).
+constexpr int kSub = 8;
+
 struct BinRule {
-  float pi_f, sphi, lo, s2;
+  float pi_f, sphi, sphi_sub, lo, s2;
   int n_phi, n_2nd;
   explicit BinRule(const OrSurface& S) {
     pi_f = static_cast<float>(kPi);
     sphi = static_cast<float>(static_cast<double>(S.n_phi) / (2.0 * kPi));
+    sphi_sub = static_cast<float>(static_cast<double>(S.n_phi) * kSub / (2.0 * kPi));
     lo = S.lo;
     s2 = static_cast<float>(static_cast<double>(S.n_2nd) / (static_cast<double>(S.hi) - static_cast<double>(S.lo)));
     n_phi = S.n_phi;
@@ -487,6 +492,14 @@ struct BinRule {
     const float f = std::floor(b);
     const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
     return std::min(std::max(k, 0), n_phi - 1);
+  }
+  int sub_bin(float phi) const {
+    const float a = phi + pi_f;
+    const float b = a * sphi_sub;
+    const float f = std::floor(b);
+    const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
+    const int fine = std::min(std::max(k, 0), n_phi * kSub - 1);
+    return std::min(std::max(fine - phi_bin(phi) * kSub, 0), kSub - 1);
   }
   int second_bin(float v) const {
     const float a = v - lo;
@@ -508,10 +521,12 @@ struct Index {
   std::vector<long long> off;   // [(e*n_surf+s)*(nb+1) + b]: global position of bin b's first hit
   std::vector<float> sorted;    // [n_hits][2]
   std::vector<int> ids;         // [n_hits] original hit id
+  std::vector<unsigned short> sub;  // [(e*n_surf+s)*nb + b][kSub]: hits of bin b with sub-bin <= j
 };
 
-// Counting sort per (event, surface) slab: bin = phi_bin * n_2nd + second_bin; within a bin,
-// ascending hit id. Slabs keep their position in the hit array.
+// Counting sort per (event, surface) slab by (bin, phi sub-bin), bin = phi_bin * n_2nd +
+// second_bin; within a (bin, sub-bin), ascending hit id. Slabs keep their position in the hit
+// array.
 void build_index(const OrGeom& g, const float* hits, const long long* slab_off, int n_events, Index& ix) {
   ix.nb = max_bins(g);
   const long long n_slabs = static_cast<long long>(n_events) * g.n_surf;
@@ -519,24 +534,32 @@ void build_index(const OrGeom& g, const float* hits, const long long* slab_off, 
   ix.off.assign(n_slabs * (ix.nb + 1), 0);
   ix.sorted.assign(2 * n_hits, 0.0f);
   ix.ids.assign(n_hits, 0);
+  ix.sub.assign(static_cast<size_t>(n_slabs) * ix.nb * kSub, 0);
   for (long long sl = 0; sl < n_slabs; ++sl) {
     const int si = static_cast<int>(sl % g.n_surf);
     const OrSurface& S = g.surf[si];
     const BinRule br(S);
     const long long h0 = slab_off[sl], h1 = slab_off[sl + 1];
-    std::vector<long long> count(ix.nb + 1, 0);
-    std::vector<int> bin(h1 - h0);
+    // key = bin * kSub + sub-bin: a counting sort on it orders bins, and sub-bins within a bin
+    std::vector<long long> count(static_cast<size_t>(ix.nb) * kSub + 1, 0);
+    std::vector<int> key(h1 - h0);
     for (long long h = h0; h < h1; ++h) {
       const int b = br.phi_bin(hits[2 * h]) * S.n_2nd + br.second_bin(hits[2 * h + 1]);
-      bin[h - h0] = b;
-      count[b + 1]++;
+      key[h - h0] = b * kSub + br.sub_bin(hits[2 * h]);
+      count[key[h - h0] + 1]++;
     }
+    std::vector<long long> start(static_cast<size_t>(ix.nb) * kSub + 1);
+    start[0] = h0;
+    for (size_t k = 0; k + 1 < start.size(); ++k) start[k + 1] = start[k] + count[k + 1];
     long long* o = &ix.off[sl * (ix.nb + 1)];
-    o[0] = h0;
-    for (int b = 0; b < ix.nb; ++b) o[b + 1] = o[b] + count[b + 1];
-    std::vector<long long> cursor(o, o + ix.nb);
-    for (long long h = h0; h < h1; ++h) {  // ascending id keeps equal bins in id order
-      const long long pos = cursor[bin[h - h0]]++;
+    for (int b = 0; b <= ix.nb; ++b) o[b] = start[static_cast<size_t>(b) * kSub];
+    unsigned short* sb = &ix.sub[static_cast<size_t>(sl) * ix.nb * kSub];
+    for (int b = 0; b < ix.nb; ++b)
+      for (int j = 0; j < kSub; ++j)
+        sb[b * kSub + j] = static_cast<unsigned short>(start[static_cast<size_t>(b) * kSub + j + 1] - o[b]);
+    std::vector<long long> cursor(start.begin(), start.end() - 1);
+    for (long long h = h0; h < h1; ++h) {  // ascending id keeps equal keys in id order
+      const long long pos = cursor[key[h - h0]]++;
       ix.sorted[2 * pos] = hits[2 * h];
       ix.sorted[2 * pos + 1] = hits[2 * h + 1];
       ix.ids[pos] = static_cast<int>(h);
@@ -1004,12 +1027,13 @@ void or_fit(const OrGeom* g, const float* hits, const int* hsurf, const int* tra
 int or_index_bins(const OrGeom* g) { return max_bins(*g); }
 
 void or_build_index(const OrGeom* g, const float* hits, const long long* slab_off, int n_events, long long* bin_off,
-                    float* sorted_hits, int* sorted_ids) {
+                    float* sorted_hits, int* sorted_ids, unsigned short* sub_off) {
   Index ix;
   build_index(*g, hits, slab_off, n_events, ix);
   std::memcpy(bin_off, ix.off.data(), sizeof(long long) * ix.off.size());
   std::memcpy(sorted_hits, ix.sorted.data(), sizeof(float) * ix.sorted.size());
   std::memcpy(sorted_ids, ix.ids.data(), sizeof(int) * ix.ids.size());
+  if (sub_off) std::memcpy(sub_off, ix.sub.data(), sizeof(unsigned short) * ix.sub.size());
 }
 
 // Bin of one value by the FP32 rule (tests compare it with the index).

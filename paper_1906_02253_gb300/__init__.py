@@ -40,7 +40,7 @@ class KfGeometry(ctypes.Structure):
 
 class KfHitIndex(ctypes.Structure):
     _fields_ = [("n_events", ctypes.c_int), ("n_bins", ctypes.c_int), ("bin_off", ctypes.c_void_p),
-                ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p), ("sorted_dir", ctypes.c_void_p)]
+                ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p), ("sorted_rec", ctypes.c_void_p), ("sub_off", ctypes.c_void_p)]
 
 
 class KfFindParams(ctypes.Structure):
@@ -53,6 +53,7 @@ EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_work
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
+PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
 
 def load_library(path: str = LIB_PATH):
@@ -153,9 +154,11 @@ class HitIndex:
         self.bin_off = torch.empty((n_events * geom.n_surf, geom.n_bins + 1), dtype=torch.int32, device=device)
         self.sorted_hits = torch.empty((n_hits, 2), dtype=torch.float32, device=device)
         self.sorted_ids = torch.empty(n_hits, dtype=torch.int32, device=device)
-        self.sorted_dir = torch.empty((n_hits, 2), dtype=torch.float32, device=device)
+        self.sorted_rec = torch.empty((n_hits, 4), dtype=torch.float32, device=device)
+        # uint16 sub-bin offsets, held as int16 (torch has no uint16 on every supported version)
+        self.sub_off = torch.empty((n_events * geom.n_surf, geom.n_bins, PHI_SUB), dtype=torch.int16, device=device)
         self.c = KfHitIndex(n_events, self.n_bins, self.bin_off.data_ptr(), self.sorted_hits.data_ptr(),
-                            self.sorted_ids.data_ptr(), self.sorted_dir.data_ptr())
+                            self.sorted_ids.data_ptr(), self.sorted_rec.data_ptr(), self.sub_off.data_ptr())
 
 
 def build_hit_index(geom: Geometry, hits, slab_offsets, n_events: int, max_slab_hits: int, index: HitIndex = None,

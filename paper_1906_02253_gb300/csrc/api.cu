@@ -12,8 +12,8 @@
 namespace kfgb {
 
 __global__ void k_build_hit_index(DevGeom G, const float2* hits, const int* slab_off, int n_slabs, int cap,
-                                  int* bin_off, float2* sorted_hits, int* sorted_ids, float2* sorted_dir,
-                                  int* d_status);
+                                  int* bin_off, float2* sorted_hits, int* sorted_ids, float4* sorted_rec,
+                                  uint4* sub_off, int* d_status);
 __global__ void k_fit_tracks(DevGeom G, const float2* hits, const int* hit_surface, const int* track_hits,
                              int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
                              int* status_out);
@@ -52,6 +52,8 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
     d->n_phi[s] = S.n_phi;
     d->n_2nd[s] = S.n_2nd;
     d->sphi[s] = static_cast<float>(static_cast<double>(S.n_phi) / (2.0 * 3.14159265358979323846));
+    d->sphi_sub[s] =
+        static_cast<float>(static_cast<double>(S.n_phi) * KF_PHI_SUB / (2.0 * 3.14159265358979323846));
     d->s2[s] = static_cast<float>(static_cast<double>(S.n_2nd) / (static_cast<double>(S.hi) - static_cast<double>(S.lo)));
     nb = std::max(nb, S.n_phi * S.n_2nd);
   }
@@ -72,6 +74,19 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
   d->n_barrel = ib;
   d->n_dpos = ip;
   d->n_dneg = in;
+  for (int s = 0; s < kMaxSurf; ++s) d->ord[s] = -1;
+  for (int i = 0; i < ib; ++i) {
+    d->ord[d->barrel_order[i]] = static_cast<signed char>(i);
+    d->barrel_r[i] = d->r_or_z[d->barrel_order[i]];
+  }
+  for (int i = 0; i < ip; ++i) {
+    d->ord[d->dpos_order[i]] = static_cast<signed char>(i);
+    d->dpos_z[i] = d->r_or_z[d->dpos_order[i]];
+  }
+  for (int i = 0; i < in; ++i) {
+    d->ord[d->dneg_order[i]] = static_cast<signed char>(i);
+    d->dneg_z[i] = d->r_or_z[d->dneg_order[i]];
+  }
   return KF_OK;
 }
 
@@ -142,9 +157,12 @@ int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* sla
   if (index->n_events != n_events || index->n_bins != G.n_bins) return KF_ERR_ARG;
   if (n_events == 0) return KF_OK;
   if (!index->bin_off || !index->sorted_hits || !index->sorted_ids || (!hits && max_slab_hits > 0)) return KF_ERR_ARG;
+  if ((reinterpret_cast<size_t>(index->sorted_rec) & 15) || (reinterpret_cast<size_t>(index->sub_off) & 15))
+    return KF_ERR_ARG;
   const int n_slabs = n_events * G.n_surf;
   const int cap = std::max(2, (max_slab_hits + 1) & ~1);
-  const size_t smem = static_cast<size_t>(G.n_bins + 1) * sizeof(int) + 2 * static_cast<size_t>(cap) * sizeof(unsigned short);
+  const size_t smem = static_cast<size_t>(G.n_bins + 1) * sizeof(int) + 2 * static_cast<size_t>(cap) * sizeof(unsigned short) +
+                      static_cast<size_t>(cap) * sizeof(unsigned char);
   // Raise the kernel's dynamic shared memory limit once per device (and only when a larger slab
   // needs it), so later calls, e.g. inside a stream capture, make no attribute call.
   static int smem_set[64] = {0};
@@ -158,8 +176,8 @@ int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* sla
   }
   k_build_hit_index<<<n_slabs, 512, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
       G, reinterpret_cast<const float2*>(hits), slab_offsets, n_slabs, cap, index->bin_off,
-      reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, reinterpret_cast<float2*>(index->sorted_dir),
-      d_status);
+      reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, reinterpret_cast<float4*>(index->sorted_rec),
+      reinterpret_cast<uint4*>(index->sub_off), d_status);
   return launch_status();
 }
 
@@ -211,7 +229,7 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   if (rc != KF_OK) return rc;
   if (n_seeds == 0) return KF_OK;
   if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
-      !index->sorted_dir)
+      !index->sorted_rec || (reinterpret_cast<size_t>(index->sorted_rec) & 15) || !index->sub_off)
     return KF_ERR_ARG;
   if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
       !cov_out || !status_out)
@@ -221,7 +239,8 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   A.bin_off = index->bin_off;
   A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
   A.sorted_ids = index->sorted_ids;
-  A.sorted_dir = index->sorted_dir;
+  A.sorted_rec = reinterpret_cast<const float4*>(index->sorted_rec);
+  A.sub_off = index->sub_off;
   A.hits = reinterpret_cast<const float2*>(hits);
   A.hit_surface = hit_surface;
   A.seed_hits = seed_hits;
@@ -276,7 +295,7 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   if (plan.ws_bytes > KF_STATIC_SCRATCH_BYTES) return KF_ERR_CAPACITY;
   if (n_seeds == 0) return KF_OK;
   if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
-      !index->sorted_dir)
+      !index->sorted_rec || (reinterpret_cast<size_t>(index->sorted_rec) & 15) || !index->sub_off)
     return KF_ERR_ARG;
   if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
       !cov_out || !status_out)
@@ -288,7 +307,8 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   A.bin_off = index->bin_off;
   A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
   A.sorted_ids = index->sorted_ids;
-  A.sorted_dir = index->sorted_dir;
+  A.sorted_rec = reinterpret_cast<const float4*>(index->sorted_rec);
+  A.sub_off = index->sub_off;
   A.hits = reinterpret_cast<const float2*>(hits);
   A.hit_surface = hit_surface;
   A.seed_hits = seed_hits;

@@ -4,16 +4,18 @@
 // (Sec. 3.2).
 //
 // Design: a warp owns floor(32 / KC) seeds with KC candidate slots each, one lane per slot, and
-// keeps the candidates in shared memory. One step of all its seeds:
+// keeps the candidates in shared memory (the geometry too, one copy per block). One step of all
+// its seeds:
 //  1. every lane with a live candidate picks the next surface and propagates it (state and
 //     covariance in registers), then sets up its search window: the inverse innovation covariance
-//     and up to kRows runs [a, b) of sorted hit positions (one run per phi bin of the window);
+//     and up to kRows runs of sorted hit positions (one run per phi bin of the window);
 //  2. the hits of all the warp's windows are flattened with a warp prefix sum and every lane
 //     evaluates chi2 for every 32nd of them (full SIMT width whatever the window sizes); hits
-//     below the cut are buffered and each owner lane keeps its k_max best in a sorted list;
-//  3. per seed, the k_max best of all children (hit children, miss child, carried candidate) are
-//     selected by a group arg-min over the seed's lanes with shuffles; lane j materialises the
-//     j-th winner (Kalman update for a hit child) from its parent's record;
+//     below the cut are buffered in flattened order, so each owner's pairs form one contiguous
+//     run, which the owner merges into its list of the k_max best by (total chi2, hit id);
+//  3. per seed, every child (hit children, miss child, carried candidate) counts the children of
+//     the seed's other lanes that rank before it; the one of rank j < k_max goes to slot j, and
+//     lane j materialises it (Kalman update for a hit child) from its parent's record;
 //  4. a seed whose candidates have all stopped writes its best track (backtracking a per-step
 //     trace of parent slot and hit) and its lanes take the next seed from an atomic queue.
 // Seeds are consumed in order (one event after another, neighbouring directions together), so the
@@ -27,23 +29,37 @@ namespace kfgb {
 
 constexpr int kWords = 32;      // candidate record: p[6], C[21], chi2, nh, nm, stopped, surf
 constexpr int kHitBits = 27;    // trace entry: parent slot << 27 | (hit id + 1)
-constexpr int kRows = 4;        // window runs per lane scanned cooperatively
+constexpr int kRows = 4;        // window runs (one per bin) per lane scanned cooperatively
 constexpr int kPList = 128;     // buffered passing (candidate, hit) pairs per warp
 constexpr unsigned kFull = 0xffffffffu;
+static_assert(kPList >= 32, "the pair buffer holds one scan round");
+
+// Geometry copy at the start of the block's shared memory.
+constexpr size_t kGeomBytes = (sizeof(DevGeom) + 15) / 16 * 16;
+static_assert(sizeof(DevGeom) % 4 == 0, "geometry is copied in 4-byte words");
 
 template <int KC>
 struct WarpSmem {
   float cand[kWords][32];  // candidate records, one column per lane
-  float win[8][32];        // window of each lane: x, y, centre of 2nd coord, transverse scale, S^-1
-  int rowa[kRows][32];
-  int rowb[kRows][32];
-  float hl_c2[KC][32];     // per lane: best passing hits, sorted by (chi2, hit id)
+  float4 win_a[32];        // window of each lane: x, y, centre of the 2nd coordinate, transverse scale
+  float4 win_b[32];        // S^-1 (00, 01, 11) and the far-hit threshold of window_chi2
+  int2 rows[kRows][32];    // runs: (end of the run in the lane's flattened window, position - start)
+  float hl_tot[KC][32];    // per lane: best passing hits, sorted by (total chi2, hit id)
   int hl_id[KC][32];
   int hl_pos[KC][32];
-  float pl_c2[kPList];
-  int pl_id[kPList];
-  int pl_pos[kPList];
-  int pl_own[kPList];
+  int sel_n[32];           // children offered by each lane
+  unsigned long long tab_key[32];  // winner table of each group, by rank
+  int tab_id[32];
+  int tab_pos[32];
+  union {
+    struct {
+      float c2[kPList];
+      int id[kPList];
+      int pos[kPList];
+      int own[kPList];
+    } pl;                               // buffered passing pairs (scan)
+    unsigned long long key[KC][32];     // ranking keys of each lane's children (selection)
+  } u;
 };
 
 // Learned proposal, per warp: each lane's features (predicted state, log covariance diagonal,
@@ -62,11 +78,12 @@ __host__ __device__ size_t warp_smem_bytes(int lmax) {
           (LEARNED ? sizeof(WarpLearned<KC>) : 0) + 15) / 16 * 16;
 }
 
+__device__ __forceinline__ bool before(float t, int id, float u, int uid) { return t < u || (t == u && id < uid); }
 
 // Insert into a lane's kept list ordered by (score descending, hit id ascending), capacity cap.
 template <int KC>
 __device__ __forceinline__ void hl_insert_scored(WarpSmem<KC>& W, WarpLearned<KC>& L, int lane, int& n, int cap,
-                                                 float sc, float c2, int id, int pos) {
+                                                 float sc, float tot, int id, int pos) {
   if (n == cap) {
     const float ls = L.hl_sc[cap - 1][lane];
     const int li = W.hl_id[cap - 1][lane];
@@ -79,32 +96,32 @@ __device__ __forceinline__ void hl_insert_scored(WarpSmem<KC>& W, WarpLearned<KC
     const int pi = W.hl_id[i - 1][lane];
     if (!(sc > ps || (sc == ps && id < pi))) break;
     L.hl_sc[i][lane] = ps;
-    W.hl_c2[i][lane] = W.hl_c2[i - 1][lane];
+    W.hl_tot[i][lane] = W.hl_tot[i - 1][lane];
     W.hl_id[i][lane] = pi;
     W.hl_pos[i][lane] = W.hl_pos[i - 1][lane];
     --i;
   }
   L.hl_sc[i][lane] = sc;
-  W.hl_c2[i][lane] = c2;
+  W.hl_tot[i][lane] = tot;
   W.hl_id[i][lane] = id;
   W.hl_pos[i][lane] = pos;
   ++n;
 }
 
-// Reorder a lane's kept list by (chi2, hit id) and keep at most cap entries.
+// Reorder a lane's kept list by (total chi2, hit id) and keep at most cap entries.
 template <int KC>
 __device__ __forceinline__ void hl_sort_by_chi2(WarpSmem<KC>& W, int lane, int& n, int cap) {
   for (int i = 1; i < n; ++i) {
-    const float c = W.hl_c2[i][lane];
+    const float c = W.hl_tot[i][lane];
     const int id = W.hl_id[i][lane], pos = W.hl_pos[i][lane];
     int j = i;
-    while (j > 0 && (c < W.hl_c2[j - 1][lane] || (c == W.hl_c2[j - 1][lane] && id < W.hl_id[j - 1][lane]))) {
-      W.hl_c2[j][lane] = W.hl_c2[j - 1][lane];
+    while (j > 0 && before(c, id, W.hl_tot[j - 1][lane], W.hl_id[j - 1][lane])) {
+      W.hl_tot[j][lane] = W.hl_tot[j - 1][lane];
       W.hl_id[j][lane] = W.hl_id[j - 1][lane];
       W.hl_pos[j][lane] = W.hl_pos[j - 1][lane];
       --j;
     }
-    W.hl_c2[j][lane] = c;
+    W.hl_tot[j][lane] = c;
     W.hl_id[j][lane] = id;
     W.hl_pos[j][lane] = pos;
   }
@@ -144,29 +161,60 @@ __device__ __forceinline__ void store_cand(WarpSmem<KC>& W, int col, const Cand&
   W.cand[31][col] = __int_as_float(c.surf);
 }
 
-// Residual angle phi_hit - phi_pred from the hit direction (c, s) rotated into the frame of the
-// predicted position (x, y); series of atan for the small angles of a search window.
-__device__ __forceinline__ float resid_angle(float x, float y, float c, float s) {
-  const float a = x * s - y * c, b = x * c + y * s;
-  if (b > 0.f && fabsf(a) < 0.05f * b) {
-    const float t = a / b, t2 = t * t;
-    return t * (1.f + t2 * (-1.f / 3.f + t2 * (1.f / 5.f + t2 * (-1.f / 7.f))));
-  }
-  return atan2f(a, b);
+// Full-range angle, out of line: only hits far from the prediction in azimuth need it.
+__device__ __noinline__ float atan2_cold(float a, float b) { return atan2f(a, b); }
+
+// atan(a / b) for b > 0 and |a| < 0.05 b: its series to t^7 (next term below 2e-11 relative).
+__device__ __forceinline__ float atan_small(float a, float b) {
+  const float t = a / b, t2 = t * t;
+  return t * (1.f + t2 * (-1.f / 3.f + t2 * (1.f / 5.f + t2 * (-1.f / 7.f))));
 }
 
-// Kalman update of candidate c on surface si with the hit (phi, v) of direction d.
-__device__ __forceinline__ void update_with(const DevGeom& G, int si, Cand& c, float2 h, float2 d) {
+// Residual angle phi_hit - phi_pred from the hit direction (c, s) rotated into the frame of the
+// predicted position (x, y).
+__device__ __forceinline__ float resid_angle(float x, float y, float c, float s) {
+  const float a = x * s - y * c, b = x * c + y * s;
+  if (b > 0.f && fabsf(a) < 0.05f * b) return atan_small(a, b);
+  return atan2_cold(a, b);
+}
+
+// chi2 of a hit's search record against a window (wa: x, y, centre of the 2nd coordinate,
+// transverse scale R; wb: S^-1 00, 01, 11 and the far-hit threshold t). With a = rho sin(dphi),
+// b = rho cos(dphi) (rho the predicted transverse radius), chi2 >= R^2 dphi^2 / S_00 >=
+// R^2 sin^2(dphi) / S_00 (the minimum over the second residual, then |dphi| >= |sin dphi|). Hits
+// outside the series range of the angle are rejected (infinite chi2) when that bound reaches
+// 1.002 x the cut, i.e. when a^2 >= t (a^2 + b^2) with t = 1.002 cut S_00 / R^2; the others get
+// the full-range angle.
+__device__ __forceinline__ float window_chi2(const float4& wa, const float4& wb, const float4& h, float& r0, float& r1) {
+  const float a = wa.x * h.y - wa.y * h.x, b = wa.x * h.x + wa.y * h.y;
+  float dphi;
+  if (b > 0.f && fabsf(a) < 0.05f * b) {
+    dphi = atan_small(a, b);
+  } else {
+    const float a2 = a * a;
+    if (a2 >= wb.w * (a2 + b * b)) {
+      r0 = r1 = 0.f;
+      return __int_as_float(0x7f800000);
+    }
+    dphi = atan2_cold(a, b);
+  }
+  r0 = wa.w * dphi;
+  r1 = h.z - wa.z;
+  return r0 * (wb.x * r0 + wb.y * r1) + r1 * (wb.y * r0 + wb.z * r1);
+}
+
+// Kalman update of candidate c on surface si with the hit of search record h.
+__device__ __forceinline__ void update_with(const DevGeom& G, int si, Cand& c, const float4& h) {
   Meas m;
   float rho;
   meas_setup(G, si, c.p, m, rho);
-  const float dphi = resid_angle(c.p[0], c.p[1], d.x, d.y);
+  const float dphi = resid_angle(c.p[0], c.p[1], h.x, h.y);
   if (G.type[si] == 0) {
     m.r0 = G.r_or_z[si] * dphi;
-    m.r1 = h.y - c.p[2];
+    m.r1 = h.z - c.p[2];
   } else {
     m.r0 = rho * dphi;
-    m.r1 = h.y - rho;
+    m.r1 = h.z - rho;
   }
   Innov in;
   innovation(G, c.C, m, in);
@@ -183,26 +231,24 @@ __device__ __forceinline__ float update_exact(const DevGeom& G, int si, Cand& c,
   return kalman_update(c.p, c.C, in, m.r0, m.r1);
 }
 
-// Insert (c2, id, pos) into lane's sorted list of capacity cap (holding n entries).
+// Insert (tot, id, pos) into lane's list sorted by (total chi2, hit id), capacity cap (holding n).
 template <int KC>
-__device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int cap, float c2, int id, int pos) {
+__device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int cap, float tot, int id, int pos) {
   if (n == cap) {
-    const float lc = W.hl_c2[cap - 1][lane];
-    const int li = W.hl_id[cap - 1][lane];
-    if (!(c2 < lc || (c2 == lc && id < li))) return;
+    if (!before(tot, id, W.hl_tot[cap - 1][lane], W.hl_id[cap - 1][lane])) return;
     n = cap - 1;
   }
   int i = n;
   while (i > 0) {
-    const float pc = W.hl_c2[i - 1][lane];
+    const float pc = W.hl_tot[i - 1][lane];
     const int pi = W.hl_id[i - 1][lane];
-    if (!(c2 < pc || (c2 == pc && id < pi))) break;
-    W.hl_c2[i][lane] = pc;
+    if (!before(tot, id, pc, pi)) break;
+    W.hl_tot[i][lane] = pc;
     W.hl_id[i][lane] = pi;
     W.hl_pos[i][lane] = W.hl_pos[i - 1][lane];
     --i;
   }
-  W.hl_c2[i][lane] = c2;
+  W.hl_tot[i][lane] = tot;
   W.hl_id[i][lane] = id;
   W.hl_pos[i][lane] = pos;
   ++n;
@@ -211,34 +257,44 @@ __device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int
 // Next surface outward and the path to it: the next barrel layer beyond the candidate's radius
 // (accepted if crossed within its z extent) and the next disk beyond |z| in the direction of
 // motion (accepted if crossed within its r extent and half a turn); the nearer one. -1 if none.
-__device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, Prop& best) {
+// The layer lists are sorted, so each "next" is a lower bound, searched from the candidate's
+// current surface `cur` (one or two steps). st, ct: sin and cos of the polar angle p[5].
+__device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, float st, float ct,
+                                            Prop& best) {
   const float w = -kCurvF * G.bz * p[3];
   const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
-  float st, ct;
-  sincosf(p[5], &st, &ct);
   const float cot = ct / st;
+  const bool cur_ok = cur >= 0 && cur < G.n_surf;
   int sel = -1;
-  for (int i = 0; i < G.n_barrel; ++i) {
-    const int s = G.barrel_order[i];
-    if (G.r_or_z[s] > rho + 0.01f) {
+  {
+    const float lim = rho + 0.01f;  // first barrel radius above lim
+    int i = (cur_ok && G.type[cur] == 0) ? max(0, static_cast<int>(G.ord[cur])) : 0;
+    while (i > 0 && G.barrel_r[i - 1] > lim) --i;
+    while (i < G.n_barrel && !(G.barrel_r[i] > lim)) ++i;
+    if (i < G.n_barrel) {
       Prop pr;
-      if (path_to_cylinder(p, w, G.r_or_z[s], pr)) {
+      if (path_to_cylinder(p, w, G.barrel_r[i], pr)) {
+        const int s = G.barrel_order[i];
         const float z = p[2] + pr.s * cot;
         if (z >= G.lo[s] && z <= G.hi[s]) {
           sel = s;
           best = pr;
         }
       }
-      break;
     }
   }
-  const int nd = cot > 0.f ? G.n_dpos : (cot < 0.f ? G.n_dneg : 0);
-  for (int i = 0; i < nd; ++i) {
-    const int s = cot > 0.f ? G.dpos_order[i] : G.dneg_order[i];
-    const float Z = G.r_or_z[s];
-    if ((cot > 0.f && Z > p[2] + 0.01f) || (cot < 0.f && Z < p[2] - 0.01f)) {
+  if (cot > 0.f || cot < 0.f) {
+    const bool fwd = cot > 0.f;
+    const int nd = fwd ? G.n_dpos : G.n_dneg;
+    const float* zs = fwd ? G.dpos_z : G.dneg_z;
+    const float zlo = p[2] + 0.01f, zhi = p[2] - 0.01f;  // first disk beyond z in the direction of motion
+    int i = (cur_ok && G.type[cur] != 0 && ((G.r_or_z[cur] > 0.f) == fwd)) ? max(0, static_cast<int>(G.ord[cur])) : 0;
+    while (i > 0 && (fwd ? zs[i - 1] > zlo : zs[i - 1] < zhi)) --i;
+    while (i < nd && !(fwd ? zs[i] > zlo : zs[i] < zhi)) ++i;
+    if (i < nd) {
       Prop pr;
-      if (path_to_disk(p, w, Z, pr)) {
+      if (path_to_disk(p, w, zs[i], st, ct, pr)) {
+        const int s = fwd ? G.dpos_order[i] : G.dneg_order[i];
         float x, y, z;
         prop_position(p, pr, cot, x, y, z);
         const float r = sqrtf(x * x + y * y);
@@ -247,7 +303,6 @@ __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, Pr
           best = pr;
         }
       }
-      break;
     }
   }
   return sel;
@@ -285,10 +340,12 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
   for (int k = 0; k < 3 && ok; ++k) {
     if (k > 0) {
       const float w = -kCurvF * G.bz * c.p[3];
+      float st, ct;
+      sincosf(c.p[5], &st, &ct);
       Prop pr;
       ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
-                              : path_to_disk(c.p, w, G.r_or_z[ss[k]], pr);
-      ok = ok && apply_propagation(G, ss[k], c.p, c.C, pr);
+                              : path_to_disk(c.p, w, G.r_or_z[ss[k]], st, ct, pr);
+      ok = ok && apply_propagation(G, ss[k], c.p, c.C, pr, st, ct);
       if (!ok) break;
     }
     const float2 h = A.hits[ids[k]];
@@ -314,11 +371,54 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
   }
 }
 
+// Runs of sorted positions of a window: per phi bin pb0 .. pb0 + npb - 1 (wrapping) and 2nd bin
+// zb0 .. zb1, the sub-bins [sub_of(flo), sub_of(fhi)] of the first and last phi bins and every
+// sub-bin of the others (a phi bin whose sub-bins are all in gives one run over its 2nd bins).
+template <class F>
+__device__ __forceinline__ void for_window_runs(const int* off, const unsigned short* sub, int pb0, int npb, int nphi,
+                                                int n2, int zb0, int zb1, int flo, int fhi, F&& visit) {
+  for (int r = 0; r < npb; ++r) {
+    int pb = pb0 + r;
+    if (pb >= nphi) pb -= nphi;
+    const int slo = r == 0 ? sub_of(flo, pb) : 0;
+    const int shi = r == npb - 1 ? sub_of(fhi, pb) : kPhiSub - 1;
+    if (slo == 0 && shi == kPhiSub - 1) {
+      visit(__ldg(off + pb * n2 + zb0), __ldg(off + pb * n2 + zb1 + 1));
+    } else {
+      for (int zb = zb0; zb <= zb1; ++zb) {
+        const int bb = pb * n2 + zb;
+        const int s0 = __ldg(off + bb);
+        visit(s0 + (slo > 0 ? __ldg(sub + bb * kPhiSub + slo - 1) : 0), s0 + __ldg(sub + bb * kPhiSub + shi));
+      }
+    }
+  }
+}
+
+// Window with more than kRows bins (large uncertainty, or a full ring): the owner lane scans it
+// alone. Out of line: rare.
+template <int KC>
+__device__ __noinline__ int scan_wide(WarpSmem<KC>& W, int lane, int hl_n, int keep, const int* off,
+                                      const unsigned short* sub, const float4* rec, int pb0, int npb, int nphi,
+                                      int n2, int zb0, int zb1, int flo, int fhi, float cut, float chi2) {
+  const float4 wa = W.win_a[lane], wb = W.win_b[lane];
+  for_window_runs(off, sub, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, [&](int a, int b) {
+    for (int p = a; p < b; ++p) {
+      const float4 h = __ldg(rec + p);
+      float r0, r1;
+      const float c2v = window_chi2(wa, wb, h, r0, r1);
+      if (c2v < cut) hl_insert(W, lane, hl_n, keep, chi2 + c2v, __float_as_int(h.w), p);
+    }
+  });
+  return hl_n;
+}
+
 // Packed ranking key: (63 - hits) << 58 | chi2 bits << 26 | (parent slot << 2 | kind) << 20.
-// chi2 >= 0, so its IEEE bits order like its value; the hit id breaks remaining ties.
+// For chi2 >= 0 its IEEE bits order like its value (a rounding-negative chi2 ranks as 0); the hit
+// id breaks remaining ties.
 __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk) {
   return (static_cast<unsigned long long>(63 - nh) << 58) |
-         (static_cast<unsigned long long>(__float_as_uint(c2)) << 26) | (static_cast<unsigned long long>(pk) << 20);
+         (static_cast<unsigned long long>(__float_as_uint(fmaxf(c2, 0.f))) << 26) |
+         (static_cast<unsigned long long>(pk) << 20);
 }
 
 // Network score of a pair, out of line: scoring is rare (only windows with more passing hits
@@ -326,13 +426,22 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
 __device__ __noinline__ float mlp_score(const float* w, const float* f) { return mlp_logit(w, f); }
 
 template <int KC, bool LEARNED>
-__global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
+__global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
+  {
+    // Geometry into shared memory: lanes index it by their own surface, which would serialise
+    // constant-bank loads.
+    const int* src = reinterpret_cast<const int*>(&Gp);
+    int* dst = reinterpret_cast<int*>(smem);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(DevGeom) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+  }
+  const DevGeom& G = *reinterpret_cast<const DevGeom*>(smem);
   constexpr int NS = 32 / KC;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const size_t wbytes = warp_smem_bytes<KC, LEARNED>(A.lmax);
-  unsigned char* wbase = smem + wid * wbytes;
+  unsigned char* wbase = smem + kGeomBytes + wid * wbytes;
   WarpSmem<KC>& W = *reinterpret_cast<WarpSmem<KC>*>(wbase);
   int* trace = reinterpret_cast<int*>(wbase + sizeof(WarpSmem<KC>));  // [step][32]
   WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
@@ -347,7 +456,6 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
   const int n = A.n_seeds;
   const int max_steps = A.lmax - 3;
   const float cut = A.chi2_cut;
-  const float nanf_ = __int_as_float(0x7fc00000);
 
   int seed = -1, ev = 0, step = 0;
   bool exhausted = !in_grp;
@@ -405,7 +513,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
     // ---- 1. propagation and window set-up -------------------------------------------------
     Cand c;
     int kind = 3;  // 0 hit children, 1 miss child, 2 carried, 3 empty slot
-    int si = -1, T = 0, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, hl_n = 0;
+    int si = -1, T = 0, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, flo = 0, fhi = 0, hl_n = 0;
     bool scored = false;  // learned: this lane's kept hits carry network scores
     float s00v = 1.f, s11v = 1.f;  // innovation variances of this lane's window
     bool wide = false;
@@ -414,8 +522,10 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
       kind = 2;
       if (!c.stopped) {
         Prop pr;
-        si = next_surface(G, c.p, pr);
-        if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr)) {
+        float st, ct;
+        sincosf(c.p[5], &st, &ct);
+        si = next_surface(G, c.p, c.surf, st, ct, pr);
+        if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr, st, ct)) {
           kind = 1;
           Meas m;
           float rho;
@@ -428,13 +538,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
             const bool barrel = G.type[si] == 0;
             const float rref = barrel ? G.r_or_z[si] : rho;
             const float cz = barrel ? c.p[2] : rho;
-            W.win[0][lane] = c.p[0];
-            W.win[1][lane] = c.p[1];
-            W.win[2][lane] = cz;
-            W.win[3][lane] = rref;
-            W.win[4][lane] = in.s11 * inv;
-            W.win[5][lane] = -in.s01 * inv;
-            W.win[6][lane] = in.s00 * inv;
+            W.win_a[lane] = make_float4(c.p[0], c.p[1], cz, rref);
+            W.win_b[lane] = make_float4(in.s11 * inv, -in.s01 * inv, in.s00 * inv, 1.002f * cut * in.s00 / (rref * rref));
             s00v = in.s00;
             s11v = in.s11;
             const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
@@ -443,31 +548,53 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
             if (!(dphi < kPiF * (1.f - 2.f / nphi))) {
               pb0 = 0;
               npb = nphi;
+              flo = 0;
+              fhi = nphi * kPhiSub - 1;
             } else {
               const float phip = atan2f(c.p[1], c.p[0]);
-              pb0 = phi_bin(G, si, wrap_pi(phip - dphi));
-              const int pb1 = phi_bin(G, si, wrap_pi(phip + dphi));
-              npb = ((pb1 - pb0) % nphi + nphi) % nphi + 1;
+              const float plo = wrap_pi(phip - dphi), phi_ = wrap_pi(phip + dphi);
+              pb0 = phi_bin(G, si, plo);
+              const int pb1 = phi_bin(G, si, phi_);
+              int dp = pb1 - pb0;  // both in [0, nphi)
+              if (dp < 0) dp += nphi;
+              npb = dp + 1;
+              flo = phi_fine(G, si, plo);
+              fhi = phi_fine(G, si, phi_);
             }
             zb0 = second_bin(G, si, cz - d2);
             zb1 = second_bin(G, si, cz + d2);
-            wide = npb > kRows;
+            // One run of sorted positions per (phi bin, 2nd bin) of the window, limited to the phi
+            // sub-bins the window touches in its first and last phi bins.
+            const int nzb = zb1 - zb0 + 1;
+            const int nrun = npb * nzb;
+            wide = nrun > kRows;
             if (!wide) {
               const int n2 = G.n_2nd[si];
-              const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
+              const size_t slab = static_cast<size_t>(ev * G.n_surf + si);
+              const int* off = A.bin_off + slab * (G.n_bins + 1);
+              const unsigned short* sub = A.sub_off + slab * G.n_bins * kPhiSub;
+              int cum = 0, r = 0, zb = zb0;
 #pragma unroll
-              for (int r = 0; r < kRows; ++r) {
+              for (int k = 0; k < kRows; ++k) {
                 int a = 0, b = 0;
-                if (r < npb) {
+                if (k < nrun) {
                   int pb = pb0 + r;
                   if (pb >= nphi) pb -= nphi;
-                  a = __ldg(off + pb * n2 + zb0);
-                  b = __ldg(off + pb * n2 + zb1 + 1);
+                  const int slo = r == 0 ? sub_of(flo, pb) : 0;
+                  const int shi = r == npb - 1 ? sub_of(fhi, pb) : kPhiSub - 1;
+                  const int bb = pb * n2 + zb;
+                  const int s0 = __ldg(off + bb);
+                  a = s0 + (slo > 0 ? __ldg(sub + bb * kPhiSub + slo - 1) : 0);
+                  b = s0 + __ldg(sub + bb * kPhiSub + shi);
+                  if (++zb > zb1) {
+                    zb = zb0;
+                    ++r;
+                  }
                 }
-                W.rowa[r][lane] = a;
-                W.rowb[r][lane] = b;
-                T += b - a;
+                W.rows[k][lane] = make_int2(cum + (b - a), a - cum);
+                cum += b - a;
               }
+              T = cum;
             }
           }
         } else {
@@ -485,21 +612,26 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
     }
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - T;
-    int np = 0;
-    // Buffered passing pairs go to their owner's list: the k_max best by chi2 (plain), or, with the
-    // learned proposal, the top_n best by network score, scored here by all lanes together.
-    // Buffered passing pairs go to their owner's list: the k_max best by chi2 (plain), or, with the
-    // learned proposal, the top_n best by network score. A pair is scored (by all lanes together)
-    // only when its owner has more passing hits than top_n; otherwise every hit is kept anyway.
-    // A flush in the middle of the scan (buffer nearly full) scores all its pairs.
+    int np = 0;      // buffered pairs
+    int my_cnt = 0;  // buffered pairs of this lane's window: one contiguous run of the buffer
+    // Buffered passing pairs go to their owner's list: the k_max best by (total chi2, hit id)
+    // (plain), or, with the learned proposal, the top_n best by network score. A pair is scored
+    // (by all lanes together) only when its owner has more passing hits than top_n; otherwise
+    // every hit is kept anyway. A flush in the middle of the scan (buffer full) scores all its
+    // pairs.
     auto flush = [&](int count, bool final_flush) {
+      int run = my_cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, run, o);
+        if (lane >= o) run += v;
+      }
+      const int start = run - my_cnt;
       if (LEARNED) {
-        int cnt = 0;
-        for (int k = 0; k < count; ++k) cnt += W.pl_own[k] == lane;
-        const bool need = !final_flush || scored || hl_n + cnt > keep;
+        const bool need = !final_flush || scored || hl_n + my_cnt > keep;
         const unsigned needmask = __ballot_sync(kFull, need);
         // Features of the owners that need scores, from their predictions still in registers.
-        if (need && cnt > 0 && !scored) {
+        if (need && my_cnt > 0 && !scored) {
 #pragma unroll
           for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
 #pragma unroll
@@ -509,41 +641,41 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
         }
         __syncwarp();
         for (int k = lane; k < count; k += 32) {
-          const int o = W.pl_own[k];
+          const int o = W.u.pl.own[k];
           if ((needmask >> o) & 1u) {
             float f[kMlpIn];
 #pragma unroll
             for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][o];
-            const int pos = W.pl_pos[k];
-            const float2 h = __ldg(A.sorted_hits + pos);
-            const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
-            const float r0 = W.win[3][o] * resid_angle(W.win[0][o], W.win[1][o], d.x, d.y);
-            const float r1 = h.y - W.win[2][o];
+            const float4 h = __ldg(A.sorted_rec + W.u.pl.pos[k]);
+            float r0, r1;
+            window_chi2(W.win_a[o], W.win_b[o], h, r0, r1);
             f[12] = r0 / WL.feat[12][o];
             f[13] = r1 / WL.feat[13][o];
             WL.pl_sc[k] = mlp_score(wmlp, f);
           }
         }
         __syncwarp();
-        for (int k = 0; k < count; ++k) {
-          if (W.pl_own[k] != lane) continue;
+        for (int k = start; k < start + my_cnt; ++k) {
           if (need) {
-            hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+            hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
           } else {  // kept unconditionally (at most top_n of them)
-            W.hl_c2[hl_n][lane] = W.pl_c2[k];
-            W.hl_id[hl_n][lane] = W.pl_id[k];
-            W.hl_pos[hl_n][lane] = W.pl_pos[k];
+            W.hl_tot[hl_n][lane] = c.chi2 + W.u.pl.c2[k];
+            W.hl_id[hl_n][lane] = W.u.pl.id[k];
+            W.hl_pos[hl_n][lane] = W.u.pl.pos[k];
             ++hl_n;
           }
         }
-        scored = scored || (need && cnt > 0);
+        scored = scored || (need && my_cnt > 0);
       } else {
-        for (int k = 0; k < count; ++k)
-          if (W.pl_own[k] == lane) hl_insert(W, lane, hl_n, keep, W.pl_c2[k], W.pl_id[k], W.pl_pos[k]);
+        for (int k = start; k < start + my_cnt; ++k)
+          hl_insert(W, lane, hl_n, keep, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
       }
+      my_cnt = 0;
     };
     __syncwarp();
     for (int q0 = 0; q0 < total; q0 += 32) {
+      // Owner of hit q (binary search over the inclusive prefix), its position in the index (the
+      // run of the owner's window it falls in) and its search record.
       const int q = q0 + lane;
       int owner = 0;
 #pragma unroll
@@ -552,47 +684,54 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
         if (v <= q) owner += bit;
       }
       owner = min(owner, 31);
-      const int obase = __shfl_sync(kFull, excl, owner);
-      bool pass = false;
-      float c2v = 0.f;
-      int pos = 0, hid = 0;
-      if (q < total) {
-        int o = q - obase;
+      const int o = q - __shfl_sync(kFull, excl, owner);
+      int adj = W.rows[kRows - 1][owner].y;
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const int ra = W.rowa[r][owner];
-          const int len = W.rowb[r][owner] - ra;
-          if (o >= 0 && o < len) pos = ra + o;
-          o -= len;
-        }
-        const float2 h = __ldg(A.sorted_hits + pos);
-        const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
-        const float dphi = resid_angle(W.win[0][owner], W.win[1][owner], d.x, d.y);
-        const float r0 = W.win[3][owner] * dphi, r1 = h.y - W.win[2][owner];
-        c2v = r0 * (W.win[4][owner] * r0 + W.win[5][owner] * r1) + r1 * (W.win[5][owner] * r0 + W.win[6][owner] * r1);
-        pass = c2v < cut;
-        if (pass) hid = __ldg(A.sorted_ids + pos);
+      for (int r = kRows - 2; r >= 0; --r) {
+        const int2 rr = W.rows[r][owner];
+        if (o < rr.x) adj = rr.y;
       }
+      const int pos = o + adj;
+      float c2v = __int_as_float(0x7f800000);
+      int hid = 0;
+      if (q < total) {
+        const float4 h = __ldg(A.sorted_rec + pos);
+        float r0, r1;
+        c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
+        hid = __float_as_int(h.w);
+      }
+      const bool pass = c2v < cut;
       const unsigned m = __ballot_sync(kFull, pass);
-      if (pass) {
-        const int k = np + __popc(m & ((1u << lane) - 1u));
-        W.pl_c2[k] = c2v;
-        W.pl_id[k] = hid;
-        W.pl_pos[k] = pos;
-        W.pl_own[k] = owner;
-      }
-      np += __popc(m);
-      if (np > kPList - 32) {
+      if (np + __popc(m) > kPList) {
         __syncwarp();
         flush(np, false);
         np = 0;
         __syncwarp();
       }
+      // passing hits of this lane's own window in this round
+      const int lo = excl - q0, hi = incl - q0;
+      if (hi > 0 && lo < 32) {
+        const unsigned lom = lo <= 0 ? kFull : (kFull << lo);
+        const unsigned him = hi >= 32 ? kFull : ((1u << hi) - 1u);
+        my_cnt += __popc(m & lom & him);
+      }
+      if (pass) {
+        const int k = np + __popc(m & ((1u << lane) - 1u));
+        W.u.pl.c2[k] = c2v;
+        W.u.pl.id[k] = hid;
+        W.u.pl.pos[k] = pos;
+        if (LEARNED) W.u.pl.own[k] = owner;
+      }
+      np += __popc(m);
     }
     __syncwarp();
     flush(np, true);
-    // Windows wider than kRows phi bins: the owner scans them alone.
+    // Windows with more than kRows bins: the owner scans them alone.
     if (wide) {
+      const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
+      const size_t slab = static_cast<size_t>(ev * G.n_surf + si);
+      const int* off = A.bin_off + slab * (G.n_bins + 1);
+      const unsigned short* sub = A.sub_off + slab * G.n_bins * kPhiSub;
       if (LEARNED) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
@@ -600,34 +739,25 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
         for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
         WL.feat[12][lane] = sqrtf(s00v);
         WL.feat[13][lane] = sqrtf(s11v);
-      }
-      const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
-      const int* off = A.bin_off + static_cast<size_t>(ev * G.n_surf + si) * (G.n_bins + 1);
-      const float w0 = W.win[0][lane], w1 = W.win[1][lane], w2 = W.win[2][lane], w3 = W.win[3][lane];
-      const float i00 = W.win[4][lane], i01 = W.win[5][lane], i11 = W.win[6][lane];
-      for (int r = 0; r < npb; ++r) {
-        int pb = pb0 + r;
-        if (pb >= nphi) pb -= nphi;
-        const int a = __ldg(off + pb * n2 + zb0), b = __ldg(off + pb * n2 + zb1 + 1);
-        for (int pos = a; pos < b; ++pos) {
-          const float2 h = __ldg(A.sorted_hits + pos);
-          const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + pos);
-          const float dphi = resid_angle(w0, w1, d.x, d.y);
-          const float r0 = w3 * dphi, r1 = h.y - w2;
-          const float c2v = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
-          if (c2v < cut) {
-            if (LEARNED) {
+        const float4 wa = W.win_a[lane], wb = W.win_b[lane];
+        for_window_runs(off, sub, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, [&](int a, int b) {
+          for (int p = a; p < b; ++p) {
+            const float4 h = __ldg(A.sorted_rec + p);
+            float r0, r1;
+            const float c2v = window_chi2(wa, wb, h, r0, r1);
+            if (c2v < cut) {
               float f[kMlpIn];
 #pragma unroll
               for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][lane];
               f[12] = r0 / WL.feat[12][lane];
               f[13] = r1 / WL.feat[13][lane];
-              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_score(wmlp, f), c2v, __ldg(A.sorted_ids + pos), pos);
-            } else {
-              hl_insert(W, lane, hl_n, keep, c2v, __ldg(A.sorted_ids + pos), pos);
+              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_score(wmlp, f), c.chi2 + c2v, __float_as_int(h.w), p);
             }
           }
-        }
+        });
+      } else {
+        hl_n = scan_wide(W, lane, hl_n, keep, off, sub, A.sorted_rec, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, cut,
+                         c.chi2);
       }
     }
     // With the learned proposal the kept hits are reordered by chi2 for the ranking below.
@@ -643,56 +773,52 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
     __syncwarp();
 
     // ---- 3. selection of the k_max best children of each seed -----------------------------
-    // Each lane offers the head of its list; a butterfly over the group's lanes (partners outside
-    // the group read themselves) leaves the group minimum in the group's first lane, which then
-    // broadcasts it. Lane j of the group keeps the j-th winner; the winner's lane pops its head.
-    int head = 0;
+    // Each lane offers its children in ranking order (hit children by total chi2, or one miss or
+    // carried child); a child's rank in its seed is its index in its lane's list plus the number
+    // of the group's other children that rank before it. Ranks are distinct (slots differ between
+    // lanes, hit ids within a lane); the child of rank j < k_max goes to the group's slot j.
+    const int nch = (on && kind != 3) ? (kind == 0 ? hl_n : 1) : 0;
+    if (kind == 0) {
+      for (int i = 0; i < hl_n; ++i) W.u.key[i][lane] = pack_key(c.nh + 1, W.hl_tot[i][lane], slot << 2);
+    } else if (nch == 1) {
+      W.u.key[0][lane] = pack_key(c.nh, c.chi2, (slot << 2) | kind);
+      W.hl_id[0][lane] = -1;
+    }
+    W.sel_n[lane] = nch;
+    W.tab_key[lane] = ~0ull;
+    __syncwarp();
+    for (int i = 0; i < nch; ++i) {
+      const unsigned long long mk = W.u.key[i][lane];
+      const int mid = W.hl_id[i][lane];
+      int r = i;
+      for (int sm = 0; sm < KC; ++sm) {
+        if (sm == slot) continue;
+        const int col = gbase + sm;
+        const int nm = W.sel_n[col];
+        for (int j = 0; j < nm; ++j) {
+          const unsigned long long ok = W.u.key[j][col];
+          if (ok < mk || (ok == mk && W.hl_id[j][col] < mid)) ++r;
+          else break;
+        }
+      }
+      if (r >= cap) break;  // later children of this lane rank later still
+      W.tab_key[gbase + r] = mk;
+      W.tab_id[gbase + r] = mid;
+      W.tab_pos[gbase + r] = W.hl_pos[i][lane];
+    }
+    __syncwarp();
     int w_par = 0, w_kind = 3, w_id = -1, w_pos = 0, w_nh = 0;
     float w_c2 = 0.f;
-    for (int w = 0; w < cap; ++w) {
-      unsigned long long key = ~0ull;
-      int hk = 0x7fffffff, kpos = 0;
-      if (on && kind != 3) {
-        if (kind == 0) {
-          if (head < hl_n) {
-            key = pack_key(c.nh + 1, c.chi2 + W.hl_c2[head][lane], slot << 2);
-            hk = W.hl_id[head][lane];
-            kpos = W.hl_pos[head][lane];
-          }
-        } else if (head == 0) {
-          key = pack_key(c.nh, c.chi2, (slot << 2) | kind);
-          hk = -1;
-        }
-      }
-      if (!__any_sync(kFull, key != ~0ull)) break;
-      unsigned long long mk = key;
-      int mh = hk;
-#pragma unroll
-      for (int off = 1; off < KC; off <<= 1) {
-        const int partner = slot ^ off;
-        const int src = (in_grp && partner < KC) ? gbase + partner : lane;
-        const unsigned long long ok = __shfl_sync(kFull, mk, src);
-        const int oh = __shfl_sync(kFull, mh, src);
-        if (ok < mk || (ok == mk && oh < mh)) {
-          mk = ok;
-          mh = oh;
-        }
-      }
-      mk = __shfl_sync(kFull, mk, gbase);
-      mh = __shfl_sync(kFull, mh, gbase);
-      const int pk = static_cast<int>((mk >> 20) & 63ull);
-      const int wslot = pk >> 2;
-      const int wpos = __shfl_sync(kFull, kpos, in_grp ? gbase + wslot : lane);
-      if (on && mk != ~0ull) {
-        if (slot == w) {
-          w_par = wslot;
-          w_kind = pk & 3;
-          w_id = mh;
-          w_pos = wpos;
-          w_nh = 63 - static_cast<int>(mk >> 58);
-          w_c2 = __uint_as_float(static_cast<unsigned>((mk >> 26) & 0xffffffffull));
-        }
-        if (wslot == slot) ++head;
+    if (on) {
+      const unsigned long long mk = W.tab_key[lane];
+      if (mk != ~0ull) {
+        const int pk = static_cast<int>((mk >> 20) & 63ull);
+        w_par = pk >> 2;
+        w_kind = pk & 3;
+        w_id = W.tab_id[lane];
+        w_pos = W.tab_pos[lane];
+        w_nh = 63 - static_cast<int>(mk >> 58);
+        w_c2 = __uint_as_float(static_cast<unsigned>((mk >> 26) & 0xffffffffull));
       }
     }
 
@@ -702,9 +828,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(DevGeom G, FindArgs A) {
     if (won) {
       load_cand(W, gbase + w_par, nc);
       if (w_kind == 0) {
-        const float2 h = __ldg(A.sorted_hits + w_pos);
-        const float2 d = __ldg(reinterpret_cast<const float2*>(A.sorted_dir) + w_pos);
-        update_with(G, nc.surf, nc, h, d);
+        const float4 h = __ldg(A.sorted_rec + w_pos);
+        update_with(G, nc.surf, nc, h);
         nc.chi2 = w_c2;
         nc.nh = w_nh;
       } else if (w_kind == 1) {
@@ -820,7 +945,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   auto occupancy = [&](int blk, size_t* smem_out, int* occ_out) {
     size_t sm = 0;
     dispatch_find(kc, learned, [&](auto k) {
-      sm = warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
+      sm = kGeomBytes + warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
       return KF_OK;
     });
     *smem_out = sm;

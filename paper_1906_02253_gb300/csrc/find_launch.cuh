@@ -12,7 +12,8 @@ struct FindArgs {
   const int* bin_off;
   const float2* sorted_hits;
   const int* sorted_ids;
-  const float* sorted_dir;  // (cos phi, sin phi) per sorted hit
+  const float4* sorted_rec;  // (cos phi, sin phi, second coordinate, id bits) per sorted hit
+  const unsigned short* sub_off;  // per bin: hits with phi sub-bin <= j, j < kPhiSub
   const float2* hits;
   const int* hit_surface;
   const int* seed_hits;

@@ -3,28 +3,33 @@
 // structure behind the per-layer search windows (paper Sec. 3.1) and the reuse of hit data by
 // nearby seeds (Sec. 3.2).
 //
-// One CTA per slab, everything staged in shared memory: the bin of each hit (u16), the bin
-// histogram and its exclusive scan, then an unstable scatter of local hit numbers by shared
-// atomics, then a per-bin insertion sort that restores ascending id (bins hold a handful of
-// hits), then a coalesced gather-write of the sorted hits and ids and, when asked for, of each
-// hit's direction (cos phi, sin phi) so that the search computes residual angles without trig.
+// One CTA per slab, everything staged in shared memory: the bin (u16) and phi sub-bin (u8) of each
+// hit, the bin histogram and its exclusive scan, then an unstable scatter of local hit numbers by
+// shared atomics, then a per-bin insertion sort by (sub-bin, id) (bins hold a handful of hits) and
+// the per-bin sub-bin offsets, then a coalesced gather-write of the sorted hits and ids and, when
+// asked for, of each
+// hit's 16-byte search record (cos phi, sin phi, second coordinate, id), so that the search reads
+// one aligned record per hit and computes residual angles without trig.
 // Global traffic per hit: one 8-byte read (plus an L2 re-read in the gather) and a 12-byte write
-// (20 bytes with directions).
+// (28 bytes with search records).
 #include "kf_math.cuh"
 
 namespace kfgb {
+
+static_assert(kPhiSub == 8, "sub-bin offsets are written as eight 16-bit counts");
 
 __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2* __restrict__ hits,
                                                          const int* __restrict__ slab_off, int n_slabs,
                                                          int cap, int* __restrict__ bin_off,
                                                          float2* __restrict__ sorted_hits,
-                                                         int* __restrict__ sorted_ids, float2* __restrict__ sorted_dir,
-                                                         int* __restrict__ d_status) {
+                                                         int* __restrict__ sorted_ids, float4* __restrict__ sorted_rec,
+                                                         uint4* __restrict__ sub_off, int* __restrict__ d_status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = G.n_bins;
   int* hist = reinterpret_cast<int*>(smem_raw);                       // [nb + 1]
   unsigned short* bin = reinterpret_cast<unsigned short*>(hist + nb + 1);  // [cap]
   unsigned short* order = bin + cap;                                  // [cap]
+  unsigned char* sub = reinterpret_cast<unsigned char*>(order + cap);  // [cap]
   __shared__ int warp_sums[32];
 
   for (int sl = blockIdx.x; sl < n_slabs; sl += gridDim.x) {
@@ -32,8 +37,11 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
     const int h0 = slab_off[sl];
     const int n = slab_off[sl + 1] - h0;
     int* out = bin_off + static_cast<size_t>(sl) * (nb + 1);
+    uint4* sout = sub_off ? sub_off + static_cast<size_t>(sl) * nb : nullptr;
     if (n > cap || n < 0) {
       for (int b = threadIdx.x; b <= nb; b += blockDim.x) out[b] = h0;
+      if (sout)
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) sout[b] = make_uint4(0u, 0u, 0u, 0u);
       if (threadIdx.x == 0 && d_status) atomicOr(d_status, 1);
       __syncthreads();
       continue;
@@ -44,8 +52,10 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const float2 h = hits[h0 + i];
-      const int b = phi_bin(G, si, h.x) * n2 + second_bin(G, si, h.y);
+      const int pb = phi_bin(G, si, h.x);
+      const int b = pb * n2 + second_bin(G, si, h.y);
       bin[i] = static_cast<unsigned short>(b);
+      sub[i] = static_cast<unsigned char>(sub_of(phi_fine(G, si, h.x), pb));
       atomicAdd(&hist[b], 1);
     }
     __syncthreads();
@@ -89,18 +99,39 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
       order[pos] = static_cast<unsigned short>(i);
     }
     __syncthreads();
-    // Restore ascending hit id inside each bin.
-    for (int b = threadIdx.x; b < nbs; b += blockDim.x) {
-      const int e = hist[b];
-      const int s = b > 0 ? hist[b - 1] : 0;
-      for (int i = s + 1; i < e; ++i) {
-        const unsigned short v = order[i];
-        int j = i - 1;
-        while (j >= s && order[j] > v) {
-          order[j + 1] = order[j];
-          --j;
+    // Order each bin by (sub-bin, hit id) and write its sub-bin offsets.
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      unsigned long long c03 = 0, c47 = 0;  // 16-bit hit counts of sub-bins 0-3 and 4-7
+      if (b < nbs) {
+        const int e = hist[b];
+        const int s = b > 0 ? hist[b - 1] : 0;
+        for (int i = s + 1; i < e; ++i) {
+          const unsigned short v = order[i];
+          const unsigned kv = (static_cast<unsigned>(sub[v]) << 16) | v;
+          int j = i - 1;
+          while (j >= s && ((static_cast<unsigned>(sub[order[j]]) << 16) | order[j]) > kv) {
+            order[j + 1] = order[j];
+            --j;
+          }
+          order[j + 1] = v;
         }
-        order[j + 1] = v;
+        for (int i = s; i < e; ++i) {
+          const unsigned sv = sub[order[i]];
+          const unsigned long long inc = 1ull << (16 * (sv & 3));
+          if (sv < 4) c03 += inc;
+          else c47 += inc;
+        }
+      }
+      if (sout) {
+        unsigned cum[kPhiSub];
+        unsigned run = 0;
+#pragma unroll
+        for (int j = 0; j < kPhiSub; ++j) {
+          run += static_cast<unsigned>(((j < 4 ? c03 : c47) >> (16 * (j & 3))) & 0xffffull);
+          cum[j] = run;
+        }
+        sout[b] = make_uint4(cum[0] | (cum[1] << 16), cum[2] | (cum[3] << 16), cum[4] | (cum[5] << 16),
+                             cum[6] | (cum[7] << 16));
       }
     }
     __syncthreads();
@@ -109,10 +140,10 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
       const float2 h = hits[h0 + i];
       sorted_hits[h0 + p] = h;
       sorted_ids[h0 + p] = h0 + i;
-      if (sorted_dir) {
+      if (sorted_rec) {
         float s, c;
         sincosf(h.x, &s, &c);
-        sorted_dir[h0 + p] = make_float2(c, s);
+        sorted_rec[h0 + p] = make_float4(c, s, h.y, __int_as_float(h0 + i));
       }
     }
     __syncthreads();

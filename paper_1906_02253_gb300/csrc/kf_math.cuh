@@ -19,6 +19,7 @@ constexpr int kMaxSurf = 64;
 constexpr float kPiF = 3.14159265358979323846f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kCurvF = 0.00299792458f;  // GeV / (T cm)
+constexpr int kPhiSub = 8;                 // phi sub-bins per phi bin (KF_PHI_SUB)
 
 // Geometry as the kernels see it: passed by value, so it lives in the constant bank.
 struct DevGeom {
@@ -30,9 +31,13 @@ struct DevGeom {
   float r_or_z[kMaxSurf], lo[kMaxSurf], hi[kMaxSurf], x0[kMaxSurf];
   int n_phi[kMaxSurf], n_2nd[kMaxSurf];
   float sphi[kMaxSurf], s2[kMaxSurf];        // FP32 bin scales, rounded once from FP64 on the host
+  float sphi_sub[kMaxSurf];                  // FP32 scale of the fine phi index (n_phi * kPhiSub bins)
   signed char barrel_order[kMaxSurf];        // barrel surfaces by increasing radius
   signed char dpos_order[kMaxSurf];          // disks at z > 0 by increasing z
   signed char dneg_order[kMaxSurf];          // disks at z < 0 by decreasing z
+  signed char ord[kMaxSurf];                 // index of each surface in its order list above
+  float barrel_r[kMaxSurf];                  // radius of barrel_order[i]
+  float dpos_z[kMaxSurf], dneg_z[kMaxSurf];  // z of dpos_order[i], dneg_order[i]
 };
 
 // Packed symmetric 6x6 index, i <= j (upper triangle, row-major).
@@ -130,9 +135,7 @@ __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float 
 
 // Path to the plane z = Z; reached only within half a turn in the transverse plane
 // (|omega s| < pi): beyond that the particle would be coming back inward.
-__device__ __forceinline__ bool path_to_disk(const float* p, float w, float Z, Prop& pr) {
-  float st, ct;
-  sincosf(p[5], &st, &ct);
+__device__ __forceinline__ bool path_to_disk(const float* p, float w, float Z, float st, float ct, Prop& pr) {
   if (ct == 0.f) return false;
   pr.s = (Z - p[2]) * st / ct;
   if (!(pr.s > 0.f)) return false;
@@ -157,13 +160,13 @@ __device__ __forceinline__ float highland_var(float p, float x_over_x0) {
 
 // Move state p and covariance C along the helix by pr.s onto surface `si`; C' = J C J^T + Q where
 // J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface.
-__device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, float* p, float* C, const Prop& pr) {
+// st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation).
+__device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, float* p, float* C, const Prop& pr,
+                                                  float st, float ct) {
   const float a = -kCurvF * G.bz;  // d omega / d kappa
   const float w = a * p[3];
   const float s = pr.s;
   const float D = w * s;
-  float st, ct;
-  sincosf(p[5], &st, &ct);
   const float cot = ct / st;
   const float dx = s * (pr.c0 * pr.f1 - pr.s0 * pr.f2);
   const float dy = s * (pr.s0 * pr.f1 + pr.c0 * pr.f2);
@@ -431,6 +434,17 @@ __device__ __forceinline__ int phi_bin(const DevGeom& G, int si, float phi) {
   const int k = (f >= 0.f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;
   return min(max(k, 0), G.n_phi[si] - 1);
 }
+
+// Fine phi index (n_phi * kPhiSub bins) by the same rule; the sub-bin of a hit in phi-bin pb is
+// clamp(fine - pb * kPhiSub, 0, kPhiSub - 1), non-decreasing in phi within the bin.
+__device__ __forceinline__ int phi_fine(const DevGeom& G, int si, float phi) {
+  const float a = __fmul_rn(__fadd_rn(phi, kPiF), G.sphi_sub[si]);
+  const float f = floorf(a);
+  const int k = (f >= 0.f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;
+  return min(max(k, 0), G.n_phi[si] * kPhiSub - 1);
+}
+
+__device__ __forceinline__ int sub_of(int fine, int pb) { return min(max(fine - pb * kPhiSub, 0), kPhiSub - 1); }
 
 __device__ __forceinline__ int second_bin(const DevGeom& G, int si, float v) {
   const float a = __fmul_rn(__fsub_rn(v, G.lo[si]), G.s2[si]);

@@ -41,22 +41,26 @@ def _index_both(kf, wl, b):
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
     torch.cuda.synchronize()
-    off, sh, si = oracle.build_index(oracle.Geometry(wl), b.hits, b.slab_offsets, b.n_events)
-    return idx, (off, sh, si), dev, g
+    off, sh, si, sub = oracle.build_index(oracle.Geometry(wl), b.hits, b.slab_offsets, b.n_events, with_sub=True)
+    return idx, (off, sh, si, sub), dev, g
 
 
 @pytest.mark.parametrize("wl_name,n_ev,nt", [("find", 3, 2500), ("hi_occ", 2, 1500), ("fit_batched", 2, 20000)])
 def test_hit_index_bit_exact(kf, wl_name, n_ev, nt):
     wl = synth.workload(wl_name, n_events=n_ev, tracks_lo=nt // 2, tracks_hi=nt)
     b = synth.generate(wl)
-    idx, (off, sh, si), _, _ = _index_both(kf, wl, b)
+    idx, (off, sh, si, sub), _, _ = _index_both(kf, wl, b)
     assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
+    assert np.array_equal(idx.sub_off.cpu().numpy().view(np.uint16), sub)
     assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
     assert np.array_equal(idx.sorted_hits.cpu().numpy().view(np.uint32), sh.view(np.uint32))
-    # hit directions: (cos phi, sin phi) of the sorted hits, to FP32 accuracy
-    d = idx.sorted_dir.cpu().numpy().astype(np.float64)
+    # search records: (cos phi, sin phi) to FP32 accuracy, the second coordinate and the id exact
+    rec = idx.sorted_rec.cpu().numpy()
+    d = rec[:, :2].astype(np.float64)
     ph = sh[:, 0].astype(np.float64)
     assert np.abs(d[:, 0] - np.cos(ph)).max() < 3e-7 and np.abs(d[:, 1] - np.sin(ph)).max() < 3e-7
+    assert np.array_equal(rec[:, 2].view(np.uint32), sh[:, 1].view(np.uint32))
+    assert np.array_equal(rec[:, 3].view(np.int32), si)
 
 
 def test_hit_index_edge_cases(kf):
@@ -73,8 +77,9 @@ def test_hit_index_edge_cases(kf):
     slab[0] = 0
     b.hits, b.slab_offsets = hits, slab
     b.hit_surface = np.zeros(n, np.int32)
-    idx, (off, sh, si), _, _ = _index_both(kf, wl, b)
+    idx, (off, sh, si, sub), _, _ = _index_both(kf, wl, b)
     assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
+    assert np.array_equal(idx.sub_off.cpu().numpy().view(np.uint16), sub)
     assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
 
 

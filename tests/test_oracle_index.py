@@ -11,6 +11,16 @@ import oracle
 import synth
 
 
+def _np_sub(wl, surf, phi, pb):
+    """Phi sub-bin: fine = clamp(floor((phi + pi_f) * (float)(n_phi*8/2pi)), 0, n_phi*8 - 1) in
+    float32, then clamp(fine - pb*8, 0, 7)."""
+    s = wl.surfaces[surf]
+    a = (np.asarray(phi, np.float32) + np.float32(np.pi)).astype(np.float32)
+    a = (a * np.float32(s.n_phi * 8 / (2.0 * np.pi))).astype(np.float32)
+    fine = np.clip(np.floor(a), -1, 1e8).astype(np.int64).clip(0, s.n_phi * 8 - 1)
+    return np.clip(fine - pb * 8, 0, 7)
+
+
 def _np_bins(wl, surf, phi, second):
     """phi-bin = clamp(floor((phi + pi_f) * (float)(n_phi/2pi)), 0, n_phi-1); second coordinate
     likewise with (float)(n_2nd / (hi_f - lo_f)); every operation in float32."""
@@ -48,24 +58,47 @@ def test_bin_rule_matches_float32_arithmetic():
 
 
 @pytest.mark.parametrize("wl_name", ["find", "hi_occ"])
-def test_index_is_stable_sort_by_bin(wl_name):
+def test_index_is_sort_by_bin_subbin_id(wl_name):
     wl = synth.workload(wl_name, n_events=2, tracks_lo=400, tracks_hi=600)
     g = oracle.Geometry(wl)
     b = synth.generate(wl)
-    off, sh, si = oracle.build_index(g, b.hits, b.slab_offsets, b.n_events)
+    off, sh, si, sub = oracle.build_index(g, b.hits, b.slab_offsets, b.n_events, with_sub=True)
     ns = b.n_surf
     for sl in range(b.n_events * ns):
         surf = sl % ns
         s = wl.surfaces[surf]
+        nbs = s.n_phi * s.n_2nd
         h0, h1 = b.slab_offsets[sl], b.slab_offsets[sl + 1]
         pb, zb = _np_bins(wl, surf, b.hits[h0:h1, 0], b.hits[h0:h1, 1])
         key = pb * s.n_2nd + zb
-        order = np.argsort(key, kind="stable")
+        sb = _np_sub(wl, surf, b.hits[h0:h1, 0], pb)
+        order = np.lexsort((np.arange(h1 - h0), sb, key))
         assert np.array_equal(si[h0:h1], h0 + order)
         assert np.array_equal(sh[h0:h1], b.hits[h0 + order])
-        counts = np.bincount(key, minlength=s.n_phi * s.n_2nd)
+        counts = np.bincount(key, minlength=nbs)
         assert off[sl, 0] == h0
-        assert np.array_equal(np.diff(off[sl, : s.n_phi * s.n_2nd + 1]), counts)
+        assert np.array_equal(np.diff(off[sl, : nbs + 1]), counts)
+        # sub-bin offsets: hits of each bin with sub-bin <= j
+        per = np.zeros((nbs, 8), np.int64)
+        np.add.at(per, (key, sb), 1)
+        assert np.array_equal(sub[sl, :nbs].astype(np.int64), np.cumsum(per, axis=1))
+        assert not sub[sl, nbs:].any()
+
+
+def test_subbin_rule_is_monotone_within_a_bin():
+    """Within a phi bin the sub-bin never decreases with phi (windows rely on it), including across
+    the rounding of the fine index at the bin edges."""
+    wl = synth.workload("find")
+    g = oracle.Geometry(wl)
+    phi = np.sort(np.concatenate([np.linspace(-np.pi, np.pi, 200001),
+                                  (np.arange(65) * 2 * np.pi / 64 - np.pi)]).astype(np.float32))
+    phi = np.unique(np.concatenate([phi, np.nextafter(phi, np.float32(-10)), np.nextafter(phi, np.float32(10))]))
+    phi = phi[(phi >= -np.float32(np.pi)) & (phi <= np.float32(np.pi))]
+    pb, _ = _np_bins(wl, 0, phi, np.zeros_like(phi))
+    sb = _np_sub(wl, 0, phi, pb)
+    same = pb[1:] == pb[:-1]
+    assert (sb[1:][same] >= sb[:-1][same]).all()
+    assert set(np.unique(sb)) == set(range(8))
 
 
 def _candidate_states(b, g, rng, n):
