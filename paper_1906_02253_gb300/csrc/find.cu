@@ -18,6 +18,7 @@
 //     lane j materialises it (Kalman update for a hit child) from its parent's record;
 //  4. a seed whose candidates have all stopped writes its best track (backtracking a per-step
 //     trace of parent slot and hit) and its lanes take the next seed from an atomic queue.
+// The warps of a block vote once per step (block barrier), which keeps them in the same phase.
 // Seeds are consumed in order (one event after another, neighbouring directions together), so the
 // warps of an SM read neighbouring bins of the same event's index through L1/L2.
 #include <algorithm>
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
     if (k > 0) {
       const float w = -kCurvF * G.bz * c.p[3];
       float st, ct;
-      sincosf(c.p[5], &st, &ct);
+      sincos_small(c.p[5], st, ct);
       Prop pr;
       ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
                               : path_to_disk(c.p, w, G.r_or_z[ss[k]], st, ct, pr);
@@ -412,6 +413,42 @@ __device__ __noinline__ int scan_wide(WarpSmem<KC>& W, int lane, int hl_n, int k
   return hl_n;
 }
 
+// A fresh seed's state (fitted by k_seed_states, structure of arrays with stride n) into the
+// candidate record of `lane`; false for a failed seed. Out of line: once per seed.
+template <int KC>
+__device__ __noinline__ bool load_seed(WarpSmem<KC>& W, int lane, const float* in, int surf, int n) {
+  const float chi2 = in[static_cast<size_t>(27) * n];
+  if (!(chi2 >= 0.f)) return false;
+  for (int i = 0; i < 27; ++i) W.cand[i][lane] = in[static_cast<size_t>(i) * n];
+  W.cand[27][lane] = chi2;
+  W.cand[28][lane] = __int_as_float(3);  // hits
+  W.cand[29][lane] = __int_as_float(0);  // misses
+  W.cand[30][lane] = __int_as_float(0);  // stopped
+  W.cand[31][lane] = __int_as_float(surf);
+  return true;
+}
+
+// Output of a finished seed: the best candidate (slot 0 of the group at gbase) and its hit list,
+// backtracked through the per-step trace of (parent slot, hit id + 1). Out of line: once per seed.
+template <int KC>
+__device__ __noinline__ void write_track(const WarpSmem<KC>& W, const int* trace, int gbase, int step, int seed, int n,
+                                         int lmax, const int* seed_hits, int* hits_out, int* nhits_out,
+                                         float* chi2_out, float* state_out, float* cov_out, int* status_out) {
+  int sl = 0;
+  for (int st = step - 1; st >= 0; --st) {
+    const int e = trace[st * 32 + gbase + sl];
+    hits_out[static_cast<size_t>(3 + st) * n + seed] = (e & ((1 << kHitBits) - 1)) - 1;
+    sl = e >> kHitBits;
+  }
+  for (int k = 3 + step; k < lmax; ++k) hits_out[static_cast<size_t>(k) * n + seed] = -1;
+  for (int k = 0; k < 3; ++k) hits_out[static_cast<size_t>(k) * n + seed] = seed_hits[static_cast<size_t>(k) * n + seed];
+  nhits_out[seed] = __float_as_int(W.cand[28][gbase]);
+  chi2_out[seed] = W.cand[27][gbase];
+  for (int i = 0; i < 6; ++i) state_out[static_cast<size_t>(i) * n + seed] = W.cand[i][gbase];
+  for (int i = 0; i < 21; ++i) cov_out[static_cast<size_t>(i) * n + seed] = W.cand[6 + i][gbase];
+  status_out[seed] = 0;
+}
+
 // Packed ranking key: (63 - hits) << 58 | chi2 bits << 26 | (parent slot << 2 | kind) << 20.
 // For chi2 >= 0 its IEEE bits order like its value (a rounding-negative chi2 ranks as 0); the hit
 // id breaks remaining ties.
@@ -479,29 +516,16 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         ev = A.seed_event[seed];
       }
     }
-    if (!__any_sync(kFull, seed >= 0)) break;
+    // One block-wide vote per step: the block's warps stay in step with each other, so the SM
+    // fetches the code of one or two phases at a time (the kernel is larger than the instruction
+    // cache); the block ends when none of its warps has a seed.
+    if (!__syncthreads_or(seed >= 0)) break;
 
     // ---- a fresh group loads its seed state into slot 0 ------------------------------------
     int failed = 0;
     if (fresh && slot == 0) {
-      const float* in = A.seed_state + seed;
-      const float chi2 = in[static_cast<size_t>(27) * n];
-      if (chi2 >= 0.f) {
-        Cand c;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) c.p[i] = in[static_cast<size_t>(i) * n];
-#pragma unroll
-        for (int i = 0; i < 21; ++i) c.C[i] = in[static_cast<size_t>(6 + i) * n];
-        c.chi2 = chi2;
-        c.nh = 3;
-        c.nm = 0;
-        c.stopped = 0;
-        c.surf = A.seed_surf[seed];
-        store_cand(W, lane, c);
-        valid = true;
-      } else {
-        failed = 1;  // outputs already written by the seed-state kernel
-      }
+      valid = load_seed(W, lane, A.seed_state + seed, A.seed_surf[seed], n);
+      failed = !valid;  // a failed seed's outputs were written by the seed-state kernel
     }
     failed = __shfl_sync(kFull, failed, gbase);
     if (fresh && failed) {
@@ -523,7 +547,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       if (!c.stopped) {
         Prop pr;
         float st, ct;
-        sincosf(c.p[5], &st, &ct);
+        sincos_small(c.p[5], st, ct);
         si = next_surface(G, c.p, c.surf, st, ct, pr);
         if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr, st, ct)) {
           kind = 1;
@@ -673,59 +697,63 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       my_cnt = 0;
     };
     __syncwarp();
-    for (int q0 = 0; q0 < total; q0 += 32) {
-      // Owner of hit q (binary search over the inclusive prefix), its position in the index (the
-      // run of the owner's window it falls in) and its search record.
-      const int q = q0 + lane;
-      int owner = 0;
+    // Rounds of 32 window hits; the buffer is merged after the last round, or earlier when it
+    // could not take another round.
+    for (int q0 = 0;; q0 += 32) {
+      if (q0 < total) {
+        // Owner of hit q (binary search over the inclusive prefix), its position in the index
+        // (the run of the owner's window it falls in) and its search record.
+        const int q = q0 + lane;
+        int owner = 0;
 #pragma unroll
-      for (int bit = 16; bit > 0; bit >>= 1) {
-        const int v = __shfl_sync(kFull, incl, owner + bit - 1);
-        if (v <= q) owner += bit;
-      }
-      owner = min(owner, 31);
-      const int o = q - __shfl_sync(kFull, excl, owner);
-      int adj = W.rows[kRows - 1][owner].y;
+        for (int bit = 16; bit > 0; bit >>= 1) {
+          const int v = __shfl_sync(kFull, incl, owner + bit - 1);
+          if (v <= q) owner += bit;
+        }
+        owner = min(owner, 31);
+        const int o = q - __shfl_sync(kFull, excl, owner);
+        int adj = W.rows[kRows - 1][owner].y;
 #pragma unroll
-      for (int r = kRows - 2; r >= 0; --r) {
-        const int2 rr = W.rows[r][owner];
-        if (o < rr.x) adj = rr.y;
+        for (int r = kRows - 2; r >= 0; --r) {
+          const int2 rr = W.rows[r][owner];
+          if (o < rr.x) adj = rr.y;
+        }
+        const int pos = o + adj;
+        float c2v = __int_as_float(0x7f800000);
+        int hid = 0;
+        if (q < total) {
+          const float4 h = __ldg(A.sorted_rec + pos);
+          float r0, r1;
+          c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
+          hid = __float_as_int(h.w);
+        }
+        const bool pass = c2v < cut;
+        const unsigned m = __ballot_sync(kFull, pass);
+        // passing hits of this lane's own window in this round
+        const int lo = excl - q0, hi = incl - q0;
+        if (hi > 0 && lo < 32) {
+          const unsigned lom = lo <= 0 ? kFull : (kFull << lo);
+          const unsigned him = hi >= 32 ? kFull : ((1u << hi) - 1u);
+          my_cnt += __popc(m & lom & him);
+        }
+        if (pass) {
+          const int k = np + __popc(m & ((1u << lane) - 1u));
+          W.u.pl.c2[k] = c2v;
+          W.u.pl.id[k] = hid;
+          W.u.pl.pos[k] = pos;
+          if (LEARNED) W.u.pl.own[k] = owner;
+        }
+        np += __popc(m);
       }
-      const int pos = o + adj;
-      float c2v = __int_as_float(0x7f800000);
-      int hid = 0;
-      if (q < total) {
-        const float4 h = __ldg(A.sorted_rec + pos);
-        float r0, r1;
-        c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
-        hid = __float_as_int(h.w);
-      }
-      const bool pass = c2v < cut;
-      const unsigned m = __ballot_sync(kFull, pass);
-      if (np + __popc(m) > kPList) {
+      const bool last = q0 + 32 >= total;
+      if (last || np > kPList - 32) {
         __syncwarp();
-        flush(np, false);
+        flush(np, last);
         np = 0;
         __syncwarp();
       }
-      // passing hits of this lane's own window in this round
-      const int lo = excl - q0, hi = incl - q0;
-      if (hi > 0 && lo < 32) {
-        const unsigned lom = lo <= 0 ? kFull : (kFull << lo);
-        const unsigned him = hi >= 32 ? kFull : ((1u << hi) - 1u);
-        my_cnt += __popc(m & lom & him);
-      }
-      if (pass) {
-        const int k = np + __popc(m & ((1u << lane) - 1u));
-        W.u.pl.c2[k] = c2v;
-        W.u.pl.id[k] = hid;
-        W.u.pl.pos[k] = pos;
-        if (LEARNED) W.u.pl.own[k] = owner;
-      }
-      np += __popc(m);
+      if (last) break;
     }
-    __syncwarp();
-    flush(np, true);
     // Windows with more than kRows bins: the owner scans them alone.
     if (wide) {
       const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
@@ -850,27 +878,9 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     if (on) ++step;
     const unsigned live = __ballot_sync(kFull, on && won && !nc.stopped);
     const bool done = on && (((live & gmask) == 0u) || step >= max_steps);
-    if (done && slot == 0) {
-      Cand b;
-      load_cand(W, gbase, b);
-      int sl = 0;
-      for (int st = step - 1; st >= 0; --st) {
-        const int e = trace[st * 32 + gbase + sl];
-        A.hits_out[static_cast<size_t>(3 + st) * n + seed] = (e & ((1 << kHitBits) - 1)) - 1;
-        sl = e >> kHitBits;
-      }
-      for (int k = 3 + step; k < A.lmax; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        A.hits_out[static_cast<size_t>(k) * n + seed] = A.seed_hits[static_cast<size_t>(k) * n + seed];
-      A.nhits_out[seed] = b.nh;
-      A.chi2_out[seed] = b.chi2;
-#pragma unroll
-      for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = b.p[i];
-#pragma unroll
-      for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = b.C[i];
-      A.status_out[seed] = 0;
-    }
+    if (done && slot == 0)
+      write_track(W, trace, gbase, step, seed, n, A.lmax, A.seed_hits, A.hits_out, A.nhits_out, A.chi2_out,
+                  A.state_out, A.cov_out, A.status_out);
     __syncwarp();
     if (done) {
       seed = -1;

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __r
         if (k > 0) {
           const float w = -kCurvF * G.bz * p[3];
           float st, ct;
-          sincosf(p[5], &st, &ct);
+          sincos_small(p[5], st, ct);
           Prop pr;
           const bool ok = G.type[si] == 0 ? path_to_cylinder(p, w, G.r_or_z[si], pr)
                                           : path_to_disk(p, w, G.r_or_z[si], st, ct, pr);

@@ -49,6 +49,29 @@ __device__ __forceinline__ float wrap_pi(float a) {
   return a;
 }
 
+// sin and cos of state angles and half helix steps by the Cody-Waite reduction (W. J. Cody
+// and W. Waite, Software Manual for the Elementary Functions, 1980): x = k pi/2 + r with k =
+// rint(2x/pi) and r = ((x - k P1) - k P2) - k P3, pi/2 = P1 + P2 + P3 split into FP32 parts (each
+// step one fused multiply-add), |r| <= pi/4 up to rounding; then the Taylor series of sin r to r^9
+// and of cos r to r^10 (truncation below 3e-9 at pi/4) and the quadrant rotation by k mod 4. The
+// fused reduction keeps r accurate while k is exact in FP32; beyond |x| = 1e5 (no state angle or
+// helix step comes near) the result is NaN.
+__device__ __forceinline__ void sincos_small(float x, float& s, float& c) {
+  if (!(fabsf(x) <= 1e5f)) x = __int_as_float(0x7fc00000);
+  const float k = rintf(x * 0.636619747f);  // 2/pi
+  float r = fmaf(-k, 1.57079637f, x);
+  r = fmaf(-k, -4.37113883e-08f, r);
+  r = fmaf(-k, -1.71512451e-15f, r);
+  const float r2 = r * r;
+  const float sr = fmaf(r * r2, -1.f / 6.f + r2 * (1.f / 120.f + r2 * (-1.f / 5040.f + r2 * (1.f / 362880.f))), r);
+  const float cr =
+      fmaf(r2, -0.5f + r2 * (1.f / 24.f + r2 * (-1.f / 720.f + r2 * (1.f / 40320.f + r2 * (-1.f / 3628800.f)))), 1.f);
+  const int q = static_cast<int>(k) & 3;  // quadrant (two's complement for k < 0)
+  const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+  s = (q & 2) ? -ss : ss;
+  c = ((q + 1) & 2) ? -cc : cc;
+}
+
 // sin(D/2), cos(D/2) and q = sin(D/2)/(D/2); then f1 = sin(D)/D = q cos(D/2) and
 // f2 = (1 - cos D)/D = q sin(D/2).
 // Below |D/2| = 0.1 (every step of a track above ~0.1 GeV over a few cm) the Taylor series are
@@ -62,7 +85,7 @@ __device__ __forceinline__ void half_angle(float D, float& q, float& sh, float& 
     sh = h * q;
     ch = 1.f + h2 * (-0.5f + h2 * (1.f / 24.f + h2 * (-1.f / 720.f)));
   } else {
-    sincosf(h, &sh, &ch);
+    sincos_small(h, sh, ch);
     q = sh / h;
   }
 }
@@ -97,7 +120,7 @@ __device__ __forceinline__ void prop_eval(Prop& pr, float w) {
 // expansion dp = s t0 + (omega s^2 / 2) n0: (1 + omega B) s^2 + 2 A s + (rho0^2 - R^2) = 0 with
 // A = p0.t0, B = p0.n0 (t0, n0 the unit direction and its left normal).
 __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float R, Prop& pr) {
-  sincosf(p[4], &pr.s0, &pr.c0);
+  sincos_small(p[4], pr.s0, pr.c0);
   const float x0 = p[0], y0 = p[1];
   const float rho0 = sqrtf(x0 * x0 + y0 * y0);
   const float d0 = (rho0 - R) * (rho0 + R);
@@ -115,8 +138,13 @@ __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float 
     pr.s = -d0 / den;
   }
   if (!(pr.s > 0.f)) return false;
-  for (int it = 0; it < 12; ++it) {
+  // At most 12 Newton steps; the helix functions are evaluated once per pass, the last pass at the
+  // final s (one evaluation site keeps the code short).
+  bool done = false;
+#pragma unroll 1
+  for (int it = 0;; ++it) {
     prop_eval(pr, w);
+    if (done || it == 12) break;
     const float dx = pr.s * (pr.c0 * pr.f1 - pr.s0 * pr.f2);
     const float dy = pr.s * (pr.s0 * pr.f1 + pr.c0 * pr.f2);
     const float g = d0 + 2.f * (x0 * dx + y0 * dy) + (dx * dx + dy * dy);
@@ -126,11 +154,9 @@ __device__ __forceinline__ bool path_to_cylinder(const float* p, float w, float 
     if (!(gp > 0.f)) return false;
     const float ds = g / gp;
     pr.s -= ds;
-    if (fabsf(ds) <= 2e-7f * pr.s) break;
+    done = fabsf(ds) <= 2e-7f * pr.s;
   }
-  if (!(pr.s > 0.f)) return false;
-  prop_eval(pr, w);
-  return true;
+  return pr.s > 0.f;
 }
 
 // Path to the plane z = Z; reached only within half a turn in the transverse plane
@@ -140,7 +166,7 @@ __device__ __forceinline__ bool path_to_disk(const float* p, float w, float Z, f
   pr.s = (Z - p[2]) * st / ct;
   if (!(pr.s > 0.f)) return false;
   if (!(fabsf(w * pr.s) < kPiF)) return false;
-  sincosf(p[4], &pr.s0, &pr.c0);
+  sincos_small(p[4], pr.s0, pr.c0);
   prop_eval(pr, w);
   return true;
 }
@@ -302,7 +328,7 @@ __device__ __forceinline__ void meas_setup(const DevGeom& G, int si, const float
 __device__ __forceinline__ void meas_residual(const DevGeom& G, int si, const float* p, float rho, float phi_h,
                                               float v, Meas& m) {
   float sh, ch;
-  sincosf(phi_h, &sh, &ch);
+  sincos_small(phi_h, sh, ch);
   const float x = p[0], y = p[1];
   const float dphi = atan2f(x * sh - y * ch, x * ch + y * sh);
   if (G.type[si] == 0) {
@@ -364,7 +390,7 @@ __device__ __forceinline__ float kalman_update(float* p, float* C, const Innov& 
 __device__ __forceinline__ void hit_xyz(const DevGeom& G, int si, float phi_h, float v, float& x, float& y,
                                         float& z) {
   float sh, ch;
-  sincosf(phi_h, &sh, &ch);
+  sincos_small(phi_h, sh, ch);
   if (G.type[si] == 0) {
     const float R = G.r_or_z[si];
     x = R * ch;
