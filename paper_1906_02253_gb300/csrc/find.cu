@@ -372,47 +372,6 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
   }
 }
 
-// Runs of sorted positions of a window: per phi bin pb0 .. pb0 + npb - 1 (wrapping) and 2nd bin
-// zb0 .. zb1, the sub-bins [sub_of(flo), sub_of(fhi)] of the first and last phi bins and every
-// sub-bin of the others (a phi bin whose sub-bins are all in gives one run over its 2nd bins).
-template <class F>
-__device__ __forceinline__ void for_window_runs(const int* off, const unsigned short* sub, int pb0, int npb, int nphi,
-                                                int n2, int zb0, int zb1, int flo, int fhi, F&& visit) {
-  for (int r = 0; r < npb; ++r) {
-    int pb = pb0 + r;
-    if (pb >= nphi) pb -= nphi;
-    const int slo = r == 0 ? sub_of(flo, pb) : 0;
-    const int shi = r == npb - 1 ? sub_of(fhi, pb) : kPhiSub - 1;
-    if (slo == 0 && shi == kPhiSub - 1) {
-      visit(__ldg(off + pb * n2 + zb0), __ldg(off + pb * n2 + zb1 + 1));
-    } else {
-      for (int zb = zb0; zb <= zb1; ++zb) {
-        const int bb = pb * n2 + zb;
-        const int s0 = __ldg(off + bb);
-        visit(s0 + (slo > 0 ? __ldg(sub + bb * kPhiSub + slo - 1) : 0), s0 + __ldg(sub + bb * kPhiSub + shi));
-      }
-    }
-  }
-}
-
-// Window with more than kRows bins (large uncertainty, or a full ring): the owner lane scans it
-// alone. Out of line: rare.
-template <int KC>
-__device__ __noinline__ int scan_wide(WarpSmem<KC>& W, int lane, int hl_n, int keep, const int* off,
-                                      const unsigned short* sub, const float4* rec, int pb0, int npb, int nphi,
-                                      int n2, int zb0, int zb1, int flo, int fhi, float cut, float chi2) {
-  const float4 wa = W.win_a[lane], wb = W.win_b[lane];
-  for_window_runs(off, sub, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, [&](int a, int b) {
-    for (int p = a; p < b; ++p) {
-      const float4 h = __ldg(rec + p);
-      float r0, r1;
-      const float c2v = window_chi2(wa, wb, h, r0, r1);
-      if (c2v < cut) hl_insert(W, lane, hl_n, keep, chi2 + c2v, __float_as_int(h.w), p);
-    }
-  });
-  return hl_n;
-}
-
 // A fresh seed's state (fitted by k_seed_states, structure of arrays with stride n) into the
 // candidate record of `lane`; false for a failed seed. Out of line: once per seed.
 template <int KC>
@@ -537,10 +496,11 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     // ---- 1. propagation and window set-up -------------------------------------------------
     Cand c;
     int kind = 3;  // 0 hit children, 1 miss child, 2 carried, 3 empty slot
-    int si = -1, T = 0, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, flo = 0, fhi = 0, hl_n = 0;
+    // Window: phi bins pb0 .. pb0 + npb - 1 (wrapping), 2nd bins zb0 .. zb1, fine phi range
+    // [flo, fhi]; its runs are enumerated from the cursor (row, zrun), row == npb when done.
+    int si = -1, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, flo = 0, fhi = 0, hl_n = 0, row = 0, zrun = 0;
     bool scored = false;  // learned: this lane's kept hits carry network scores
     float s00v = 1.f, s11v = 1.f;  // innovation variances of this lane's window
-    bool wide = false;
     if (on && valid) {
       load_cand(W, lane, c);
       kind = 2;
@@ -587,39 +547,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
             }
             zb0 = second_bin(G, si, cz - d2);
             zb1 = second_bin(G, si, cz + d2);
-            // One run of sorted positions per (phi bin, 2nd bin) of the window, limited to the phi
-            // sub-bins the window touches in its first and last phi bins.
-            const int nzb = zb1 - zb0 + 1;
-            const int nrun = npb * nzb;
-            wide = nrun > kRows;
-            if (!wide) {
-              const int n2 = G.n_2nd[si];
-              const size_t slab = static_cast<size_t>(ev * G.n_surf + si);
-              const int* off = A.bin_off + slab * (G.n_bins + 1);
-              const unsigned short* sub = A.sub_off + slab * G.n_bins * kPhiSub;
-              int cum = 0, r = 0, zb = zb0;
-#pragma unroll
-              for (int k = 0; k < kRows; ++k) {
-                int a = 0, b = 0;
-                if (k < nrun) {
-                  int pb = pb0 + r;
-                  if (pb >= nphi) pb -= nphi;
-                  const int slo = r == 0 ? sub_of(flo, pb) : 0;
-                  const int shi = r == npb - 1 ? sub_of(fhi, pb) : kPhiSub - 1;
-                  const int bb = pb * n2 + zb;
-                  const int s0 = __ldg(off + bb);
-                  a = s0 + (slo > 0 ? __ldg(sub + bb * kPhiSub + slo - 1) : 0);
-                  b = s0 + __ldg(sub + bb * kPhiSub + shi);
-                  if (++zb > zb1) {
-                    zb = zb0;
-                    ++r;
-                  }
-                }
-                W.rows[k][lane] = make_int2(cum + (b - a), a - cum);
-                cum += b - a;
-              }
-              T = cum;
-            }
+            zrun = zb0;
           }
         } else {
           si = -1;
@@ -628,14 +556,14 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     }
 
     // ---- 2. cooperative chi2 over every window hit of the warp ------------------------------
-    int incl = T;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - T;
+    // Passes: every lane lists its next kRows runs of sorted positions (one per (phi bin, 2nd bin)
+    // of its window, limited to the sub-bins its phi range touches; a phi bin whose sub-bins are
+    // all in gives one run over its 2nd bins); the runs of the warp are flattened with a prefix
+    // sum and scanned in rounds of 32 hits; passes repeat while any lane has runs left.
+    const size_t slab = static_cast<size_t>(ev * G.n_surf + (si >= 0 ? si : 0));
+    const int* off = A.bin_off + slab * (G.n_bins + 1);
+    const unsigned short* sub = A.sub_off + slab * G.n_bins * kPhiSub;
+    const int nphi = si >= 0 ? G.n_phi[si] : 1, n2 = si >= 0 ? G.n_2nd[si] : 1;
     int np = 0;      // buffered pairs
     int my_cnt = 0;  // buffered pairs of this lane's window: one contiguous run of the buffer
     // Buffered passing pairs go to their owner's list: the k_max best by (total chi2, hit id)
@@ -696,97 +624,104 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       }
       my_cnt = 0;
     };
-    __syncwarp();
-    // Rounds of 32 window hits; the buffer is merged after the last round, or earlier when it
-    // could not take another round.
-    for (int q0 = 0;; q0 += 32) {
-      if (q0 < total) {
-        // Owner of hit q (binary search over the inclusive prefix), its position in the index
-        // (the run of the owner's window it falls in) and its search record.
-        const int q = q0 + lane;
-        int owner = 0;
-#pragma unroll
-        for (int bit = 16; bit > 0; bit >>= 1) {
-          const int v = __shfl_sync(kFull, incl, owner + bit - 1);
-          if (v <= q) owner += bit;
-        }
-        owner = min(owner, 31);
-        const int o = q - __shfl_sync(kFull, excl, owner);
-        int adj = W.rows[kRows - 1][owner].y;
-#pragma unroll
-        for (int r = kRows - 2; r >= 0; --r) {
-          const int2 rr = W.rows[r][owner];
-          if (o < rr.x) adj = rr.y;
-        }
-        const int pos = o + adj;
-        float c2v = __int_as_float(0x7f800000);
-        int hid = 0;
-        if (q < total) {
-          const float4 h = __ldg(A.sorted_rec + pos);
-          float r0, r1;
-          c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
-          hid = __float_as_int(h.w);
-        }
-        const bool pass = c2v < cut;
-        const unsigned m = __ballot_sync(kFull, pass);
-        // passing hits of this lane's own window in this round
-        const int lo = excl - q0, hi = incl - q0;
-        if (hi > 0 && lo < 32) {
-          const unsigned lom = lo <= 0 ? kFull : (kFull << lo);
-          const unsigned him = hi >= 32 ? kFull : ((1u << hi) - 1u);
-          my_cnt += __popc(m & lom & him);
-        }
-        if (pass) {
-          const int k = np + __popc(m & ((1u << lane) - 1u));
-          W.u.pl.c2[k] = c2v;
-          W.u.pl.id[k] = hid;
-          W.u.pl.pos[k] = pos;
-          if (LEARNED) W.u.pl.own[k] = owner;
-        }
-        np += __popc(m);
-      }
-      const bool last = q0 + 32 >= total;
-      if (last || np > kPList - 32) {
-        __syncwarp();
-        flush(np, last);
-        np = 0;
-        __syncwarp();
-      }
-      if (last) break;
-    }
-    // Windows with more than kRows bins: the owner scans them alone.
-    if (wide) {
-      const int nphi = G.n_phi[si], n2 = G.n_2nd[si];
-      const size_t slab = static_cast<size_t>(ev * G.n_surf + si);
-      const int* off = A.bin_off + slab * (G.n_bins + 1);
-      const unsigned short* sub = A.sub_off + slab * G.n_bins * kPhiSub;
-      if (LEARNED) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
-        WL.feat[12][lane] = sqrtf(s00v);
-        WL.feat[13][lane] = sqrtf(s11v);
-        const float4 wa = W.win_a[lane], wb = W.win_b[lane];
-        for_window_runs(off, sub, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, [&](int a, int b) {
-          for (int p = a; p < b; ++p) {
-            const float4 h = __ldg(A.sorted_rec + p);
-            float r0, r1;
-            const float c2v = window_chi2(wa, wb, h, r0, r1);
-            if (c2v < cut) {
-              float f[kMlpIn];
-#pragma unroll
-              for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][lane];
-              f[12] = r0 / WL.feat[12][lane];
-              f[13] = r1 / WL.feat[13][lane];
-              hl_insert_scored(W, WL, lane, hl_n, keep, mlp_score(wmlp, f), c.chi2 + c2v, __float_as_int(h.w), p);
+    for (;;) {
+      int T = 0;
+#pragma unroll 1
+      for (int k = 0; k < kRows; ++k) {
+        int a = 0, b = 0;
+        if (row < npb) {
+          int pb = pb0 + row;
+          if (pb >= nphi) pb -= nphi;
+          const int slo = row == 0 ? sub_of(flo, pb) : 0;
+          const int shi = row == npb - 1 ? sub_of(fhi, pb) : kPhiSub - 1;
+          if (slo == 0 && shi == kPhiSub - 1) {
+            a = __ldg(off + pb * n2 + zb0);
+            b = __ldg(off + pb * n2 + zb1 + 1);
+            ++row;
+          } else {
+            const int bb = pb * n2 + zrun;
+            const int s0 = __ldg(off + bb);
+            a = s0 + (slo > 0 ? __ldg(sub + bb * kPhiSub + slo - 1) : 0);
+            b = s0 + __ldg(sub + bb * kPhiSub + shi);
+            if (++zrun > zb1) {
+              zrun = zb0;
+              ++row;
             }
           }
-        });
-      } else {
-        hl_n = scan_wide(W, lane, hl_n, keep, off, sub, A.sorted_rec, pb0, npb, nphi, n2, zb0, zb1, flo, fhi, cut,
-                         c.chi2);
+        }
+        W.rows[k][lane] = make_int2(T + (b - a), a - T);
+        T += b - a;
       }
+      const bool more = __any_sync(kFull, row < npb);
+      int incl = T;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - T;
+      __syncwarp();
+      // Rounds of 32 hits; the buffer is merged after the last round of each pass (pairs of one
+      // pass are in owner order, so each owner's pairs are one run of the buffer), or earlier when
+      // it could not take another round.
+      for (int q0 = 0;; q0 += 32) {
+        if (q0 < total) {
+          // Owner of hit q (binary search over the inclusive prefix), its position in the index
+          // (the run of the owner's list it falls in) and its search record.
+          const int q = q0 + lane;
+          int owner = 0;
+#pragma unroll
+          for (int bit = 16; bit > 0; bit >>= 1) {
+            const int v = __shfl_sync(kFull, incl, owner + bit - 1);
+            if (v <= q) owner += bit;
+          }
+          owner = min(owner, 31);
+          const int o = q - __shfl_sync(kFull, excl, owner);
+          int adj = W.rows[kRows - 1][owner].y;
+#pragma unroll
+          for (int r = kRows - 2; r >= 0; --r) {
+            const int2 rr = W.rows[r][owner];
+            if (o < rr.x) adj = rr.y;
+          }
+          const int pos = o + adj;
+          float c2v = __int_as_float(0x7f800000);
+          int hid = 0;
+          if (q < total) {
+            const float4 h = __ldg(A.sorted_rec + pos);
+            float r0, r1;
+            c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
+            hid = __float_as_int(h.w);
+          }
+          const bool pass = c2v < cut;
+          const unsigned m = __ballot_sync(kFull, pass);
+          // passing hits of this lane's own runs in this round
+          const int lo = excl - q0, hi = incl - q0;
+          if (hi > 0 && lo < 32) {
+            const unsigned lom = lo <= 0 ? kFull : (kFull << lo);
+            const unsigned him = hi >= 32 ? kFull : ((1u << hi) - 1u);
+            my_cnt += __popc(m & lom & him);
+          }
+          if (pass) {
+            const int k = np + __popc(m & ((1u << lane) - 1u));
+            W.u.pl.c2[k] = c2v;
+            W.u.pl.id[k] = hid;
+            W.u.pl.pos[k] = pos;
+            if (LEARNED) W.u.pl.own[k] = owner;
+          }
+          np += __popc(m);
+        }
+        const bool last = q0 + 32 >= total;
+        if (last || np > kPList - 32) {
+          __syncwarp();
+          flush(np, last && !more);
+          np = 0;
+          __syncwarp();
+        }
+        if (last) break;
+      }
+      if (!more) break;
+      __syncwarp();
     }
     // With the learned proposal the kept hits are reordered by chi2 for the ranking below.
     if (LEARNED && hl_n > 0) hl_sort_by_chi2(W, lane, hl_n, cap);
