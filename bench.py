@@ -416,12 +416,14 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     if counters is None:
         return {"kernel": "k_find_tracks", "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None}
-    n_prop, n_pass, n_upd, n_scan = counters
-    per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_scan * FLOP_CHI2
+    # chi2 work: the hits of the windows the finder scans (limited to the phi sub-bins they touch)
+    n_prop, n_pass, n_upd, n_scan, n_win = counters
+    per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
     ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
     return {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz",
-            "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_scan, "flop": per_seed}}
+            "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win, "chi2_whole_bins": n_scan,
+                              "flop": per_seed}}
 
 
 def main():

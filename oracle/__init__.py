@@ -245,7 +245,7 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     """Combinatorial finding from seeds; with ``mlp`` = (weights, mean, sd) and top_n > 0 the
     learned proposal keeps the top_n passing hits by score. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
-    evaluated in a window)."""
+    evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch)."""
     lib = _load()
     wl = geom.wl
     prm = OrFindParams(wl.chi2_cut if chi2_cut is None else chi2_cut, wl.k_max if k_max is None else k_max,
@@ -259,7 +259,7 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     lmax = wl.lmax
     out = dict(hits=np.empty((n, lmax), np.int32), n_hits=np.empty(n, np.int32), chi2=np.empty(n),
                p=np.empty((n, 6)), cov=np.empty((n, 21)), status=np.empty(n, np.int32))
-    counters = np.zeros(4, np.int64)
+    counters = np.zeros(5, np.int64)
     lib.or_find(geom.ref, hits.ctypes.data, hs.ctypes.data, so.ctypes.data, batch.n_events, sh.ctypes.data,
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,

@@ -493,14 +493,14 @@ struct BinRule {
     const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
     return std::min(std::max(k, 0), n_phi - 1);
   }
-  int sub_bin(float phi) const {
+  int fine_bin(float phi) const {
     const float a = phi + pi_f;
     const float b = a * sphi_sub;
     const float f = std::floor(b);
     const int k = (f >= 0.0f) ? (f > 1e8f ? 100000000 : static_cast<int>(f)) : -1;  // NaN -> -1
-    const int fine = std::min(std::max(k, 0), n_phi * kSub - 1);
-    return std::min(std::max(fine - phi_bin(phi) * kSub, 0), kSub - 1);
+    return std::min(std::max(k, 0), n_phi * kSub - 1);
   }
+  int sub_bin(float phi) const { return std::min(std::max(fine_bin(phi) - phi_bin(phi) * kSub, 0), kSub - 1); }
   int second_bin(float v) const {
     const float a = v - lo;
     const float b = a * s2;
@@ -733,7 +733,7 @@ struct Ctx {
 // Binned: the window is the bounding box of the chi2 ellipse, padded, turned into bin ranges by
 // the same FP32 rule as the index; brute force: every hit of the surface.
 void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<Found>& out,
-                 long long* scanned = nullptr) {
+                 long long* scanned = nullptr, long long* window_hits = nullptr) {
   out.clear();
   const OrGeom& g = *cx.g;
   const OrSurface& S = g.surf[si];
@@ -783,6 +783,25 @@ void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<F
     const long long a = o[pb * S.n_2nd + zb0], b = o[pb * S.n_2nd + zb1 + 1];
     for (long long q = a; q < b; ++q) try_hit(cx.ix->sorted[2 * q], cx.ix->sorted[2 * q + 1], cx.ix->ids[q]);
   }
+  if (window_hits) {
+    // Hits of the window limited to the phi sub-bins its phi range touches in its first and last
+    // phi bins (a count only: the search above scans whole bins).
+    int flo = 0, fhi = S.n_phi * kSub - 1;
+    if (npb < S.n_phi) {
+      flo = br.fine_bin(static_cast<float>(wrap_angle(phip - dphi)));
+      fhi = br.fine_bin(static_cast<float>(wrap_angle(phip + dphi)));
+    }
+    const unsigned short* sb = &cx.ix->sub[static_cast<size_t>(sl) * cx.ix->nb * kSub];
+    for (int k = 0; k < npb; ++k) {
+      const int pb = (pb0 + k) % S.n_phi;
+      const int slo = k == 0 ? std::min(std::max(flo - pb * kSub, 0), kSub - 1) : 0;
+      const int shi = k == npb - 1 ? std::min(std::max(fhi - pb * kSub, 0), kSub - 1) : kSub - 1;
+      for (int zb = zb0; zb <= zb1; ++zb) {
+        const int b = pb * S.n_2nd + zb;
+        *window_hits += sb[b * kSub + shi] - (slo > 0 ? sb[b * kSub + slo - 1] : 0);
+      }
+    }
+  }
 }
 
 struct Child {
@@ -803,7 +822,7 @@ bool child_less(const Child& a, const Child& b) {
 }
 
 struct Counters {
-  long long n_prop = 0, n_chi2 = 0, n_upd = 0, n_scan = 0;
+  long long n_prop = 0, n_chi2 = 0, n_upd = 0, n_scan = 0, n_win = 0;
 };
 
 // Beam search for one seed. Returns false if the seed could not be formed.
@@ -855,7 +874,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       }
       cnt.n_prop++;
       pred_surf[ci] = si;
-      search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan);
+      search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan, &cnt.n_win);
       cnt.n_chi2 += static_cast<long long>(found.size());
       if (sink) {  // training pairs: every passing (candidate, hit) pair, labelled by truth
         double f[kIn];
@@ -1094,8 +1113,9 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 // top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
 // that has more. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
-// status (0 ok, 1 seed failed). counters[4] += propagations, chi2 evaluations that passed the
-// cut, Kalman updates, hits whose chi2 was evaluated (window scans).
+// status (0 ok, 1 seed failed). counters[5] += propagations, chi2 evaluations that passed the
+// cut, Kalman updates, hits whose chi2 was evaluated (whole bins of the windows), hits of the
+// windows limited to the phi sub-bins their phi range touches.
 void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
@@ -1103,7 +1123,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
   Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}};
-  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0);
+  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;
     Counters cnt;
@@ -1117,6 +1137,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     c_prop += cnt.n_prop;
     c_chi2 += cnt.n_chi2;
     c_scan += cnt.n_scan;
+    c_win += cnt.n_win;
     c_upd += cnt.n_upd;
   });
   if (counters) {
@@ -1124,6 +1145,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     counters[1] += c_chi2.load();
     counters[2] += c_upd.load();
     counters[3] += c_scan.load();
+    counters[4] += c_win.load();
   }
 }
 

@@ -147,3 +147,18 @@ def test_binned_and_brute_force_finding_agree(wl_name):
     for k in ("hits", "n_hits", "status"):
         assert np.array_equal(a[k], c[k])
     assert np.array_equal(a["chi2"], c["chi2"])
+
+
+@pytest.mark.parametrize("wl_name", ["find", "hi_occ"])
+def test_window_counters_are_ordered(wl_name):
+    """The windows limited to the phi sub-bins they touch hold every hit that passes the cut and
+    no more hits than the windows' whole bins: passing <= sub-bin window hits <= whole-bin hits."""
+    wl = synth.workload(wl_name, n_events=2, tracks_lo=300, tracks_hi=300, noise_frac=1.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    c = oracle.find(g, b, sh, b.track_event[st])["counters"]
+    n_prop, n_pass, n_upd, n_scan, n_win = (int(v) for v in c)
+    n_window_pass = n_pass - 3 * len(st)  # the pass counter includes the three seed-hit updates
+    assert 0 < n_window_pass <= n_win <= n_scan
+    assert n_win < n_scan  # the sub-bins cut the scan on these windows
