@@ -41,7 +41,7 @@ static_assert(sizeof(DevGeom) % 4 == 0, "geometry is copied in 4-byte words");
 
 template <int KC>
 struct WarpSmem {
-  float cand[kWords][32];  // candidate records, one column per lane
+  float4 cand[kWords / 4][32];  // candidate records: words 4i..4i+3 of lane l at [i][l]
   float4 win_a[32];        // window of each lane: x, y, centre of the 2nd coordinate, transverse scale
   float4 win_b[32];        // S^-1 (00, 01, 11) and the far-hit threshold of window_chi2
   int2 rows[kRows][32];    // runs: (end of the run in the lane's flattened window, position - start)
@@ -138,28 +138,50 @@ struct Cand {
 
 template <int KC>
 __device__ __forceinline__ void load_cand(const WarpSmem<KC>& W, int col, Cand& c) {
+  float v[kWords];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) c.p[i] = W.cand[i][col];
+  for (int i = 0; i < kWords / 4; ++i) {
+    const float4 q = W.cand[i][col];
+    v[4 * i] = q.x;
+    v[4 * i + 1] = q.y;
+    v[4 * i + 2] = q.z;
+    v[4 * i + 3] = q.w;
+  }
 #pragma unroll
-  for (int i = 0; i < 21; ++i) c.C[i] = W.cand[6 + i][col];
-  c.chi2 = W.cand[27][col];
-  c.nh = __float_as_int(W.cand[28][col]);
-  c.nm = __float_as_int(W.cand[29][col]);
-  c.stopped = __float_as_int(W.cand[30][col]);
-  c.surf = __float_as_int(W.cand[31][col]);
+  for (int i = 0; i < 6; ++i) c.p[i] = v[i];
+#pragma unroll
+  for (int i = 0; i < 21; ++i) c.C[i] = v[6 + i];
+  c.chi2 = v[27];
+  c.nh = __float_as_int(v[28]);
+  c.nm = __float_as_int(v[29]);
+  c.stopped = __float_as_int(v[30]);
+  c.surf = __float_as_int(v[31]);
 }
 
 template <int KC>
 __device__ __forceinline__ void store_cand(WarpSmem<KC>& W, int col, const Cand& c) {
+  float v[kWords];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) W.cand[i][col] = c.p[i];
+  for (int i = 0; i < 6; ++i) v[i] = c.p[i];
 #pragma unroll
-  for (int i = 0; i < 21; ++i) W.cand[6 + i][col] = c.C[i];
-  W.cand[27][col] = c.chi2;
-  W.cand[28][col] = __int_as_float(c.nh);
-  W.cand[29][col] = __int_as_float(c.nm);
-  W.cand[30][col] = __int_as_float(c.stopped);
-  W.cand[31][col] = __int_as_float(c.surf);
+  for (int i = 0; i < 21; ++i) v[6 + i] = c.C[i];
+  v[27] = c.chi2;
+  v[28] = __int_as_float(c.nh);
+  v[29] = __int_as_float(c.nm);
+  v[30] = __int_as_float(c.stopped);
+  v[31] = __int_as_float(c.surf);
+#pragma unroll
+  for (int i = 0; i < kWords / 4; ++i) W.cand[i][col] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+// Word w of lane col's candidate record.
+template <int KC>
+__device__ __forceinline__ float& cand_word(WarpSmem<KC>& W, int w, int col) {
+  return reinterpret_cast<float*>(&W.cand[w >> 2][col])[w & 3];
+}
+template <int KC>
+__device__ __forceinline__ float cand_word(const WarpSmem<KC>& W, int w, int col) {
+  return reinterpret_cast<const float*>(&W.cand[w >> 2][col])[w & 3];
 }
 
 // Full-range angle, out of line: only hits far from the prediction in azimuth need it.
@@ -378,12 +400,12 @@ template <int KC>
 __device__ __noinline__ bool load_seed(WarpSmem<KC>& W, int lane, const float* in, int surf, int n) {
   const float chi2 = in[static_cast<size_t>(27) * n];
   if (!(chi2 >= 0.f)) return false;
-  for (int i = 0; i < 27; ++i) W.cand[i][lane] = in[static_cast<size_t>(i) * n];
-  W.cand[27][lane] = chi2;
-  W.cand[28][lane] = __int_as_float(3);  // hits
-  W.cand[29][lane] = __int_as_float(0);  // misses
-  W.cand[30][lane] = __int_as_float(0);  // stopped
-  W.cand[31][lane] = __int_as_float(surf);
+  for (int i = 0; i < 27; ++i) cand_word(W, i, lane) = in[static_cast<size_t>(i) * n];
+  cand_word(W, 27, lane) = chi2;
+  cand_word(W, 28, lane) = __int_as_float(3);  // hits
+  cand_word(W, 29, lane) = __int_as_float(0);  // misses
+  cand_word(W, 30, lane) = __int_as_float(0);  // stopped
+  cand_word(W, 31, lane) = __int_as_float(surf);
   return true;
 }
 
@@ -401,10 +423,10 @@ __device__ __noinline__ void write_track(const WarpSmem<KC>& W, const int* trace
   }
   for (int k = 3 + step; k < lmax; ++k) hits_out[static_cast<size_t>(k) * n + seed] = -1;
   for (int k = 0; k < 3; ++k) hits_out[static_cast<size_t>(k) * n + seed] = seed_hits[static_cast<size_t>(k) * n + seed];
-  nhits_out[seed] = __float_as_int(W.cand[28][gbase]);
-  chi2_out[seed] = W.cand[27][gbase];
-  for (int i = 0; i < 6; ++i) state_out[static_cast<size_t>(i) * n + seed] = W.cand[i][gbase];
-  for (int i = 0; i < 21; ++i) cov_out[static_cast<size_t>(i) * n + seed] = W.cand[6 + i][gbase];
+  nhits_out[seed] = __float_as_int(cand_word(W, 28, gbase));
+  chi2_out[seed] = cand_word(W, 27, gbase);
+  for (int i = 0; i < 6; ++i) state_out[static_cast<size_t>(i) * n + seed] = cand_word(W, i, gbase);
+  for (int i = 0; i < 21; ++i) cov_out[static_cast<size_t>(i) * n + seed] = cand_word(W, 6 + i, gbase);
   status_out[seed] = 0;
 }
 
