@@ -40,6 +40,12 @@ WORKLOAD = "fit_batched"
 #   chi2 of one hit in a search window ...................................... 20
 #   seed from three hits ..................................................... 80
 FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
+# DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch on 30 events, per seed; profiles/step_kernels_fit_batched_100ev.md), valid while the
+# finder's sources are the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
+FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
+                "paper_1906_02253_gb300/csrc/find_launch.cuh")
+FIND_PROFILE = {"sources_sha1": "811f43ea2165f415e35701b4c8333d3a03575119", "dram_bytes_per_seed": 161488384 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 8 B direction) plus
 # the bin offsets written per (event, surface).
 INDEX_BYTES_PER_HIT = 28
@@ -393,6 +399,15 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     return res
 
 
+def find_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in FIND_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     """Roofline of the dominant kernel. The finder and the fit are FP32-ALU bound (no dense
     contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM clock. The index is HBM bound."""
@@ -420,8 +435,10 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     n_prop, n_pass, n_upd, n_scan, n_win = counters
     per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
     ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
+    traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if find_sources_sha1() == FIND_PROFILE["sources_sha1"] else None
     return {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz",
+            "frac": ach / alu_peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu, scaled by seeds)",
+            "peak_note": f"FP32 {sm_mhz:.0f} MHz",
             "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win, "chi2_whole_bins": n_scan,
                               "flop": per_seed}}
 
