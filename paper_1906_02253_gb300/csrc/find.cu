@@ -63,13 +63,9 @@ struct WarpSmem {
   } u;
 };
 
-// Learned proposal, per warp: each lane's features (predicted state, log covariance diagonal,
-// sqrt of the two innovation variances), the scores of buffered passing pairs, and the score of
-// each kept hit.
+// Learned proposal, per warp: the network score of each kept hit.
 template <int KC>
 struct WarpLearned {
-  float feat[kMlpIn][32];
-  float pl_sc[kPList];
   float hl_sc[KC][32];
 };
 
@@ -439,10 +435,6 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
          (static_cast<unsigned long long>(pk) << 20);
 }
 
-// Network score of a pair, out of line: scoring is rare (only windows with more passing hits
-// than top_n), so it does not set the finder's register budget.
-__device__ __noinline__ float mlp_score(const float* w, const float* f) { return mlp_logit(w, f); }
-
 template <int KC, bool LEARNED>
 __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -464,7 +456,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   int* trace = reinterpret_cast<int*>(wbase + sizeof(WarpSmem<KC>));  // [step][32]
   WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
-  const float* wmlp = A.mlp;  // read through L1/L2: scoring is rare
+  const float* __restrict__ wmlp = A.mlp_t;  // transposed network parameters (L1/L2)
   const int keep = LEARNED ? A.top_n : A.k_max;  // capacity of a lane's list during the scan
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
@@ -603,36 +595,47 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       const int start = run - my_cnt;
       if (LEARNED) {
         const bool need = !final_flush || scored || hl_n + my_cnt > keep;
-        const unsigned needmask = __ballot_sync(kFull, need);
-        // Features of the owners that need scores, from their predictions still in registers.
-        if (need && my_cnt > 0 && !scored) {
+        const unsigned needmask = __ballot_sync(kFull, need && my_cnt > 0);
+        if (needmask) {
+          // Every lane's raw candidate features (predicted state, log covariance diagonal) and the
+          // square roots of its innovation variances; an owner's reach the warp by shuffles.
+          float fe[kMlpIn];
 #pragma unroll
-          for (int i = 0; i < 6; ++i) WL.feat[i][lane] = c.p[i];
+          for (int i = 0; i < 6; ++i) fe[i] = c.p[i];
 #pragma unroll
-          for (int i = 0; i < 6; ++i) WL.feat[6 + i][lane] = logf(c.C[ci(i, i)] + 1e-12f);
-          WL.feat[12][lane] = sqrtf(s00v);
-          WL.feat[13][lane] = sqrtf(s11v);
-        }
-        __syncwarp();
-        for (int k = lane; k < count; k += 32) {
-          const int o = W.u.pl.own[k];
-          if ((needmask >> o) & 1u) {
-            float f[kMlpIn];
+          for (int i = 0; i < 6; ++i) fe[6 + i] = logf(c.C[ci(i, i)] + 1e-12f);
+          fe[12] = sqrtf(s00v);
+          fe[13] = sqrtf(s11v);
+          // The pairs of those owners in buffer order (owner by owner), each scored by the whole
+          // warp; the owner keeps its top_n by score as they come.
+          int prev = -1;
+          float2 base = make_float2(0.f, 0.f);
+          float d12 = 1.f, d13 = 1.f;
+          for (int k = 0; k < count; ++k) {
+            const int o = W.u.pl.own[k];
+            if (!((needmask >> o) & 1u)) continue;
+            if (o != prev) {
+              float x[12];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) f[i] = WL.feat[i][o];
+              for (int i = 0; i < 12; ++i)
+                x[i] = (__shfl_sync(kFull, fe[i], o) - __ldg(wmlp + kMlpMean + i)) / __ldg(wmlp + kMlpSd + i);
+              base = mlp_layer1_base(wmlp, x, lane);
+              d12 = __shfl_sync(kFull, fe[12], o);
+              d13 = __shfl_sync(kFull, fe[13], o);
+              prev = o;
+            }
             const float4 h = __ldg(A.sorted_rec + W.u.pl.pos[k]);
             float r0, r1;
             window_chi2(W.win_a[o], W.win_b[o], h, r0, r1);
-            f[12] = r0 / WL.feat[12][o];
-            f[13] = r1 / WL.feat[13][o];
-            WL.pl_sc[k] = mlp_score(wmlp, f);
+            const float x12 = (r0 / d12 - __ldg(wmlp + kMlpMean + 12)) / __ldg(wmlp + kMlpSd + 12);
+            const float x13 = (r1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
+            const float sc = mlp_logit_warp(wmlp, base, x12, x13, lane);
+            if (lane == o)
+              hl_insert_scored(W, WL, lane, hl_n, keep, sc, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
           }
         }
-        __syncwarp();
-        for (int k = start; k < start + my_cnt; ++k) {
-          if (need) {
-            hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
-          } else {  // kept unconditionally (at most top_n of them)
+        if (!need) {  // kept unconditionally (at most top_n of them)
+          for (int k = start; k < start + my_cnt; ++k) {
             W.hl_tot[hl_n][lane] = c.chi2 + W.u.pl.c2[k];
             W.hl_id[hl_n][lane] = W.u.pl.id[k];
             W.hl_pos[hl_n][lane] = W.u.pl.pos[k];
@@ -966,19 +969,22 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
   plan->off_state = 256;  // after the work counter
   plan->off_surf = up(plan->off_state + static_cast<size_t>(kSeedWords) * n_seeds * sizeof(float));
-  plan->ws_bytes = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
+  plan->off_mlp = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
+  plan->ws_bytes = learned ? up(plan->off_mlp + static_cast<size_t>(kMlpParamsAll) * sizeof(float)) : plan->off_mlp;
   return KF_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
-// Scratch of the allocation-free entry point (kf_find_tracks_static): the work counter and the
-// seed states for at most KF_STATIC_MAX_SEEDS seeds, laid out as plan_find lays out a caller's
-// workspace. A fixed array in the library: every GPU that loads the library holds it until the
+// Scratch of the allocation-free entry point (kf_find_tracks_static): the work counter, the seed
+// states for at most KF_STATIC_MAX_SEEDS seeds and the learned proposal's transposed parameters,
+// laid out as plan_find lays out a caller's workspace. A fixed array in the library: every GPU that loads the library holds it until the
 // process exits. In host code g_find_scratch only names the array; its device address comes from
 // cudaGetSymbolAddress, looked up once per device.
 constexpr size_t static_scratch_bytes() {
-  return ((256 + static_cast<size_t>(kSeedWords) * KF_STATIC_MAX_SEEDS * sizeof(float) + 255) / 256 * 256 +
-          static_cast<size_t>(KF_STATIC_MAX_SEEDS) * sizeof(int) + 255) /
+  return (((256 + static_cast<size_t>(kSeedWords) * KF_STATIC_MAX_SEEDS * sizeof(float) + 255) / 256 * 256 +
+           static_cast<size_t>(KF_STATIC_MAX_SEEDS) * sizeof(int) + 255) /
+              256 * 256 +
+          static_cast<size_t>(kMlpParamsAll) * sizeof(float) + 255) /
          256 * 256;
 }
 static_assert(static_scratch_bytes() == KF_STATIC_SCRATCH_BYTES, "header and library disagree on the scratch size");
@@ -1002,6 +1008,12 @@ int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, c
   A.counter = reinterpret_cast<int*>(base);
   A.seed_state = reinterpret_cast<float*>(base + plan.off_state);
   A.seed_surf = reinterpret_cast<int*>(base + plan.off_surf);
+  A.mlp_t = nullptr;
+  if (plan.learned) {
+    float* wt = reinterpret_cast<float*>(base + plan.off_mlp);
+    if (launch_mlp_transpose(A.mlp, wt, stream) != 0) return KF_ERR_CUDA;
+    A.mlp_t = wt;
+  }
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
   k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, A);
   dispatch_find(plan.kc, plan.learned, [&](auto k) {

@@ -22,7 +22,8 @@ struct FindArgs {
   int n_events;  // events in the index; seeds naming another event fail (status 1)
   float chi2_cut;
   int k_max, max_miss, lmax;
-  const float* mlp;  // learned proposal parameters (KF_MLP_BUFFER floats) or null
+  const float* mlp;    // learned proposal parameters (KF_MLP_BUFFER floats) or null
+  const float* mlp_t;  // their transposed copy in the workspace (set by launch_find)
   int top_n;         // > 0 with mlp: keep the top_n passing hits by score
   int* hits_out;
   int* nhits_out;
@@ -42,7 +43,7 @@ struct FindPlan {
   int kc, block, grid;
   bool learned;
   size_t smem;
-  size_t off_state, off_surf, ws_bytes;
+  size_t off_state, off_surf, off_mlp, ws_bytes;
 };
 
 int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan);

@@ -22,6 +22,28 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ p
   logits[s] = mlp_logit(w, x);
 }
 
+// Transposed copy for the finder (layout in mlp.cuh).
+__global__ void k_mlp_transpose(const float* __restrict__ w, float* __restrict__ wt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParamsAll; i += gridDim.x * blockDim.x) {
+    float v;
+    if (i < kMlpB1) {  // W1T[in][j] = W1[j][in]
+      const int in = i / kMlpHid, j = i % kMlpHid;
+      v = w[kMlpW1 + j * kMlpIn + in];
+    } else if (i >= kMlpW2 && i < kMlpB2) {  // W2T[in][o] = W2[o][in]
+      const int in = (i - kMlpW2) / kMlpHid, o = (i - kMlpW2) % kMlpHid;
+      v = w[kMlpW2 + o * kMlpHid + in];
+    } else {
+      v = w[i];
+    }
+    wt[i] = v;
+  }
+}
+
+int launch_mlp_transpose(const float* params, float* wt, cudaStream_t st) {
+  k_mlp_transpose<<<(kMlpParamsAll + 255) / 256, 256, 0, st>>>(params, wt);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 // Loss and gradient summed over the samples of a block of kGradBlock threads (one sample each):
 // activations and their gradients in shared memory (rows padded to 65 words), then each thread
 // reduces a stripe of parameters over the block's samples and adds it to the global sums.
