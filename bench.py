@@ -183,7 +183,10 @@ def run_gpu(args, wl, batch):
     n_seeds = host["seed_hits"].shape[1]
     n_hits = batch.n_hits
     lmax = wl.lmax
-    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm)
+    import synth
+    steer = synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3) if args.steering else None
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm,
+                         steering_tables=steer)
 
     # Device inputs and preallocated outputs.
     d = {k: v.to(dev) for k, v in host.items() if isinstance(v, torch.Tensor)}
@@ -326,6 +329,7 @@ def run_gpu(args, wl, batch):
            "config": {"workload": wl.name, "events": batch.n_events, "seeds": n_seeds, "hits": n_hits,
                       "layers": len(wl.surfaces), "k_max": wl.k_max, "chi2_cut": wl.chi2_cut,
                       "step": "hit index + find + fit, one CUDA graph", "l2": "flushed between steps (256 MB write)",
+                      "next_surface": "region steering (eta edges 0.4, 1.8)" if args.steering else "geometric rule",
                       "parallelism": f"events sharded over {ws} GPU(s), no collective"},
            "gpu_launches": launches_per_step * args.steps, "autotune": tuning,
            "kernel_ms": kern_ms, "efficiency": eff, "fake_rate": fake, "fit_ok_fraction": fit_ok,
@@ -375,6 +379,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     for top_n in (1, 2, 4):
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
                             mlp=buf, top_n=top_n)
+        lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
         lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
         times = []
         for i in range(args.warmup + args.steps):
@@ -458,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration")
+    ap.add_argument("--steering", action="store_true",
+                    help="region steering lists (5 eta regions) instead of the geometric next-surface rule")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

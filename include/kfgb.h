@@ -94,6 +94,23 @@ typedef struct {
   unsigned short* sub_off;
 } KfHitIndex;
 
+/* Steering of the finder by tracking region (Sec. 3.1: five regions in eta, each with the layers
+ * its track finding traverses). Regions: 0 barrel, 1 +z transition, 2 -z transition, 3 +z endcap,
+ * 4 -z endcap. A seed's region comes from its third hit, (z, rho) = (z, R) on a barrel and (Z, r)
+ * on a disk: barrel if |z| <= c_barrel * rho, else transition if |z| <= c_endcap * rho, else
+ * endcap; +z side when z > 0 (each product one FP32 multiplication, rounded to nearest). Its
+ * candidates step through surf[region][0 .. n[region]-1], starting after the position of the
+ * third hit's surface in that list (from the first entry if it is absent): at each step a
+ * candidate moves to the next listed surface it reaches within the surface's extent (barrel: the
+ * z extent; disk: the r extent, within half a turn), passing over surfaces it cannot reach; at the
+ * end of its list it stops. Host memory, read during the call. */
+#define KF_N_REGIONS 5
+typedef struct {
+  float c_barrel, c_endcap;
+  int n[KF_N_REGIONS];
+  signed char surf[KF_N_REGIONS][KF_MAX_SURF];
+} KfSteering;
+
 /* Finder settings. chi2_cut: hits with predicted chi2 below it make children; k_max: candidates
  * kept per seed (<= KF_MAX_K); max_miss: surfaces a candidate may cross without a hit; lmax:
  * length of each output hit list (3 seed hits + at most lmax-3 steps; 4 <= lmax <= KF_MAX_LMAX);
@@ -116,6 +133,11 @@ typedef struct {
   /* Candidate capacity of the compiled kernel (one of 1, 2, 4, 6, 8, 16, >= k_max and top_n);
    * 0 picks the smallest that fits. A larger capacity gives the same results. */
   int k_capacity;
+  /* Region steering (see KfSteering), or NULL for the geometric rule: the next surface is the
+   * nearer of the next barrel layer beyond the candidate's radius (crossed within its z extent)
+   * and the next disk beyond |z| in the direction of motion (crossed within its r extent, within
+   * half a turn). */
+  const KfSteering* steering;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,

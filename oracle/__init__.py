@@ -87,7 +87,7 @@ def _load():
             lib.or_next_surface.argtypes = [G, _P, _P]
             lib.or_find.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_longlong, ctypes.c_int,
                                     ctypes.POINTER(OrFindParams), ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
-                                    _P, _P, _P, ctypes.c_int]
+                                    _P, _P, _P, ctypes.c_int, ctypes.POINTER(OrSteering)]
             lib.or_mlp_nparams.restype = ctypes.c_int
             lib.or_find_pairs.restype = ctypes.c_longlong
             lib.or_find_pairs.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_longlong,
@@ -240,10 +240,29 @@ def next_surface(geom: Geometry, p):
     return k, s.value
 
 
+class OrSteering(ctypes.Structure):
+    _fields_ = [("c_barrel", ctypes.c_float), ("c_endcap", ctypes.c_float), ("n", ctypes.c_int * 5),
+                ("surf", (ctypes.c_int * 64) * 5)]
+
+
+def _steering(st):
+    """OrSteering from a dict(c_barrel, c_endcap, lists=[5 lists of surface ids]) or None."""
+    if st is None:
+        return None
+    o = OrSteering()
+    o.c_barrel, o.c_endcap = float(st["c_barrel"]), float(st["c_endcap"])
+    for r, lst in enumerate(st["lists"]):
+        o.n[r] = len(lst)
+        for q, sid in enumerate(lst):
+            o.surf[r][q] = int(sid)
+    return o
+
+
 def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=None, max_miss=None,
-         brute_force: bool = False, n_threads: int = 0, mlp=None, top_n: int = 0):
+         brute_force: bool = False, n_threads: int = 0, mlp=None, top_n: int = 0, steering=None):
     """Combinatorial finding from seeds; with ``mlp`` = (weights, mean, sd) and top_n > 0 the
-    learned proposal keeps the top_n passing hits by score. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
+    learned proposal keeps the top_n passing hits by score; ``steering`` (synth.steering_tables)
+    replaces the geometric next-surface rule by the region lists. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
     evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch)."""
     lib = _load()
@@ -263,7 +282,8 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     lib.or_find(geom.ref, hits.ctypes.data, hs.ctypes.data, so.ctypes.data, batch.n_events, sh.ctypes.data,
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,
-                out["status"].ctypes.data, counters.ctypes.data, *_mlp_ptrs(mlp), int(top_n))
+                out["status"].ctypes.data, counters.ctypes.data, *_mlp_ptrs(mlp), int(top_n),
+                None if steering is None else ctypes.byref(_steering(steering)))
     out["counters"] = counters
     return out
 

@@ -53,6 +53,13 @@ struct OrGeom {
   float sigma_rphi, sigma_2nd;
   float prior[5];  // sd of u, second coordinate, kappa, phi, theta at the first hit
 };
+// Region steering of the finder (Sec. 3.1 tracking regions): five regions in eta (0 barrel, 1/2
+// +z/-z transition, 3/4 +z/-z endcap), each with its ordered list of surfaces.
+struct OrSteering {
+  float c_barrel, c_endcap;
+  int n[5];
+  int surf[5][64];
+};
 struct OrFindParams {
   float chi2_cut;
   int k_max;
@@ -573,6 +580,7 @@ struct Cand {
   int n_hits = 0, n_miss = 0;
   double chi2 = 0.0;
   int surf = -1;
+  int pos = -1;  // position of surf in the steering list of the seed's region
   bool stopped = false;
   std::vector<int> hits;  // hit id per step, -1 = miss
 };
@@ -727,7 +735,51 @@ struct Ctx {
   const Index* ix;
   OrFindParams prm;
   Mlp mlp;
+  const OrSteering* steer = nullptr;  // region steering, or null for the geometric rule
 };
+
+// Whether the helix from st reaches surface s within its extent (the acceptance used by the
+// geometric rule: barrel z extent; disk r extent, the disk path rule included).
+bool reaches(const OrGeom& g, const State& st, int s) {
+  const OrSurface& S = g.surf[s];
+  double len, q[6];
+  if (S.type == 0) {
+    if (!path_to_cylinder(g, st.p, S.r_or_z, len)) return false;
+    helix_at(g, st.p, len, q);
+    return q[2] >= S.lo && q[2] <= S.hi;
+  }
+  if (!path_to_disk(g, st.p, S.r_or_z, len)) return false;
+  helix_at(g, st.p, len, q);
+  const double r = std::hypot(q[0], q[1]);
+  return r >= S.lo && r <= S.hi;
+}
+
+// Region of a seed from its third hit (phi, v) on surface s3: (z, rho) = (v, R) on a barrel and
+// (Z, v) on a disk; barrel if |z| <= c_barrel * rho, transition if |z| <= c_endcap * rho, else
+// endcap, +z side for z > 0. The products are FP32 (no contraction in this build), as the
+// steering defines them.
+int seed_region(const OrGeom& g, const OrSteering& sg, int s3, float v) {
+  const OrSurface& S = g.surf[s3];
+  const float z = S.type == 0 ? v : S.r_or_z;
+  const float rho = S.type == 0 ? S.r_or_z : v;
+  const float az = std::fabs(z);
+  const float lb = sg.c_barrel * rho;
+  if (az <= lb) return 0;
+  const float le = sg.c_endcap * rho;
+  return (az <= le ? 1 : 3) + (z > 0.0f ? 0 : 1);
+}
+
+// Next surface of a steered candidate: the first surface of its region's list after position
+// pos that it reaches; -1 at the end of the list.
+int next_steered(const OrGeom& g, const OrSteering& sg, int region, int pos, const State& st, int* newpos) {
+  for (int q = pos + 1; q < sg.n[region]; ++q) {
+    if (reaches(g, st, sg.surf[region][q])) {
+      *newpos = q;
+      return sg.surf[region][q];
+    }
+  }
+  return -1;
+}
 
 // All hits of surface si in event ev whose chi2 against the predicted state is below the cut.
 // Binned: the window is the bounding box of the chi2 ellipse, padded, turned into bin ranges by
@@ -850,6 +902,13 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
     c0.surf = si;
   }
   c0.n_hits = 3;
+  int region = 0;
+  if (cx.steer) {
+    const int id3 = seed_ids[2];
+    region = seed_region(g, *cx.steer, c0.surf, cx.hits[2 * id3 + 1]);
+    for (int q = 0; q < cx.steer->n[region]; ++q)
+      if (cx.steer->surf[region][q] == c0.surf) c0.pos = q;
+  }
   std::vector<Cand> cands{c0};
   std::vector<Found> found;
   std::vector<Child> pool;
@@ -860,20 +919,22 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
     if (!any_active) break;
     pool.clear();
     pred.assign(cands.size(), State());
-    std::vector<int> pred_surf(cands.size(), -1);
+    std::vector<int> pred_surf(cands.size(), -1), pred_pos(cands.size(), -1);
     for (int ci = 0; ci < static_cast<int>(cands.size()); ++ci) {
       const Cand& c = cands[ci];
       if (c.stopped) {
         pool.push_back({ci, -1, 2, c.n_hits, c.chi2, 0.0});
         continue;
       }
-      const int si = next_surface(g, c.st, nullptr);
+      int np = -1;
+      const int si = cx.steer ? next_steered(g, *cx.steer, region, c.pos, c.st, &np) : next_surface(g, c.st, nullptr);
       if (si < 0 || !propagate(g, c.st, si, pred[ci])) {
         pool.push_back({ci, -1, 2, c.n_hits, c.chi2, 0.0});
         continue;
       }
       cnt.n_prop++;
       pred_surf[ci] = si;
+      pred_pos[ci] = np;
       search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan, &cnt.n_win);
       cnt.n_chi2 += static_cast<long long>(found.size());
       if (sink) {  // training pairs: every passing (candidate, hit) pair, labelled by truth
@@ -921,6 +982,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       } else {
         n.st = pred[ch.parent];
         n.surf = pred_surf[ch.parent];
+        n.pos = pred_pos[ch.parent];
         if (ch.kind == 0) {
           Meas m;
           measure(g, n.surf, n.st.p, cx.hits[2 * ch.hit], cx.hits[2 * ch.hit + 1], m);
@@ -1113,16 +1175,18 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 // top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
 // that has more. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
-// status (0 ok, 1 seed failed). counters[5] += propagations, chi2 evaluations that passed the
+// status (0 ok, 1 seed failed). steering: region steering lists, or null for the geometric
+// next-surface rule. counters[5] += propagations, chi2 evaluations that passed the
 // cut, Kalman updates, hits whose chi2 was evaluated (whole bins of the windows), hits of the
 // windows limited to the phi sub-bins their phi range touches.
 void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
-             long long* counters, const double* mlp_w, const double* mlp_mean, const double* mlp_sd, int top_n) {
+             long long* counters, const double* mlp_w, const double* mlp_mean, const double* mlp_sd, int top_n,
+             const OrSteering* steering) {
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
-  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}};
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}, steering};
   std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;

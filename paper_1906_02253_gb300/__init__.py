@@ -43,10 +43,19 @@ class KfHitIndex(ctypes.Structure):
                 ("sorted_hits", ctypes.c_void_p), ("sorted_ids", ctypes.c_void_p), ("sorted_rec", ctypes.c_void_p), ("sub_off", ctypes.c_void_p)]
 
 
+N_REGIONS, MAX_SURF = 5, 64  # KF_N_REGIONS, KF_MAX_SURF
+
+
+class KfSteering(ctypes.Structure):
+    _fields_ = [("c_barrel", ctypes.c_float), ("c_endcap", ctypes.c_float), ("n", ctypes.c_int * N_REGIONS),
+                ("surf", (ctypes.c_byte * MAX_SURF) * N_REGIONS)]
+
+
 class KfFindParams(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int)]
+                ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int),
+                ("steering", ctypes.POINTER(KfSteering))]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
@@ -198,16 +207,38 @@ def fit_tracks(geom: Geometry, hits, hit_surface, track_hits, out: dict = None, 
     return out
 
 
+def steering(tables: dict) -> KfSteering:
+    """KfSteering from dict(c_barrel, c_endcap, lists=[5 lists of surface ids]) (marshalling only)."""
+    st = KfSteering()
+    st.c_barrel, st.c_endcap = float(tables["c_barrel"]), float(tables["c_endcap"])
+    lists = tables["lists"]
+    if len(lists) != N_REGIONS:
+        raise KfError(f"steering needs {N_REGIONS} region lists")
+    for r, lst in enumerate(lists):
+        if len(lst) > MAX_SURF:
+            raise KfError("steering list longer than the surface limit")
+        st.n[r] = len(lst)
+        for q, sid in enumerate(lst):
+            st.surf[r][q] = int(sid)
+    return st
+
+
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
-                blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0) -> KfFindParams:
-    """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal)."""
+                blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0,
+                steering_tables: dict = None) -> KfFindParams:
+    """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
+    ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
+    next-surface rule."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
             raise KfError(f"mlp must hold {MLP_BUFFER} floats")
+    st = None if steering_tables is None else steering(steering_tables)
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
-                       None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity))
+                       None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity),
+                       None if st is None else ctypes.pointer(st))
     prm._mlp_ref = mlp  # keep the buffer alive with the parameters
+    prm._steer_ref = st
     return prm
 
 
@@ -346,7 +377,8 @@ def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits,
     out = find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, params, stream=stream)
     ws = out["workspace"]
     tuned = KfFindParams.from_buffer_copy(params)
-    tuned._mlp_ref = getattr(params, "_mlp_ref", None)
+    tuned._mlp_ref = getattr(params, "_mlp_ref", None)  # keep what the copied pointers point to alive
+    tuned._steer_ref = getattr(params, "_steer_ref", None)
     ms = ctypes.c_float()
     rc = load_library().kf_autotune_find(geom.ref, ctypes.byref(index.c), _ptr(hits), _ptr(hit_surface),
                                          _ptr(seed_hits), _ptr(seed_event), seed_hits.shape[1], ctypes.byref(tuned),

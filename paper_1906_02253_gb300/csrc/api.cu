@@ -90,6 +90,31 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
   return KF_OK;
 }
 
+// Region steering tables into the kernels' geometry (steer = 0 without them).
+static int pack_steering(const KfSteering* st, DevGeom* d) {
+  d->steer = 0;
+  d->c_barrel = d->c_endcap = 0.f;
+  std::memset(d->steer_n, 0, sizeof(d->steer_n));
+  std::memset(d->steer_list, -1, sizeof(d->steer_list));
+  std::memset(d->steer_pos, -1, sizeof(d->steer_pos));
+  if (!st) return KF_OK;
+  if (!(st->c_barrel >= 0.f) || !(st->c_endcap >= st->c_barrel) || !std::isfinite(st->c_endcap)) return KF_ERR_ARG;
+  for (int r = 0; r < KF_N_REGIONS; ++r) {
+    if (st->n[r] < 0 || st->n[r] > KF_MAX_SURF) return KF_ERR_ARG;
+    for (int q = 0; q < st->n[r]; ++q) {
+      const int s = st->surf[r][q];
+      if (s < 0 || s >= d->n_surf || d->steer_pos[r][s] >= 0) return KF_ERR_ARG;  // in range, listed once
+      d->steer_list[r][q] = static_cast<signed char>(s);
+      d->steer_pos[r][s] = static_cast<signed char>(q);
+    }
+    d->steer_n[r] = st->n[r];
+  }
+  d->steer = 1;
+  d->c_barrel = st->c_barrel;
+  d->c_endcap = st->c_endcap;
+  return KF_OK;
+}
+
 static int sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -224,6 +249,8 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   int rc = pack_geometry(geom, &G);
   if (rc != KF_OK) return rc;
   if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
+  rc = pack_steering(params->steering, &G);
+  if (rc != KF_OK) return rc;
   FindPlan plan;
   rc = plan_find(n_seeds, params, sm_count(), &plan);
   if (rc != KF_OK) return rc;
@@ -288,6 +315,8 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   int rc = pack_geometry(geom, &G);
   if (rc != KF_OK) return rc;
   if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
+  rc = pack_steering(params->steering, &G);
+  if (rc != KF_OK) return rc;
   if (n_seeds > KF_STATIC_MAX_SEEDS) return KF_ERR_CAPACITY;
   FindPlan plan;
   rc = plan_find(n_seeds, params, sm_count(), &plan);

@@ -129,7 +129,7 @@ struct Cand {
   float p[6];
   float C[21];
   float chi2;
-  int nh, nm, stopped, surf;
+  int nh, nm, stopped, surf;  // surf: (position in the steering list + 1) << 8 | surface id
 };
 
 template <int KC>
@@ -273,55 +273,98 @@ __device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int
   ++n;
 }
 
-// Next surface outward and the path to it: the next barrel layer beyond the candidate's radius
-// (accepted if crossed within its z extent) and the next disk beyond |z| in the direction of
-// motion (accepted if crossed within its r extent and half a turn); the nearer one. -1 if none.
-// The layer lists are sorted, so each "next" is a lower bound, searched from the candidate's
-// current surface `cur` (one or two steps). st, ct: sin and cos of the polar angle p[5].
-__device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, float st, float ct,
-                                            Prop& best) {
+// Whether the helix from state p reaches surface s within its extent (barrel: z extent; disk: r
+// extent, within half a turn), and the path to it. st, ct: sin and cos of the polar angle p[5].
+__device__ __forceinline__ bool reach_surface(const DevGeom& G, const float* p, float w, int s, float st, float ct,
+                                              float cot, Prop& pr) {
+  if (G.type[s] == 0) {
+    // z moves monotonically along the helix: past the z extent and moving away, it stays out.
+    if ((cot >= 0.f && p[2] > G.hi[s]) || (cot <= 0.f && p[2] < G.lo[s])) return false;
+    if (!path_to_cylinder(p, w, G.r_or_z[s], pr)) return false;
+    const float z = p[2] + pr.s * cot;
+    return z >= G.lo[s] && z <= G.hi[s];
+  }
+  if (!path_to_disk(p, w, G.r_or_z[s], st, ct, pr)) return false;
+  float x, y, z;
+  prop_position(p, pr, cot, x, y, z);
+  const float r = sqrtf(x * x + y * y);
+  return r >= G.lo[s] && r <= G.hi[s];
+}
+
+// Region of a seed from its third hit h on surface s3 (KfSteering): (z, rho) = (z, R) on a barrel,
+// (Z, r) on a disk; barrel if |z| <= c_barrel rho, transition if |z| <= c_endcap rho, else endcap,
+// +z side for z > 0 (regions 0 barrel, 1/2 transition, 3/4 endcap).
+__device__ __forceinline__ int seed_region(const DevGeom& G, int s3, float2 h) {
+  const bool barrel = G.type[s3] == 0;
+  const float z = barrel ? h.y : G.r_or_z[s3];
+  const float rho = barrel ? G.r_or_z[s3] : h.y;
+  const float az = fabsf(z);
+  if (az <= __fmul_rn(G.c_barrel, rho)) return 0;
+  return (az <= __fmul_rn(G.c_endcap, rho) ? 1 : 3) + (z > 0.f ? 0 : 1);
+}
+
+// Next surface of a candidate and the path to it; -1 if none. With region steering: the next
+// surface of the region's list after position pos that the candidate reaches (its position goes
+// to newpos). Geometric rule: the next barrel layer beyond the candidate's radius (accepted if
+// crossed within its z extent) and the next disk beyond |z| in the direction of motion (accepted if
+// crossed within its r extent and half a turn), the nearer one; the layer lists are sorted, so
+// each "next" is a lower bound, searched from the candidate's current surface `cur`. The barrel
+// candidate of the geometric rule is tried in straight-line code; disks and steering lists go
+// through one loop (a single further copy of the path solvers in the code).
+__device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, int region, int pos, float st,
+                                            float ct, Prop& best, int& newpos) {
   const float w = -kCurvF * G.bz * p[3];
-  const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
   const float cot = ct / st;
-  const bool cur_ok = cur >= 0 && cur < G.n_surf;
-  int sel = -1;
-  {
+  const bool steer = G.steer != 0;
+  int sb = -1, sd = -1;  // geometric candidates: next barrel layer, next disk
+  if (!steer) {
+    const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
+    const bool cur_ok = cur >= 0 && cur < G.n_surf;
     const float lim = rho + 0.01f;  // first barrel radius above lim
     int i = (cur_ok && G.type[cur] == 0) ? max(0, static_cast<int>(G.ord[cur])) : 0;
     while (i > 0 && G.barrel_r[i - 1] > lim) --i;
     while (i < G.n_barrel && !(G.barrel_r[i] > lim)) ++i;
-    if (i < G.n_barrel) {
+    if (i < G.n_barrel) sb = G.barrel_order[i];
+    if (cot > 0.f || cot < 0.f) {
+      const bool fwd = cot > 0.f;
+      const int nd = fwd ? G.n_dpos : G.n_dneg;
+      const float* zs = fwd ? G.dpos_z : G.dneg_z;
+      const float zlo = p[2] + 0.01f, zhi = p[2] - 0.01f;  // first disk beyond z in the direction of motion
+      int j = (cur_ok && G.type[cur] != 0 && ((G.r_or_z[cur] > 0.f) == fwd)) ? max(0, static_cast<int>(G.ord[cur])) : 0;
+      while (j > 0 && (fwd ? zs[j - 1] > zlo : zs[j - 1] < zhi)) --j;
+      while (j < nd && !(fwd ? zs[j] > zlo : zs[j] < zhi)) ++j;
+      if (j < nd) sd = fwd ? G.dpos_order[j] : G.dneg_order[j];
+    }
+  }
+  int sel = -1;
+  if (!steer) {
+    if (sb >= 0) {
       Prop pr;
-      if (path_to_cylinder(p, w, G.barrel_r[i], pr)) {
-        const int s = G.barrel_order[i];
+      if (path_to_cylinder(p, w, G.r_or_z[sb], pr)) {
         const float z = p[2] + pr.s * cot;
-        if (z >= G.lo[s] && z <= G.hi[s]) {
-          sel = s;
+        if (z >= G.lo[sb] && z <= G.hi[sb]) {
+          sel = sb;
           best = pr;
         }
       }
     }
+    if (sd < 0) return sel;
   }
-  if (cot > 0.f || cot < 0.f) {
-    const bool fwd = cot > 0.f;
-    const int nd = fwd ? G.n_dpos : G.n_dneg;
-    const float* zs = fwd ? G.dpos_z : G.dneg_z;
-    const float zlo = p[2] + 0.01f, zhi = p[2] - 0.01f;  // first disk beyond z in the direction of motion
-    int i = (cur_ok && G.type[cur] != 0 && ((G.r_or_z[cur] > 0.f) == fwd)) ? max(0, static_cast<int>(G.ord[cur])) : 0;
-    while (i > 0 && (fwd ? zs[i - 1] > zlo : zs[i - 1] < zhi)) --i;
-    while (i < nd && !(fwd ? zs[i] > zlo : zs[i] < zhi)) ++i;
-    if (i < nd) {
-      Prop pr;
-      if (path_to_disk(p, w, zs[i], st, ct, pr)) {
-        const int s = fwd ? G.dpos_order[i] : G.dneg_order[i];
-        float x, y, z;
-        prop_position(p, pr, cot, x, y, z);
-        const float r = sqrtf(x * x + y * y);
-        if (r >= G.lo[s] && r <= G.hi[s] && (sel < 0 || pr.s < best.s)) {
-          sel = s;
-          best = pr;
-        }
-      }
+  const int q1 = steer ? G.steer_n[region] : 2;
+#pragma unroll 1
+  for (int q = steer ? pos + 1 : 1; q < q1; ++q) {
+    const int s = steer ? G.steer_list[region][q] : sd;
+    if (s < 0) continue;
+    Prop pr;
+    if (!reach_surface(G, p, w, s, st, ct, cot, pr)) continue;
+    if (steer) {
+      best = pr;
+      newpos = q;
+      return s;
+    }
+    if (sel < 0 || pr.s < best.s) {
+      sel = s;
+      best = pr;
     }
   }
   return sel;
@@ -393,7 +436,7 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
 // A fresh seed's state (fitted by k_seed_states, structure of arrays with stride n) into the
 // candidate record of `lane`; false for a failed seed. Out of line: once per seed.
 template <int KC>
-__device__ __noinline__ bool load_seed(WarpSmem<KC>& W, int lane, const float* in, int surf, int n) {
+__device__ __noinline__ bool load_seed(WarpSmem<KC>& W, int lane, const float* in, int surf_word, int n) {
   const float chi2 = in[static_cast<size_t>(27) * n];
   if (!(chi2 >= 0.f)) return false;
   for (int i = 0; i < 27; ++i) cand_word(W, i, lane) = in[static_cast<size_t>(i) * n];
@@ -401,7 +444,7 @@ __device__ __noinline__ bool load_seed(WarpSmem<KC>& W, int lane, const float* i
   cand_word(W, 28, lane) = __int_as_float(3);  // hits
   cand_word(W, 29, lane) = __int_as_float(0);  // misses
   cand_word(W, 30, lane) = __int_as_float(0);  // stopped
-  cand_word(W, 31, lane) = __int_as_float(surf);
+  cand_word(W, 31, lane) = __int_as_float(surf_word);
   return true;
 }
 
@@ -467,7 +510,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   const int max_steps = A.lmax - 3;
   const float cut = A.chi2_cut;
 
-  int seed = -1, ev = 0, step = 0;
+  int seed = -1, ev = 0, step = 0, region = 0;
   bool exhausted = !in_grp;
   bool valid = false;
 
@@ -497,10 +540,18 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     // ---- a fresh group loads its seed state into slot 0 ------------------------------------
     int failed = 0;
     if (fresh && slot == 0) {
-      valid = load_seed(W, lane, A.seed_state + seed, A.seed_surf[seed], n);
+      // Candidate surface word: (position in the region's list + 1) << 8 | surface.
+      const int s3 = A.seed_surf[seed];
+      int pos = -1;
+      if (G.steer && s3 >= 0 && s3 < G.n_surf) {
+        region = seed_region(G, s3, A.hits[A.seed_hits[static_cast<size_t>(2) * n + seed]]);
+        pos = G.steer_pos[region][s3];
+      }
+      valid = load_seed(W, lane, A.seed_state + seed, ((pos + 1) << 8) | (s3 & 255), n);
       failed = !valid;  // a failed seed's outputs were written by the seed-state kernel
     }
     failed = __shfl_sync(kFull, failed, gbase);
+    region = __shfl_sync(kFull, region, gbase);
     if (fresh && failed) {
       seed = -1;
       valid = false;
@@ -512,7 +563,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     int kind = 3;  // 0 hit children, 1 miss child, 2 carried, 3 empty slot
     // Window: phi bins pb0 .. pb0 + npb - 1 (wrapping), 2nd bins zb0 .. zb1, fine phi range
     // [flo, fhi]; its runs are enumerated from the cursor (row, zrun), row == npb when done.
-    int si = -1, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, flo = 0, fhi = 0, hl_n = 0, row = 0, zrun = 0;
+    int si = -1, npb = 0, pb0 = 0, zb0 = 0, zb1 = 0, flo = 0, fhi = 0, hl_n = 0, row = 0, zrun = 0, newpos = -1;
     bool scored = false;  // learned: this lane's kept hits carry network scores
     float s00v = 1.f, s11v = 1.f;  // innovation variances of this lane's window
     if (on && valid) {
@@ -522,7 +573,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         Prop pr;
         float st, ct;
         sincos_small(c.p[5], st, ct);
-        si = next_surface(G, c.p, c.surf, st, ct, pr);
+        si = next_surface(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
         if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr, st, ct)) {
           kind = 1;
           Meas m;
@@ -754,7 +805,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     if (kind == 1) {
       kind = hl_n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
       if (kind != 2) {
-        c.surf = si;
+        c.surf = ((newpos + 1) << 8) | si;
         store_cand(W, lane, c);
       }
     }
@@ -817,7 +868,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       load_cand(W, gbase + w_par, nc);
       if (w_kind == 0) {
         const float4 h = __ldg(A.sorted_rec + w_pos);
-        update_with(G, nc.surf, nc, h);
+        update_with(G, nc.surf & 255, nc, h);
         nc.chi2 = w_c2;
         nc.nh = w_nh;
       } else if (w_kind == 1) {

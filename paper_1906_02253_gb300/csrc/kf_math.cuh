@@ -20,6 +20,7 @@ constexpr float kPiF = 3.14159265358979323846f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kCurvF = 0.00299792458f;  // GeV / (T cm)
 constexpr int kPhiSub = 8;                 // phi sub-bins per phi bin (KF_PHI_SUB)
+constexpr int kRegions = 5;                // tracking regions of the steering (KF_N_REGIONS)
 
 // Geometry as the kernels see it: passed by value, so it lives in the constant bank.
 struct DevGeom {
@@ -38,6 +39,12 @@ struct DevGeom {
   signed char ord[kMaxSurf];                 // index of each surface in its order list above
   float barrel_r[kMaxSurf];                  // radius of barrel_order[i]
   float dpos_z[kMaxSurf], dneg_z[kMaxSurf];  // z of dpos_order[i], dneg_order[i]
+  // Region steering of the finder (steer = 1) or the geometric next-surface rule (steer = 0).
+  int steer;
+  float c_barrel, c_endcap;
+  int steer_n[kRegions];
+  signed char steer_list[kRegions][kMaxSurf];  // surfaces of each region, in traversal order
+  signed char steer_pos[kRegions][kMaxSurf];   // position of each surface in each list, -1 if absent
 };
 
 // Packed symmetric 6x6 index, i <= j (upper triangle, row-major).

@@ -170,6 +170,22 @@ def _wl_hi_occ() -> Workload:
                     tracks_hi=8000, seed=5, eta_max=2.4, noise_frac=1.0, k_max=8)
 
 
+def steering_tables(wl, eta_barrel: float, eta_endcap: float, endcap_barrels=None) -> dict:
+    """Tracking-region steering lists for a workload's geometry (regions in eta: 0 barrel, 1/2 +z/-z
+    transition, 3/4 +z/-z endcap). Barrel: the barrel layers by radius; transition: the barrel
+    layers by radius, then that side's disks by |z|; endcap: the innermost `endcap_barrels` barrel
+    layers (all when None), then that side's disks by |z|. The region edges in eta become the FP32
+    slopes c = sinh(eta) of |z| against rho. Configuration only: the finder and the oracle apply
+    the lists."""
+    surf = wl.surfaces
+    barrels = sorted((i for i, s in enumerate(surf) if s.type == BARREL), key=lambda i: surf[i].r_or_z)
+    pos = sorted((i for i, s in enumerate(surf) if s.type == DISK and s.r_or_z > 0), key=lambda i: surf[i].r_or_z)
+    neg = sorted((i for i, s in enumerate(surf) if s.type == DISK and s.r_or_z < 0), key=lambda i: -surf[i].r_or_z)
+    eb = barrels if endcap_barrels is None else barrels[:endcap_barrels]
+    return {"c_barrel": float(np.float32(math.sinh(eta_barrel))), "c_endcap": float(np.float32(math.sinh(eta_endcap))),
+            "lists": [barrels, barrels + pos, barrels + neg, eb + pos, eb + neg]}
+
+
 WORKLOADS = {
     "fit_small": _wl_fit_small(),
     "fit_batched": _wl_fit_batched(),

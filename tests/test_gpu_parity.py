@@ -180,7 +180,7 @@ def _find_both(kf, wl, b, **kw):
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
     prm = kf.find_params(kw.get("chi2_cut", wl.chi2_cut), kw.get("k_max", wl.k_max), kw.get("max_miss", wl.max_miss),
-                         wl.lmax)
+                         wl.lmax, steering_tables=kw.get("steering"))
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
     torch.cuda.synchronize()
     sh, st = b.seeds()
@@ -211,6 +211,58 @@ def test_find_parity(kf, wl_name, n_ev, nt, k):
     b = synth.generate(wl)
     gpu, ora, st = _find_both(kf, wl, b, k_max=k)
     _assert_find_parity(b, gpu, ora, st)
+
+
+def _steering_without(wl, surfaces):
+    tab = synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3)
+    tab["lists"] = [[x for x in lst if x not in surfaces] for lst in tab["lists"]]
+    return tab
+
+
+@pytest.mark.parametrize("dropped", [(), (6, 20)])
+def test_find_parity_region_steering(kf, dropped):
+    """Region steering on the barrel + disk geometry against the oracle: lists in crossing order,
+    and lists without barrel layer 6 and the third +z disk."""
+    wl = synth.workload("hi_occ", n_events=2, tracks_lo=800, tracks_hi=1500)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b, steering=_steering_without(wl, dropped))
+    _assert_find_parity(b, gpu, ora, st)
+    if dropped:
+        assert not np.isin(gpu["hits"], np.nonzero(np.isin(b.hit_surface, dropped))[0]).any()
+
+
+def test_region_steering_in_crossing_order_equals_geometric_rule_on_gpu(kf):
+    wl = synth.workload("hi_occ", n_events=2, tracks_lo=800, tracks_hi=1500)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    outs = []
+    for tab in (None, _steering_without(wl, ())):
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, steering_tables=tab)
+        out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+        outs.append({k: v.cpu().numpy() for k, v in out.items() if k != "workspace"})
+    for k in ("hits", "nhits", "status"):
+        assert np.array_equal(outs[0][k], outs[1][k])
+
+
+def test_region_steering_rejects_invalid_lists(kf):
+    wl = synth.workload("hi_occ", n_events=1, tracks_lo=50, tracks_hi=50)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    for bad in ("duplicate", "range", "edges"):
+        tab = synth.steering_tables(wl, 0.4, 1.8)
+        if bad == "duplicate":
+            tab["lists"][0] = tab["lists"][0] + [tab["lists"][0][0]]
+        elif bad == "range":
+            tab["lists"][1] = tab["lists"][1] + [len(wl.surfaces)]
+        else:
+            tab["c_barrel"], tab["c_endcap"] = 2.0, 1.0
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, steering_tables=tab)
+        with pytest.raises(kf.KfError):
+            kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
 
 
 def test_find_parity_dense_noise(kf):

@@ -162,3 +162,48 @@ def test_window_counters_are_ordered(wl_name):
     n_window_pass = n_pass - 3 * len(st)  # the pass counter includes the three seed-hit updates
     assert 0 < n_window_pass <= n_win <= n_scan
     assert n_win < n_scan  # the sub-bins cut the scan on these windows
+
+
+def test_steering_that_lists_the_crossing_order_equals_the_geometric_rule():
+    """Region steering (Sec. 3.1) on the barrel + disk geometry, whose disks start beyond the barrel
+    half-length: every region list holds the surfaces a track of that region can reach in the order
+    it crosses them (endcap lists truncated to the barrel layers an endcap track can reach), so the
+    steered finder must reproduce the geometric next-surface rule exactly."""
+    wl = synth.workload("hi_occ", n_events=2, tracks_lo=150, tracks_hi=150)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    geo = oracle.find(g, b, sh, ev)
+    steered = oracle.find(g, b, sh, ev, steering=synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3))
+    for k in ("hits", "n_hits", "status"):
+        assert np.array_equal(geo[k], steered[k])
+    assert np.array_equal(geo["chi2"], steered["chi2"], equal_nan=True)
+    # the seeds span the regions: third seed hits on barrels (|z|/rho below and above the barrel
+    # edge) and on disks
+    s3 = b.hit_surface[sh[:, 2]]
+    types = np.array([wl.surfaces[s].type for s in s3])
+    zr = np.abs(b.hits[sh[:, 2], 1]) / np.array([wl.surfaces[s].r_or_z for s in s3])
+    assert (types == synth.DISK).any() and ((types == synth.BARREL) & (zr > 0.42)).any()
+    assert ((types == synth.BARREL) & (zr < 0.40)).any()
+
+
+def test_steering_list_without_a_layer_passes_it_over():
+    """A barrel list without layer 7: the found tracks hold no hit of layer 7, count no miss for
+    it, and on clean sparse events lose exactly that hit."""
+    wl = synth.workload("find", n_events=1, tracks_lo=60, tracks_hi=60, noise_frac=0.0)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl, ms=False)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    tab = synth.steering_tables(wl, 10.0, 20.0)
+    tab["lists"] = [[s for s in lst if s != 7] for lst in tab["lists"]]
+    full = oracle.find(g, b, sh, ev)
+    cut = oracle.find(g, b, sh, ev, steering=tab)
+    on7 = np.isin(cut["hits"], np.nonzero(b.hit_surface == 7)[0])
+    assert not on7.any()
+    assert np.array_equal(full["n_hits"] - 1, cut["n_hits"])
+    for i in range(len(st)):
+        a = [h for h in full["hits"][i] if h >= 0 and b.hit_surface[h] != 7]
+        c = [h for h in cut["hits"][i] if h >= 0]
+        assert a == c
