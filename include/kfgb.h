@@ -63,7 +63,19 @@ typedef struct {
   const KfSurface* surf;
   float sigma_rphi, sigma_2nd;
   float prior[5];
+  /* Material and energy loss (Sec. 3.1: material tables indexed in r-z, energy loss). ms_off: 1
+   * turns multiple scattering off. material: NULL (each surface's x_over_x0 everywhere) or a host
+   * array [n_surf][KF_MAT_NODES] of x/X0 at points spread evenly over the surface's extent (z on a
+   * barrel, r on a disk), interpolated linearly at the crossing and clamped at the ends. eloss:
+   * mean ionisation loss in GeV per unit of x/X0 crossed (0: none), taken along the path through
+   * the layer, |p| -> p' with E' = E - eloss x/X0 / |cos a| for a particle of mass `mass` GeV,
+   * direction kept; in the covariance kappa's row and column scale by (p/p')^3 E'/E. Zero-filled
+   * fields keep the plain behaviour. */
+  int ms_off;
+  const float* material;
+  float eloss, mass;
 } KfGeometry;
+#define KF_MAT_NODES 8
 
 /* Hit index: per (event, surface) slab, hits sorted by bin (phi-bin * n_2nd + second-bin) and,
  * within a bin, by phi sub-bin and then ascending hit id. The phi sub-bin refines the phi bin

@@ -50,7 +50,9 @@ class OrSurface(ctypes.Structure):
 
 class OrGeom(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_float), ("n_surf", ctypes.c_int), ("surf", ctypes.POINTER(OrSurface)),
-                ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5)]
+                ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5),
+                ("ms_off", ctypes.c_int), ("material", ctypes.c_void_p), ("eloss", ctypes.c_float),
+                ("mass", ctypes.c_float)]
 
 
 class OrFindParams(ctypes.Structure):
@@ -111,10 +113,13 @@ class Geometry:
         n = len(wl.surfaces)
         self._surf = (OrSurface * n)()
         for i, s in enumerate(wl.surfaces):
-            self._surf[i] = OrSurface(s.type, s.r_or_z, s.lo, s.hi, s.x_over_x0 if wl.ms_on else 0.0,
-                                      s.n_phi, s.n_2nd)
+            self._surf[i] = OrSurface(s.type, s.r_or_z, s.lo, s.hi, s.x_over_x0, s.n_phi, s.n_2nd)
+        mat = getattr(wl, "material", None)
+        self._mat = None if mat is None else np.ascontiguousarray(mat, dtype=np.float32)
         self.g = OrGeom(wl.bz, n, ctypes.cast(self._surf, ctypes.POINTER(OrSurface)), wl.sigma_rphi,
-                        wl.sigma_2nd, (ctypes.c_float * 5)(*wl.prior))
+                        wl.sigma_2nd, (ctypes.c_float * 5)(*wl.prior), int(not wl.ms_on),
+                        None if self._mat is None else self._mat.ctypes.data, getattr(wl, "eloss", 0.0),
+                        getattr(wl, "mass", 0.13957))
 
     @property
     def ref(self):

@@ -52,7 +52,15 @@ struct OrGeom {
   const OrSurface* surf;
   float sigma_rphi, sigma_2nd;
   float prior[5];  // sd of u, second coordinate, kappa, phi, theta at the first hit
+  // Material and energy loss (Sec. 3.1: material tables indexed in r-z; energy loss): x/X0 of
+  // surface s at 8 points spread evenly over its extent (z on barrels, r on disks), interpolated
+  // linearly at the crossing (null: the surface's x_over_x0); scattering switch; mean ionisation
+  // loss eloss GeV per unit of x/X0 crossed (0: none) for a particle of mass `mass` GeV.
+  int ms_off;
+  const float* material;
+  float eloss, mass;
 };
+constexpr int kMatNodes = 8;
 // Region steering of the finder (Sec. 3.1 tracking regions): five regions in eta (0 barrel, 1/2
 // +z/-z transition, 3/4 +z/-z endcap), each with its ordered list of surfaces.
 struct OrSteering {
@@ -222,8 +230,22 @@ double highland(double p, double x_over_x0) {
   return 0.0136 / p * std::sqrt(x_over_x0) * (1.0 + 0.038 * std::log(x_over_x0));
 }
 
+// x/X0 of surface si at second coordinate v (linear between the map's nodes, clamped at the ends).
+double material_at(const OrGeom& g, int si, double v) {
+  const OrSurface& S = g.surf[si];
+  if (!g.material) return S.x_over_x0;
+  double u = (v - S.lo) / (static_cast<double>(S.hi) - S.lo) * (kMatNodes - 1);
+  u = std::min(std::max(u, 0.0), static_cast<double>(kMatNodes - 1));
+  const int k = std::min(static_cast<int>(std::floor(u)), kMatNodes - 2);
+  const float* nd = g.material + static_cast<size_t>(si) * kMatNodes;
+  return nd[k] + (u - k) * (static_cast<double>(nd[k + 1]) - nd[k]);
+}
+
 // Propagate to surface `si`: state moves along the helix, covariance by J C J^T with J
-// projected onto the surface, plus multiple-scattering noise of the surface's material.
+// projected onto the surface, plus multiple-scattering noise of the material at the crossing,
+// then the mean energy loss in it: |p| -> p' with E' = E - eloss x/X0 / |cos a| (direction kept),
+// kappa scaled by p/p' and the kappa row and column of C by d kappa'/d kappa = (p/p')^3 E'/E (the
+// loss taken as fixed; its dependence on theta and on the crossing angle is not propagated).
 bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_out = nullptr,
                double* s_used = nullptr) {
   const OrSurface& S = g.surf[si];
@@ -254,8 +276,10 @@ bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_o
   matmul(J, in.C, JC);
   transpose(J, Jt);
   matmul(JC, Jt, out.C);
-  // Thin-layer multiple scattering at the crossing.
-  if (S.x_over_x0 > 0.0f) {
+  // Thin-layer multiple scattering and energy loss at the crossing.
+  const double xx0 = material_at(g, si, S.type == 0 ? out.p[2] : std::hypot(out.p[0], out.p[1]));
+  const bool ms = !g.ms_off && xx0 > 0.0, el = g.eloss > 0.0f && xx0 > 0.0;
+  if (ms || el) {
     const double kap = out.p[3], th = out.p[5];
     const double sth = std::sin(th), cth = std::cos(th);
     double cos_a;
@@ -266,14 +290,28 @@ bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_o
       cos_a = cth;
     }
     const double p = 1.0 / (std::fabs(kap) * sth);
-    const double t0 = highland(p, static_cast<double>(S.x_over_x0) / std::fabs(cos_a));
-    const double v = t0 * t0;
-    const double cot = cth / sth;
-    out.C[5][5] += v;
-    out.C[4][4] += v / (sth * sth);
-    out.C[3][5] += -kap * cot * v;
-    out.C[5][3] += -kap * cot * v;
-    out.C[3][3] += kap * kap * cot * cot * v;
+    if (ms) {
+      const double t0 = highland(p, xx0 / std::fabs(cos_a));
+      const double v = t0 * t0;
+      const double cot = cth / sth;
+      out.C[5][5] += v;
+      out.C[4][4] += v / (sth * sth);
+      out.C[3][5] += -kap * cot * v;
+      out.C[5][3] += -kap * cot * v;
+      out.C[3][3] += kap * kap * cot * cot * v;
+    }
+    if (el) {
+      const double m = g.mass, e = std::sqrt(p * p + m * m);
+      const double e1 = e - static_cast<double>(g.eloss) * xx0 / std::fabs(cos_a);
+      if (!(e1 > m)) return false;  // stopped in the layer
+      const double p1 = std::sqrt(e1 * e1 - m * m), ratio = p / p1;
+      const double gk = ratio * ratio * ratio * e1 / e;
+      out.p[3] = kap * ratio;
+      for (int i = 0; i < 6; ++i) {
+        out.C[3][i] *= gk;
+        out.C[i][3] *= gk;
+      }
+    }
   }
   if (jac_out)
     for (int i = 0; i < 6; ++i)

@@ -35,7 +35,12 @@ class KfSurface(ctypes.Structure):
 
 class KfGeometry(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_float), ("n_surf", ctypes.c_int), ("surf", ctypes.POINTER(KfSurface)),
-                ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5)]
+                ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5),
+                ("ms_off", ctypes.c_int), ("material", ctypes.c_void_p), ("eloss", ctypes.c_float),
+                ("mass", ctypes.c_float)]
+
+
+MAT_NODES = 8  # KF_MAT_NODES
 
 
 class KfHitIndex(ctypes.Structure):
@@ -114,7 +119,8 @@ def _check(rc: int, what: str):
 
 class Geometry:
     """C-ABI geometry built from any object with ``surfaces`` (type, r_or_z, lo, hi, x_over_x0,
-    n_phi, n_2nd), ``bz``, ``sigma_rphi``, ``sigma_2nd``, ``prior`` and ``ms_on``."""
+    n_phi, n_2nd), ``bz``, ``sigma_rphi``, ``sigma_2nd``, ``prior``, ``ms_on`` and optionally
+    ``material`` ([n_surf][MAT_NODES] x/X0), ``eloss`` and ``mass``."""
 
     def __init__(self, wl):
         self.wl = wl
@@ -122,9 +128,15 @@ class Geometry:
         self._surf = (KfSurface * n)()
         ms = getattr(wl, "ms_on", True)
         for i, s in enumerate(wl.surfaces):
-            self._surf[i] = KfSurface(s.type, s.r_or_z, s.lo, s.hi, s.x_over_x0 if ms else 0.0, s.n_phi, s.n_2nd)
+            self._surf[i] = KfSurface(s.type, s.r_or_z, s.lo, s.hi, s.x_over_x0, s.n_phi, s.n_2nd)
+        mat = getattr(wl, "material", None)
+        self._mat = None if mat is None else np.ascontiguousarray(mat, dtype=np.float32)
+        if self._mat is not None and self._mat.shape != (n, MAT_NODES):
+            raise KfError(f"material map must be [{n}][{MAT_NODES}]")
         self.g = KfGeometry(wl.bz, n, ctypes.cast(self._surf, ctypes.POINTER(KfSurface)), wl.sigma_rphi, wl.sigma_2nd,
-                            (ctypes.c_float * 5)(*wl.prior))
+                            (ctypes.c_float * 5)(*wl.prior), int(not ms),
+                            None if self._mat is None else self._mat.ctypes.data, getattr(wl, "eloss", 0.0),
+                            getattr(wl, "mass", 0.13957))
         self.n_surf = n
         self.n_bins = load_library().kf_index_bins(ctypes.byref(self.g))
         if self.n_bins < 0:

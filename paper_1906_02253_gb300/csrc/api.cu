@@ -14,7 +14,8 @@ namespace kfgb {
 __global__ void k_build_hit_index(DevGeom G, const float2* hits, const int* slab_off, int n_slabs, int cap,
                                   int* bin_off, float2* sorted_hits, int* sorted_ids, float4* sorted_rec,
                                   uint4* sub_off, int* d_status);
-__global__ void k_fit_tracks(DevGeom G, const float2* hits, const int* hit_surface, const int* track_hits,
+__global__ void k_fit_tracks(DevGeom G, const __grid_constant__ DevMat M, const float2* hits, const int* hit_surface,
+                             const int* track_hits,
                              int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
                              int* status_out);
 
@@ -37,6 +38,7 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
     d->prior[i] = g->prior[i];
   }
   d->n_surf = g->n_surf;
+  d->ms_on = g->ms_off ? 0 : 1;
   int nb = 0;
   for (int s = 0; s < g->n_surf; ++s) {
     const KfSurface& S = g->surf[s];
@@ -86,6 +88,25 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
   for (int i = 0; i < in; ++i) {
     d->ord[d->dneg_order[i]] = static_cast<signed char>(i);
     d->dneg_z[i] = d->r_or_z[d->dneg_order[i]];
+  }
+  return KF_OK;
+}
+
+// Material map and energy loss of the geometry into their launch parameter.
+static int pack_material(const KfGeometry* g, DevMat* m) {
+  std::memset(m, 0, sizeof(*m));
+  if (!(g->eloss >= 0.f) || !std::isfinite(g->eloss)) return KF_ERR_ARG;
+  if (g->eloss > 0.f && !(g->mass > 0.f)) return KF_ERR_ARG;
+  m->eloss = g->eloss;
+  m->mass = g->mass;
+  if (g->material) {
+    for (int s = 0; s < g->n_surf; ++s)
+      for (int k = 0; k < kMatNodes; ++k) {
+        const float v = g->material[s * kMatNodes + k];
+        if (!(v >= 0.f) || !std::isfinite(v)) return KF_ERR_ARG;
+        m->node[s][k] = v;
+      }
+    m->map_on = 1;
   }
   return KF_OK;
 }
@@ -212,6 +233,9 @@ int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surf
   DevGeom G;
   int rc = pack_geometry(geom, &G);
   if (rc != KF_OK) return rc;
+  DevMat M;
+  rc = pack_material(geom, &M);
+  if (rc != KF_OK) return rc;
   if (n_tracks < 0 || lmax < 3 || lmax > KF_MAX_LMAX) return KF_ERR_ARG;
   if (block_threads == 0) block_threads = 128;
   if (block_threads < 32 || block_threads > 256 || block_threads % 32) return KF_ERR_ARG;
@@ -230,7 +254,7 @@ int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surf
   const long long want = (static_cast<long long>(n_tracks) + block_threads - 1) / block_threads;
   const int grid = static_cast<int>(std::min<long long>(want, static_cast<long long>(sm_count()) * occ));
   k_fit_tracks<<<grid, block_threads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-      G, reinterpret_cast<const float2*>(hits), hit_surface, track_hits, n_tracks, lmax, state_out, cov_out, chi2_out,
+      G, M, reinterpret_cast<const float2*>(hits), hit_surface, track_hits, n_tracks, lmax, state_out, cov_out, chi2_out,
       ndof_out, status_out);
   return launch_status();
 }
@@ -250,6 +274,9 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   if (rc != KF_OK) return rc;
   if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
   rc = pack_steering(params->steering, &G);
+  if (rc != KF_OK) return rc;
+  DevMat M;
+  rc = pack_material(geom, &M);
   if (rc != KF_OK) return rc;
   FindPlan plan;
   rc = plan_find(n_seeds, params, sm_count(), &plan);
@@ -286,7 +313,7 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   A.status_out = status_out;
   A.mlp = params->mlp;
   A.top_n = params->mlp ? params->top_n : 0;
-  return launch_find(G, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
+  return launch_find(G, M, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream) {
@@ -316,6 +343,9 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   if (rc != KF_OK) return rc;
   if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
   rc = pack_steering(params->steering, &G);
+  if (rc != KF_OK) return rc;
+  DevMat M;
+  rc = pack_material(geom, &M);
   if (rc != KF_OK) return rc;
   if (n_seeds > KF_STATIC_MAX_SEEDS) return KF_ERR_CAPACITY;
   FindPlan plan;
@@ -356,7 +386,7 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   A.status_out = status_out;
   A.mlp = params->mlp;
   A.top_n = params->mlp ? params->top_n : 0;
-  return launch_find(G, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
+  return launch_find(G, M, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ---- autotuners: time each configuration with CUDA events on the caller's stream ---------------

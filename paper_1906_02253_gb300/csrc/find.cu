@@ -376,7 +376,7 @@ __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, in
 // are written here).
 constexpr int kSeedWords = 28;
 
-__global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
+__global__ void __launch_bounds__(128) k_seed_states(DevGeom G, const __grid_constant__ DevMat M, FindArgs A) {
   const int seed = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = A.n_seeds;
   if (seed >= n) return;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, FindArgs A) {
       Prop pr;
       ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
                               : path_to_disk(c.p, w, G.r_or_z[ss[k]], st, ct, pr);
-      ok = ok && apply_propagation(G, ss[k], c.p, c.C, pr, st, ct);
+      ok = ok && apply_propagation(G, M, ss[k], c.p, c.C, pr, st, ct);
       if (!ok) break;
     }
     const float2 h = A.hits[ids[k]];
@@ -479,7 +479,8 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
 }
 
 template <int KC, bool LEARNED>
-__global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp, FindArgs A) {
+__global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp,
+                                                        const __grid_constant__ DevMat M, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   {
     // Geometry into shared memory: lanes index it by their own surface, which would serialise
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         float st, ct;
         sincos_small(c.p[5], st, ct);
         si = next_surface(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
-        if (si >= 0 && apply_propagation(G, si, c.p, c.C, pr, st, ct)) {
+        if (si >= 0 && apply_propagation(G, M, si, c.p, c.C, pr, st, ct)) {
           kind = 1;
           Meas m;
           float rho;
@@ -1054,7 +1055,7 @@ int static_scratch(void** ptr) {
   return KF_OK;
 }
 
-int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream) {
+int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream) {
   char* base = static_cast<char*>(ws);
   A.counter = reinterpret_cast<int*>(base);
   A.seed_state = reinterpret_cast<float*>(base + plan.off_state);
@@ -1066,9 +1067,9 @@ int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, c
     A.mlp_t = wt;
   }
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
-  k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, A);
+  k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, M, A);
   dispatch_find(plan.kc, plan.learned, [&](auto k) {
-    k_find_tracks<decltype(k)::kc, decltype(k)::learned><<<plan.grid, plan.block, plan.smem, stream>>>(G, A);
+    k_find_tracks<decltype(k)::kc, decltype(k)::learned><<<plan.grid, plan.block, plan.smem, stream>>>(G, M, A);
     return KF_OK;
   });
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;

@@ -47,7 +47,7 @@ struct FindPlan {
 };
 
 int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan);
-int launch_find(const DevGeom& G, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream);
+int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream);
 // Device address of the library's fixed finder scratch on the current device (looked up on the
 // first call per device; no allocation).
 int static_scratch(void** ptr);

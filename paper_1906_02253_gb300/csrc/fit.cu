@@ -6,7 +6,8 @@
 
 namespace kfgb {
 
-__global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __restrict__ hits,
+__global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const __grid_constant__ DevMat M,
+                                                    const float2* __restrict__ hits,
                                                     const int* __restrict__ hit_surface,
                                                     const int* __restrict__ track_hits, int n_tracks, int lmax,
                                                     float* __restrict__ state_out, float* __restrict__ cov_out,
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const float2* __r
           Prop pr;
           const bool ok = G.type[si] == 0 ? path_to_cylinder(p, w, G.r_or_z[si], pr)
                                           : path_to_disk(p, w, G.r_or_z[si], st, ct, pr);
-          if (!ok || !apply_propagation(G, si, p, C, pr, st, ct)) {
+          if (!ok || !apply_propagation(G, M, si, p, C, pr, st, ct)) {
             status = 2;
             break;
           }

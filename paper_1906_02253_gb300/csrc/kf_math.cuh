@@ -39,12 +39,22 @@ struct DevGeom {
   signed char ord[kMaxSurf];                 // index of each surface in its order list above
   float barrel_r[kMaxSurf];                  // radius of barrel_order[i]
   float dpos_z[kMaxSurf], dneg_z[kMaxSurf];  // z of dpos_order[i], dneg_order[i]
+  int ms_on;  // multiple scattering
   // Region steering of the finder (steer = 1) or the geometric next-surface rule (steer = 0).
   int steer;
   float c_barrel, c_endcap;
   int steer_n[kRegions];
   signed char steer_list[kRegions][kMaxSurf];  // surfaces of each region, in traversal order
   signed char steer_pos[kRegions][kMaxSurf];   // position of each surface in each list, -1 if absent
+};
+
+// Material map and energy loss, a separate launch parameter (read from the constant bank; not in
+// the finder's shared-memory geometry copy): x/X0 of surface s at kMatNodes points over its extent.
+constexpr int kMatNodes = 8;
+struct DevMat {
+  int map_on;
+  float eloss, mass;  // GeV per unit x/X0 (0: none); particle mass, GeV
+  float node[kMaxSurf][kMatNodes];
 };
 
 // Packed symmetric 6x6 index, i <= j (upper triangle, row-major).
@@ -191,11 +201,21 @@ __device__ __forceinline__ float highland_var(float p, float x_over_x0) {
   return t0 * t0;
 }
 
+// x/X0 of surface si at second coordinate v: linear between the map's nodes, clamped at the ends.
+__device__ __forceinline__ float material_at(const DevMat& M, const DevGeom& G, int si, float v) {
+  float u = (v - G.lo[si]) / (G.hi[si] - G.lo[si]) * static_cast<float>(kMatNodes - 1);
+  u = fminf(fmaxf(u, 0.f), static_cast<float>(kMatNodes - 1));
+  const int k = min(static_cast<int>(floorf(u)), kMatNodes - 2);
+  const float a = M.node[si][k], b = M.node[si][k + 1];
+  return a + (u - static_cast<float>(k)) * (b - a);
+}
+
 // Move state p and covariance C along the helix by pr.s onto surface `si`; C' = J C J^T + Q where
-// J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface.
-// st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation).
-__device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, float* p, float* C, const Prop& pr,
-                                                  float st, float ct) {
+// J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface; then
+// the mean energy loss in the layer (kappa scaled by p/p', its row and column of C by
+// (p/p')^3 E'/E). st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation).
+__device__ __forceinline__ bool apply_propagation(const DevGeom& G, const DevMat& M, int si, float* p, float* C,
+                                                  const Prop& pr, float st, float ct) {
   const float a = -kCurvF * G.bz;  // d omega / d kappa
   const float w = a * p[3];
   const float s = pr.s;
@@ -279,9 +299,12 @@ __device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, floa
       C[ci(i, j)] += -t[i] * v[j] - v[i] * t[j] + alpha * t[i] * t[j];
     }
   }
-  // Thin-layer multiple scattering (Highland, beta = 1) in (kappa, phi, theta).
-  const float xx0 = G.x0[si];
-  if (xx0 > 0.f) {
+  // Thin-layer multiple scattering (Highland, beta = 1) in (kappa, phi, theta) and the mean energy
+  // loss, with the material at the crossing.
+  float xx0 = G.x0[si];
+  if (M.map_on) xx0 = material_at(M, G, si, G.type[si] == 0 ? p[2] : sqrtf(p[0] * p[0] + p[1] * p[1]));
+  const bool ms = G.ms_on && xx0 > 0.f, el = M.eloss > 0.f && xx0 > 0.f;
+  if (ms || el) {
     float cos_a;
     if (G.type[si] == 0) {
       const float r = sqrtf(p[0] * p[0] + p[1] * p[1]);
@@ -291,11 +314,23 @@ __device__ __forceinline__ bool apply_propagation(const DevGeom& G, int si, floa
     }
     const float kap = p[3];
     const float pm = 1.f / (fabsf(kap) * st);
-    const float var = highland_var(pm, xx0 / fabsf(cos_a));
-    C[ci(5, 5)] += var;
-    C[ci(4, 4)] += var / (st * st);
-    C[ci(3, 5)] += -kap * cot * var;
-    C[ci(3, 3)] += kap * kap * cot * cot * var;
+    if (ms) {
+      const float var = highland_var(pm, xx0 / fabsf(cos_a));
+      C[ci(5, 5)] += var;
+      C[ci(4, 4)] += var / (st * st);
+      C[ci(3, 5)] += -kap * cot * var;
+      C[ci(3, 3)] += kap * kap * cot * cot * var;
+    }
+    if (el) {
+      const float m = M.mass, e = sqrtf(pm * pm + m * m);
+      const float e1 = e - M.eloss * xx0 / fabsf(cos_a);
+      if (!(e1 > m)) return false;  // stopped in the layer
+      const float ratio = pm / sqrtf((e1 - m) * (e1 + m));
+      const float gk = ratio * ratio * ratio * (e1 / e);
+      p[3] = kap * ratio;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) C[ci(3, j)] *= (j == 3 ? gk * gk : gk);
+    }
   }
   return true;
 }

@@ -50,7 +50,11 @@ class _SynthParams(ctypes.Structure):
                 ("pt_lo", ctypes.c_double), ("pt_hi", ctypes.c_double), ("eta_max", ctypes.c_double),
                 ("bz", ctypes.c_double), ("sigma_rphi", ctypes.c_double), ("sigma_2nd", ctypes.c_double),
                 ("noise_frac", ctypes.c_double), ("seed", ctypes.c_uint64), ("ms_on", ctypes.c_int),
-                ("smear_on", ctypes.c_int), ("record_truth", ctypes.c_int), ("n_threads", ctypes.c_int)]
+                ("smear_on", ctypes.c_int), ("record_truth", ctypes.c_int), ("n_threads", ctypes.c_int),
+                ("material", ctypes.c_void_p), ("eloss", ctypes.c_double), ("mass", ctypes.c_double)]
+
+
+MAT_NODES = 8  # material map nodes per surface
 
 
 def _load():
@@ -115,6 +119,12 @@ class Workload:
     # prior standard deviations at the first hit: u (transverse, cm), z or r (cm), kappa (1/GeV),
     # phi (rad), theta (rad); chosen broad compared with one hit and with scattering
     prior: tuple = (0.1, 1.0, 0.5, 0.05, 0.05)
+    # material map (per surface, MAT_NODES values of x/X0 spread evenly over its extent; None: each
+    # surface's x_over_x0) and mean energy loss (GeV per unit x/X0; 0: none) of a particle of mass
+    # `mass` GeV (charged pion)
+    material: tuple = None
+    eloss: float = 0.0
+    mass: float = 0.13957
 
     @property
     def lmax(self) -> int:
@@ -186,12 +196,35 @@ def steering_tables(wl, eta_barrel: float, eta_endcap: float, endcap_barrels=Non
             "lists": [barrels, barrels + pos, barrels + neg, eb + pos, eb + neg]}
 
 
+def material_map(surfaces, x_over_x0: float = 0.02, end_factor: float = 2.0) -> tuple:
+    """A synthetic r-z material map (the CMS tables are not available): on each barrel layer x/X0
+    grows from x_over_x0 at z = 0 to (1 + end_factor) x_over_x0 at the layer ends (services), on
+    each disk it grows likewise from the inner to the outer radius."""
+    out = []
+    for s in surfaces:
+        nodes = []
+        for k in range(MAT_NODES):
+            v = s.lo + (s.hi - s.lo) * k / (MAT_NODES - 1)
+            u = abs(v) / max(abs(s.lo), abs(s.hi)) if s.type == BARREL else (v - s.lo) / (s.hi - s.lo)
+            nodes.append(x_over_x0 * (1.0 + end_factor * u * u))
+        out.append(tuple(nodes))
+    return tuple(out)
+
+
+def _wl_material() -> Workload:
+    surf = tuple(barrel_layers(17))
+    # mean ionisation loss of a minimum-ionising particle in silicon: 3.87 MeV/cm over X0 = 9.37 cm
+    return Workload("fit_100ev_17layers_material_eloss", surf, n_events=100, tracks_lo=2000, tracks_hi=20000,
+                    seed=6, material=material_map(surf), eloss=0.0363)
+
+
 WORKLOADS = {
     "fit_small": _wl_fit_small(),
     "fit_batched": _wl_fit_batched(),
     "find": _wl_find(),
     "learned": _wl_learned(),
     "hi_occ": _wl_hi_occ(),
+    "material": _wl_material(),
 }
 
 
@@ -268,9 +301,15 @@ def generate(wl, *, n_events: int = None, seed: int = None, smear: bool = True, 
     surf = (_SynthSurface * len(wl.surfaces))()
     for i, s in enumerate(wl.surfaces):
         surf[i] = _SynthSurface(s.type, f32(s.r_or_z), f32(s.lo), f32(s.hi), f32(s.x_over_x0) if wl.ms_on else 0.0)
+    mat = None
+    if wl.material is not None:
+        mat = np.array([[f32(v) for v in nodes] for nodes in wl.material], np.float64)
+        if mat.shape != (len(wl.surfaces), MAT_NODES):
+            raise ValueError(f"material map must be [{len(wl.surfaces)}][{MAT_NODES}]")
     prm = _SynthParams(wl.n_events, wl.tracks_lo, wl.tracks_hi, wl.pt_lo, wl.pt_hi, wl.eta_max, f32(wl.bz),
                        wl.sigma_rphi, wl.sigma_2nd, wl.noise_frac, wl.seed, int(wl.ms_on), int(smear),
-                       int(record_truth), n_threads)
+                       int(record_truth), n_threads, None if mat is None else mat.ctypes.data, f32(wl.eloss),
+                       f32(wl.mass))
     lmax = wl.lmax
     h = lib.synth_generate(ctypes.byref(prm), surf, len(wl.surfaces), lmax)
     if not h:

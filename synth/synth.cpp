@@ -93,7 +93,15 @@ struct SynthParams {
   int smear_on;              // smear hits (0: hits at exact crossings)
   int record_truth;          // keep true states at every crossing
   int n_threads;
+  // Material map and mean energy loss (optional): x/X0 of surface s at kMatNodes points spread
+  // evenly over its extent (z on barrels, r on disks), interpolated linearly at the crossing
+  // (null: the surface's x_over_x0 everywhere); mean ionisation loss eloss GeV per unit of x/X0
+  // crossed (0: none) for a particle of mass `mass` GeV.
+  const double* material;    // [n_surf][kMatNodes] or null
+  double eloss;
+  double mass;
 };
+constexpr int kMatNodes = 8;
 
 }  // extern "C"
 
@@ -232,6 +240,16 @@ void kick(Particle& p, double normal_cos, double x_over_x0, Rng& rng) {
   p.pz = pmag * d[2];
 }
 
+// x/X0 of surface s at second coordinate v (linear between the map's nodes, clamped at the ends).
+double material_at(const SynthParams& prm, const SynthSurface& S, int s, double v) {
+  if (!prm.material) return S.x_over_x0;
+  double u = (v - S.lo) / (S.hi - S.lo) * (kMatNodes - 1);
+  u = std::min(std::max(u, 0.0), static_cast<double>(kMatNodes - 1));
+  const int k = std::min(static_cast<int>(std::floor(u)), kMatNodes - 2);
+  const double* nd = prm.material + static_cast<size_t>(s) * kMatNodes;
+  return nd[k] + (u - k) * (nd[k + 1] - nd[k]);
+}
+
 void simulate_track(Particle p, const std::vector<SynthSurface>& surf, const std::vector<int>& barrel_order,
                     const std::vector<int>& disk_pos, const std::vector<int>& disk_neg, const SynthParams& prm,
                     Rng& rng, TrackOut& out) {
@@ -283,7 +301,8 @@ void simulate_track(Particle p, const std::vector<SynthSurface>& surf, const std
     Crossing c{best_surf, x, y, z, p.px, p.py, p.pz};
     if (prm.record_truth) out.truth_in.push_back(state_of(p));
     const SynthSurface& S = surf[best_surf];
-    if (prm.ms_on && S.x_over_x0 > 0.0) {
+    const double xx0 = material_at(prm, S, best_surf, S.type == 0 ? z : std::hypot(x, y));
+    if ((prm.ms_on && xx0 > 0.0) || prm.eloss > 0.0) {
       const double pmag = std::sqrt(p.px * p.px + p.py * p.py + p.pz * p.pz);
       double ncos;
       if (S.type == 0) {
@@ -292,7 +311,17 @@ void simulate_track(Particle p, const std::vector<SynthSurface>& surf, const std
       } else {
         ncos = p.pz / pmag;
       }
-      kick(p, ncos, S.x_over_x0, rng);
+      if (prm.ms_on && xx0 > 0.0) kick(p, ncos, xx0, rng);
+      if (prm.eloss > 0.0 && xx0 > 0.0) {
+        // Mean ionisation loss over the path through the layer; the direction is kept.
+        const double e = std::sqrt(pmag * pmag + prm.mass * prm.mass);
+        const double e1 = e - prm.eloss * xx0 / std::max(std::fabs(ncos), 1e-6);
+        if (!(e1 > prm.mass)) return;  // stopped in the layer
+        const double f = std::sqrt(e1 * e1 - prm.mass * prm.mass) / pmag;
+        p.px *= f;
+        p.py *= f;
+        p.pz *= f;
+      }
     }
     if (prm.record_truth) out.truth_out.push_back(state_of(p));
     out.cross.push_back(c);

@@ -160,6 +160,22 @@ def test_fit_parity_scattering_and_disks(kf):
         _assert_fit_parity(gpu, ora)
 
 
+def test_fit_parity_material_map_and_energy_loss(kf):
+    """Material map + mean energy loss, with and without scattering."""
+    for ms in (True, False):
+        wl = synth.workload("material", n_events=2, tracks_lo=1500, tracks_hi=3000, ms_on=ms)
+        b = synth.generate(wl)
+        gpu, ora = _fit_both(kf, wl, b)
+        _assert_fit_parity(gpu, ora)
+
+
+def test_find_parity_material_map_and_energy_loss(kf):
+    wl = synth.workload("material", n_events=2, tracks_lo=1500, tracks_hi=2500, noise_frac=0.3)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b)
+    _assert_find_parity(b, gpu, ora, st)
+
+
 def test_fit_with_misses_and_short_tracks(kf):
     """-1 entries inside a list are skipped; lists with fewer than three seed hits are rejected."""
     wl = synth.workload("fit_batched", n_events=1, tracks_lo=700, tracks_hi=700)
