@@ -120,9 +120,10 @@ def _peaks():
 # Oracle legs (host cores only)
 # ------------------------------------------------------------------------------------------------
 
-def oracle_sample(wl, batch, n_seeds_max: int):
-    """Run the FP64 oracle (index + find + fit of the found tracks) on the first seeds of the batch,
-    all host cores. Returns (seconds, n_seeds, counters, threads)."""
+def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False):
+    """Run the FP64 oracle (index + find + fit of the found tracks; with ``clean``, seed cleaning
+    before finding and duplicate removal after it) on the first seeds of the batch, all host
+    cores. Returns (seconds, n_seeds, counters, threads)."""
     import numpy as np
     import oracle
 
@@ -133,9 +134,16 @@ def oracle_sample(wl, batch, n_seeds_max: int):
     last_ev = int(ev[n - 1])
     sub = np.nonzero(ev <= last_ev)[0][:n]
     t0 = time.perf_counter()
+    if clean:
+        keep = oracle.clean_seeds(seeds[sub], ev[sub], oracle.seed_params(g, batch, seeds[sub]))
+        sub = sub[keep != 0]
     f = oracle.find(g, batch, seeds[sub], ev[sub])
+    if clean:
+        oracle.remove_duplicates(f["hits"], f["n_hits"], f["chi2"], f["p"][:, 4], f["p"][:, 5], ev[sub])
     oracle.fit(g, batch.hits, batch.hit_surface, f["hits"])
     dt = time.perf_counter() - t0
+    if clean:
+        return dt, len(keep), f["counters"], os.cpu_count() or 1
     return dt, len(sub), f["counters"], os.cpu_count() or 1
 
 
@@ -145,18 +153,20 @@ def run_reference(args, wl, batch):
     if rank != 0:
         return
     per_step = args.ref_seeds
+    clean = args.clean or getattr(wl, "combinatorial_seeds", False)
     for _ in range(args.warmup):
-        oracle_sample(wl, batch, min(per_step, 2000))
+        oracle_sample(wl, batch, min(per_step, 2000), clean)
     times, n = [], 0
     for _ in range(args.steps):
-        dt, n, _, cores = oracle_sample(wl, batch, per_step)
+        dt, n, _, cores = oracle_sample(wl, batch, per_step, clean)
         times.append(dt)
     value = n / statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator)",
-            "config": {"workload": wl.name, "sample": f"first {n} seeds of the batch (index, find, fit)"},
+            "config": {"workload": wl.name, "sample": f"first {n} seeds of the batch (index, "
+                       + ("seed cleaning, find, duplicate removal, fit)" if clean else "find, fit)")},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} seeds per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -185,11 +195,18 @@ def run_gpu(args, wl, batch):
     lmax = wl.lmax
     import synth
     steer = synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3) if args.steering else None
-    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm,
-                         steering_tables=steer)
+    clean = args.clean or getattr(wl, "combinatorial_seeds", False)
 
     # Device inputs and preallocated outputs.
     d = {k: v.to(dev) for k, v in host.items() if isinstance(v, torch.Tensor)}
+    seed_keep = track_keep = dws = None
+    if clean:  # seed cleaning before finding, duplicate removal after it
+        seed_keep = torch.ones(n_seeds, dtype=torch.int32, device=dev)
+        track_keep = torch.ones(n_seeds, dtype=torch.int32, device=dev)
+        dws = torch.empty(max(kf.dedup_workspace_size(n_seeds, lmax, n_hits), 256), dtype=torch.uint8,
+                          device=dev)
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm,
+                         steering_tables=steer, seed_keep=seed_keep)
     idx = kf.HitIndex(g, batch.n_events, n_hits, dev)
     fout = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32, device=dev),
                 nhits=torch.empty(n_seeds, dtype=torch.int32, device=dev),
@@ -212,6 +229,9 @@ def run_gpu(args, wl, batch):
     if not args.no_autotune:
         with torch.cuda.stream(stream):
             kf.build_hit_index(g, d["hits"], d["slab_offsets"], batch.n_events, max_slab, index=idx, stream=stream)
+            if clean:
+                kf.clean_seeds(g, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], keep=seed_keep,
+                               workspace=dws, stream=stream)
             n_cal = int(np.searchsorted(host["seed_event"].numpy(), min(10, batch.n_events)))
             cal_s = d["seed_hits"][:, :n_cal].contiguous()
             cal_e = d["seed_event"][:n_cal].contiguous()
@@ -222,21 +242,28 @@ def run_gpu(args, wl, batch):
         tuning = {"calibration_seeds": n_cal, "find_block_threads": prm.block_threads,
                   "find_k_capacity": prm.k_capacity, "find_ms": ms_find, "fit_block_threads": fit_block,
                   "fit_ms": ms_fit}
-    launches = {"index": 0, "find": 0, "fit": 0}
+    parts = ["index"] + (["clean"] if clean else []) + ["find"] + (["dedup"] if clean else []) + ["fit"]
 
     def step(s, events=None):
-        if events:
-            events[0].record(s)
+        def mark(i):
+            if events:
+                events[i].record(s)
+        mark(0)
         kf.build_hit_index(g, d["hits"], d["slab_offsets"], batch.n_events, max_slab, index=idx, stream=s)
-        if events:
-            events[1].record(s)
+        mark(1)
+        if clean:
+            kf.clean_seeds(g, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], keep=seed_keep,
+                           workspace=dws, stream=s)
+            mark(2)
         kf.find_tracks(g, idx, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], prm, out=fout,
                        workspace=wsb, stream=s)
-        if events:
-            events[2].record(s)
+        mark(parts.index("find") + 1)
+        if clean:
+            kf.remove_duplicates(fout["hits"], fout["nhits"], fout["chi2"], fout["state"], d["seed_event"], n_hits,
+                                 keep=track_keep, workspace=dws, stream=s)
+            mark(parts.index("dedup") + 1)
         kf.fit_tracks(g, d["hits"], d["hit_surface"], fout["hits"], out=fit_out, block_threads=fit_block, stream=s)
-        if events:
-            events[3].record(s)
+        mark(len(parts))
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -276,19 +303,20 @@ def run_gpu(args, wl, batch):
         dist.barrier()
     from paper_1906_02253_gb300 import shard
     ms_step = shard.max_over_ranks(statistics.mean(t_steps), device=dev)
-    launches_per_step = 4  # index, seed states, find, fit kernels (plus one memset node)
+    # index, seed states, find, fit kernels (plus one memset node); cleaning: count, 3 scan kernels,
+    # fill, seed directions, decision; duplicate removal: count, 3 scan kernels, fill, decision
+    launches_per_step = 4 + (7 + 6 if clean else 0)
 
-    # Per-kernel durations: the same three launches eager, events on the launching stream.
-    kern = {"index": [], "find": [], "fit": []}
+    # Per-part durations: the same launches eager, events on the launching stream.
+    kern = {k: [] for k in parts}
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
             step(stream, ev)
         torch.cuda.synchronize()
-        kern["index"].append(ev[0].elapsed_time(ev[1]))
-        kern["find"].append(ev[1].elapsed_time(ev[2]))
-        kern["fit"].append(ev[2].elapsed_time(ev[3]))
+        for i, k in enumerate(parts):
+            kern[k].append(ev[i].elapsed_time(ev[i + 1]))
     kern_ms = {k: statistics.mean(v) for k, v in kern.items()}
 
     # End to end through the public API with host buffers: H2D of the step's inputs from pinned
@@ -315,6 +343,16 @@ def run_gpu(args, wl, batch):
     from paper_1906_02253_gb300 import metrics
     eff, fake = metrics.efficiency(batch, host["seed_track"], res_host["hits"].numpy().T,
                                    fout["nhits"].cpu().numpy())
+    dups = None
+    if clean:
+        nh_all = fout["nhits"].cpu().numpy()
+        hl = res_host["hits"].numpy().T
+        sk, tk = seed_keep.cpu().numpy(), track_keep.cpu().numpy()
+        dups = {"seeds": n_seeds, "seeds_kept": int(sk.sum()), "tracks_kept": int((sk * tk).sum())}
+        for nm, k in (("after_cleaning", sk), ("after_cleaning_and_removal", sk * tk)):
+            e, dr, fr = metrics.track_rates(batch, host["seed_track"], hl, nh_all, k)
+            dups[nm] = {"efficiency": e, "duplicate_rate": dr, "fake_rate": fr}
+        eff, fake = dups["after_cleaning_and_removal"]["efficiency"], dups["after_cleaning_and_removal"]["fake_rate"]
     fit_ok = float((fit_out["status"] == 0).float().mean().item())
 
     learned = None
@@ -328,7 +366,9 @@ def run_gpu(args, wl, batch):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, no datasets)",
            "config": {"workload": wl.name, "events": batch.n_events, "seeds": n_seeds, "hits": n_hits,
                       "layers": len(wl.surfaces), "k_max": wl.k_max, "chi2_cut": wl.chi2_cut,
-                      "step": "hit index + find + fit, one CUDA graph", "l2": "flushed between steps (256 MB write)",
+                      "step": ("hit index + seed cleaning + find + duplicate removal + fit" if clean
+                               else "hit index + find + fit") + ", one CUDA graph",
+                      "l2": "flushed between steps (256 MB write)",
                       "next_surface": "region steering (eta edges 0.4, 1.8)" if args.steering else "geometric rule",
                       "parallelism": f"events sharded over {ws} GPU(s), no collective"},
            "gpu_launches": launches_per_step * args.steps, "autotune": tuning,
@@ -340,14 +380,17 @@ def run_gpu(args, wl, batch):
     out["clocks"] = clk.summary()
     if learned is not None:
         out["learned_vs_plain"] = learned
+    if dups is not None:
+        out["duplicates"] = dups
 
     # CPU baseline (oracle on a bounded sample) and the finder's algorithmic work per seed.
     counters = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, n, counters, cores = oracle_sample(wl, batch, args.cpu_seeds)
+        dt, n, counters, cores = oracle_sample(wl, batch, args.cpu_seeds, clean)
         out["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"first {n} seeds of the batch: index, find, fit of the found tracks "
-                                         f"(FP64, {dt:.1f} s)"}
+                               "sample": f"first {n} seeds of the batch: index, "
+                                         + ("seed cleaning, find, duplicate removal, " if clean else "find, ")
+                                         + f"fit of the found tracks (FP64, {dt:.1f} s)"}
         counters = np.asarray(counters, np.float64) / n
     out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
     if rank == 0:
@@ -380,6 +423,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
                             mlp=buf, top_n=top_n)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
+        lp.seed_keep, lp._keep_ref = prm.seed_keep, getattr(prm, "_keep_ref", None)  # same seeds
         lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
         times = []
         for i in range(args.warmup + args.steps):
@@ -463,6 +507,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration")
+    ap.add_argument("--clean", action="store_true",
+                    help="seed cleaning and duplicate-track removal in the step (on for combinatorial seeds)")
     ap.add_argument("--steering", action="store_true",
                     help="region steering lists (5 eta regions) instead of the geometric next-surface rule")
     args = ap.parse_args()

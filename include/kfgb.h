@@ -150,6 +150,9 @@ typedef struct {
    * and the next disk beyond |z| in the direction of motion (crossed within its r extent, within
    * half a turn). */
   const KfSteering* steering;
+  /* Optional device int [n_seeds] (kf_clean_seeds' keep_out): seeds with 0 are not processed;
+   * their outputs are empty (no hits, NaN state) with status 2. NULL: every seed. */
+  const int* seed_keep;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,
@@ -210,11 +213,36 @@ size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params);
  *   workspace          device memory of kf_find_workspace_size bytes, 256-byte aligned.
  * Outputs (device): hits_out int [lmax][n_seeds] (best candidate's hit ids in path order, -1 for
  * a miss or no further step), nhits_out int, chi2_out float, state_out float [6][n_seeds],
- * cov_out float [21][n_seeds], status_out int (0 ok, 1 seed failed). */
+ * cov_out float [21][n_seeds], status_out int (0 ok, 1 seed failed, 2 seed removed by seed_keep). */
 int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
                    const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
                    int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
                    int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
+
+/* Seed cleaning and duplicate-track removal. Seeds and tracks of one event that share a hit are
+ * compared through an inverted index hit -> items built in the workspace; the decisions depend on
+ * no processing order.
+ * kf_clean_seeds (Sec. 3.2: several seeds of one particle, e.g. from overlapping modules, are
+ * removed before finding, by hit identity and seed direction): seed j is removed (keep_out[j] =
+ * 0, else 1) when a seed i < j of the same event shares a hit with it and their directions at the
+ * first hit agree, |d phi| < dphi and |d theta| < dtheta (the direction of the circle through the
+ * three hits and of the line through hits 1 and 3, as the finder's seed state; a seed whose hits
+ * give no state is kept).
+ * kf_remove_duplicates (Sec. 4: duplicate tracks from several seeds per particle): track j is
+ * removed when a better track i of the same event (more hits, then lower chi2, then lower index)
+ * whose final direction agrees (state[4], state[5]: |d phi| < dphi, |d theta| < dtheta) holds
+ * more than half of j's hits.
+ *   seed_hits  device int [3][n_seeds]; track_hits device int [lmax][n_tracks] (-1: none), nhits,
+ *              chi2, state [6][n_tracks] (the finder's outputs); *_event device int; hit ids < n_hits.
+ *   workspace  device memory of kf_dedup_workspace_size(n_items, 3 or lmax, n_hits) bytes, 256-byte
+ *              aligned. */
+size_t kf_dedup_workspace_size(int n_items, int refs_per_item, int n_hits);
+int kf_clean_seeds(const KfGeometry* geom, const float* hits, const int* hit_surface, int n_hits, const int* seed_hits,
+                   const int* seed_event, int n_seeds, float dphi, float dtheta, int* keep_out, void* workspace,
+                   size_t workspace_bytes, kf_stream_t stream);
+int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
+                         const int* track_event, int n_tracks, int lmax, int n_hits, float dphi, float dtheta,
+                         int* keep_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
 
 /* Learned hit proposal network (not in the paper): MLP 14 -> 64 -> 64 -> 1 with ReLU, scoring a
  * (predicted candidate, hit) pair from 14 features: the predicted state (x, y, z, kappa, phi,

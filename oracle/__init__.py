@@ -90,6 +90,10 @@ def _load():
             lib.or_find.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_longlong, ctypes.c_int,
                                     ctypes.POINTER(OrFindParams), ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
                                     _P, _P, _P, ctypes.c_int, ctypes.POINTER(OrSteering)]
+            lib.or_seed_params.argtypes = [G, _P, _P, _P, ctypes.c_longlong, _P]
+            lib.or_clean_seeds.argtypes = [_P, _P, _P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, _P]
+            lib.or_remove_duplicates.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_int,
+                                                 ctypes.c_double, ctypes.c_double, _P]
             lib.or_mlp_nparams.restype = ctypes.c_int
             lib.or_find_pairs.restype = ctypes.c_longlong
             lib.or_find_pairs.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_longlong,
@@ -374,6 +378,75 @@ def unpack_cov(c21):
             out[..., j, i] = c21[..., k]
             k += 1
     return out
+
+
+def seed_params(geom: Geometry, batch, seed_hits):
+    """(kappa, phi, theta) of each seed from its three hits ([n, 3]; NaN when no seed)."""
+    lib = _load()
+    sh = _c(seed_hits, np.int32)
+    out = np.empty((sh.shape[0], 3))
+    lib.or_seed_params(geom.ref, _c(batch.hits, np.float32).ctypes.data, _c(batch.hit_surface, np.int32).ctypes.data,
+                       sh.ctypes.data, sh.shape[0], out.ctypes.data)
+    return out
+
+
+def clean_seeds(seed_hits, seed_event, params, dphi: float = 0.02, dtheta: float = 0.05):
+    """Seed cleaning: keep[n] (0 for a seed with a lower-index duplicate)."""
+    lib = _load()
+    sh, se, pr = _c(seed_hits, np.int32), _c(seed_event, np.int32), _c(params, np.float64)
+    keep = np.empty(sh.shape[0], np.int32)
+    lib.or_clean_seeds(sh.ctypes.data, se.ctypes.data, pr.ctypes.data, sh.shape[0], float(dphi), float(dtheta),
+                       keep.ctypes.data)
+    return keep
+
+
+def remove_duplicates(hits, n_hits, chi2, phi, theta, track_event, dphi: float = 0.02, dtheta: float = 0.05):
+    """Duplicate-track removal: keep[n] (0 for a track with a better duplicate)."""
+    lib = _load()
+    h = _c(hits, np.int32)
+    keep = np.empty(h.shape[0], np.int32)
+    lib.or_remove_duplicates(h.ctypes.data, _c(n_hits, np.int32).ctypes.data, _c(chi2, np.float64).ctypes.data,
+                             _c(phi, np.float64).ctypes.data, _c(theta, np.float64).ctypes.data,
+                             _c(track_event, np.int32).ctypes.data, h.shape[0], h.shape[1], float(dphi),
+                             float(dtheta), keep.ctypes.data)
+    return keep
+
+
+def majority_sim(batch, found_hits, found_nhits, min_hits: int = 10, match_frac: float = 0.5):
+    """Simulated track each found track is matched to, whatever its seed (-1: none): the sim track
+    holding more than ``match_frac`` of the track's hits, for tracks with >= min(min_hits, that
+    sim track's crossings - 1) hits (the paper's hit-fraction matching, Sec. 4)."""
+    fh = np.asarray(found_hits)
+    nh = np.asarray(found_nhits)
+    out = np.full(len(fh), -1, np.int64)
+    for i in range(len(fh)):
+        sims = batch.hit_sim[fh[i][fh[i] >= 0]]
+        sims = sims[sims >= 0]
+        if len(sims) == 0:
+            continue
+        vals, cnt = np.unique(sims, return_counts=True)
+        t = int(vals[np.argmax(cnt)])
+        if cnt.max() > match_frac * (fh[i] >= 0).sum() and nh[i] >= min(min_hits, int(batch.track_nhits[t]) - 1):
+            out[i] = t
+    return out
+
+
+def track_rates(batch, seed_track, matched, keep=None, min_hits: int = 10, track_sim=None):
+    """Per simulated track (several seeds may share one): efficiency = reference tracks (>=
+    min_hits hits, with a seed) with at least one matched kept track; duplicate rate = reference
+    tracks with two or more (the paper's duplicate track rate, Sec. 4). A track counts for its
+    seed's sim track, or, with ``track_sim`` (majority_sim), for the sim track it is matched to."""
+    st = np.asarray(seed_track)
+    m = np.asarray(matched, bool) & (np.ones(len(st), bool) if keep is None else np.asarray(keep) != 0)
+    owner = st
+    if track_sim is not None:
+        owner = np.asarray(track_sim)
+        m &= owner >= 0
+    counts = np.bincount(owner[m], minlength=batch.n_tracks)
+    ref = np.zeros(batch.n_tracks, bool)
+    ref[st] = True
+    ref &= batch.track_nhits >= min_hits
+    return float((counts[ref] >= 1).mean()), float((counts[ref] >= 2).mean())
 
 
 def efficiency(batch, seed_track, found_hits, found_nhits, min_hits: int = 10, match_frac: float = 0.5):

@@ -28,6 +28,7 @@
 #include <cstdint>
 #include <cstring>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 namespace {
@@ -1312,6 +1313,86 @@ void or_adam(double* w, const double* grad, double* m, double* v, int t, double 
     m[i] = b1 * m[i] + (1.0 - b1) * grad[i];
     v[i] = b2 * v[i] + (1.0 - b2) * grad[i] * grad[i];
     w[i] -= lr * (m[i] / c1) / (std::sqrt(v[i] / c2) + eps);
+  }
+}
+
+// ---- seed cleaning and duplicate-track removal (Sec. 3.2 and Sec. 4 readings) -----------------
+// Seed parameters (kappa, phi, theta) from the circle through the three hits and the line through
+// hits 1 and 3 (the seed state at hit 1); NaN when the hits give no seed.
+void or_seed_params(const OrGeom* g, const float* hits, const int* hsurf, const int* seeds, long long n,
+                    double* out) {
+  for (long long i = 0; i < n; ++i) {
+    State st;
+    const bool ok = seeds[3 * i] >= 0 && seeds[3 * i + 1] >= 0 && seeds[3 * i + 2] >= 0 &&
+                    seed_state(*g, hits, hsurf, seeds + 3 * i, st);
+    out[3 * i] = ok ? st.p[3] : NAN;
+    out[3 * i + 1] = ok ? st.p[4] : NAN;
+    out[3 * i + 2] = ok ? st.p[5] : NAN;
+  }
+}
+
+// Seeds i < j of the same event are duplicates when they share a hit and their directions agree
+// (|d phi| < dphi, |d theta| < dtheta); a seed with a duplicate of lower index is removed
+// (keep = 0). The rule depends on no processing order. params: or_seed_params.
+void or_clean_seeds(const int* seeds, const int* seed_event, const double* params, long long n, double dphi,
+                    double dtheta, int* keep) {
+  std::unordered_map<int, std::vector<long long>> users;  // hit -> seeds using it
+  for (long long i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k)
+      if (seeds[3 * i + k] >= 0) users[seeds[3 * i + k]].push_back(i);
+  for (long long j = 0; j < n; ++j) {
+    keep[j] = 1;
+    if (!(params[3 * j + 1] == params[3 * j + 1])) continue;  // no seed: nothing to compare
+    for (int k = 0; k < 3 && keep[j]; ++k) {
+      const int h = seeds[3 * j + k];
+      if (h < 0) continue;
+      for (long long i : users[h]) {
+        if (i >= j || seed_event[i] != seed_event[j]) continue;
+        const double a = std::fabs(wrap_angle(params[3 * i + 1] - params[3 * j + 1]));
+        const double b = std::fabs(params[3 * i + 2] - params[3 * j + 2]);
+        if (a < dphi && b < dtheta) {
+          keep[j] = 0;
+          break;
+        }
+      }
+    }
+  }
+}
+
+// Found tracks (hits[n][lmax], -1 = none; n_hits, chi2, final phi and theta): track j is removed
+// (keep = 0) when a better track i of the same event (more hits, then lower chi2, then lower
+// index) with |d phi| < dphi and |d theta| < dtheta holds more than half of j's hits.
+void or_remove_duplicates(const int* hits, const int* n_hits, const double* chi2, const double* phi,
+                          const double* theta, const int* track_event, long long n, int lmax, double dphi,
+                          double dtheta, int* keep) {
+  std::unordered_map<int, std::vector<long long>> users;
+  for (long long i = 0; i < n; ++i)
+    for (int k = 0; k < lmax; ++k)
+      if (hits[i * lmax + k] >= 0) users[hits[i * lmax + k]].push_back(i);
+  auto better = [&](long long i, long long j) {
+    if (n_hits[i] != n_hits[j]) return n_hits[i] > n_hits[j];
+    if (chi2[i] != chi2[j]) return chi2[i] < chi2[j];
+    return i < j;
+  };
+  for (long long j = 0; j < n; ++j) {
+    keep[j] = 1;
+    int own = 0;
+    std::unordered_map<long long, int> shared;
+    for (int k = 0; k < lmax; ++k) {
+      const int h = hits[j * lmax + k];
+      if (h < 0) continue;
+      ++own;
+      for (long long i : users[h])
+        if (i != j && track_event[i] == track_event[j]) ++shared[i];
+    }
+    for (const auto& kv : shared) {
+      const long long i = kv.first;
+      if (2 * kv.second <= own || !better(i, j)) continue;
+      if (std::fabs(wrap_angle(phi[i] - phi[j])) < dphi && std::fabs(theta[i] - theta[j]) < dtheta) {
+        keep[j] = 0;
+        break;
+      }
+    }
   }
 }
 

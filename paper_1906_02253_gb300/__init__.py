@@ -60,12 +60,13 @@ class KfFindParams(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int),
-                ("steering", ctypes.POINTER(KfSteering))]
+                ("steering", ctypes.POINTER(KfSteering)), ("seed_keep", ctypes.c_void_p)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
-           "kf_autotune_fit", "kf_status_string")
+           "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
+           "kf_remove_duplicates")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
@@ -105,6 +106,12 @@ def load_library(path: str = LIB_PATH):
             lib.kf_autotune_fit.restype = I
             lib.kf_autotune_fit.argtypes = [G, P, P, P, I, I, P, P, P, P, P, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_float), P]
+            lib.kf_dedup_workspace_size.restype = S
+            lib.kf_dedup_workspace_size.argtypes = [I, I, I]
+            lib.kf_clean_seeds.restype = I
+            lib.kf_clean_seeds.argtypes = [G, P, P, I, P, P, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
+            lib.kf_remove_duplicates.restype = I
+            lib.kf_remove_duplicates.argtypes = [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -237,7 +244,7 @@ def steering(tables: dict) -> KfSteering:
 
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
                 blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0,
-                steering_tables: dict = None) -> KfFindParams:
+                steering_tables: dict = None, seed_keep=None) -> KfFindParams:
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
     ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
     next-surface rule."""
@@ -246,12 +253,61 @@ def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_thr
         if mlp.numel() != MLP_BUFFER:
             raise KfError(f"mlp must hold {MLP_BUFFER} floats")
     st = None if steering_tables is None else steering(steering_tables)
+    if seed_keep is not None:
+        _cuda(seed_keep, torch.int32, "seed_keep")
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
                        None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity),
-                       None if st is None else ctypes.pointer(st))
-    prm._mlp_ref = mlp  # keep the buffer alive with the parameters
+                       None if st is None else ctypes.pointer(st), None if seed_keep is None else seed_keep.data_ptr())
+    prm._mlp_ref = mlp  # keep the buffers alive with the parameters
     prm._steer_ref = st
+    prm._keep_ref = seed_keep
     return prm
+
+
+def dedup_workspace_size(n_items: int, refs_per_item: int, n_hits: int) -> int:
+    """kf_dedup_workspace_size: bytes for kf_clean_seeds (refs 3) or kf_remove_duplicates (lmax)."""
+    return int(load_library().kf_dedup_workspace_size(n_items, refs_per_item, n_hits))
+
+
+def clean_seeds(geom: Geometry, hits, hit_surface, seed_hits, seed_event, dphi: float = 0.02, dtheta: float = 0.05,
+                keep=None, workspace=None, stream=None):
+    """kf_clean_seeds: keep [n_seeds] int32 (0: a seed with a lower-index duplicate)."""
+    lib = load_library()
+    for t, nm in ((hit_surface, "hit_surface"), (seed_hits, "seed_hits"), (seed_event, "seed_event")):
+        _cuda(t, torch.int32, nm)
+    _cuda(hits, torch.float32, "hits")
+    n, nh = seed_hits.shape[1], hits.shape[0]
+    if keep is None:
+        keep = torch.empty(n, dtype=torch.int32, device=hits.device)
+    ws = workspace
+    if ws is None:
+        ws = torch.empty(max(int(lib.kf_dedup_workspace_size(n, 3, nh)), 256), dtype=torch.uint8, device=hits.device)
+    rc = lib.kf_clean_seeds(geom.ref, _ptr(hits), _ptr(hit_surface), nh, _ptr(seed_hits), _ptr(seed_event), n,
+                            float(dphi), float(dtheta), _ptr(keep), _ptr(ws), ws.numel(), _stream(stream))
+    _check(rc, "kf_clean_seeds")
+    return keep
+
+
+def remove_duplicates(track_hits, nhits, chi2, state, track_event, n_hits: int, dphi: float = 0.02,
+                      dtheta: float = 0.05, keep=None, workspace=None, stream=None):
+    """kf_remove_duplicates on the finder's outputs: keep [n_tracks] int32 (0: a duplicate)."""
+    lib = load_library()
+    for t, nm in ((track_hits, "track_hits"), (nhits, "nhits"), (track_event, "track_event")):
+        _cuda(t, torch.int32, nm)
+    _cuda(chi2, torch.float32, "chi2")
+    _cuda(state, torch.float32, "state")
+    lmax, n = track_hits.shape
+    if keep is None:
+        keep = torch.empty(n, dtype=torch.int32, device=track_hits.device)
+    ws = workspace
+    if ws is None:
+        ws = torch.empty(max(int(lib.kf_dedup_workspace_size(n, lmax, n_hits)), 256), dtype=torch.uint8,
+                         device=track_hits.device)
+    rc = lib.kf_remove_duplicates(_ptr(track_hits), _ptr(nhits), _ptr(chi2), _ptr(state), _ptr(track_event), n, lmax,
+                                  int(n_hits), float(dphi), float(dtheta), _ptr(keep), _ptr(ws), ws.numel(),
+                                  _stream(stream))
+    _check(rc, "kf_remove_duplicates")
+    return keep
 
 
 def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:
@@ -391,6 +447,7 @@ def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits,
     tuned = KfFindParams.from_buffer_copy(params)
     tuned._mlp_ref = getattr(params, "_mlp_ref", None)  # keep what the copied pointers point to alive
     tuned._steer_ref = getattr(params, "_steer_ref", None)
+    tuned._keep_ref = getattr(params, "_keep_ref", None)
     ms = ctypes.c_float()
     rc = load_library().kf_autotune_find(geom.ref, ctypes.byref(index.c), _ptr(hits), _ptr(hit_surface),
                                          _ptr(seed_hits), _ptr(seed_event), seed_hits.shape[1], ctypes.byref(tuned),

@@ -19,6 +19,14 @@ __global__ void k_fit_tracks(DevGeom G, const __grid_constant__ DevMat M, const 
                              int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
                              int* status_out);
 
+size_t dup_workspace_bytes(int n, int m, int n_hits);
+int launch_clean_seeds(const DevGeom& G, const float2* hits, const int* hit_surface, const int* seed_hits,
+                       const int* seed_event, int n, int n_hits, float dphi, float dtheta, int* keep, void* ws,
+                       cudaStream_t st);
+int launch_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
+                             const int* event, int n, int lmax, int n_hits, float dphi, float dtheta, int* keep,
+                             void* ws, cudaStream_t st);
+
 }  // namespace kfgb
 
 #include "find_launch.cuh"
@@ -313,6 +321,7 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   A.status_out = status_out;
   A.mlp = params->mlp;
   A.top_n = params->mlp ? params->top_n : 0;
+  A.seed_keep = params->seed_keep;
   return launch_find(G, M, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -386,6 +395,7 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   A.status_out = status_out;
   A.mlp = params->mlp;
   A.top_n = params->mlp ? params->top_n : 0;
+  A.seed_keep = params->seed_keep;
   return launch_find(G, M, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -448,6 +458,40 @@ int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_su
   *block_threads = best_b;
   *best_ms = best_t;
   return KF_OK;
+}
+
+size_t kf_dedup_workspace_size(int n_items, int refs_per_item, int n_hits) {
+  if (n_items < 0 || refs_per_item < 1 || n_hits < 0) return 0;
+  return dup_workspace_bytes(n_items, refs_per_item, n_hits);
+}
+
+int kf_clean_seeds(const KfGeometry* geom, const float* hits, const int* hit_surface, int n_hits, const int* seed_hits,
+                   const int* seed_event, int n_seeds, float dphi, float dtheta, int* keep_out, void* workspace,
+                   size_t workspace_bytes, kf_stream_t stream) {
+  DevGeom G;
+  const int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  if (n_seeds < 0 || n_hits < 0 || !(dphi >= 0.f) || !(dtheta >= 0.f)) return KF_ERR_ARG;
+  if (n_seeds == 0) return KF_OK;
+  if (!hits || !hit_surface || !seed_hits || !seed_event || !keep_out || !workspace) return KF_ERR_ARG;
+  if (workspace_bytes < dup_workspace_bytes(n_seeds, 3, n_hits) || (reinterpret_cast<size_t>(workspace) & 255))
+    return KF_ERR_ARG;
+  return launch_clean_seeds(G, reinterpret_cast<const float2*>(hits), hit_surface, seed_hits, seed_event, n_seeds,
+                            n_hits, dphi, dtheta, keep_out, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
+                         const int* track_event, int n_tracks, int lmax, int n_hits, float dphi, float dtheta,
+                         int* keep_out, void* workspace, size_t workspace_bytes, kf_stream_t stream) {
+  if (n_tracks < 0 || n_hits < 0 || lmax < 1 || lmax > KF_MAX_LMAX || !(dphi >= 0.f) || !(dtheta >= 0.f))
+    return KF_ERR_ARG;
+  if (n_tracks == 0) return KF_OK;
+  if (!track_hits || !nhits || !chi2 || !state || !track_event || !keep_out || !workspace) return KF_ERR_ARG;
+  if (static_cast<long long>(n_tracks) * lmax > 0x7fffffffLL) return KF_ERR_CAPACITY;
+  if (workspace_bytes < dup_workspace_bytes(n_tracks, lmax, n_hits) || (reinterpret_cast<size_t>(workspace) & 255))
+    return KF_ERR_ARG;
+  return launch_remove_duplicates(track_hits, nhits, chi2, state, track_event, n_tracks, lmax, n_hits, dphi, dtheta,
+                                  keep_out, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char* kf_status_string(int status) {

@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, const __grid_con
 #pragma unroll
   for (int k = 0; k < 3; ++k) ids[k] = A.seed_hits[static_cast<size_t>(k) * n + seed];
   const int ev = A.seed_event[seed];
-  bool ok = ids[0] >= 0 && ids[1] >= 0 && ids[2] >= 0 && ev >= 0 && ev < A.n_events;
+  const bool removed = A.seed_keep && A.seed_keep[seed] == 0;
+  bool ok = !removed && ids[0] >= 0 && ids[1] >= 0 && ids[2] >= 0 && ev >= 0 && ev < A.n_events;
   Cand c;
   int ss[3] = {0, 0, 0};
   if (ok) {
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, const __grid_con
     A.chi2_out[seed] = nanf_;
     for (int i = 0; i < 6; ++i) A.state_out[static_cast<size_t>(i) * n + seed] = nanf_;
     for (int i = 0; i < 21; ++i) A.cov_out[static_cast<size_t>(i) * n + seed] = nanf_;
-    A.status_out[seed] = 1;
+    A.status_out[seed] = removed ? 2 : 1;
   }
 }
 

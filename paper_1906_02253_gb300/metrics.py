@@ -28,3 +28,45 @@ def efficiency(batch, seed_track, found_hits, found_nhits, min_hits: int = 10, m
     eff = float(matched[ref].mean()) if ref.any() else float("nan")
     fake = float(1.0 - matched.mean()) if matched.size else float("nan")
     return eff, fake
+
+
+def majority_sim(batch, found_hits, found_nhits, min_hits: int = 10, match_frac: float = 0.5, chunk: int = 32768):
+    """Simulated track each found track belongs to, whatever its seed (-1: none): the one holding
+    more than ``match_frac`` of the track's hits, for tracks with at least min(min_hits,
+    crossings - 1) hits (hit-fraction matching, as in the paper's validation, Sec. 4)."""
+    fh = np.asarray(found_hits)
+    nh = np.asarray(found_nhits)
+    out = np.full(len(fh), -1, np.int64)
+    for a in range(0, len(fh), chunk):
+        h = fh[a:a + chunk]
+        valid = h >= 0
+        sim = np.where(valid, batch.hit_sim[np.where(valid, h, 0)], -1)
+        same = (sim[:, :, None] == sim[:, None, :]) & (sim[:, None, :] >= 0)
+        cnt = np.where(sim >= 0, same.sum(axis=2), 0)
+        best = cnt.argmax(axis=1)
+        rows = np.arange(len(h))
+        top, s = cnt[rows, best], sim[rows, best]
+        need = np.minimum(min_hits, batch.track_nhits[np.maximum(s, 0)] - 1)
+        ok = (top > match_frac * valid.sum(axis=1)) & (s >= 0) & (nh[a:a + chunk] >= need)
+        out[a:a + chunk] = np.where(ok, s, -1)
+    return out
+
+
+def track_rates(batch, seed_track, found_hits, found_nhits, keep=None, min_hits: int = 10):
+    """(efficiency, duplicate rate, fake rate) per simulated track when several seeds may come from
+    one particle. Reference tracks: simulated tracks with >= min_hits hits and a seed. Efficiency:
+    reference tracks with at least one kept track matched to them (majority_sim); duplicate rate:
+    those with two or more; fake rate: kept tracks with hits matched to no simulated track."""
+    st = np.asarray(seed_track)
+    sim = majority_sim(batch, found_hits, found_nhits, min_hits)
+    kept = np.ones(len(st), bool) if keep is None else np.asarray(keep) != 0
+    kept &= np.asarray(found_nhits) > 0
+    m = kept & (sim >= 0)
+    counts = np.bincount(sim[m], minlength=batch.n_tracks)
+    ref = np.zeros(batch.n_tracks, bool)
+    ref[st] = True
+    ref &= batch.track_nhits >= min_hits
+    eff = float((counts[ref] >= 1).mean()) if ref.any() else float("nan")
+    dup = float((counts[ref] >= 2).mean()) if ref.any() else float("nan")
+    fake = float(1.0 - m.sum() / kept.sum()) if kept.any() else float("nan")
+    return eff, dup, fake

@@ -51,7 +51,8 @@ class _SynthParams(ctypes.Structure):
                 ("bz", ctypes.c_double), ("sigma_rphi", ctypes.c_double), ("sigma_2nd", ctypes.c_double),
                 ("noise_frac", ctypes.c_double), ("seed", ctypes.c_uint64), ("ms_on", ctypes.c_int),
                 ("smear_on", ctypes.c_int), ("record_truth", ctypes.c_int), ("n_threads", ctypes.c_int),
-                ("material", ctypes.c_void_p), ("eloss", ctypes.c_double), ("mass", ctypes.c_double)]
+                ("material", ctypes.c_void_p), ("eloss", ctypes.c_double), ("mass", ctypes.c_double),
+                ("overlap_frac", ctypes.c_double)]
 
 
 MAT_NODES = 8  # material map nodes per surface
@@ -125,6 +126,10 @@ class Workload:
     material: tuple = None
     eloss: float = 0.0
     mass: float = 0.13957
+    # module overlaps: probability that a crossing leaves a second hit of the particle on the
+    # surface; seeds from every combination of a track's hits on its first three surfaces
+    overlap_frac: float = 0.0
+    combinatorial_seeds: bool = False
 
     @property
     def lmax(self) -> int:
@@ -218,6 +223,11 @@ def _wl_material() -> Workload:
                     seed=6, material=material_map(surf), eloss=0.0363)
 
 
+def _wl_duplicates() -> Workload:
+    return Workload("find_20x5k_17layers_overlaps30_noise30", tuple(barrel_layers(17)), n_events=20, tracks_lo=5000,
+                    tracks_hi=5000, seed=7, noise_frac=0.3, k_max=6, overlap_frac=0.3, combinatorial_seeds=True)
+
+
 WORKLOADS = {
     "fit_small": _wl_fit_small(),
     "fit_batched": _wl_fit_batched(),
@@ -225,6 +235,7 @@ WORKLOADS = {
     "learned": _wl_learned(),
     "hi_occ": _wl_hi_occ(),
     "material": _wl_material(),
+    "duplicates": _wl_duplicates(),
 }
 
 
@@ -272,10 +283,40 @@ class EventBatch:
     def n_surf(self) -> int:
         return len(self.wl.surfaces)
 
-    def seeds(self, min_hits: int = 3):
-        """Seeds from each track's first three true hits: (seed_hits [n,3], seed_track [n])."""
+    def seeds(self, min_hits: int = 3, combinations: bool = None):
+        """Seeds: (seed_hits [n,3], seed_track [n]). One per track from its first three true hits,
+        or (combinations, the workload's default) one per combination of the track's hits on its
+        first three surfaces (overlap hits included), seeds of a track consecutive, in
+        lexicographic order of hit ids."""
+        if combinations is None:
+            combinations = getattr(self.wl, "combinatorial_seeds", False)
         ok = np.nonzero(self.track_nhits >= min_hits)[0].astype(np.int32)
-        return np.ascontiguousarray(self.track_hits[ok, :3]), ok
+        if not combinations:
+            return np.ascontiguousarray(self.track_hits[ok, :3]), ok
+        ns = self.n_surf
+        sig = np.nonzero(self.hit_sim >= 0)[0]
+        key = self.hit_sim[sig].astype(np.int64) * ns + self.hit_surface[sig]
+        order = np.lexsort((sig, key))
+        sk, sh = key[order], sig[order]
+        lists = []
+        for k in range(3):
+            kk = ok.astype(np.int64) * ns + self.track_surf[ok, k]
+            lo = np.searchsorted(sk, kk, side="left")
+            hi = np.searchsorted(sk, kk, side="right")
+            lists.append((lo, hi - lo))
+        counts = lists[0][1] * lists[1][1] * lists[2][1]
+        n = int(counts.sum())
+        out = np.empty((n, 3), np.int32)
+        trk = np.repeat(ok, counts)
+        start = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        for t_i in range(len(ok)):  # a handful of combinations per track
+            c = start[t_i]
+            for a in range(lists[0][1][t_i]):
+                for b in range(lists[1][1][t_i]):
+                    for d in range(lists[2][1][t_i]):
+                        out[c] = (sh[lists[0][0][t_i] + a], sh[lists[1][0][t_i] + b], sh[lists[2][0][t_i] + d])
+                        c += 1
+        return out, trk.astype(np.int32)
 
 
 def generate(wl, *, n_events: int = None, seed: int = None, smear: bool = True, ms: bool = None,
@@ -309,7 +350,7 @@ def generate(wl, *, n_events: int = None, seed: int = None, smear: bool = True, 
     prm = _SynthParams(wl.n_events, wl.tracks_lo, wl.tracks_hi, wl.pt_lo, wl.pt_hi, wl.eta_max, f32(wl.bz),
                        wl.sigma_rphi, wl.sigma_2nd, wl.noise_frac, wl.seed, int(wl.ms_on), int(smear),
                        int(record_truth), n_threads, None if mat is None else mat.ctypes.data, f32(wl.eloss),
-                       f32(wl.mass))
+                       f32(wl.mass), wl.overlap_frac)
     lmax = wl.lmax
     h = lib.synth_generate(ctypes.byref(prm), surf, len(wl.surfaces), lmax)
     if not h:

@@ -100,6 +100,9 @@ struct SynthParams {
   const double* material;    // [n_surf][kMatNodes] or null
   double eloss;
   double mass;
+  // Module overlaps: with this probability a crossing leaves a second hit of the same particle
+  // on the surface (an overlapping module; smeared independently).
+  double overlap_frac;
 };
 constexpr int kMatNodes = 8;
 
@@ -406,6 +409,17 @@ void generate_event(int e, int n_tracks, const std::vector<SynthSurface>& surf, 
         second = r + (prm.smear_on ? rng.gauss() * prm.sigma_2nd : 0.0);
       }
       per_surf[c.surf].push_back({wrap_phi_f(phi_h), static_cast<float>(second), t, t, k});
+      if (prm.overlap_frac > 0.0 && rng.uniform() < prm.overlap_frac) {
+        double phi2 = std::atan2(c.y, c.x), second2;
+        if (S.type == 0) {
+          if (prm.smear_on) phi2 += rng.gauss() * prm.sigma_rphi / S.r_or_z;
+          second2 = c.z + (prm.smear_on ? rng.gauss() * prm.sigma_2nd : 0.0);
+        } else {
+          if (prm.smear_on) phi2 += rng.gauss() * prm.sigma_rphi / r;
+          second2 = r + (prm.smear_on ? rng.gauss() * prm.sigma_2nd : 0.0);
+        }
+        per_surf[c.surf].push_back({wrap_phi_f(phi2), static_cast<float>(second2), t, -1, -1});
+      }
       if (prm.record_truth) {
         for (int i = 0; i < 6; ++i) {
           ev.truth_in[(static_cast<size_t>(t) * lmax + k) * 6 + i] = tout.truth_in[k][i];
