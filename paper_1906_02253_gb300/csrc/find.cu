@@ -520,7 +520,13 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     // ---- refill: a group without a seed takes the next one --------------------------------
     const bool want = !exhausted && seed < 0;
     int s = -1;
-    if (want && slot == 0) s = atomicAdd(A.counter, 1);
+    // Seeds that failed or were removed by cleaning (their outputs written by the seed-state
+    // kernel) are passed over here rather than costing the group a step each.
+    if (want && slot == 0) {
+      do {
+        s = atomicAdd(A.counter, 1);
+      } while (s < n && !(A.seed_state[static_cast<size_t>(27) * n + s] >= 0.f));
+    }
     s = __shfl_sync(kFull, s, gbase);
     bool fresh = false;
     if (want) {
