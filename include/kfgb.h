@@ -74,6 +74,14 @@ typedef struct {
   int ms_off;
   const float* material;
   float eloss, mass;
+  /* Parametrised solenoid field (Sec. 3.1: constant or parametrised magnetic field): Bz(r, z) =
+   * bz (1 + field_z2 z^2 + field_r2 r^2), cm^-2, radial component neglected. Each step between
+   * surfaces is a helix in the field at the midpoint of its chord p + (s/2)(cos phi, sin phi,
+   * cot theta), s the path in the field at the step's start (which also decides the next
+   * surface); the field's gradient is not propagated into the covariance; a seed's kappa uses
+   * the field at its first hit. Both zero (zero-filled): uniform field bz. Non-finite:
+   * KF_ERR_ARG. */
+  float field_z2, field_r2;
 } KfGeometry;
 #define KF_MAT_NODES 8
 

@@ -52,7 +52,7 @@ class OrGeom(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_float), ("n_surf", ctypes.c_int), ("surf", ctypes.POINTER(OrSurface)),
                 ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5),
                 ("ms_off", ctypes.c_int), ("material", ctypes.c_void_p), ("eloss", ctypes.c_float),
-                ("mass", ctypes.c_float)]
+                ("mass", ctypes.c_float), ("field_z2", ctypes.c_float), ("field_r2", ctypes.c_float)]
 
 
 class OrFindParams(ctypes.Structure):
@@ -123,7 +123,7 @@ class Geometry:
         self.g = OrGeom(wl.bz, n, ctypes.cast(self._surf, ctypes.POINTER(OrSurface)), wl.sigma_rphi,
                         wl.sigma_2nd, (ctypes.c_float * 5)(*wl.prior), int(not wl.ms_on),
                         None if self._mat is None else self._mat.ctypes.data, getattr(wl, "eloss", 0.0),
-                        getattr(wl, "mass", 0.13957))
+                        getattr(wl, "mass", 0.13957), getattr(wl, "field_z2", 0.0), getattr(wl, "field_r2", 0.0))
 
     @property
     def ref(self):

@@ -60,6 +60,9 @@ struct OrGeom {
   int ms_off;
   const float* material;
   float eloss, mass;
+  // Parametrised solenoid field (Sec. 3.1: constant or parametrised field): Bz(r, z) = bz (1 +
+  // field_z2 z^2 + field_r2 r^2), cm^-2; both zero: uniform. The radial component is neglected.
+  float field_z2, field_r2;
 };
 constexpr int kMatNodes = 8;
 // Region steering of the finder (Sec. 3.1 tracking regions): five regions in eta (0 barrel, 1/2
@@ -94,7 +97,20 @@ inline double wrap_angle(double a) {
   return a;
 }
 
-inline double omega_of(const OrGeom& g, double kappa) { return -kCurv * static_cast<double>(g.bz) * kappa; }
+inline double omega_of(double bz, double kappa) { return -kCurv * bz * kappa; }
+
+inline bool field_map(const OrGeom& g) { return g.field_z2 != 0.0f || g.field_r2 != 0.0f; }
+
+// Bz at (x, y, z).
+inline double field_at(const OrGeom& g, double x, double y, double z) {
+  return static_cast<double>(g.bz) *
+         (1.0 + static_cast<double>(g.field_z2) * z * z + static_cast<double>(g.field_r2) * (x * x + y * y));
+}
+
+// Field at the start of a step from state p (the field that decides which surface is next).
+inline double start_field(const OrGeom& g, const double* p) {
+  return field_map(g) ? field_at(g, p[0], p[1], p[2]) : static_cast<double>(g.bz);
+}
 
 // ---- helix at fixed transverse path s -------------------------------------------------------
 // f1 = sin(D)/D, f2 = (1-cos D)/D with D = omega*s; position change
@@ -122,8 +138,8 @@ inline void helix_df(double D, double& d1, double& d2) {
   }
 }
 
-void helix_at(const OrGeom& g, const double* p0, double s, double* p1) {
-  const double w = omega_of(g, p0[3]);
+void helix_at(double bz, const double* p0, double s, double* p1) {
+  const double w = omega_of(bz, p0[3]);
   double f1, f2;
   helix_f(w * s, f1, f2);
   const double c = std::cos(p0[4]), sn = std::sin(p0[4]);
@@ -136,9 +152,9 @@ void helix_at(const OrGeom& g, const double* p0, double s, double* p1) {
 }
 
 // Smallest s > 0 at which the helix reaches radius R; false when it does not.
-bool path_to_cylinder(const OrGeom& g, const double* p0, double R, double& s_out) {
+bool path_to_cylinder(double bz, const double* p0, double R, double& s_out) {
   const double x = p0[0], y = p0[1], phi = p0[4];
-  const double w = omega_of(g, p0[3]);
+  const double w = omega_of(bz, p0[3]);
   const double c = std::cos(phi), sn = std::sin(phi);
   if (std::fabs(w) < 1e-9) {  // straight line
     const double a = x * c + y * sn;
@@ -182,21 +198,21 @@ bool path_to_cylinder(const OrGeom& g, const double* p0, double R, double& s_out
 // Path to the plane z = Z. A track is followed for at most half a turn in the transverse plane
 // (|omega s| < pi), as the generator follows particles: beyond that it would be coming back
 // inward, and the disk is not reached.
-bool path_to_disk(const OrGeom& g, const double* p0, double Z, double& s_out) {
+bool path_to_disk(double bz, const double* p0, double Z, double& s_out) {
   const double cot = std::cos(p0[5]) / std::sin(p0[5]);
   if (cot == 0.0) return false;
   const double s = (Z - p0[2]) / cot;
   if (!(s > 1e-9)) return false;
-  if (!(std::fabs(omega_of(g, p0[3]) * s) < kPi)) return false;
+  if (!(std::fabs(omega_of(bz, p0[3]) * s) < kPi)) return false;
   s_out = s;
   return true;
 }
 
 // Jacobian d(state at s)/d(state at 0) at fixed s.
-void jacobian_fixed_s(const OrGeom& g, const double* p0, double s, Mat6 J) {
+void jacobian_fixed_s(double bz, const double* p0, double s, Mat6 J) {
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) J[i][j] = (i == j) ? 1.0 : 0.0;
-  const double dwdk = -kCurv * static_cast<double>(g.bz);
+  const double dwdk = -kCurv * bz;
   const double w = dwdk * p0[3];
   const double D = w * s;
   double f1, f2, d1, d2;
@@ -247,17 +263,35 @@ double material_at(const OrGeom& g, int si, double v) {
 // then the mean energy loss in it: |p| -> p' with E' = E - eloss x/X0 / |cos a| (direction kept),
 // kappa scaled by p/p' and the kappa row and column of C by d kappa'/d kappa = (p/p')^3 E'/E (the
 // loss taken as fixed; its dependence on theta and on the crossing angle is not propagated).
+// With a parametrised field the step is a helix in the field at the midpoint of its chord: the path
+// in the field at the start gives the chord p + (s/2) (cos phi, sin phi, cot theta) to its
+// midpoint, and the path is solved again in the field there (Bz's gradient is not propagated
+// into the covariance).
+bool path_to_surface(const OrGeom& g, double bz, const double* p0, int si, double& s) {
+  const OrSurface& S = g.surf[si];
+  return (S.type == 0) ? path_to_cylinder(bz, p0, S.r_or_z, s) : path_to_disk(bz, p0, S.r_or_z, s);
+}
+
+bool step_field(const OrGeom& g, const double* p0, int si, double& bz, double& s) {
+  bz = start_field(g, p0);
+  if (!path_to_surface(g, bz, p0, si, s)) return false;
+  if (!field_map(g)) return true;
+  const double h = 0.5 * s;
+  bz = field_at(g, p0[0] + h * std::cos(p0[4]), p0[1] + h * std::sin(p0[4]),
+                p0[2] + h * std::cos(p0[5]) / std::sin(p0[5]));
+  return path_to_surface(g, bz, p0, si, s);
+}
+
 bool propagate(const OrGeom& g, const State& in, int si, State& out, Mat6* jac_out = nullptr,
                double* s_used = nullptr) {
   const OrSurface& S = g.surf[si];
-  double s;
-  const bool ok = (S.type == 0) ? path_to_cylinder(g, in.p, S.r_or_z, s) : path_to_disk(g, in.p, S.r_or_z, s);
-  if (!ok) return false;
-  helix_at(g, in.p, s, out.p);
+  double s, bz;
+  if (!step_field(g, in.p, si, bz, s)) return false;
+  helix_at(bz, in.p, s, out.p);
   Mat6 Js, J;
-  jacobian_fixed_s(g, in.p, s, Js);
+  jacobian_fixed_s(bz, in.p, s, Js);
   // Direction of motion along s at the crossing and the surface gradient.
-  const double w = omega_of(g, in.p[3]);
+  const double w = omega_of(bz, in.p[3]);
   const double t[6] = {std::cos(out.p[4]), std::sin(out.p[4]), std::cos(out.p[5]) / std::sin(out.p[5]), 0.0, w, 0.0};
   double gr[6] = {0, 0, 0, 0, 0, 0};
   if (S.type == 0) {
@@ -457,7 +491,7 @@ bool seed_state(const OrGeom& g, const float* hits, const int* hsurf, const int*
   st.p[0] = x1;
   st.p[1] = y1;
   st.p[2] = P[0][2];
-  st.p[3] = -w / (kCurv * static_cast<double>(g.bz));
+  st.p[3] = -w / (kCurv * start_field(g, P[0]));  // the field at hit 1
   st.p[4] = phi;
   st.p[5] = theta;
   for (int i = 0; i < 6; ++i)
@@ -638,11 +672,12 @@ int next_surface(const OrGeom& g, const State& st, double* s_next) {
     const OrSurface& S = g.surf[s];
     if (S.type == 0 && S.r_or_z > rho + 0.01 && (nb < 0 || S.r_or_z < g.surf[nb].r_or_z)) nb = s;
   }
+  const double bz = start_field(g, st.p);
   if (nb >= 0) {
     double s;
-    if (path_to_cylinder(g, st.p, g.surf[nb].r_or_z, s)) {
+    if (path_to_cylinder(bz, st.p, g.surf[nb].r_or_z, s)) {
       double q[6];
-      helix_at(g, st.p, s, q);
+      helix_at(bz, st.p, s, q);
       if (q[2] >= g.surf[nb].lo && q[2] <= g.surf[nb].hi) {
         best = nb;
         best_s = s;
@@ -659,9 +694,9 @@ int next_surface(const OrGeom& g, const State& st, double* s_next) {
   }
   if (nd >= 0) {
     double s;
-    if (path_to_disk(g, st.p, g.surf[nd].r_or_z, s)) {
+    if (path_to_disk(bz, st.p, g.surf[nd].r_or_z, s)) {
       double q[6];
-      helix_at(g, st.p, s, q);
+      helix_at(bz, st.p, s, q);
       const double r = std::hypot(q[0], q[1]);
       if (r >= g.surf[nd].lo && r <= g.surf[nd].hi && (best < 0 || s < best_s)) {
         best = nd;
@@ -782,13 +817,14 @@ struct Ctx {
 bool reaches(const OrGeom& g, const State& st, int s) {
   const OrSurface& S = g.surf[s];
   double len, q[6];
+  const double bz = start_field(g, st.p);
   if (S.type == 0) {
-    if (!path_to_cylinder(g, st.p, S.r_or_z, len)) return false;
-    helix_at(g, st.p, len, q);
+    if (!path_to_cylinder(bz, st.p, S.r_or_z, len)) return false;
+    helix_at(bz, st.p, len, q);
     return q[2] >= S.lo && q[2] <= S.hi;
   }
-  if (!path_to_disk(g, st.p, S.r_or_z, len)) return false;
-  helix_at(g, st.p, len, q);
+  if (!path_to_disk(bz, st.p, S.r_or_z, len)) return false;
+  helix_at(bz, st.p, len, q);
   const double r = std::hypot(q[0], q[1]);
   return r >= S.lo && r <= S.hi;
 }
@@ -1073,7 +1109,9 @@ int or_propagate(const OrGeom* g, const double* p, const double* C, int surf, do
 }
 
 // Position of the helix at fixed transverse path s (no surface), for finite-difference tests.
-void or_helix_at(const OrGeom* g, const double* p, double s, double* p_out) { helix_at(*g, p, s, p_out); }
+void or_helix_at(const OrGeom* g, const double* p, double s, double* p_out) {
+  helix_at(start_field(*g, p), p, s, p_out);
+}
 
 // Seed state + prior from three hit ids.
 int or_seed(const OrGeom* g, const float* hits, const int* hsurf, const int* ids, double* p_out, double* C_out) {

@@ -37,7 +37,7 @@ class KfGeometry(ctypes.Structure):
     _fields_ = [("bz", ctypes.c_float), ("n_surf", ctypes.c_int), ("surf", ctypes.POINTER(KfSurface)),
                 ("sigma_rphi", ctypes.c_float), ("sigma_2nd", ctypes.c_float), ("prior", ctypes.c_float * 5),
                 ("ms_off", ctypes.c_int), ("material", ctypes.c_void_p), ("eloss", ctypes.c_float),
-                ("mass", ctypes.c_float)]
+                ("mass", ctypes.c_float), ("field_z2", ctypes.c_float), ("field_r2", ctypes.c_float)]
 
 
 MAT_NODES = 8  # KF_MAT_NODES
@@ -127,7 +127,7 @@ def _check(rc: int, what: str):
 class Geometry:
     """C-ABI geometry built from any object with ``surfaces`` (type, r_or_z, lo, hi, x_over_x0,
     n_phi, n_2nd), ``bz``, ``sigma_rphi``, ``sigma_2nd``, ``prior``, ``ms_on`` and optionally
-    ``material`` ([n_surf][MAT_NODES] x/X0), ``eloss`` and ``mass``."""
+    ``material`` ([n_surf][MAT_NODES] x/X0), ``eloss``, ``mass``, ``field_z2`` and ``field_r2``."""
 
     def __init__(self, wl):
         self.wl = wl
@@ -143,7 +143,8 @@ class Geometry:
         self.g = KfGeometry(wl.bz, n, ctypes.cast(self._surf, ctypes.POINTER(KfSurface)), wl.sigma_rphi, wl.sigma_2nd,
                             (ctypes.c_float * 5)(*wl.prior), int(not ms),
                             None if self._mat is None else self._mat.ctypes.data, getattr(wl, "eloss", 0.0),
-                            getattr(wl, "mass", 0.13957))
+                            getattr(wl, "mass", 0.13957), getattr(wl, "field_z2", 0.0),
+                            getattr(wl, "field_r2", 0.0))
         self.n_surf = n
         self.n_bins = load_library().kf_index_bins(ctypes.byref(self.g))
         if self.n_bins < 0:

@@ -47,6 +47,10 @@ static int pack_geometry(const KfGeometry* g, DevGeom* d) {
   }
   d->n_surf = g->n_surf;
   d->ms_on = g->ms_off ? 0 : 1;
+  if (!std::isfinite(g->field_z2) || !std::isfinite(g->field_r2)) return KF_ERR_ARG;
+  d->field_on = (g->field_z2 != 0.f || g->field_r2 != 0.f) ? 1 : 0;
+  d->fz2 = g->field_z2;
+  d->fr2 = g->field_r2;
   int nb = 0;
   for (int s = 0; s < g->n_surf; ++s) {
     const KfSurface& S = g->surf[s];

@@ -313,7 +313,7 @@ __device__ __forceinline__ int seed_region(const DevGeom& G, int s3, float2 h) {
 // through one loop (a single further copy of the path solvers in the code).
 __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, int region, int pos, float st,
                                             float ct, Prop& best, int& newpos) {
-  const float w = -kCurvF * G.bz * p[3];
+  const float w = -kCurvF * start_field(G, p) * p[3];
   const float cot = ct / st;
   const bool steer = G.steer != 0;
   int sb = -1, sd = -1;  // geometric candidates: next barrel layer, next disk
@@ -402,13 +402,12 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, const __grid_con
   c.chi2 = 0.f;
   for (int k = 0; k < 3 && ok; ++k) {
     if (k > 0) {
-      const float w = -kCurvF * G.bz * c.p[3];
-      float st, ct;
+      const float w = -kCurvF * start_field(G, c.p) * c.p[3];
+      float st, ct, bz;
       sincos_small(c.p[5], st, ct);
       Prop pr;
-      ok = G.type[ss[k]] == 0 ? path_to_cylinder(c.p, w, G.r_or_z[ss[k]], pr)
-                              : path_to_disk(c.p, w, G.r_or_z[ss[k]], st, ct, pr);
-      ok = ok && apply_propagation(G, M, ss[k], c.p, c.C, pr, st, ct);
+      ok = path_to_surface(G, ss[k], c.p, w, st, ct, pr) && step_field(G, ss[k], c.p, st, ct, pr, bz);
+      ok = ok && apply_propagation(G, M, ss[k], c.p, c.C, pr, st, ct, bz);
       if (!ok) break;
     }
     const float2 h = A.hits[ids[k]];
@@ -582,7 +581,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         float st, ct;
         sincos_small(c.p[5], st, ct);
         si = next_surface(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
-        if (si >= 0 && apply_propagation(G, M, si, c.p, c.C, pr, st, ct)) {
+        float bz;
+        if (si >= 0 && step_field(G, si, c.p, st, ct, pr, bz) && apply_propagation(G, M, si, c.p, c.C, pr, st, ct, bz)) {
           kind = 1;
           Meas m;
           float rho;

@@ -48,13 +48,12 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const __grid_cons
           break;
         }
         if (k > 0) {
-          const float w = -kCurvF * G.bz * p[3];
-          float st, ct;
+          const float w = -kCurvF * start_field(G, p) * p[3];
+          float st, ct, bz;
           sincos_small(p[5], st, ct);
           Prop pr;
-          const bool ok = G.type[si] == 0 ? path_to_cylinder(p, w, G.r_or_z[si], pr)
-                                          : path_to_disk(p, w, G.r_or_z[si], st, ct, pr);
-          if (!ok || !apply_propagation(G, M, si, p, C, pr, st, ct)) {
+          const bool ok = path_to_surface(G, si, p, w, st, ct, pr) && step_field(G, si, p, st, ct, pr, bz);
+          if (!ok || !apply_propagation(G, M, si, p, C, pr, st, ct, bz)) {
             status = 2;
             break;
           }

@@ -40,6 +40,9 @@ struct DevGeom {
   float barrel_r[kMaxSurf];                  // radius of barrel_order[i]
   float dpos_z[kMaxSurf], dneg_z[kMaxSurf];  // z of dpos_order[i], dneg_order[i]
   int ms_on;  // multiple scattering
+  // Parametrised solenoid field (field_on): Bz(r, z) = bz (1 + fz2 z^2 + fr2 r^2); else bz.
+  int field_on;
+  float fz2, fr2;
   // Region steering of the finder (steer = 1) or the geometric next-surface rule (steer = 0).
   int steer;
   float c_barrel, c_endcap;
@@ -196,6 +199,35 @@ __device__ __forceinline__ void prop_position(const float* p, const Prop& pr, fl
   z = p[2] + pr.s * cot;
 }
 
+// Bz at (x, y, z) of the parametrised field.
+__device__ __forceinline__ float field_at(const DevGeom& G, float x, float y, float z) {
+  return G.bz * (1.f + G.fz2 * z * z + G.fr2 * (x * x + y * y));
+}
+
+// Field at the start of a step from state p (the field that decides which surface is next).
+__device__ __forceinline__ float start_field(const DevGeom& G, const float* p) {
+  return G.field_on ? field_at(G, p[0], p[1], p[2]) : G.bz;
+}
+
+__device__ __forceinline__ bool path_to_surface(const DevGeom& G, int si, const float* p, float w, float st, float ct,
+                                                Prop& pr) {
+  return G.type[si] == 0 ? path_to_cylinder(p, w, G.r_or_z[si], pr) : path_to_disk(p, w, G.r_or_z[si], st, ct, pr);
+}
+
+// Field of the step to surface si, whose path in the field at the start is in pr: uniform field,
+// that field; parametrised field, the field at the midpoint of the chord p + (s/2) (cos phi,
+// sin phi, cot theta), with the path solved again in it. False when that path misses the surface.
+__device__ __forceinline__ bool step_field(const DevGeom& G, int si, const float* p, float st, float ct, Prop& pr,
+                                           float& bz) {
+  if (!G.field_on) {
+    bz = G.bz;
+    return true;
+  }
+  const float h = 0.5f * pr.s;
+  bz = field_at(G, p[0] + h * pr.c0, p[1] + h * pr.s0, p[2] + h * ct / st);
+  return path_to_surface(G, si, p, -kCurvF * bz * p[3], st, ct, pr);
+}
+
 __device__ __forceinline__ float highland_var(float p, float x_over_x0) {
   const float t0 = 0.0136f / p * sqrtf(x_over_x0) * (1.f + 0.038f * logf(x_over_x0));
   return t0 * t0;
@@ -213,10 +245,11 @@ __device__ __forceinline__ float material_at(const DevMat& M, const DevGeom& G, 
 // Move state p and covariance C along the helix by pr.s onto surface `si`; C' = J C J^T + Q where
 // J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface; then
 // the mean energy loss in the layer (kappa scaled by p/p', its row and column of C by
-// (p/p')^3 E'/E). st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation).
+// (p/p')^3 E'/E). st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation); bz:
+// the field of the step (step_field; its gradient is not propagated into C).
 __device__ __forceinline__ bool apply_propagation(const DevGeom& G, const DevMat& M, int si, float* p, float* C,
-                                                  const Prop& pr, float st, float ct) {
-  const float a = -kCurvF * G.bz;  // d omega / d kappa
+                                                  const Prop& pr, float st, float ct, float bz) {
+  const float a = -kCurvF * bz;  // d omega / d kappa
   const float w = a * p[3];
   const float s = pr.s;
   const float D = w * s;
@@ -470,7 +503,7 @@ __device__ __forceinline__ bool seed_from_hits(const DevGeom& G, const float* xs
   p[0] = xs[0];
   p[1] = ys[0];
   p[2] = zs[0];
-  p[3] = -w / (kCurvF * G.bz);
+  p[3] = -w / (kCurvF * (G.field_on ? field_at(G, xs[0], ys[0], zs[0]) : G.bz));  // the field at hit 1
   p[4] = phi;
   p[5] = theta;
 #pragma unroll

@@ -52,7 +52,7 @@ class _SynthParams(ctypes.Structure):
                 ("noise_frac", ctypes.c_double), ("seed", ctypes.c_uint64), ("ms_on", ctypes.c_int),
                 ("smear_on", ctypes.c_int), ("record_truth", ctypes.c_int), ("n_threads", ctypes.c_int),
                 ("material", ctypes.c_void_p), ("eloss", ctypes.c_double), ("mass", ctypes.c_double),
-                ("overlap_frac", ctypes.c_double)]
+                ("overlap_frac", ctypes.c_double), ("field_z2", ctypes.c_double), ("field_r2", ctypes.c_double)]
 
 
 MAT_NODES = 8  # material map nodes per surface
@@ -130,6 +130,9 @@ class Workload:
     # surface; seeds from every combination of a track's hits on its first three surfaces
     overlap_frac: float = 0.0
     combinatorial_seeds: bool = False
+    # non-uniform solenoid field Bz(r, z) = bz (1 + field_z2 z^2 + field_r2 r^2), cm^-2 (0, 0: uniform)
+    field_z2: float = 0.0
+    field_r2: float = 0.0
 
     @property
     def lmax(self) -> int:
@@ -228,6 +231,13 @@ def _wl_duplicates() -> Workload:
                     tracks_hi=5000, seed=7, noise_frac=0.3, k_max=6, overlap_frac=0.3, combinatorial_seeds=True)
 
 
+def _wl_field() -> Workload:
+    surf = barrel_layers(17, half_length=29.0, eta_max=2.4) + endcap_disks()
+    # Bz falls by 5.8% from the centre to |z| = 120 cm and by 0.5% to r = 68 cm
+    return Workload("find_20ev_barrel_disks_field_map", tuple(surf), n_events=20, tracks_lo=3000, tracks_hi=8000,
+                    seed=8, eta_max=2.4, noise_frac=1.0, k_max=8, field_z2=-4e-6, field_r2=-1e-6)
+
+
 WORKLOADS = {
     "fit_small": _wl_fit_small(),
     "fit_batched": _wl_fit_batched(),
@@ -236,6 +246,7 @@ WORKLOADS = {
     "hi_occ": _wl_hi_occ(),
     "material": _wl_material(),
     "duplicates": _wl_duplicates(),
+    "field": _wl_field(),
 }
 
 
@@ -350,7 +361,7 @@ def generate(wl, *, n_events: int = None, seed: int = None, smear: bool = True, 
     prm = _SynthParams(wl.n_events, wl.tracks_lo, wl.tracks_hi, wl.pt_lo, wl.pt_hi, wl.eta_max, f32(wl.bz),
                        wl.sigma_rphi, wl.sigma_2nd, wl.noise_frac, wl.seed, int(wl.ms_on), int(smear),
                        int(record_truth), n_threads, None if mat is None else mat.ctypes.data, f32(wl.eloss),
-                       f32(wl.mass), wl.overlap_frac)
+                       f32(wl.mass), wl.overlap_frac, f32(wl.field_z2), f32(wl.field_r2))
     lmax = wl.lmax
     h = lib.synth_generate(ctypes.byref(prm), surf, len(wl.surfaces), lmax)
     if not h:

@@ -103,8 +103,13 @@ struct SynthParams {
   // Module overlaps: with this probability a crossing leaves a second hit of the same particle
   // on the surface (an overlapping module; smeared independently).
   double overlap_frac;
+  // Non-uniform solenoid field (optional): Bz(r, z) = bz (1 + field_z2 z^2 + field_r2 r^2), cm^-2;
+  // the radial component is neglected. With either coefficient non-zero, particles are moved in
+  // helix substeps of at most kFieldStep cm of transverse path, each with Bz at its midpoint.
+  double field_z2, field_r2;
 };
 constexpr int kMatNodes = 8;
+constexpr double kFieldStep = 0.5;
 
 }  // extern "C"
 
@@ -253,79 +258,135 @@ double material_at(const SynthParams& prm, const SynthSurface& S, int s, double 
   return nd[k] + (u - k) * (nd[k + 1] - nd[k]);
 }
 
+double field_at(const SynthParams& prm, double x, double y, double z) {
+  return prm.bz * (1.0 + prm.field_z2 * z * z + prm.field_r2 * (x * x + y * y));
+}
+
+// Earliest crossing of a surface within turning angle psi_max along the helix (the next barrel
+// layer beyond the current radius whose crossing lies within its z extent, and the nearer disk
+// in the direction of motion within its r extent): best (turning angle) and its surface, or -1.
+int first_crossing(const Helix& hx, const Particle& p, const std::vector<SynthSurface>& surf,
+                   const std::vector<int>& barrel_order, const std::vector<int>& disk_pos,
+                   const std::vector<int>& disk_neg, double psi_max, double& best) {
+  const double rho_now = std::hypot(p.x, p.y);
+  best = -1.0;
+  int best_surf = -1;
+  for (int s : barrel_order) {
+    const SynthSurface& S = surf[s];
+    if (S.r_or_z <= rho_now + 1e-9) continue;
+    const double psi = cross_cylinder(hx, S.r_or_z);
+    if (psi <= 0.0 || psi > psi_max) break;  // cannot reach this radius (in range), nor any larger one
+    double x, y, z;
+    hx.at(psi, x, y, z);
+    if (z >= S.lo && z <= S.hi) {
+      best = psi;
+      best_surf = s;
+      break;
+    }
+  }
+  const std::vector<int>& disks = (hx.cot_theta >= 0.0) ? disk_pos : disk_neg;
+  for (int s : disks) {
+    const SynthSurface& S = surf[s];
+    if (std::fabs(S.r_or_z) <= std::fabs(p.z) + 1e-9) continue;
+    const double psi = cross_disk(hx, S.r_or_z);
+    if (psi <= 0.0 || psi > psi_max) continue;
+    if (best >= 0.0 && psi >= best) break;
+    double x, y, z;
+    hx.at(psi, x, y, z);
+    const double r = std::hypot(x, y);
+    if (r >= S.lo && r <= S.hi) {
+      best = psi;
+      best_surf = s;
+      break;
+    }
+  }
+  return best_surf;
+}
+
+// Move the particle along the helix by turning angle psi.
+void advance(Particle& p, const Helix& hx, double psi) {
+  double x, y, z;
+  hx.at(psi, x, y, z);
+  const double phi = hx.phi0 - hx.h * psi;
+  p.x = x;
+  p.y = y;
+  p.z = z;
+  p.px = hx.pt * std::cos(phi);
+  p.py = hx.pt * std::sin(phi);
+}
+
+// Scattering and energy loss at a crossing of surface `si` (the particle is on it); false when
+// the particle stops in the layer.
+bool interact(Particle& p, int si, const std::vector<SynthSurface>& surf, const SynthParams& prm, Rng& rng) {
+  const SynthSurface& S = surf[si];
+  const double x = p.x, y = p.y, z = p.z;
+  const double xx0 = material_at(prm, S, si, S.type == 0 ? z : std::hypot(x, y));
+  if ((prm.ms_on && xx0 > 0.0) || prm.eloss > 0.0) {
+    const double pmag = std::sqrt(p.px * p.px + p.py * p.py + p.pz * p.pz);
+    double ncos;
+    if (S.type == 0) {
+      const double r = std::hypot(x, y);
+      ncos = (p.px * x + p.py * y) / (pmag * r);
+    } else {
+      ncos = p.pz / pmag;
+    }
+    if (prm.ms_on && xx0 > 0.0) kick(p, ncos, xx0, rng);
+    if (prm.eloss > 0.0 && xx0 > 0.0) {
+      // Mean ionisation loss over the path through the layer; the direction is kept.
+      const double e = std::sqrt(pmag * pmag + prm.mass * prm.mass);
+      const double e1 = e - prm.eloss * xx0 / std::max(std::fabs(ncos), 1e-6);
+      if (!(e1 > prm.mass)) return false;  // stopped in the layer
+      const double f = std::sqrt(e1 * e1 - prm.mass * prm.mass) / pmag;
+      p.px *= f;
+      p.py *= f;
+      p.pz *= f;
+    }
+  }
+  return true;
+}
+
 void simulate_track(Particle p, const std::vector<SynthSurface>& surf, const std::vector<int>& barrel_order,
                     const std::vector<int>& disk_pos, const std::vector<int>& disk_neg, const SynthParams& prm,
                     Rng& rng, TrackOut& out) {
   const int max_steps = static_cast<int>(surf.size());
+  const bool stepped = prm.field_z2 != 0.0 || prm.field_r2 != 0.0;
   for (int step = 0; step < max_steps; ++step) {
-    Helix hx(p, prm.bz);
-    const double rho_now = std::hypot(p.x, p.y);
-    double best = -1.0;
     int best_surf = -1;
-    for (int s : barrel_order) {
-      const SynthSurface& S = surf[s];
-      if (S.r_or_z <= rho_now + 1e-9) continue;
-      const double psi = cross_cylinder(hx, S.r_or_z);
-      if (psi <= 0.0) break;  // cannot reach this radius, nor any larger one
-      double x, y, z;
-      hx.at(psi, x, y, z);
-      if (z >= S.lo && z <= S.hi) {
-        best = psi;
-        best_surf = s;
-        break;
+    if (!stepped) {
+      // Uniform field: the exact helix to the next crossing.
+      Helix hx(p, prm.bz);
+      double best;
+      best_surf = first_crossing(hx, p, surf, barrel_order, disk_pos, disk_neg, kPi, best);
+      if (best_surf < 0) return;
+      advance(p, hx, best);
+    } else {
+      // Non-uniform field: substeps of at most kFieldStep cm transverse path, each a helix with
+      // the field at its midpoint (second order); the crossing is solved on the substep's helix.
+      // A particle is followed for at most half a turn between crossings, and not at all when
+      // the helix of the local field reaches no surface (it has left the detector).
+      {
+        double best;
+        const Helix hl(p, field_at(prm, p.x, p.y, p.z));
+        if (first_crossing(hl, p, surf, barrel_order, disk_pos, disk_neg, kPi, best) < 0) return;
       }
-    }
-    const std::vector<int>& disks = (hx.cot_theta >= 0.0) ? disk_pos : disk_neg;
-    for (int s : disks) {
-      const SynthSurface& S = surf[s];
-      if (std::fabs(S.r_or_z) <= std::fabs(p.z) + 1e-9) continue;
-      const double psi = cross_disk(hx, S.r_or_z);
-      if (psi <= 0.0) continue;
-      if (best >= 0.0 && psi >= best) break;
-      double x, y, z;
-      hx.at(psi, x, y, z);
-      const double r = std::hypot(x, y);
-      if (r >= S.lo && r <= S.hi) {
-        best = psi;
-        best_surf = s;
-        break;
+      double turned = 0.0;
+      for (int sub = 0; sub < 100000 && best_surf < 0; ++sub) {
+        const Helix h0(p, field_at(prm, p.x, p.y, p.z));
+        double xm, ym, zm;
+        h0.at(0.5 * kFieldStep / h0.rho, xm, ym, zm);
+        const Helix hx(p, field_at(prm, xm, ym, zm));
+        const double psi_sub = std::min(kFieldStep / hx.rho, kPi - turned);
+        if (!(psi_sub > 0.0)) return;
+        double best;
+        best_surf = first_crossing(hx, p, surf, barrel_order, disk_pos, disk_neg, psi_sub, best);
+        advance(p, hx, best_surf >= 0 ? best : psi_sub);
+        turned += best_surf >= 0 ? best : psi_sub;
       }
+      if (best_surf < 0) return;
     }
-    if (best_surf < 0) return;
-    // Move to the crossing.
-    double x, y, z;
-    hx.at(best, x, y, z);
-    const double phi = hx.phi0 - hx.h * best;
-    p.x = x;
-    p.y = y;
-    p.z = z;
-    p.px = hx.pt * std::cos(phi);
-    p.py = hx.pt * std::sin(phi);
-    Crossing c{best_surf, x, y, z, p.px, p.py, p.pz};
+    Crossing c{best_surf, p.x, p.y, p.z, p.px, p.py, p.pz};
     if (prm.record_truth) out.truth_in.push_back(state_of(p));
-    const SynthSurface& S = surf[best_surf];
-    const double xx0 = material_at(prm, S, best_surf, S.type == 0 ? z : std::hypot(x, y));
-    if ((prm.ms_on && xx0 > 0.0) || prm.eloss > 0.0) {
-      const double pmag = std::sqrt(p.px * p.px + p.py * p.py + p.pz * p.pz);
-      double ncos;
-      if (S.type == 0) {
-        const double r = std::hypot(x, y);
-        ncos = (p.px * x + p.py * y) / (pmag * r);
-      } else {
-        ncos = p.pz / pmag;
-      }
-      if (prm.ms_on && xx0 > 0.0) kick(p, ncos, xx0, rng);
-      if (prm.eloss > 0.0 && xx0 > 0.0) {
-        // Mean ionisation loss over the path through the layer; the direction is kept.
-        const double e = std::sqrt(pmag * pmag + prm.mass * prm.mass);
-        const double e1 = e - prm.eloss * xx0 / std::max(std::fabs(ncos), 1e-6);
-        if (!(e1 > prm.mass)) return;  // stopped in the layer
-        const double f = std::sqrt(e1 * e1 - prm.mass * prm.mass) / pmag;
-        p.px *= f;
-        p.py *= f;
-        p.pz *= f;
-      }
-    }
+    if (!interact(p, best_surf, surf, prm, rng)) return;
     if (prm.record_truth) out.truth_out.push_back(state_of(p));
     out.cross.push_back(c);
   }

@@ -176,6 +176,33 @@ def test_find_parity_material_map_and_energy_loss(kf):
     _assert_find_parity(b, gpu, ora, st)
 
 
+def test_fit_parity_field_map(kf):
+    """Parametrised solenoid field on the barrel + disk geometry (|eta| < 2.4), with and without
+    scattering."""
+    for ms in (True, False):
+        wl = synth.workload("field", n_events=2, tracks_lo=1500, tracks_hi=3000, ms_on=ms)
+        b = synth.generate(wl)
+        gpu, ora = _fit_both(kf, wl, b)
+        _assert_fit_parity(gpu, ora)
+
+
+def test_find_parity_field_map(kf):
+    wl = synth.workload("field", n_events=2, tracks_lo=800, tracks_hi=1500)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b)
+    _assert_find_parity(b, gpu, ora, st)
+
+
+def test_field_coefficients_rejected_when_not_finite(kf):
+    import dataclasses
+    wl = synth.workload("field", n_events=1, tracks_lo=50, tracks_hi=50)
+    b = synth.generate(wl)
+    dev = kf.to_device_event_batch(b)
+    with pytest.raises(kf.KfError):
+        g = kf.Geometry(dataclasses.replace(wl, field_z2=float("nan")))
+        kf.fit_tracks(g, dev["hits"], dev["hit_surface"], dev["track_hits"])
+
+
 def test_fit_with_misses_and_short_tracks(kf):
     """-1 entries inside a list are skipped; lists with fewer than three seed hits are rejected."""
     wl = synth.workload("fit_batched", n_events=1, tracks_lo=700, tracks_hi=700)
