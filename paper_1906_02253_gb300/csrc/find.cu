@@ -311,11 +311,13 @@ __device__ __forceinline__ int seed_region(const DevGeom& G, int s3, float2 h) {
 // each "next" is a lower bound, searched from the candidate's current surface `cur`. The barrel
 // candidate of the geometric rule is tried in straight-line code; disks and steering lists go
 // through one loop (a single further copy of the path solvers in the code).
+// GEN = false: the geometric rule in a uniform field only.
+template <bool GEN>
 __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, int region, int pos, float st,
                                             float ct, Prop& best, int& newpos) {
-  const float w = -kCurvF * start_field(G, p) * p[3];
+  const float w = -kCurvF * (GEN ? start_field(G, p) : G.bz) * p[3];
   const float cot = ct / st;
-  const bool steer = G.steer != 0;
+  const bool steer = GEN && G.steer != 0;
   int sb = -1, sd = -1;  // geometric candidates: next barrel layer, next disk
   if (!steer) {
     const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
@@ -478,7 +480,10 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
          (static_cast<unsigned long long>(pk) << 20);
 }
 
-template <int KC, bool LEARNED>
+// GEN: the general kernel (region steering, material map and energy loss, parametrised field);
+// without it the geometric next-surface rule, the surfaces' x/X0 and the uniform field are
+// compiled in alone.
+template <int KC, bool LEARNED, bool GEN>
 __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp,
                                                         const __grid_constant__ DevMat M, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -519,12 +524,12 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     // ---- refill: a group without a seed takes the next one --------------------------------
     const bool want = !exhausted && seed < 0;
     int s = -1;
-    // Seeds that failed or were removed by cleaning (their outputs written by the seed-state
-    // kernel) are passed over here rather than costing the group a step each.
+    // Seeds removed by cleaning (their outputs written by the seed-state kernel) are passed over
+    // here rather than costing the group a step each.
     if (want && slot == 0) {
-      do {
-        s = atomicAdd(A.counter, 1);
-      } while (s < n && !(A.seed_state[static_cast<size_t>(27) * n + s] >= 0.f));
+      s = atomicAdd(A.counter, 1);
+      if (A.seed_keep)
+        while (s < n && A.seed_keep[s] == 0) s = atomicAdd(A.counter, 1);
     }
     s = __shfl_sync(kFull, s, gbase);
     bool fresh = false;
@@ -550,7 +555,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       // Candidate surface word: (position in the region's list + 1) << 8 | surface.
       const int s3 = A.seed_surf[seed];
       int pos = -1;
-      if (G.steer && s3 >= 0 && s3 < G.n_surf) {
+      if (GEN && G.steer && s3 >= 0 && s3 < G.n_surf) {
         region = seed_region(G, s3, A.hits[A.seed_hits[static_cast<size_t>(2) * n + seed]]);
         pos = G.steer_pos[region][s3];
       }
@@ -580,9 +585,10 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         Prop pr;
         float st, ct;
         sincos_small(c.p[5], st, ct);
-        si = next_surface(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
-        float bz;
-        if (si >= 0 && step_field(G, si, c.p, st, ct, pr, bz) && apply_propagation(G, M, si, c.p, c.C, pr, st, ct, bz)) {
+        si = next_surface<GEN>(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
+        float bz = G.bz;
+        if (si >= 0 && (!GEN || step_field(G, si, c.p, st, ct, pr, bz)) &&
+            apply_propagation<GEN>(G, M, si, c.p, c.C, pr, st, ct, bz)) {
           kind = 1;
           Meas m;
           float rho;
@@ -908,40 +914,48 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   }
 }
 
-// Compile-time choice of capacity and mode, dispatched from the runtime plan.
-template <int KC, bool L>
+// Compile-time choice of capacity and mode, dispatched from the runtime plan. The learned
+// proposal always runs the general kernel.
+template <int KC, bool L, bool GEN>
 struct FindKernel {
   static constexpr int kc = KC;
   static constexpr bool learned = L;
+  static constexpr bool general = GEN;
 };
 
+template <int KC, class F>
+static int dispatch_mode(bool learned, bool general, F&& f) {
+  if (learned) return f(FindKernel<KC, true, true>{});
+  return general ? f(FindKernel<KC, false, true>{}) : f(FindKernel<KC, false, false>{});
+}
+
 template <class F>
-static int dispatch_find(int kc, bool learned, F&& f) {
+static int dispatch_find(int kc, bool learned, bool general, F&& f) {
   switch (kc) {
-    case 1: return learned ? f(FindKernel<1, true>{}) : f(FindKernel<1, false>{});
-    case 2: return learned ? f(FindKernel<2, true>{}) : f(FindKernel<2, false>{});
-    case 4: return learned ? f(FindKernel<4, true>{}) : f(FindKernel<4, false>{});
-    case 6: return learned ? f(FindKernel<6, true>{}) : f(FindKernel<6, false>{});
-    case 8: return learned ? f(FindKernel<8, true>{}) : f(FindKernel<8, false>{});
-    case 16: return learned ? f(FindKernel<16, true>{}) : f(FindKernel<16, false>{});
+    case 1: return dispatch_mode<1>(learned, general, f);
+    case 2: return dispatch_mode<2>(learned, general, f);
+    case 4: return dispatch_mode<4>(learned, general, f);
+    case 6: return dispatch_mode<6>(learned, general, f);
+    case 8: return dispatch_mode<8>(learned, general, f);
+    case 16: return dispatch_mode<16>(learned, general, f);
     default: return KF_ERR_ARG;
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 
-template <int KC, bool L>
+template <int KC, bool L, bool GEN>
 static int kc_occupancy(int block, size_t smem, int* bps) {
   static int attr_set[16] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_CUDA;
   if (static_cast<int>(smem) > attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_find_tracks<KC, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_find_tracks<KC, L, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
       return KF_ERR_CUDA;
     attr_set[dev] = static_cast<int>(smem);
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC, L>, block, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC, L, GEN>, block, smem) != cudaSuccess)
     return KF_ERR_CUDA;
   return KF_OK;
 }
@@ -953,7 +967,7 @@ static int pick_kc(int need) {
   return -1;
 }
 
-int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
+int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPlan* plan) {
   if (!p || n_seeds < 0 || sms <= 0) return KF_ERR_ARG;
   if (p->k_max < 1 || p->k_max > KF_MAX_K || p->max_miss < 0 || p->lmax < 4 || p->lmax > KF_MAX_LMAX) return KF_ERR_ARG;
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
@@ -967,24 +981,25 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   if (kc < 0) return KF_ERR_ARG;
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
-  static int occ_cache[16][6][2][8][32] = {};
+  general = general || learned;
+  static int occ_cache[16][6][2][2][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
   const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
   auto occupancy = [&](int blk, size_t* smem_out, int* occ_out) {
     size_t sm = 0;
-    dispatch_find(kc, learned, [&](auto k) {
+    dispatch_find(kc, learned, general, [&](auto k) {
       sm = kGeomBytes + warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
       return KF_OK;
     });
     *smem_out = sm;
     *occ_out = 0;
     if (sm > 227 * 1024) return KF_OK;
-    int& cached = occ_cache[dev][ki][learned][blk / 32 - 1][p->lmax];
+    int& cached = occ_cache[dev][ki][learned][general][blk / 32 - 1][p->lmax];
     if (cached == 0) {
       int o = 0;
-      const int rc = dispatch_find(kc, learned, [&](auto k) {
-        return kc_occupancy<decltype(k)::kc, decltype(k)::learned>(blk, sm, &o);
+      const int rc = dispatch_find(kc, learned, general, [&](auto k) {
+        return kc_occupancy<decltype(k)::kc, decltype(k)::learned, decltype(k)::general>(blk, sm, &o);
       });
       if (rc != KF_OK) return rc;
       cached = o > 0 ? o : -1;
@@ -1022,6 +1037,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, FindPlan* plan) {
   const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
   plan->kc = kc;
   plan->learned = learned;
+  plan->general = general;
   plan->block = block;
   plan->grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
   plan->smem = smem;
@@ -1075,8 +1091,9 @@ int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& 
   }
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
   k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, M, A);
-  dispatch_find(plan.kc, plan.learned, [&](auto k) {
-    k_find_tracks<decltype(k)::kc, decltype(k)::learned><<<plan.grid, plan.block, plan.smem, stream>>>(G, M, A);
+  dispatch_find(plan.kc, plan.learned, plan.general, [&](auto k) {
+    k_find_tracks<decltype(k)::kc, decltype(k)::learned, decltype(k)::general>
+        <<<plan.grid, plan.block, plan.smem, stream>>>(G, M, A);
     return KF_OK;
   });
   return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;

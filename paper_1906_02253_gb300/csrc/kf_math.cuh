@@ -246,7 +246,9 @@ __device__ __forceinline__ float material_at(const DevMat& M, const DevGeom& G, 
 // J = (I - t g^T / g^T t) J_s: J_s at fixed s, t = d(state)/ds, g = gradient of the surface; then
 // the mean energy loss in the layer (kappa scaled by p/p', its row and column of C by
 // (p/p')^3 E'/E). st, ct: sin and cos of the polar angle p[5] (unchanged by the propagation); bz:
-// the field of the step (step_field; its gradient is not propagated into C).
+// the field of the step (step_field; its gradient is not propagated into C). EXTRAS = false: a
+// variant for geometries without material map and energy loss (the surfaces' x/X0 only).
+template <bool EXTRAS = true>
 __device__ __forceinline__ bool apply_propagation(const DevGeom& G, const DevMat& M, int si, float* p, float* C,
                                                   const Prop& pr, float st, float ct, float bz) {
   const float a = -kCurvF * bz;  // d omega / d kappa
@@ -335,8 +337,8 @@ __device__ __forceinline__ bool apply_propagation(const DevGeom& G, const DevMat
   // Thin-layer multiple scattering (Highland, beta = 1) in (kappa, phi, theta) and the mean energy
   // loss, with the material at the crossing.
   float xx0 = G.x0[si];
-  if (M.map_on) xx0 = material_at(M, G, si, G.type[si] == 0 ? p[2] : sqrtf(p[0] * p[0] + p[1] * p[1]));
-  const bool ms = G.ms_on && xx0 > 0.f, el = M.eloss > 0.f && xx0 > 0.f;
+  if (EXTRAS && M.map_on) xx0 = material_at(M, G, si, G.type[si] == 0 ? p[2] : sqrtf(p[0] * p[0] + p[1] * p[1]));
+  const bool ms = G.ms_on && xx0 > 0.f, el = EXTRAS && M.eloss > 0.f && xx0 > 0.f;
   if (ms || el) {
     float cos_a;
     if (G.type[si] == 0) {
