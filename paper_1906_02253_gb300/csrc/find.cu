@@ -273,8 +273,19 @@ __device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int
   ++n;
 }
 
-// Whether the helix from state p reaches surface s within its extent (barrel: z extent; disk: r
-// extent, within half a turn), and the path to it. st, ct: sin and cos of the polar angle p[5].
+// Whether the helix from state p reaches disk s within its r extent and half a turn, and the path
+// to it. st, ct: sin and cos of the polar angle p[5].
+__device__ __forceinline__ bool reach_disk(const DevGeom& G, const float* p, float w, int s, float st, float ct,
+                                           float cot, Prop& pr) {
+  if (!path_to_disk(p, w, G.r_or_z[s], st, ct, pr)) return false;
+  float x, y, z;
+  prop_position(p, pr, cot, x, y, z);
+  const float r = sqrtf(x * x + y * y);
+  return r >= G.lo[s] && r <= G.hi[s];
+}
+
+// Whether the helix from state p reaches surface s within its extent (barrel: z extent; disk:
+// reach_disk), and the path to it.
 __device__ __forceinline__ bool reach_surface(const DevGeom& G, const float* p, float w, int s, float st, float ct,
                                               float cot, Prop& pr) {
   if (G.type[s] == 0) {
@@ -284,11 +295,7 @@ __device__ __forceinline__ bool reach_surface(const DevGeom& G, const float* p, 
     const float z = p[2] + pr.s * cot;
     return z >= G.lo[s] && z <= G.hi[s];
   }
-  if (!path_to_disk(p, w, G.r_or_z[s], st, ct, pr)) return false;
-  float x, y, z;
-  prop_position(p, pr, cot, x, y, z);
-  const float r = sqrtf(x * x + y * y);
-  return r >= G.lo[s] && r <= G.hi[s];
+  return reach_disk(G, p, w, s, st, ct, cot, pr);
 }
 
 // Region of a seed from its third hit h on surface s3 (KfSteering): (z, rho) = (z, R) on a barrel,
@@ -351,6 +358,14 @@ __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, in
       }
     }
     if (sd < 0) return sel;
+    if (!GEN) {  // the disk candidate of the geometric rule
+      Prop pr;
+      if (reach_disk(G, p, w, sd, st, ct, cot, pr) && (sel < 0 || pr.s < best.s)) {
+        sel = sd;
+        best = pr;
+      }
+      return sel;
+    }
   }
   const int q1 = steer ? G.steer_n[region] : 2;
 #pragma unroll 1
@@ -559,11 +574,11 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         region = seed_region(G, s3, A.hits[A.seed_hits[static_cast<size_t>(2) * n + seed]]);
         pos = G.steer_pos[region][s3];
       }
-      valid = load_seed(W, lane, A.seed_state + seed, ((pos + 1) << 8) | (s3 & 255), n);
+      valid = load_seed(W, lane, A.seed_state + seed, GEN ? ((pos + 1) << 8) | (s3 & 255) : s3, n);
       failed = !valid;  // a failed seed's outputs were written by the seed-state kernel
     }
     failed = __shfl_sync(kFull, failed, gbase);
-    region = __shfl_sync(kFull, region, gbase);
+    if (GEN) region = __shfl_sync(kFull, region, gbase);
     if (fresh && failed) {
       seed = -1;
       valid = false;
@@ -585,7 +600,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         Prop pr;
         float st, ct;
         sincos_small(c.p[5], st, ct);
-        si = next_surface<GEN>(G, c.p, c.surf & 255, region, (c.surf >> 8) - 1, st, ct, pr, newpos);
+        si = next_surface<GEN>(G, c.p, GEN ? c.surf & 255 : c.surf, region, GEN ? (c.surf >> 8) - 1 : -1, st, ct, pr,
+                               newpos);
         float bz = G.bz;
         if (si >= 0 && (!GEN || step_field(G, si, c.p, st, ct, pr, bz)) &&
             apply_propagation<GEN>(G, M, si, c.p, c.C, pr, st, ct, bz)) {
@@ -819,7 +835,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     if (kind == 1) {
       kind = hl_n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
       if (kind != 2) {
-        c.surf = ((newpos + 1) << 8) | si;
+        c.surf = GEN ? ((newpos + 1) << 8) | si : si;
         store_cand(W, lane, c);
       }
     }
@@ -882,7 +898,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       load_cand(W, gbase + w_par, nc);
       if (w_kind == 0) {
         const float4 h = __ldg(A.sorted_rec + w_pos);
-        update_with(G, nc.surf & 255, nc, h);
+        update_with(G, GEN ? nc.surf & 255 : nc.surf, nc, h);
         nc.chi2 = w_c2;
         nc.nh = w_nh;
       } else if (w_kind == 1) {
