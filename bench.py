@@ -41,11 +41,12 @@ WORKLOAD = "fit_batched"
 #   seed from three hits ..................................................... 80
 FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch on 30 events, per seed; profiles/step_kernels_fit_batched_100ev.md), valid while the
-# finder's sources are the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
+# launch on 30 events of the 100-event workload, per seed; profiles/step_kernels_fit_batched_100ev.md),
+# valid for that workload while the finder's sources are the ones profiled (SHA-1 over
+# FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh")
-FIND_PROFILE = {"sources_sha1": "a253a2e66a1675291bea21c7b63c90df94703e20", "dram_bytes_per_seed": 162617600 / 302063}
+FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "a253a2e66a1675291bea21c7b63c90df94703e20", "dram_bytes_per_seed": 162617600 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 8 B direction) plus
 # the bin offsets written per (event, surface).
 INDEX_BYTES_PER_HIT = 28
@@ -484,7 +485,8 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     n_prop, n_pass, n_upd, n_scan, n_win = counters
     per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
     ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
-    traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if find_sources_sha1() == FIND_PROFILE["sources_sha1"] else None
+    profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and batch.wl.name == FIND_PROFILE["workload"]
+    traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if profiled else None
     return {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": ach / alu_peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu, scaled by seeds)",
             "peak_note": f"FP32 {sm_mhz:.0f} MHz",
