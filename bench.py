@@ -245,25 +245,31 @@ def run_gpu(args, wl, batch):
                   "fit_ms": ms_fit}
     parts = ["index"] + (["clean"] if clean else []) + ["find"] + (["dedup"] if clean else []) + ["fit"]
 
-    def step(s, events=None):
+    def step(s, events=None, dd=None, fo=None, fi=None):
+        """One step on stream s; dd, fo, fi: input, finder-output and fit-output buffers (default
+        the main set)."""
+        dd = d if dd is None else dd
+        fo = fout if fo is None else fo
+        fi = fit_out if fi is None else fi
+
         def mark(i):
             if events:
                 events[i].record(s)
         mark(0)
-        kf.build_hit_index(g, d["hits"], d["slab_offsets"], batch.n_events, max_slab, index=idx, stream=s)
+        kf.build_hit_index(g, dd["hits"], dd["slab_offsets"], batch.n_events, max_slab, index=idx, stream=s)
         mark(1)
         if clean:
-            kf.clean_seeds(g, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], keep=seed_keep,
+            kf.clean_seeds(g, dd["hits"], dd["hit_surface"], dd["seed_hits"], dd["seed_event"], keep=seed_keep,
                            workspace=dws, stream=s)
             mark(2)
-        kf.find_tracks(g, idx, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], prm, out=fout,
+        kf.find_tracks(g, idx, dd["hits"], dd["hit_surface"], dd["seed_hits"], dd["seed_event"], prm, out=fo,
                        workspace=wsb, stream=s)
         mark(parts.index("find") + 1)
         if clean:
-            kf.remove_duplicates(fout["hits"], fout["nhits"], fout["chi2"], fout["state"], d["seed_event"], n_hits,
+            kf.remove_duplicates(fo["hits"], fo["nhits"], fo["chi2"], fo["state"], dd["seed_event"], n_hits,
                                  keep=track_keep, workspace=dws, stream=s)
             mark(parts.index("dedup") + 1)
-        kf.fit_tracks(g, d["hits"], d["hit_surface"], fout["hits"], out=fit_out, block_threads=fit_block, stream=s)
+        kf.fit_tracks(g, dd["hits"], dd["hit_surface"], fo["hits"], out=fi, block_threads=fit_block, stream=s)
         mark(len(parts))
 
     with torch.cuda.stream(stream):
@@ -321,7 +327,10 @@ def run_gpu(args, wl, batch):
     kern_ms = {k: statistics.mean(v) for k, v in kern.items()}
 
     # End to end through the public API with host buffers: H2D of the step's inputs from pinned
-    # memory, the three calls, D2H of the step's result (found hit lists, fitted states, chi2).
+    # memory, the calls, D2H of the step's result (found hit lists, fitted states, chi2). Serial:
+    # copy in, compute, copy out on one stream. Pipelined: copies on their own streams with two
+    # buffer sets, so the H2D of step i+1 and the D2H of step i-1 overlap the compute of step i
+    # (every step's copies stay inside the timed region).
     pinned = {k: host[k].pin_memory() for k in ("hits", "hit_surface", "slab_offsets", "seed_hits", "seed_event")}
     res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory(),
                     state=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
@@ -329,16 +338,55 @@ def run_gpu(args, wl, batch):
     h2d = sum(t.numel() * t.element_size() for t in pinned.values())
     d2h = sum(t.numel() * t.element_size() for t in res_host.values())
 
+    def copy_out(fo, fi):
+        res_host["hits"].copy_(fo["hits"], non_blocking=True)
+        res_host["state"].copy_(fi["state"], non_blocking=True)
+        res_host["chi2"].copy_(fi["chi2"], non_blocking=True)
+
     def e2e_step():
         for k, t in pinned.items():
             d[k].copy_(t, non_blocking=True)
         step(stream)
-        res_host["hits"].copy_(fout["hits"], non_blocking=True)
-        res_host["state"].copy_(fit_out["state"], non_blocking=True)
-        res_host["chi2"].copy_(fit_out["chi2"], non_blocking=True)
+        copy_out(fout, fit_out)
 
     t_e2e = timed_steps(args.steps, e2e_step)
-    ms_e2e = shard.max_over_ranks(statistics.mean(t_e2e), device=dev)
+    ms_e2e_serial = shard.max_over_ranks(statistics.mean(t_e2e), device=dev)
+
+    sets = [(d, fout, fit_out), ({k: torch.empty_like(d[k]) for k in pinned},
+                                 {k: torch.empty_like(v) for k, v in fout.items()},
+                                 {k: torch.empty_like(v) for k, v in fit_out.items()})]
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def e2e_pipeline(k):
+        ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(k)] for _ in range(3))
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        s_in.wait_event(t0)
+        s_out.wait_event(t0)
+        for i in range(k):
+            dd, fo, fi = sets[i % 2]
+            with torch.cuda.stream(s_in):
+                if i >= 2:
+                    s_in.wait_event(ev_c[i - 2])  # step i-2 has read this input set
+                for key, t in pinned.items():
+                    dd[key].copy_(t, non_blocking=True)
+                ev_in[i].record(s_in)
+            stream.wait_event(ev_in[i])
+            if i >= 2:
+                stream.wait_event(ev_out[i - 2])  # step i-2's results in this output set are read back
+            step(stream, dd=dd, fo=fo, fi=fi)
+            ev_c[i].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_c[i])
+                copy_out(fo, fi)
+                ev_out[i].record(s_out)
+        stream.wait_event(ev_out[k - 1])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / k
+
+    e2e_pipeline(min(args.warmup, 3))
+    ms_e2e = shard.max_over_ranks(e2e_pipeline(args.steps), device=dev)
 
     # Result sanity on the last step (efficiency of the found tracks, host logic only).
     from paper_1906_02253_gb300 import metrics
@@ -377,7 +425,10 @@ def run_gpu(args, wl, batch):
            "fit_tracks_per_s": ws * n_seeds / (kern_ms["fit"] / 1000.0),
            "find_seeds_per_s": ws * n_seeds / (kern_ms["find"] / 1000.0),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "ms_per_step": ms_e2e}}
+                   "ms_per_step": ms_e2e, "pipelined": "H2D of step i+1 and D2H of step i-1 on their own "
+                   "streams overlap step i (two buffer sets); L2: the H2D rewrites the inputs each step",
+                   "serial_ms_per_step": ms_e2e_serial,
+                   "serial_value": ws * n_seeds / (ms_e2e_serial / 1000.0)}}
     out["clocks"] = clk.summary()
     if learned is not None:
         out["learned_vs_plain"] = learned
