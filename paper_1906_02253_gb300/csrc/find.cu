@@ -48,7 +48,6 @@ struct WarpSmem {
   float hl_tot[KC][32];    // per lane: best passing hits, sorted by (total chi2, hit id)
   int hl_id[KC][32];
   int hl_pos[KC][32];
-  int sel_n[32];           // children offered by each lane
   unsigned long long tab_key[32];  // winner table of each group, by rank
   int tab_id[32];
   int tab_pos[32];
@@ -59,7 +58,6 @@ struct WarpSmem {
       int pos[kPList];
       int own[kPList];
     } pl;                               // buffered passing pairs (scan)
-    unsigned long long key[KC][32];     // ranking keys of each lane's children (selection)
   } u;
 };
 
@@ -732,7 +730,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     };
     for (;;) {
       int T = 0;
-#pragma unroll 1
+#pragma unroll
       for (int k = 0; k < kRows; ++k) {
         int a = 0, b = 0;
         if (row < npb) {
@@ -843,37 +841,42 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
 
     // ---- 3. selection of the k_max best children of each seed -----------------------------
     // Each lane offers its children in ranking order (hit children by total chi2, or one miss or
-    // carried child); a child's rank in its seed is its index in its lane's list plus the number
-    // of the group's other children that rank before it. Ranks are distinct (slots differ between
-    // lanes, hit ids within a lane); the child of rank j < k_max goes to the group's slot j.
+    // carried child) as a list whose head key is in a register; k_max rounds of a tournament
+    // over the group's heads (a segmented minimum by shuffles) give the seed's children in rank
+    // order, and the child of rank j goes to the group's slot j. Keys of different lanes differ
+    // (they carry the slot), so the order is the same total order as comparing all children.
     const int nch = (on && kind != 3) ? (kind == 0 ? hl_n : 1) : 0;
-    if (kind == 0) {
-      for (int i = 0; i < hl_n; ++i) W.u.key[i][lane] = pack_key(c.nh + 1, W.hl_tot[i][lane], slot << 2);
-    } else if (nch == 1) {
-      W.u.key[0][lane] = pack_key(c.nh, c.chi2, (slot << 2) | kind);
-      W.hl_id[0][lane] = -1;
+    // Rounds: the most children any group of the warp has, up to k_max.
+    int tot = nch;
+#pragma unroll
+    for (int off = 1; off < KC; off <<= 1) {
+      const int v = __shfl_down_sync(kFull, tot, off);
+      if (slot + off < KC) tot += v;
     }
-    W.sel_n[lane] = nch;
+    const int rounds = min(cap, static_cast<int>(__reduce_max_sync(kFull, in_grp && slot == 0 ? tot : 0)));
+    unsigned long long mk = ~0ull, nk = ~0ull;  // this lane's head key and the one after it
+    if (nch > 0) mk = kind == 0 ? pack_key(c.nh + 1, W.hl_tot[0][lane], slot << 2) : pack_key(c.nh, c.chi2, (slot << 2) | kind);
+    if (nch > 1) nk = pack_key(c.nh + 1, W.hl_tot[1][lane], slot << 2);
+    int head = 0;
     W.tab_key[lane] = ~0ull;
     __syncwarp();
-    for (int i = 0; i < nch; ++i) {
-      const unsigned long long mk = W.u.key[i][lane];
-      const int mid = W.hl_id[i][lane];
-      int r = i;
-      for (int sm = 0; sm < KC; ++sm) {
-        if (sm == slot) continue;
-        const int col = gbase + sm;
-        const int nm = W.sel_n[col];
-        for (int j = 0; j < nm; ++j) {
-          const unsigned long long ok = W.u.key[j][col];
-          if (ok < mk || (ok == mk && W.hl_id[j][col] < mid)) ++r;
-          else break;
-        }
+#pragma unroll 1
+    for (int r = 0; r < rounds; ++r) {
+      unsigned long long m = mk;
+#pragma unroll
+      for (int off = 1; off < KC; off <<= 1) {
+        const unsigned long long v = __shfl_down_sync(kFull, m, off);
+        if (slot + off < KC) m = v < m ? v : m;
       }
-      if (r >= cap) break;  // later children of this lane rank later still
-      W.tab_key[gbase + r] = mk;
-      W.tab_id[gbase + r] = mid;
-      W.tab_pos[gbase + r] = W.hl_pos[i][lane];
+      const unsigned long long gm = __shfl_sync(kFull, m, gbase);
+      if (in_grp && mk != ~0ull && mk == gm) {
+        W.tab_key[gbase + r] = mk;
+        W.tab_id[gbase + r] = kind == 0 ? W.hl_id[head][lane] : -1;
+        W.tab_pos[gbase + r] = kind == 0 ? W.hl_pos[head][lane] : 0;
+        ++head;
+        mk = nk;
+        nk = head + 1 < nch ? pack_key(c.nh + 1, W.hl_tot[head + 1][lane], slot << 2) : ~0ull;
+      }
     }
     __syncwarp();
     int w_par = 0, w_kind = 3, w_id = -1, w_pos = 0, w_nh = 0;
