@@ -46,7 +46,7 @@ FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20
 # FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh")
-FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "a253a2e66a1675291bea21c7b63c90df94703e20", "dram_bytes_per_seed": 162617600 / 302063}
+FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "ebeb27bc11d7d18b8ae5761899191ba72d96734c", "dram_bytes_per_seed": 161582592 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 8 B direction) plus
 # the bin offsets written per (event, surface).
 INDEX_BYTES_PER_HIT = 28
