@@ -316,6 +316,31 @@ def test_find_parity_dense_noise(kf):
     _assert_find_parity(b, gpu, ora, st)
 
 
+def test_general_and_plain_finder_instances_agree(kf):
+    """A flat material map (every node at the surface's x/X0) and no energy loss select the general
+    finder kernel (the one that serves steering, material map and field map) with the physics of
+    the plain one: the two instances find the same tracks."""
+    import dataclasses
+    base = synth.workload("hi_occ", n_events=2, tracks_lo=800, tracks_hi=1500)
+    flat = dataclasses.replace(base, material=tuple(tuple([s.x_over_x0] * synth.MAT_NODES) for s in base.surfaces))
+    b = synth.generate(base)
+    outs = []
+    for wl in (base, flat):
+        g = kf.Geometry(wl)
+        dev = kf.to_device_event_batch(b)
+        idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+        out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+        outs.append({k: v.cpu().numpy() for k, v in out.items() if k != "workspace"})
+    same = (outs[0]["hits"] == outs[1]["hits"]).all(axis=0)
+    assert same.mean() >= 0.9999, same.mean()  # the two compilations may round a contraction apart
+    assert np.array_equal(outs[0]["status"], outs[1]["status"])
+    ok = same & (outs[0]["status"] == 0)
+    for k in ("chi2", "state"):
+        a, c = outs[0][k][..., ok].astype(np.float64), outs[1][k][..., ok].astype(np.float64)
+        assert np.all(np.abs(a - c) <= 1e-5 * np.maximum(np.abs(a), 1.0)), k
+
+
 def test_autotuner_configurations_give_identical_results(kf):
     """Block size and candidate capacity change the schedule, never the result: every configuration
     the autotuner tries finds the same tracks, and it returns one of them."""
