@@ -193,6 +193,19 @@ def test_find_parity_field_map(kf):
     _assert_find_parity(b, gpu, ora, st)
 
 
+def test_find_and_fit_parity_with_every_option_at_once(kf):
+    """Field map, material map, energy loss and region steering together on the barrel + disk
+    geometry (the general finder kernel with all its branches live)."""
+    import dataclasses
+    base = synth.workload("field", n_events=2, tracks_lo=800, tracks_hi=1500)
+    wl = dataclasses.replace(base, material=synth.material_map(base.surfaces), eloss=0.0363)
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b, steering=_steering_without(wl, ()))
+    _assert_find_parity(b, gpu, ora, st)
+    gpu_f, ora_f = _fit_both(kf, wl, b)
+    _assert_fit_parity(gpu_f, ora_f)
+
+
 def test_field_coefficients_rejected_when_not_finite(kf):
     import dataclasses
     wl = synth.workload("field", n_events=1, tracks_lo=50, tracks_hi=50)
