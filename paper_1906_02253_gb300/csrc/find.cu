@@ -271,6 +271,13 @@ __device__ __forceinline__ void hl_insert(WarpSmem<KC>& W, int lane, int& n, int
   ++n;
 }
 
+// Barrel s is certainly crossed outside its z extent: the transverse path to radius R is at least
+// R - rho (a straight line), so z moves by at least (R - rho) cot theta before the crossing.
+__device__ __forceinline__ bool barrel_beyond_z(const DevGeom& G, int s, const float* p, float rho, float cot) {
+  const float dz = (G.r_or_z[s] - rho) * cot;
+  return (cot > 0.f && p[2] + dz > G.hi[s]) || (cot < 0.f && p[2] + dz < G.lo[s]);
+}
+
 // Whether the helix from state p reaches disk s within its r extent and half a turn, and the path
 // to it. st, ct: sin and cos of the polar angle p[5].
 __device__ __forceinline__ bool reach_disk(const DevGeom& G, const float* p, float w, int s, float st, float ct,
@@ -287,8 +294,10 @@ __device__ __forceinline__ bool reach_disk(const DevGeom& G, const float* p, flo
 __device__ __forceinline__ bool reach_surface(const DevGeom& G, const float* p, float w, int s, float st, float ct,
                                               float cot, Prop& pr) {
   if (G.type[s] == 0) {
-    // z moves monotonically along the helix: past the z extent and moving away, it stays out.
+    // z moves monotonically along the helix: past the z extent and moving away, it stays out; a
+    // steering list's later barrel layers are passed over by the bound without a crossing search.
     if ((cot >= 0.f && p[2] > G.hi[s]) || (cot <= 0.f && p[2] < G.lo[s])) return false;
+    if (barrel_beyond_z(G, s, p, sqrtf(p[0] * p[0] + p[1] * p[1]), cot)) return false;
     if (!path_to_cylinder(p, w, G.r_or_z[s], pr)) return false;
     const float z = p[2] + pr.s * cot;
     return z >= G.lo[s] && z <= G.hi[s];

@@ -50,13 +50,25 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
     const int n2 = G.n_2nd[si];
     for (int b = threadIdx.x; b <= nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const float2 h = hits[h0 + i];
-      const int pb = phi_bin(G, si, h.x);
-      const int b = pb * n2 + second_bin(G, si, h.y);
-      bin[i] = static_cast<unsigned short>(b);
-      sub[i] = static_cast<unsigned char>(sub_of(phi_fine(G, si, h.x), pb));
-      atomicAdd(&hist[b], 1);
+    // Four hits per thread per iteration, their loads issued together.
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+      float2 hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        hv[u] = i < n ? __ldg(hits + h0 + i) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < n) {
+          const int pb = phi_bin(G, si, hv[u].x);
+          const int b = pb * n2 + second_bin(G, si, hv[u].y);
+          bin[i] = static_cast<unsigned short>(b);
+          sub[i] = static_cast<unsigned char>(sub_of(phi_fine(G, si, hv[u].x), pb));
+          atomicAdd(&hist[b], 1);
+        }
+      }
     }
     __syncthreads();
     // Exclusive scan of hist[0, nbs) in place: each thread scans a contiguous chunk.
@@ -135,15 +147,29 @@ __global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2
       }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-      const int i = order[p];
-      const float2 h = hits[h0 + i];
-      sorted_hits[h0 + p] = h;
-      sorted_ids[h0 + p] = h0 + i;
-      if (sorted_rec) {
-        float s, c;
-        sincosf(h.x, &s, &c);
-        sorted_rec[h0 + p] = make_float4(c, s, h.y, __int_as_float(h0 + i));
+    // Gather in sorted order, four per thread per iteration with their loads issued together.
+    for (int p0 = threadIdx.x; p0 < n; p0 += 4 * blockDim.x) {
+      int iv[4];
+      float2 hv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = p0 + u * blockDim.x;
+        iv[u] = p < n ? order[p] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) hv[u] = p0 + u * static_cast<int>(blockDim.x) < n ? __ldg(hits + h0 + iv[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = p0 + u * blockDim.x;
+        if (p < n) {
+          sorted_hits[h0 + p] = hv[u];
+          sorted_ids[h0 + p] = h0 + iv[u];
+          if (sorted_rec) {
+            float s, c;
+            sincosf(hv[u].x, &s, &c);
+            sorted_rec[h0 + p] = make_float4(c, s, hv[u].y, __int_as_float(h0 + iv[u]));
+          }
+        }
       }
     }
     __syncthreads();
