@@ -243,7 +243,11 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
  *   seed_hits  device int [3][n_seeds]; track_hits device int [lmax][n_tracks] (-1: none), nhits,
  *              chi2, state [6][n_tracks] (the finder's outputs); *_event device int; hit ids < n_hits.
  *   workspace  device memory of kf_dedup_workspace_size(n_items, 3 or lmax, n_hits) bytes, 256-byte
- *              aligned. */
+ *              aligned (0 from the size function for invalid sizes).
+ * Asynchronous on the stream. Returns KF_OK (nothing launched for zero items), KF_ERR_ARG (negative
+ * counts, negative or NaN cuts, lmax outside 1..KF_MAX_LMAX, a null pointer, a small or misaligned
+ * workspace, an invalid geometry), KF_ERR_CAPACITY (n_tracks * lmax above 2^31 - 1) or
+ * KF_ERR_CUDA. */
 size_t kf_dedup_workspace_size(int n_items, int refs_per_item, int n_hits);
 int kf_clean_seeds(const KfGeometry* geom, const float* hits, const int* hit_surface, int n_hits, const int* seed_hits,
                    const int* seed_event, int n_seeds, float dphi, float dtheta, int* keep_out, void* workspace,
