@@ -46,10 +46,11 @@ FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20
 # FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh")
-FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "ebeb27bc11d7d18b8ae5761899191ba72d96734c", "dram_bytes_per_seed": 161582592 / 302063}
-# Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 8 B direction) plus
-# the bin offsets written per (event, surface).
-INDEX_BYTES_PER_HIT = 28
+FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "02d7d9fabab7250d65674f4c14b4c95559c20a87", "dram_bytes_per_seed": 160636416 / 302063}
+# Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
+# record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
+INDEX_BYTES_PER_HIT = 36
+INDEX_BYTES_PER_BIN = 4 + 16
 
 
 def _dist():
@@ -510,39 +511,49 @@ def find_sources_sha1() -> str:
 
 
 def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
-    """Roofline of the dominant kernel. The finder and the fit are FP32-ALU bound (no dense
-    contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM clock. The index is HBM bound."""
+    """Roofline of every step kernel, and of the dominant one at the top level. The finder and the
+    fit are FP32-ALU bound (no dense contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM
+    clock. The index is HBM bound."""
     import torch
     peaks = _peaks()
-    dom = max(kern_ms, key=kern_ms.get)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    if dom == "index":
-        nbytes = INDEX_BYTES_PER_HIT * n_hits + 4 * batch.n_events * len(batch.wl.surfaces) * (2048 + 1)
-        ach = nbytes / (kern_ms["index"] / 1000.0) / 1e9
-        return {"kernel": "k_build_hit_index", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None}
-    if dom == "fit":
-        n_steps = float((batch.track_nhits - 1).sum())
-        flops = len(batch.track_nhits) * (FLOP_SEED + FLOP_UPDATE) + n_steps * (FLOP_PROP + FLOP_TRANSPORT + FLOP_UPDATE)
-        ach = flops / (kern_ms["fit"] / 1000.0) / 1e12
-        return {"kernel": "k_fit_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz"}
+    per = {}
+    n_slabs = batch.n_events * len(batch.wl.surfaces)
+    n_bins = max(s.n_phi * s.n_2nd for s in batch.wl.surfaces)
+    nbytes = INDEX_BYTES_PER_HIT * n_hits + n_slabs * (INDEX_BYTES_PER_BIN * n_bins + 4)
+    ach = nbytes / (kern_ms["index"] / 1000.0) / 1e9
+    per["index"] = {"kernel": "k_build_hit_index", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None}
+    # fit of the found tracks: N hits give N - 1 propagation steps (ndof = 2 N - 5)
+    ok = fit_out["status"] == 0
+    n_fit = int(ok.sum().item())
+    n_steps = float(((fit_out["ndof"][ok].double() + 5.0) / 2.0 - 1.0).sum().item())
+    flops = n_fit * (FLOP_SEED + FLOP_UPDATE) + n_steps * (FLOP_PROP + FLOP_TRANSPORT + FLOP_UPDATE)
+    ach = flops / (kern_ms["fit"] / 1000.0) / 1e12
+    per["fit"] = {"kernel": "k_fit_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                  "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz"}
     if counters is None:
-        return {"kernel": "k_find_tracks", "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
-    # chi2 work: the hits of the windows the finder scans (limited to the phi sub-bins they touch)
-    n_prop, n_pass, n_upd, n_scan, n_win = counters
-    per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
-    ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
-    profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and batch.wl.name == FIND_PROFILE["workload"]
-    traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if profiled else None
-    return {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": ach / alu_peak, "traffic": traffic, "traffic_unit": "bytes per launch (ncu, scaled by seeds)",
-            "peak_note": f"FP32 {sm_mhz:.0f} MHz",
-            "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win, "chi2_whole_bins": n_scan,
-                              "flop": per_seed}}
+        per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": None, "peak": alu_peak,
+                       "unit": "TFLOP/s", "frac": None, "traffic": None}
+    else:
+        # chi2 work: the hits of the windows the finder scans (limited to the phi sub-bins they touch)
+        n_prop, n_pass, n_upd, n_scan, n_win = counters
+        per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
+        ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
+        profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and batch.wl.name == FIND_PROFILE["workload"]
+        traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if profiled else None
+        per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak,
+                       "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
+                       "traffic_unit": "bytes per launch (ncu, scaled by seeds)", "peak_note": f"FP32 {sm_mhz:.0f} MHz",
+                       "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win,
+                                         "chi2_whole_bins": n_scan, "flop": per_seed}}
+    dom = max(("index", "find", "fit"), key=lambda k: kern_ms[k])
+    out = dict(per[dom])
+    out["per_kernel"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+                         for k, v in per.items()}
+    return out
 
 
 def main():
