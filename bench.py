@@ -122,7 +122,7 @@ def _peaks():
 # Oracle legs (host cores only)
 # ------------------------------------------------------------------------------------------------
 
-def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False):
+def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: int = 0):
     """Run the FP64 oracle (index + find + fit of the found tracks; with ``clean``, seed cleaning
     before finding and duplicate removal after it) on the first seeds of the batch, all host
     cores. Returns (seconds, n_seeds, counters, threads)."""
@@ -139,14 +139,15 @@ def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False):
     if clean:
         keep = oracle.clean_seeds(seeds[sub], ev[sub], oracle.seed_params(g, batch, seeds[sub]))
         sub = sub[keep != 0]
-    f = oracle.find(g, batch, seeds[sub], ev[sub])
+    f = oracle.find(g, batch, seeds[sub], ev[sub], n_threads=n_threads)
     if clean:
         oracle.remove_duplicates(f["hits"], f["n_hits"], f["chi2"], f["p"][:, 4], f["p"][:, 5], ev[sub])
-    oracle.fit(g, batch.hits, batch.hit_surface, f["hits"])
+    oracle.fit(g, batch.hits, batch.hit_surface, f["hits"], n_threads=n_threads)
     dt = time.perf_counter() - t0
+    threads = n_threads if n_threads > 0 else (os.cpu_count() or 1)
     if clean:
-        return dt, len(keep), f["counters"], os.cpu_count() or 1
-    return dt, len(sub), f["counters"], os.cpu_count() or 1
+        return dt, len(keep), f["counters"], threads
+    return dt, len(sub), f["counters"], threads
 
 
 def run_reference(args, wl, batch):
@@ -445,6 +446,9 @@ def run_gpu(args, wl, batch):
                                          + ("seed cleaning, find, duplicate removal, " if clean else "find, ")
                                          + f"fit of the found tracks (FP64, {dt:.1f} s)"}
         counters = np.asarray(counters, np.float64) / n
+        dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1)
+        out["cpu_baseline"]["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                                                "sample": f"first {n1} seeds ({dt1:.1f} s)"}
     out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
     if rank == 0:
         print(json.dumps(out), flush=True)
