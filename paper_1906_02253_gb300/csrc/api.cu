@@ -232,7 +232,7 @@ int kf_build_hit_index(const KfGeometry* geom, const float* hits, const int* sla
       return KF_ERR_CUDA;
     smem_set[dev] = static_cast<int>(smem);
   }
-  k_build_hit_index<<<n_slabs, 512, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
+  k_build_hit_index<<<n_slabs, 1024, smem, reinterpret_cast<cudaStream_t>(stream)>>>(
       G, reinterpret_cast<const float2*>(hits), slab_offsets, n_slabs, cap, index->bin_off,
       reinterpret_cast<float2*>(index->sorted_hits), index->sorted_ids, reinterpret_cast<float4*>(index->sorted_rec),
       reinterpret_cast<uint4*>(index->sub_off), d_status);

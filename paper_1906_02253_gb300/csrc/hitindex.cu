@@ -18,7 +18,7 @@ namespace kfgb {
 
 static_assert(kPhiSub == 8, "sub-bin offsets are written as eight 16-bit counts");
 
-__global__ void __launch_bounds__(512) k_build_hit_index(DevGeom G, const float2* __restrict__ hits,
+__global__ void __launch_bounds__(1024, 2) k_build_hit_index(DevGeom G, const float2* __restrict__ hits,
                                                          const int* __restrict__ slab_off, int n_slabs,
                                                          int cap, int* __restrict__ bin_off,
                                                          float2* __restrict__ sorted_hits,
