@@ -523,6 +523,9 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # context: the FP32 rate a plain FMA stream reaches on this GPU (the library's probe kernel)
+    import paper_1906_02253_gb300 as kf
+    fma_rate = kf.fp32_fma_rate()
     per = {}
     n_slabs = batch.n_events * len(batch.wl.surfaces)
     n_bins = max(s.n_phi * s.n_2nd for s in batch.wl.surfaces)
@@ -537,7 +540,8 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
     flops = n_fit * (FLOP_SEED + FLOP_UPDATE) + n_steps * (FLOP_PROP + FLOP_TRANSPORT + FLOP_UPDATE)
     ach = flops / (kern_ms["fit"] / 1000.0) / 1e12
     per["fit"] = {"kernel": "k_fit_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                  "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz"}
+                  "frac": ach / alu_peak, "traffic": None, "peak_note": f"FP32 {sm_mhz:.0f} MHz",
+                  "fma_probe_tflops": fma_rate}
     if counters is None:
         per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": None, "peak": alu_peak,
                        "unit": "TFLOP/s", "frac": None, "traffic": None}
@@ -551,6 +555,7 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
         per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak,
                        "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
                        "traffic_unit": "bytes per launch (ncu, scaled by seeds)", "peak_note": f"FP32 {sm_mhz:.0f} MHz",
+                       "fma_probe_tflops": fma_rate,
                        "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win,
                                          "chi2_whole_bins": n_scan, "flop": per_seed}}
     dom = max(("index", "find", "fit"), key=lambda k: kern_ms[k])

@@ -324,6 +324,13 @@ int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_su
                     int* status_out, int* block_threads, float* best_ms, kf_stream_t stream);
 
 /* Human-readable name of a status code. */
+/* FP32 throughput probe (measurement only, not part of the path): launches `blocks` blocks of 256
+ * threads, each running eight independent fused multiply-add chains for iters x 16 steps, on the
+ * stream, and stores the launch's flop count (2 per FMA) in *flops. The caller times the launch
+ * (CUDA events) to get the FP32 rate the ALU-bound kernels are compared with. sink: device float
+ * [blocks] (practically never written). KF_ERR_ARG for non-positive sizes or null pointers. */
+int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_stream_t stream);
+
 const char* kf_status_string(int status);
 
 #ifdef __cplusplus

@@ -66,7 +66,7 @@ class KfFindParams(ctypes.Structure):
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
-           "kf_remove_duplicates")
+           "kf_remove_duplicates", "kf_fp32_fma_probe")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH):
             lib.kf_clean_seeds.argtypes = [G, P, P, I, P, P, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
             lib.kf_remove_duplicates.restype = I
             lib.kf_remove_duplicates.argtypes = [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
+            lib.kf_fp32_fma_probe.restype = I
+            lib.kf_fp32_fma_probe.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_longlong), P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -309,6 +311,26 @@ def remove_duplicates(track_hits, nhits, chi2, state, track_event, n_hits: int, 
                                   _stream(stream))
     _check(rc, "kf_remove_duplicates")
     return keep
+
+
+def fp32_fma_rate(blocks: int = 0, iters: int = 4096, reps: int = 3, stream=None) -> float:
+    """kf_fp32_fma_probe timed with CUDA events: the best of `reps` launches, TFLOP/s (FMA = 2)."""
+    lib = load_library()
+    dev = torch.cuda.current_device()
+    if blocks <= 0:
+        blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(blocks, dtype=torch.float32, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    flops = ctypes.c_longlong()
+    best = 0.0
+    for _ in range(reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        _check(lib.kf_fp32_fma_probe(_ptr(sink), blocks, iters, ctypes.byref(flops), _stream(s)), "kf_fp32_fma_probe")
+        b.record(s)
+        b.synchronize()
+        best = max(best, flops.value / (a.elapsed_time(b) / 1000.0) / 1e12)
+    return best
 
 
 def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:

@@ -23,6 +23,7 @@ size_t dup_workspace_bytes(int n, int m, int n_hits);
 int launch_clean_seeds(const DevGeom& G, const float2* hits, const int* hit_surface, const int* seed_hits,
                        const int* seed_event, int n, int n_hits, float dphi, float dtheta, int* keep, void* ws,
                        cudaStream_t st);
+int launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t st, long long* flops);
 int launch_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
                              const int* event, int n, int lmax, int n_hits, float dphi, float dtheta, int* keep,
                              void* ws, cudaStream_t st);
@@ -496,6 +497,11 @@ int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* c
     return KF_ERR_ARG;
   return launch_remove_duplicates(track_hits, nhits, chi2, state, track_event, n_tracks, lmax, n_hits, dphi, dtheta,
                                   keep_out, workspace, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_stream_t stream) {
+  if (!sink || !flops || blocks <= 0 || iters <= 0) return KF_ERR_ARG;
+  return launch_fma_peak(sink, blocks, iters, reinterpret_cast<cudaStream_t>(stream), flops);
 }
 
 const char* kf_status_string(int status) {
