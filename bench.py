@@ -46,7 +46,7 @@ FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20
 # FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh")
-FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "02d7d9fabab7250d65674f4c14b4c95559c20a87", "dram_bytes_per_seed": 160636416 / 302063}
+FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "fb446aae27babbb4f140f9ab6ffa5a274710b870", "dram_bytes_per_seed": 160636416 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36

@@ -13,9 +13,10 @@
 //     evaluates chi2 for every 32nd of them (full SIMT width whatever the window sizes); hits
 //     below the cut are buffered in flattened order, so each owner's pairs form one contiguous
 //     run, which the owner merges into its list of the k_max best by (total chi2, hit id);
-//  3. per seed, every child (hit children, miss child, carried candidate) counts the children of
-//     the seed's other lanes that rank before it; the one of rank j < k_max goes to slot j, and
-//     lane j materialises it (Kalman update for a hit child) from its parent's record;
+//  3. per seed, each lane offers its children (hit children, miss child, carried candidate) as a
+//     sorted list; k_max rounds of a tournament over the lists' heads (a segmented minimum by
+//     shuffles) rank them, the child of rank j goes to slot j, and lane j materialises it (Kalman
+//     update for a hit child) from its parent's record;
 //  4. a seed whose candidates have all stopped writes its best track (backtracking a per-step
 //     trace of parent slot and hit) and its lanes take the next seed from an atomic queue.
 // The warps of a block vote once per step (block barrier), which keeps them in the same phase.
