@@ -18,9 +18,10 @@ LIB = os.path.join(BUILD, "libkfgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--compiler-options", "-fPIC", "-Xptxas", "-v"]
 # The Kalman arithmetic tolerates divisions and square roots within 2 ulp (its parity bars are
-# 1e-4 on the state, 1e-3 on chi2); the hit binning, which must be bit-exact, uses explicitly
-# rounded intrinsics and lives in hitindex.cu, which keeps the IEEE defaults.
-PER_FILE = {"fit.cu": ["-prec-div=false", "-prec-sqrt=false"], "find.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+# 1e-4 on the state, 1e-3 on chi2) and flushes denormals (its values stay far above 1e-38); the
+# hit binning, which must be bit-exact, uses explicitly rounded intrinsics and lives in
+# hitindex.cu, which keeps the IEEE defaults.
+PER_FILE = {"fit.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"], "find.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
 
 
 def _nvcc() -> str:
