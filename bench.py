@@ -42,10 +42,10 @@ WORKLOAD = "fit_batched"
 FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch on 30 events of the 100-event workload, per seed; profiles/step_kernels_fit_batched_100ev.md),
-# valid for that workload while the finder's sources are the ones profiled (SHA-1 over
-# FIND_SOURCES); otherwise reported as null.
+# valid for that workload while the finder's sources and build flags are the ones profiled (SHA-1
+# over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
-                "paper_1906_02253_gb300/csrc/find_launch.cuh")
+                "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
 FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "fb446aae27babbb4f140f9ab6ffa5a274710b870", "dram_bytes_per_seed": 160636416 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
