@@ -20,8 +20,8 @@
 //  4. a seed whose candidates have all stopped writes its best track (backtracking a per-step
 //     trace of parent slot and hit) and its lanes take the next seed from an atomic queue.
 // The warps of a block vote once per step (block barrier), which keeps them in the same phase.
-// Seeds are consumed in order (one event after another, neighbouring directions together), so the
-// warps of an SM read neighbouring bins of the same event's index through L1/L2.
+// Seeds are consumed in queue order, one event after another, so the warps of the GPU read the
+// index of one or two events at a time through L2.
 #include <algorithm>
 
 #include "find_launch.cuh"
