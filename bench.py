@@ -360,6 +360,7 @@ def run_gpu(args, wl, batch):
     s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def e2e_pipeline(k):
+        k = max(1, k)
         ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(k)] for _ in range(3))
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(stream)
