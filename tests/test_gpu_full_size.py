@@ -1,0 +1,78 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the benchmark times.
+
+The GPU finds tracks for every seed of the full 100-event and 200-event workloads with the
+autotuned block size and candidate capacity (calibrated on the first 10 events, as the benchmark
+does) and fits every simulated track; the FP64 oracle then computes a seeded random sample of 20,000
+seeds and 20,000 tracks one by one, and the sample is held to the parity bars: hit lists identical
+on >= 99.9% of seeds, efficiency within 0.1%, identical tracks carrying the same fitted state
+(1e-4) and chi2 (1e-3), fitted tracks within the fit bars.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FLOOR = np.array([1.0, 1.0, 1.0, 0.1, 1.0, 1.0])
+N_SAMPLE = 20000
+
+
+def _rel(p_gpu, p_ora):
+    d = p_gpu.astype(np.float64) - p_ora
+    d[:, 4] = (d[:, 4] + np.pi) % (2 * np.pi) - np.pi
+    return np.abs(d) / np.maximum(np.abs(p_ora), FLOOR)
+
+
+@pytest.mark.parametrize("wl_name", ["fit_batched", "hi_occ"])
+def test_full_size_parity_on_sampled_seeds_and_tracks(wl_name):
+    import __graft_entry__ as ge
+    ge.build_library()
+    import paper_1906_02253_gb300 as kf
+    wl = synth.workload(wl_name)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
+    cal_s = dev["seed_hits"][:, :n_cal].contiguous()
+    cal_e = dev["seed_event"][:n_cal].contiguous()
+    prm, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], cal_s, cal_e, prm)
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    fit_block, _ = kf.autotune_fit(g, dev["hits"], dev["hit_surface"], dev["track_hits"])
+    fit = kf.fit_tracks(g, dev["hits"], dev["hit_surface"], dev["track_hits"], block_threads=fit_block)
+    torch.cuda.synchronize()
+    n = dev["seed_hits"].shape[1]
+    assert n > 1_000_000
+
+    rng = np.random.default_rng(1906)
+    s = np.sort(rng.choice(n, N_SAMPLE, replace=False))
+    sh, st = b.seeds()
+    og = oracle.Geometry(wl)
+    r = oracle.find(og, b, sh[s], b.track_event[st][s])
+    gh = out["hits"].cpu().numpy().T[s]
+    same = (gh == r["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    g_status = out["status"].cpu().numpy()[s]
+    assert np.array_equal(g_status, r["status"])
+    e_g = oracle.efficiency(b, st[s], gh, out["nhits"].cpu().numpy()[s])[0]
+    e_o = oracle.efficiency(b, st[s], r["hits"], r["n_hits"])[0]
+    assert abs(e_g - e_o) <= 0.001
+    ok = same & (r["status"] == 0)
+    rel = _rel(out["state"].cpu().numpy().T[s][ok], r["p"][ok])
+    assert np.quantile(rel.max(axis=1), 0.999) < 1e-4
+    gc2 = out["chi2"].cpu().numpy()[s][ok]
+    assert np.quantile(np.abs(gc2 - r["chi2"][ok]) / np.maximum(r["chi2"][ok], 1.0), 0.999) < 1e-3
+
+    t = np.sort(rng.choice(b.n_tracks, N_SAMPLE, replace=False))
+    f = oracle.fit(og, b.hits, b.hit_surface, b.track_hits[t])
+    assert np.array_equal(fit["status"].cpu().numpy()[t], f["status"])
+    assert np.array_equal(fit["ndof"].cpu().numpy()[t], f["ndof"])
+    okf = f["status"] == 0
+    relf = _rel(fit["state"].cpu().numpy().T[t][okf], f["p"][okf])
+    assert relf.max() < 1e-4, relf.max(axis=0)
+    fc2 = fit["chi2"].cpu().numpy()[t][okf]
+    assert (np.abs(fc2 - f["chi2"][okf]) / np.maximum(f["chi2"][okf], 1.0)).max() < 1e-3
