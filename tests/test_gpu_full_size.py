@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, in the launch configuration the benchmark times.
 
-The GPU finds tracks for every seed of the full 100-event and 200-event workloads with the
+The GPU finds tracks for every seed of the full workloads (100 events; 200 events with disks and
+noise; 100 events with the material map; 20 events in the field map) with the
 autotuned block size and candidate capacity (calibrated on the first 10 events, as the benchmark
 does) and fits every simulated track; the FP64 oracle then computes a seeded random sample of 20,000
 seeds and 20,000 tracks one by one, and the sample is held to the parity bars: hit lists identical
@@ -26,7 +27,7 @@ def _rel(p_gpu, p_ora):
     return np.abs(d) / np.maximum(np.abs(p_ora), FLOOR)
 
 
-@pytest.mark.parametrize("wl_name", ["fit_batched", "hi_occ"])
+@pytest.mark.parametrize("wl_name", ["fit_batched", "hi_occ", "material", "field"])
 def test_full_size_parity_on_sampled_seeds_and_tracks(wl_name):
     import __graft_entry__ as ge
     ge.build_library()
@@ -46,7 +47,7 @@ def test_full_size_parity_on_sampled_seeds_and_tracks(wl_name):
     fit = kf.fit_tracks(g, dev["hits"], dev["hit_surface"], dev["track_hits"], block_threads=fit_block)
     torch.cuda.synchronize()
     n = dev["seed_hits"].shape[1]
-    assert n > 1_000_000
+    assert n > 100_000
 
     rng = np.random.default_rng(1906)
     s = np.sort(rng.choice(n, N_SAMPLE, replace=False))
@@ -76,3 +77,42 @@ def test_full_size_parity_on_sampled_seeds_and_tracks(wl_name):
     assert relf.max() < 1e-4, relf.max(axis=0)
     fc2 = fit["chi2"].cpu().numpy()[t][okf]
     assert (np.abs(fc2 - f["chi2"][okf]) / np.maximum(f["chi2"][okf], 1.0)).max() < 1e-3
+
+
+def test_full_size_seed_cleaning_and_duplicate_removal_chain():
+    """The overlap workload at full size (219 k combinatorial seeds): the GPU's cleaning flags
+    equal the oracle's on >= 99.9% of all seeds, and the whole chain (cleaning, finding, removal)
+    gives the oracle's efficiency and duplicate rate within 0.1%."""
+    import __graft_entry__ as ge
+    ge.build_library()
+    import paper_1906_02253_gb300 as kf
+    wl = synth.workload("duplicates")
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    keep = kf.clean_seeds(g, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"])
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, seed_keep=keep)
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    kd = kf.remove_duplicates(out["hits"], out["nhits"], out["chi2"], out["state"], dev["seed_event"], b.n_hits)
+    torch.cuda.synchronize()
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    og = oracle.Geometry(wl)
+    ok = oracle.clean_seeds(sh, ev, oracle.seed_params(og, b, sh))
+    gk = keep.cpu().numpy()
+    assert len(sh) > 200_000 and (gk == ok).mean() >= 0.999
+    k = np.nonzero(ok)[0]
+    r = oracle.find(og, b, sh[k], ev[k])
+    okd = np.zeros_like(ok)
+    okd[k] = oracle.remove_duplicates(r["hits"], r["n_hits"], r["chi2"], r["p"][:, 4], r["p"][:, 5], ev[k])
+    o_hits = np.full((len(sh), wl.lmax), -1, np.int32)
+    o_hits[k] = r["hits"]
+    o_nh = np.zeros(len(sh), np.int32)
+    o_nh[k] = r["n_hits"]
+    g_hits = out["hits"].cpu().numpy().T
+    g_nh = out["nhits"].cpu().numpy()
+    gkd = gk * kd.cpu().numpy()
+    e_g, d_g = oracle.track_rates(b, st, np.ones(len(st), bool), gkd, track_sim=oracle.majority_sim(b, g_hits, g_nh))
+    e_o, d_o = oracle.track_rates(b, st, np.ones(len(st), bool), okd, track_sim=oracle.majority_sim(b, o_hits, o_nh))
+    assert abs(e_g - e_o) <= 0.001 and abs(d_g - d_o) <= 0.001
