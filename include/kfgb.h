@@ -217,7 +217,10 @@ size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params);
  * parent rank, then child kind (hit, miss, carried), then hit id. Seeds run in parallel with no
  * hit marking across seeds (Sec. 3.2).
  *   hits, hit_surface  as for the fit (original hit ids); index built by kf_build_hit_index.
- *   seed_hits          device int [3][n_seeds] (structure of arrays), seed_event int [n_seeds].
+ *   seed_hits          device int [3][n_seeds] (structure of arrays), seed_event int [n_seeds]. A
+ *                      seed with a negative hit id, a hit on no surface of the geometry or an event
+ *                      outside [0, index->n_events) fails (status 1); hit ids must be below the
+ *                      number of hits.
  *   workspace          device memory of kf_find_workspace_size bytes, 256-byte aligned.
  * Outputs (device): hits_out int [lmax][n_seeds] (best candidate's hit ids in path order, -1 for
  * a miss or no further step), nhits_out int, chi2_out float, state_out float [6][n_seeds],

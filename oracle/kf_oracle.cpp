@@ -810,6 +810,8 @@ struct Ctx {
   OrFindParams prm;
   Mlp mlp;
   const OrSteering* steer = nullptr;  // region steering, or null for the geometric rule
+  long long n_hits = 0;  // hits of the batch and events: a seed outside them fails
+  int n_events = 0;
 };
 
 // Whether the helix from st reaches surface s within its extent (the acceptance used by the
@@ -956,6 +958,11 @@ struct Counters {
 bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, Counters& cnt,
               PairSink* sink = nullptr) {
   const OrGeom& g = *cx.g;
+  if (ev < 0 || ev >= cx.n_events) return false;
+  for (int k = 0; k < 3; ++k) {
+    const int id = seed_ids[k];
+    if (id < 0 || id >= cx.n_hits || cx.hsurf[id] < 0 || cx.hsurf[id] >= g.n_surf) return false;
+  }
   Cand c0;
   if (!seed_state(g, cx.hits, cx.hsurf, seed_ids, c0.st)) return false;
   // Fit the seed hits: update with hit 1, then propagate + update through hits 2, 3.
@@ -1264,6 +1271,8 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
   Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}, steering};
+  cx.n_hits = slab_off[static_cast<long long>(n_events) * g->n_surf];
+  cx.n_events = n_events;
   std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;
@@ -1302,6 +1311,8 @@ long long or_find_pairs(const OrGeom* g, const float* hits, const int* hsurf, co
   Index ix;
   build_index(*g, hits, slab_off, n_events, ix);
   Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{}};
+  cx.n_hits = slab_off[static_cast<long long>(n_events) * g->n_surf];
+  cx.n_events = n_events;
   std::vector<PairSink> sinks(n);
   parallel_for(n, n_threads, [&](long long i) {
     sinks[i].hit_sim = hit_sim;

@@ -321,6 +321,32 @@ def test_region_steering_rejects_invalid_lists(kf):
             kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
 
 
+def test_find_with_invalid_seeds(kf):
+    """Seeds with a missing hit or an event outside the batch fail with empty outputs on both
+    sides; the other seeds are unaffected."""
+    wl = synth.workload("find", n_events=2, tracks_lo=600, tracks_hi=600)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    sh = sh.copy()
+    ev = b.track_event[st].astype(np.int32).copy()
+    sh[0, 0] = -1
+    sh[1, 2] = -1
+    ev[2] = b.n_events
+    ev[3] = -1
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], torch.from_numpy(np.ascontiguousarray(sh.T)).cuda(),
+                         torch.from_numpy(ev).cuda(), prm)
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}
+    r = oracle.find(oracle.Geometry(wl), b, sh, ev)
+    assert gpu["status"][:4].tolist() == [1, 1, 1, 1] and r["status"][:4].tolist() == [1, 1, 1, 1]
+    assert np.all(gpu["hits"][:, :4] == -1) and np.all(gpu["nhits"][:4] == 0) and np.all(np.isnan(gpu["chi2"][:4]))
+    _assert_find_parity(b, gpu, r, st)
+
+
 def test_find_parity_dense_noise(kf):
     """Many branches per seed: 5 noise hits per signal hit."""
     wl = synth.workload("find", n_events=1, tracks_lo=1200, tracks_hi=1200, noise_frac=5.0)

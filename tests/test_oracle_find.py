@@ -207,3 +207,23 @@ def test_steering_list_without_a_layer_passes_it_over():
         a = [h for h in full["hits"][i] if h >= 0 and b.hit_surface[h] != 7]
         c = [h for h in cut["hits"][i] if h >= 0]
         assert a == c
+
+
+def test_invalid_seeds_fail_without_touching_the_rest():
+    """A seed with a missing hit id or an event outside the batch has status 1 and no hits; the
+    result of every other seed is the same as without them."""
+    wl = synth.workload("find", n_events=2, tracks_lo=300, tracks_hi=300)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st].astype(np.int32)
+    g = oracle.Geometry(wl)
+    ref = oracle.find(g, b, sh, ev)
+    bad_sh, bad_ev = sh.copy(), ev.copy()
+    bad_sh[0, 1] = -1
+    bad_sh[1, 0] = len(b.hits)
+    bad_ev[2] = b.n_events
+    bad_ev[3] = -1
+    r = oracle.find(g, b, bad_sh, bad_ev)
+    assert r["status"][:4].tolist() == [1, 1, 1, 1]
+    assert np.all(r["hits"][:4] == -1) and np.all(r["n_hits"][:4] == 0)
+    assert np.array_equal(r["hits"][4:], ref["hits"][4:]) and np.array_equal(r["status"][4:], ref["status"][4:])
