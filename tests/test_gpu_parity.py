@@ -347,6 +347,30 @@ def test_find_with_invalid_seeds(kf):
     _assert_find_parity(b, gpu, r, st)
 
 
+def test_find_and_fit_at_the_maximum_sizes(kf):
+    """31 barrel layers (lmax = KF_MAX_LMAX, the longest trace and hit list) with K = KF_MAX_K;
+    one more layer is rejected."""
+    import dataclasses
+    wl = dataclasses.replace(synth.workload("find", n_events=1, tracks_lo=400, tracks_hi=400),
+                             surfaces=tuple(synth.barrel_layers(31, dr=2.2)), k_max=kf.KF_MAX_K, noise_frac=0.3)
+    assert wl.lmax == kf.KF_MAX_LMAX
+    b = synth.generate(wl)
+    gpu, ora, st = _find_both(kf, wl, b, k_max=kf.KF_MAX_K)
+    _assert_find_parity(b, gpu, ora, st)
+    assert gpu["nhits"].max() == kf.KF_MAX_LMAX
+    gpu_f, ora_f = _fit_both(kf, wl, b)
+    _assert_fit_parity(gpu_f, ora_f)
+    big = dataclasses.replace(wl, surfaces=tuple(synth.barrel_layers(32, dr=2.1)))
+    prm = kf.find_params(big.chi2_cut, big.k_max, big.max_miss, big.lmax)
+    assert kf.find_workspace_size(10, prm) == 0
+    bb = synth.generate(big)
+    g2 = kf.Geometry(big)
+    d2 = kf.to_device_event_batch(bb)
+    idx2 = kf.build_hit_index(g2, d2["hits"], d2["slab_offsets"], bb.n_events, d2["max_slab_hits"])
+    with pytest.raises(kf.KfError):
+        kf.find_tracks(g2, idx2, d2["hits"], d2["hit_surface"], d2["seed_hits"], d2["seed_event"], prm)
+
+
 def test_find_parity_dense_noise(kf):
     """Many branches per seed: 5 noise hits per signal hit."""
     wl = synth.workload("find", n_events=1, tracks_lo=1200, tracks_hi=1200, noise_frac=5.0)
