@@ -6,9 +6,13 @@ correct: full 6x6 FP64 matrices, textbook helix/Kalman formulas (the paper, Sec.
 traditional Kalman filter and prints no formulas), an FP32 hit-binning rule evaluated with every
 operation rounded separately, and a beam search that keeps the best K candidates per seed.
 
+Also: region steering, the r-z material map with energy loss, the parametrised field, seed
+cleaning and duplicate removal, and the learned proposal's network, as the paper's options.
+
 Parity unpinned: the prior widths, the candidate ranking key, the barrel half-lengths and disk
-extents, and the efficiency definition are readings chosen where the paper is silent; they are
-fixed here, not checked against numbers the paper prints (it prints none).
+extents, the efficiency definition, the cleaning and removal cuts and the synthetic material and
+field values are readings chosen where the paper is silent; they are fixed here, not checked
+against numbers the paper prints (it prints none).
 """
 from __future__ import annotations
 

@@ -15,12 +15,17 @@
 //   * Jacobian of the fixed-s map, projected onto the surface (I - t g^T / g^T t);
 //   * covariance transport C' = J C J^T + Q, Q from the Highland formula (PDG, beta = 1);
 //   * extended Kalman update with 2D hits (barrel: r*phi and z; disk: r*phi and r);
-//   * hit binning with the FP32 rounding rule below; beam search keeping K candidates.
+//   * hit binning with the FP32 rounding rule below; beam search keeping K candidates;
+//   * the options the paper describes (Sec. 3.1, Sec. 3.2): region steering lists, an r-z material
+//     map with mean energy loss, a parametrised solenoid field (one helix per step in the field at
+//     the chord's midpoint), seed cleaning and duplicate-track removal by hit identity and
+//     direction; and the learned hit proposal's network (forward and backward, FP64).
 // Full 6x6 matrices in FP64; nothing is blocked, fused or reordered.
 //
 // Parity unpinned (the paper prints no numbers): the prior widths, the candidate ranking key,
-// the barrel half-lengths and disk extents, and the efficiency definition are readings of the
-// text, not values it gives.
+// the barrel half-lengths and disk extents, the efficiency definition, the cleaning and removal
+// cuts, and the synthetic material map and field coefficients are readings of the text, not values
+// it gives.
 
 #include <algorithm>
 #include <atomic>
