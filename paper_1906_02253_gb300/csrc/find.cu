@@ -943,8 +943,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   }
 }
 
-// Compile-time choice of capacity and mode, dispatched from the runtime plan. The learned
-// proposal always runs the general kernel.
+// Compile-time choice of capacity, mode (plain or learned proposal) and instance (plain or
+// general), dispatched from the runtime plan.
 template <int KC, bool L, bool GEN>
 struct FindKernel {
   static constexpr int kc = KC;
@@ -954,7 +954,7 @@ struct FindKernel {
 
 template <int KC, class F>
 static int dispatch_mode(bool learned, bool general, F&& f) {
-  if (learned) return f(FindKernel<KC, true, true>{});
+  if (learned) return general ? f(FindKernel<KC, true, true>{}) : f(FindKernel<KC, true, false>{});
   return general ? f(FindKernel<KC, false, true>{}) : f(FindKernel<KC, false, false>{});
 }
 
@@ -1010,7 +1010,6 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPla
   if (kc < 0) return KF_ERR_ARG;
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
-  general = general || learned;
   static int occ_cache[16][6][2][2][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;

@@ -48,7 +48,7 @@ struct FindPlan {
 };
 
 // general: the geometry or the parameters use region steering, the material map, energy loss or
-// the parametrised field (the learned proposal always plans the general kernel).
+// the parametrised field.
 int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPlan* plan);
 inline bool needs_general(const DevGeom& G, const DevMat& M) {
   return G.steer != 0 || M.map_on != 0 || M.eloss > 0.f || G.field_on != 0;
