@@ -274,7 +274,7 @@ int kf_fit_tracks(const KfGeometry* geom, const float* hits, const int* hit_surf
 
 size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params) {
   FindPlan plan;
-  if (plan_find(n_seeds, params, sm_count(), true, &plan) != KF_OK) return 0;
+  if (plan_find(n_seeds, params, sm_count(), 7, &plan) != KF_OK) return 0;
   return plan.ws_bytes;
 }
 
@@ -292,7 +292,7 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   rc = pack_material(geom, &M);
   if (rc != KF_OK) return rc;
   FindPlan plan;
-  rc = plan_find(n_seeds, params, sm_count(), needs_general(G, M), &plan);
+  rc = plan_find(n_seeds, params, sm_count(), find_features(G, M), &plan);
   if (rc != KF_OK) return rc;
   if (n_seeds == 0) return KF_OK;
   if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
@@ -363,7 +363,7 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   if (rc != KF_OK) return rc;
   if (n_seeds > KF_STATIC_MAX_SEEDS) return KF_ERR_CAPACITY;
   FindPlan plan;
-  rc = plan_find(n_seeds, params, sm_count(), needs_general(G, M), &plan);
+  rc = plan_find(n_seeds, params, sm_count(), find_features(G, M), &plan);
   if (rc != KF_OK) return rc;
   if (plan.ws_bytes > KF_STATIC_SCRATCH_BYTES) return KF_ERR_CAPACITY;
   if (n_seeds == 0) return KF_OK;

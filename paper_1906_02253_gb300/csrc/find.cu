@@ -326,13 +326,13 @@ __device__ __forceinline__ int seed_region(const DevGeom& G, int s3, float2 h) {
 // each "next" is a lower bound, searched from the candidate's current surface `cur`. The barrel
 // candidate of the geometric rule is tried in straight-line code; disks and steering lists go
 // through one loop (a single further copy of the path solvers in the code).
-// GEN = false: the geometric rule in a uniform field only.
-template <bool GEN>
+// STEER = false: the geometric rule only; FLD = false: the uniform field only.
+template <bool STEER, bool FLD>
 __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, int cur, int region, int pos, float st,
                                             float ct, Prop& best, int& newpos) {
-  const float w = -kCurvF * (GEN ? start_field(G, p) : G.bz) * p[3];
+  const float w = -kCurvF * (FLD ? start_field(G, p) : G.bz) * p[3];
   const float cot = ct / st;
-  const bool steer = GEN && G.steer != 0;
+  const bool steer = STEER && G.steer != 0;
   int sb = -1, sd = -1;  // geometric candidates: next barrel layer, next disk
   if (!steer) {
     const float rho = sqrtf(p[0] * p[0] + p[1] * p[1]);
@@ -366,7 +366,7 @@ __device__ __forceinline__ int next_surface(const DevGeom& G, const float* p, in
       }
     }
     if (sd < 0) return sel;
-    if (!GEN) {  // the disk candidate of the geometric rule
+    if (!STEER) {  // the disk candidate of the geometric rule
       Prop pr;
       if (reach_disk(G, p, w, sd, st, ct, cot, pr) && (sel < 0 || pr.s < best.s)) {
         sel = sd;
@@ -503,10 +503,12 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
          (static_cast<unsigned long long>(pk) << 20);
 }
 
-// GEN: the general kernel (region steering, material map and energy loss, parametrised field);
-// without it the geometric next-surface rule, the surfaces' x/X0 and the uniform field are
-// compiled in alone.
-template <int KC, bool LEARNED, bool GEN>
+// Options compiled into an instance (FEAT bits): region steering, material map and energy loss,
+// parametrised field. Without them the geometric next-surface rule, the surfaces' x/X0 and the
+// uniform field are compiled in alone; each option left out keeps its code out of the kernel.
+constexpr int kFeatSteer = 1, kFeatMaterial = 2, kFeatField = 4, kFeatAll = 7;
+
+template <int KC, bool LEARNED, int FEAT>
 __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp,
                                                         const __grid_constant__ DevMat M, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -519,6 +521,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     __syncthreads();
   }
   const DevGeom& G = *reinterpret_cast<const DevGeom*>(smem);
+  constexpr bool STEER = (FEAT & kFeatSteer) != 0, MAT = (FEAT & kFeatMaterial) != 0, FLD = (FEAT & kFeatField) != 0;
   constexpr int NS = 32 / KC;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -578,15 +581,15 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       // Candidate surface word: (position in the region's list + 1) << 8 | surface.
       const int s3 = A.seed_surf[seed];
       int pos = -1;
-      if (GEN && G.steer && s3 >= 0 && s3 < G.n_surf) {
+      if (STEER && G.steer && s3 >= 0 && s3 < G.n_surf) {
         region = seed_region(G, s3, A.hits[A.seed_hits[static_cast<size_t>(2) * n + seed]]);
         pos = G.steer_pos[region][s3];
       }
-      valid = load_seed(W, lane, A.seed_state + seed, GEN ? ((pos + 1) << 8) | (s3 & 255) : s3, n);
+      valid = load_seed(W, lane, A.seed_state + seed, STEER ? ((pos + 1) << 8) | (s3 & 255) : s3, n);
       failed = !valid;  // a failed seed's outputs were written by the seed-state kernel
     }
     failed = __shfl_sync(kFull, failed, gbase);
-    if (GEN) region = __shfl_sync(kFull, region, gbase);
+    if (STEER) region = __shfl_sync(kFull, region, gbase);
     if (fresh && failed) {
       seed = -1;
       valid = false;
@@ -608,11 +611,11 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
         Prop pr;
         float st, ct;
         sincos_small(c.p[5], st, ct);
-        si = next_surface<GEN>(G, c.p, GEN ? c.surf & 255 : c.surf, region, GEN ? (c.surf >> 8) - 1 : -1, st, ct, pr,
-                               newpos);
+        si = next_surface<STEER, FLD>(G, c.p, STEER ? c.surf & 255 : c.surf, region, STEER ? (c.surf >> 8) - 1 : -1,
+                                      st, ct, pr, newpos);
         float bz = G.bz;
-        if (si >= 0 && (!GEN || step_field(G, si, c.p, st, ct, pr, bz)) &&
-            apply_propagation<GEN>(G, M, si, c.p, c.C, pr, st, ct, bz)) {
+        if (si >= 0 && (!FLD || step_field(G, si, c.p, st, ct, pr, bz)) &&
+            apply_propagation<MAT>(G, M, si, c.p, c.C, pr, st, ct, bz)) {
           kind = 1;
           Meas m;
           float rho;
@@ -843,7 +846,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
     if (kind == 1) {
       kind = hl_n > 0 ? 0 : (c.nm < A.max_miss ? 1 : 2);
       if (kind != 2) {
-        c.surf = GEN ? ((newpos + 1) << 8) | si : si;
+        c.surf = STEER ? ((newpos + 1) << 8) | si : si;
         store_cand(W, lane, c);
       }
     }
@@ -911,7 +914,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       load_cand(W, gbase + w_par, nc);
       if (w_kind == 0) {
         const float4 h = __ldg(A.sorted_rec + w_pos);
-        update_with(G, GEN ? nc.surf & 255 : nc.surf, nc, h);
+        update_with(G, STEER ? nc.surf & 255 : nc.surf, nc, h);
         nc.chi2 = w_c2;
         nc.nh = w_nh;
       } else if (w_kind == 1) {
@@ -943,48 +946,56 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   }
 }
 
-// Compile-time choice of capacity, mode (plain or learned proposal) and instance (plain or
-// general), dispatched from the runtime plan.
-template <int KC, bool L, bool GEN>
+// Compile-time choice of capacity, mode (plain or learned proposal) and instance (plain, steering
+// only, every option), dispatched from the runtime plan.
+template <int KC, bool L, int FEAT>
 struct FindKernel {
   static constexpr int kc = KC;
   static constexpr bool learned = L;
-  static constexpr bool general = GEN;
+  static constexpr int feat = FEAT;
 };
 
+// The compiled instance that covers the options in use.
+static int compiled_features(bool learned, int feat) {
+  if (feat == 0) return 0;
+  return (!learned && feat == kFeatSteer) ? kFeatSteer : kFeatAll;
+}
+
 template <int KC, class F>
-static int dispatch_mode(bool learned, bool general, F&& f) {
-  if (learned) return general ? f(FindKernel<KC, true, true>{}) : f(FindKernel<KC, true, false>{});
-  return general ? f(FindKernel<KC, false, true>{}) : f(FindKernel<KC, false, false>{});
+static int dispatch_mode(bool learned, int feat, F&& f) {
+  if (learned) return feat == 0 ? f(FindKernel<KC, true, 0>{}) : f(FindKernel<KC, true, kFeatAll>{});
+  if (feat == 0) return f(FindKernel<KC, false, 0>{});
+  if (feat == kFeatSteer) return f(FindKernel<KC, false, kFeatSteer>{});
+  return f(FindKernel<KC, false, kFeatAll>{});
 }
 
 template <class F>
-static int dispatch_find(int kc, bool learned, bool general, F&& f) {
+static int dispatch_find(int kc, bool learned, int feat, F&& f) {
   switch (kc) {
-    case 1: return dispatch_mode<1>(learned, general, f);
-    case 2: return dispatch_mode<2>(learned, general, f);
-    case 4: return dispatch_mode<4>(learned, general, f);
-    case 6: return dispatch_mode<6>(learned, general, f);
-    case 8: return dispatch_mode<8>(learned, general, f);
-    case 16: return dispatch_mode<16>(learned, general, f);
+    case 1: return dispatch_mode<1>(learned, feat, f);
+    case 2: return dispatch_mode<2>(learned, feat, f);
+    case 4: return dispatch_mode<4>(learned, feat, f);
+    case 6: return dispatch_mode<6>(learned, feat, f);
+    case 8: return dispatch_mode<8>(learned, feat, f);
+    case 16: return dispatch_mode<16>(learned, feat, f);
     default: return KF_ERR_ARG;
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 
-template <int KC, bool L, bool GEN>
+template <int KC, bool L, int FEAT>
 static int kc_occupancy(int block, size_t smem, int* bps) {
   static int attr_set[16] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_CUDA;
   if (static_cast<int>(smem) > attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_find_tracks<KC, L, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_find_tracks<KC, L, FEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
       return KF_ERR_CUDA;
     attr_set[dev] = static_cast<int>(smem);
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC, L, GEN>, block, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_find_tracks<KC, L, FEAT>, block, smem) != cudaSuccess)
     return KF_ERR_CUDA;
   return KF_OK;
 }
@@ -996,7 +1007,7 @@ static int pick_kc(int need) {
   return -1;
 }
 
-int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPlan* plan) {
+int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPlan* plan) {
   if (!p || n_seeds < 0 || sms <= 0) return KF_ERR_ARG;
   if (p->k_max < 1 || p->k_max > KF_MAX_K || p->max_miss < 0 || p->lmax < 4 || p->lmax > KF_MAX_LMAX) return KF_ERR_ARG;
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
@@ -1010,24 +1021,26 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPla
   if (kc < 0) return KF_ERR_ARG;
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
-  static int occ_cache[16][6][2][2][8][32] = {};
+  const int feat = compiled_features(learned, features);
+  const int fi = feat == 0 ? 0 : feat == kFeatSteer ? 1 : 2;
+  static int occ_cache[16][6][2][3][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
   const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
   auto occupancy = [&](int blk, size_t* smem_out, int* occ_out) {
     size_t sm = 0;
-    dispatch_find(kc, learned, general, [&](auto k) {
+    dispatch_find(kc, learned, feat, [&](auto k) {
       sm = kGeomBytes + warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
       return KF_OK;
     });
     *smem_out = sm;
     *occ_out = 0;
     if (sm > 227 * 1024) return KF_OK;
-    int& cached = occ_cache[dev][ki][learned][general][blk / 32 - 1][p->lmax];
+    int& cached = occ_cache[dev][ki][learned][fi][blk / 32 - 1][p->lmax];
     if (cached == 0) {
       int o = 0;
-      const int rc = dispatch_find(kc, learned, general, [&](auto k) {
-        return kc_occupancy<decltype(k)::kc, decltype(k)::learned, decltype(k)::general>(blk, sm, &o);
+      const int rc = dispatch_find(kc, learned, feat, [&](auto k) {
+        return kc_occupancy<decltype(k)::kc, decltype(k)::learned, decltype(k)::feat>(blk, sm, &o);
       });
       if (rc != KF_OK) return rc;
       cached = o > 0 ? o : -1;
@@ -1065,7 +1078,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPla
   const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
   plan->kc = kc;
   plan->learned = learned;
-  plan->general = general;
+  plan->feat = feat;
   plan->block = block;
   plan->grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
   plan->smem = smem;
@@ -1119,8 +1132,8 @@ int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& 
   }
   if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
   k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, M, A);
-  dispatch_find(plan.kc, plan.learned, plan.general, [&](auto k) {
-    k_find_tracks<decltype(k)::kc, decltype(k)::learned, decltype(k)::general>
+  dispatch_find(plan.kc, plan.learned, plan.feat, [&](auto k) {
+    k_find_tracks<decltype(k)::kc, decltype(k)::learned, decltype(k)::feat>
         <<<plan.grid, plan.block, plan.smem, stream>>>(G, M, A);
     return KF_OK;
   });

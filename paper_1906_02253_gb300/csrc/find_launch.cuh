@@ -42,16 +42,17 @@ struct FindArgs {
 // workspace layout.
 struct FindPlan {
   int kc, block, grid;
-  bool learned, general;  // general: the kernel with region steering, material map and field
+  bool learned;
+  int feat;  // options compiled into the instance: 1 steering, 2 material map and energy loss, 4 field
   size_t smem;
   size_t off_state, off_surf, off_mlp, ws_bytes;
 };
 
 // general: the geometry or the parameters use region steering, the material map, energy loss or
 // the parametrised field.
-int plan_find(int n_seeds, const KfFindParams* p, int sms, bool general, FindPlan* plan);
-inline bool needs_general(const DevGeom& G, const DevMat& M) {
-  return G.steer != 0 || M.map_on != 0 || M.eloss > 0.f || G.field_on != 0;
+int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPlan* plan);
+inline int find_features(const DevGeom& G, const DevMat& M) {
+  return (G.steer != 0 ? 1 : 0) | ((M.map_on != 0 || M.eloss > 0.f) ? 2 : 0) | (G.field_on != 0 ? 4 : 0);
 }
 int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream);
 // Device address of the library's fixed finder scratch on the current device (looked up on the
