@@ -7,6 +7,15 @@ batched uneven-event configuration: 100 events with 2,000-20,000 tracks each (ab
 17 barrel layers at r = 4..68 cm with 0.02 X0 each, 3.8 T, pT 0.5-10 GeV, |eta| < 1, hit
 resolution 0.01 cm (r phi) and 0.1 cm (z); finding with chi2 < 30, K = 6, one miss allowed.
 The metric is seeds per second through the step (every seed is found and its track fitted).
+Other workloads (--workload): hi_occ (barrel + disks, noise 100%, K = 8; --steering for the
+region steering lists), material (r-z material map and energy loss), field (parametrised field),
+duplicates (module overlaps and combinatorial seeds; the step adds seed cleaning before finding
+and duplicate-track removal after it).
+
+Besides the device-timed step the line carries the end-to-end figure (host copies in and out,
+pipelined on their own streams), the roofline of every step kernel (the finder's DRAM traffic from
+the committed ncu capture while its sources and flags match), the clocks seen during the timed
+region, and the learned proposal against plain finding.
 
 The FP64 oracle runs only in the CPU baseline leg (and as the whole reference arm, --impl
 reference), on a bounded sample of the same workload, on the host cores.
