@@ -41,7 +41,9 @@ def _worker(rank, world, port, results):
         seed = shard.rank_seed(wl.seed, rank)
         b = synth.generate(wl, seed=seed)
         step_ms = 10.0 + 5.0 * rank  # stand-in for a measured step time
-        results[rank] = (seed, float(b.hits[:, 0].sum()), shard.max_over_ranks(step_ms))
+        n_seeds = len(b.seeds()[1])
+        results[rank] = (seed, float(b.hits[:, 0].sum()), shard.max_over_ranks(step_ms), n_seeds,
+                         shard.sum_over_ranks(n_seeds))
     finally:
         dist.destroy_process_group()
 
@@ -56,3 +58,4 @@ def test_weak_scaling_ranks_and_max_time():
     assert r0[0] != r1[0]            # different generator seeds: different events per rank
     assert r0[1] != r1[1]
     assert r0[2] == r1[2] == 15.0    # both ranks report the slowest rank's time
+    assert r0[4] == r1[4] == r0[3] + r1[3]  # the job's seeds: every rank's own count
