@@ -77,11 +77,11 @@ def test_gpu_training_lowers_the_loss(kf, pairs):
     assert hist[-1] < 0.8 * first, (first, hist)
 
 
-def _find(kf, wl, b, buf, top_n, k):
+def _find(kf, wl, b, buf, top_n, k, steering=None):
     g = kf.Geometry(wl)
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
-    prm = kf.find_params(wl.chi2_cut, k, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n)
+    prm = kf.find_params(wl.chi2_cut, k, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, steering_tables=steering)
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
     torch.cuda.synchronize()
     return {kk: v.cpu().numpy() for kk, v in out.items() if kk != "workspace"}
@@ -115,3 +115,27 @@ def test_learned_with_large_top_n_equals_plain_on_gpu(kf, pairs):
     # coordinate differently in its last bit; a residual of ~0.01 cm against a ~50 cm coordinate
     # turns that into up to ~1e-3 relative in chi2, the parity bar against the oracle.
     assert np.allclose(learned["chi2"], plain["chi2"], rtol=1e-3, atol=1e-3, equal_nan=True)
+
+
+def test_learned_finding_with_region_steering_and_material_matches_oracle(kf, pairs):
+    """The learned proposal in the finder instance with every option: region steering and the
+    material map with energy loss on the barrel + disk geometry."""
+    import dataclasses
+    _, _, mean, sd = pairs
+    w = synth.mlp_init(11)
+    base = synth.workload("hi_occ", n_events=2, tracks_lo=800, tracks_hi=1500)
+    wl = dataclasses.replace(base, material=synth.material_map(base.surfaces), eloss=0.0363)
+    b = synth.generate(wl)
+    tab = synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3)
+    # top_n = 4 here: with top_n = 2 on this dense geometry the FP32 network scores and the
+    # oracle's FP64 ones order a near-tie differently on 0.04-0.10% of the seeds (measured), at the
+    # edge of the 99.9% bar; the learned-finding parity cases above use top_n = 1 and 2.
+    gpu = _find(kf, wl, b, kf.mlp_buffer(w, mean, sd), 4, 8, steering=tab)
+    sh, st = b.seeds()
+    ora = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], k_max=8, steering=tab,
+                      mlp=(w.astype(np.float64), mean.astype(np.float64), sd.astype(np.float64)), top_n=4)
+    same = (gpu["hits"].T == ora["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    assert np.array_equal(gpu["status"], ora["status"])
+    plain = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], k_max=8, steering=tab)
+    assert (plain["hits"] != ora["hits"]).any(axis=1).sum() > 0  # the pruning acted
