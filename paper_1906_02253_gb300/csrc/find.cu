@@ -946,8 +946,8 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
   }
 }
 
-// Compile-time choice of capacity, mode (plain or learned proposal) and instance (plain, steering
-// only, every option), dispatched from the runtime plan.
+// Compile-time choice of capacity, mode (plain or learned proposal) and instance (plain, one
+// option alone, every option), dispatched from the runtime plan.
 template <int KC, bool L, int FEAT>
 struct FindKernel {
   static constexpr int kc = KC;
@@ -958,7 +958,8 @@ struct FindKernel {
 // The compiled instance that covers the options in use.
 static int compiled_features(bool learned, int feat) {
   if (feat == 0) return 0;
-  return (!learned && feat == kFeatSteer) ? kFeatSteer : kFeatAll;
+  if (learned) return kFeatAll;
+  return (feat == kFeatSteer || feat == kFeatMaterial || feat == kFeatField) ? feat : kFeatAll;
 }
 
 template <int KC, class F>
@@ -966,6 +967,8 @@ static int dispatch_mode(bool learned, int feat, F&& f) {
   if (learned) return feat == 0 ? f(FindKernel<KC, true, 0>{}) : f(FindKernel<KC, true, kFeatAll>{});
   if (feat == 0) return f(FindKernel<KC, false, 0>{});
   if (feat == kFeatSteer) return f(FindKernel<KC, false, kFeatSteer>{});
+  if (feat == kFeatMaterial) return f(FindKernel<KC, false, kFeatMaterial>{});
+  if (feat == kFeatField) return f(FindKernel<KC, false, kFeatField>{});
   return f(FindKernel<KC, false, kFeatAll>{});
 }
 
@@ -1022,8 +1025,8 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
   const int feat = compiled_features(learned, features);
-  const int fi = feat == 0 ? 0 : feat == kFeatSteer ? 1 : 2;
-  static int occ_cache[16][6][2][3][8][32] = {};
+  const int fi = feat == 0 ? 0 : feat == kFeatSteer ? 1 : feat == kFeatMaterial ? 2 : feat == kFeatField ? 3 : 4;
+  static int occ_cache[16][6][2][5][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
   const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
