@@ -2,8 +2,11 @@
 
 The propagator is checked against things other than itself: the generator's independent
 root-finding crossing solver (a different helix parametrisation), central finite differences
-for the Jacobian, the straight-line limit and geometric invariants of the helix.
+for the Jacobian, the straight-line limit, geometric invariants of the helix, and a hand-worked
+Highland value with the deflection geometry for the scattering noise.
 """
+from dataclasses import replace
+
 import numpy as np
 import pytest
 
@@ -173,3 +176,68 @@ def test_next_surface_rule_follows_generator_paths():
             assert nxt == want, (t, k, nxt, want)
             n_checked += 1
     assert n_checked > 5000
+
+
+def _scatter_cov(x_over_x0, p0, surf, wl_name="hi_occ"):
+    """Covariance after propagating a zero covariance to ``surf`` in a near-zero field (straight
+    tracks from the origin), with every surface's x/X0 set to ``x_over_x0``: the scattering noise."""
+    base = synth.workload(wl_name)
+    surfs = [replace(s, x_over_x0=float(x_over_x0)) for s in base.surfaces]
+    wl = synth.workload(wl_name, bz=1e-6, ms_on=True, surfaces=surfs)
+    r = oracle.propagate(oracle.Geometry(wl), p0, None, surf)
+    assert r is not None
+    return r[1]
+
+
+def _kick_jacobian(kap, phi, th):
+    """d(kappa, phi, theta) / d(deflection) for the two deflections perpendicular to the
+    direction (in the theta plane and across it), by central differences of a rotated direction
+    at fixed |p| and charge; kappa = q / (p sin theta)."""
+    q_over_p = kap * np.sin(th)
+    u = np.array([np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)])
+    e1 = np.array([np.cos(th) * np.cos(phi), np.cos(th) * np.sin(phi), -np.sin(th)])
+    e2 = np.array([-np.sin(phi), np.cos(phi), 0.0])
+    G = np.zeros((3, 2))
+    eps = 1e-6
+    for j, e in enumerate((e1, e2)):
+        cols = []
+        for sgn in (1.0, -1.0):
+            v = u + sgn * eps * e
+            v /= np.linalg.norm(v)
+            t = np.arccos(v[2])
+            cols.append(np.array([q_over_p / np.sin(t), np.arctan2(v[1], v[0]), t]))
+        d = cols[0] - cols[1]
+        d[1] = _wrap(d[1])
+        G[:, j] = d / (2 * eps)
+    return G
+
+
+def test_multiple_scattering_noise_follows_highland_and_the_deflection_geometry():
+    """Sec. 3.1 multiple scattering (Highland formula, beta = 1, PDG): a 1 GeV track crossing
+    2% X0 at normal incidence gets theta0 = 1.6374e-3 rad (worked out by hand: 13.6 MeV / 1 GeV x
+    sqrt(0.02) x (1 + 0.038 ln 0.02)); theta0^2 scales as 1/p^2; an oblique crossing equals a
+    normal one through x/X0 divided by |cos a| (the path in the layer), on barrels and disks; and
+    the noise on (kappa, phi, theta) is theta0^2 G G^T with G the deflection Jacobian taken from a
+    rotated direction vector."""
+    x0 = np.float32(0.02)
+    p_norm = np.array([0.0, 0.0, 0.0, 1.0, 0.3, np.pi / 2])  # kappa = 1 / (p sin theta): p = 1 GeV
+    C = _scatter_cov(x0, p_norm, 4)
+    theta0 = 1.6374e-3
+    assert abs(np.sqrt(C[5, 5]) / theta0 - 1) < 1e-4
+    assert abs(C[4, 4] / C[5, 5] - 1) < 1e-9
+    assert abs(C[3, 3]) < 1e-15 and abs(C[3, 5]) < 1e-15
+    assert np.abs(C[:3, :]).max() == 0.0
+
+    p_two = p_norm.copy()
+    p_two[3] = 0.5  # p = 2 GeV
+    assert abs(_scatter_cov(x0, p_two, 4)[5, 5] * 4 / C[5, 5] - 1) < 1e-9
+
+    for th, surf, cos_a in ((1.0, 4, np.sin(1.0)), (0.3, 17, np.cos(0.3)), (2.7, 26, np.cos(2.7))):
+        kap = -1.0 / np.sin(th)  # p = 1 GeV, negative charge
+        p_obl = np.array([0.0, 0.0, 0.0, kap, -2.0, th])
+        C_obl = _scatter_cov(x0, p_obl, surf)
+        v_ref = _scatter_cov(np.float32(x0 / abs(cos_a)), p_norm, 4)[5, 5]
+        assert abs(C_obl[5, 5] / v_ref - 1) < 1e-6, (th, surf)
+        G = _kick_jacobian(kap, -2.0, th)
+        Q = C_obl[3:, 3:]
+        assert np.abs(Q - C_obl[5, 5] * G @ G.T).max() < 1e-8 * np.abs(Q).max()
