@@ -55,7 +55,7 @@ FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20
 # over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "f6fa99f7def3e663cafaf83d7c308012dbdc5c5d", "dram_bytes_per_seed": 160092160 / 302063}
+FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "82e9fa34012c627d5b99d4e209ef75dc2e5a8e9c", "dram_bytes_per_seed": 160092160 / 302063}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36

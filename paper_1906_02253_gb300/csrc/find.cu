@@ -62,6 +62,9 @@ struct WarpSmem {
   } u;
 };
 
+// Learned proposal: the floor of its log-variance features, log(1e-12).
+constexpr float kLogFloor = -27.631021f;
+
 // Learned proposal, per warp: the network score of each kept hit.
 template <int KC>
 struct WarpLearned {
@@ -696,6 +699,14 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
           for (int i = 0; i < 6; ++i) fe[i] = c.p[i];
 #pragma unroll
           for (int i = 0; i < 6; ++i) fe[6 + i] = logf(c.C[ci(i, i)] + 1e-12f);
+          // On a disk z is fixed by the surface: after the projection onto it the z variance is
+          // exactly zero, and in FP32 what is left is rounding residue of the projected terms
+          // (up to ~1e-7 cm^2, far above the 1e-12 floor), so the feature takes the exact value.
+          // On a barrel the x or y variance nears zero for crossings close to an axis, where the
+          // residue may be negative: the floor also stands in for a NaN there (fmaxf drops it).
+          if (si >= 0 && G.type[si] != 0) fe[8] = kLogFloor;
+          fe[6] = fmaxf(fe[6], kLogFloor);
+          fe[7] = fmaxf(fe[7], kLogFloor);
           fe[12] = sqrtf(s00v);
           fe[13] = sqrtf(s11v);
           // The pairs of those owners in buffer order (owner by owner), each scored by the whole

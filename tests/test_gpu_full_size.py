@@ -116,3 +116,41 @@ def test_full_size_seed_cleaning_and_duplicate_removal_chain():
     e_g, d_g = oracle.track_rates(b, st, np.ones(len(st), bool), gkd, track_sim=oracle.majority_sim(b, g_hits, g_nh))
     e_o, d_o = oracle.track_rates(b, st, np.ones(len(st), bool), okd, track_sim=oracle.majority_sim(b, o_hits, o_nh))
     assert abs(e_g - e_o) <= 0.001 and abs(d_g - d_o) <= 0.001
+
+
+@pytest.mark.parametrize("wl_name,net,top_n", [("learned", "mlp_learned.npz", 1), ("learned", "mlp_learned.npz", 4),
+                                               ("hi_occ", "mlp_hi_occ.npz", 2), ("hi_occ", "mlp_hi_occ.npz", 4)])
+def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n):
+    """The learned proposal at full size, in the autotuned launch configuration the benchmark's
+    learned-versus-plain comparison uses: hit lists identical to the FP64 oracle's (same network,
+    same top_n) on >= 99.9% of a 20,000-seed sample, efficiency within 0.1%."""
+    import os
+    import __graft_entry__ as ge
+    ge.build_library()
+    import paper_1906_02253_gb300 as kf
+    wl = synth.workload(wl_name)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
+    prm, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"][:, :n_cal].contiguous(),
+                              dev["seed_event"][:n_cal].contiguous(), prm)
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+    buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"])
+    lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
+                        mlp=buf, top_n=top_n)
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], lp)
+    torch.cuda.synchronize()
+    n = dev["seed_hits"].shape[1]
+    s = np.sort(np.random.default_rng(2253).choice(n, N_SAMPLE, replace=False))
+    sh, st = b.seeds()
+    w = (z["weights"].astype(np.float64), z["mean"].astype(np.float64), z["sd"].astype(np.float64))
+    r = oracle.find(oracle.Geometry(wl), b, sh[s], b.track_event[st][s], mlp=w, top_n=top_n)
+    gh = out["hits"].cpu().numpy().T[s]
+    same = (gh == r["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    e_g = oracle.efficiency(b, st[s], gh, out["nhits"].cpu().numpy()[s])[0]
+    e_o = oracle.efficiency(b, st[s], r["hits"], r["n_hits"])[0]
+    assert abs(e_g - e_o) <= 0.001
