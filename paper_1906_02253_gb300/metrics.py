@@ -1,9 +1,9 @@
 """Track-finding efficiency and fake rate (host-side validation of found tracks).
 
-Adapted from the paper's standalone validation (Sec. 4): reference tracks are simulated tracks
-with at least 10 hits; a seed's found track is matched to the seed's simulated track when it has
-at least min(10, crossings - 1) hits and at least 50% of its hits beyond the three seed hits
-belong to that track (the paper's seeds have 4 hits; ours have 3).
+Follows the standalone validation of Sec. 4, adapted to these events: the denominator holds the
+simulated tracks that leave 10 or more hits; the track found from a seed counts for the seed's
+simulated track when it carries min(10, crossings - 1) hits or more and half or more of its
+non-seed hits come from that track (seeds here have 3 hits, the paper's 4).
 """
 from __future__ import annotations
 
