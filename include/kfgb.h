@@ -261,8 +261,11 @@ int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* c
 
 /* Learned hit proposal network (not in the paper): MLP 14 -> 64 -> 64 -> 1 with ReLU, scoring a
  * (predicted candidate, hit) pair from 14 features: the predicted state (x, y, z, kappa, phi,
- * theta), log(C_ii + 1e-12) of the six covariance diagonal terms, and the two residuals divided by
- * the square roots of the innovation variances. Parameter buffer, FP32, KF_MLP_BUFFER floats:
+ * theta), log(C_ii + 1e-12) of the six covariance diagonal terms (exact value on a disk, where the
+ * z variance is zero after the projection onto the surface, so log(1e-12) whatever the rounding
+ * residue; x and y floored at log(1e-12), as their rounding residue near an axis can be
+ * negative), and the two residuals divided by the square roots of the
+ * innovation variances. Parameter buffer, FP32, KF_MLP_BUFFER floats:
  * W1[64][14], b1[64], W2[64][64], b2[64], W3[64], b3 (KF_MLP_PARAMS weights), then the feature
  * normaliser mean[14], sd[14] (x -> (x - mean) / sd before the first layer). All pointers are
  * device memory. */
