@@ -1,6 +1,7 @@
 """Pins of the oracle's learned hit proposal (CPU only): backpropagation against central finite
-differences, training that lowers the loss, and the pruning wired into the beam search checked
-against a plain loop over the oracle's single-step primitives."""
+differences, training that lowers the loss, the pruning wired into the beam search checked
+against a plain loop over the oracle's single-step primitives, and the disk value of the z-variance
+feature."""
 import numpy as np
 import pytest
 
@@ -117,3 +118,33 @@ def test_learned_top1_matches_a_plain_loop():
                 break
         assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
     assert pruned > 10
+
+
+def test_disk_z_variance_feature_is_the_floor():
+    """On a disk the state's z is fixed by the surface, so after propagation the z variance is
+    zero (the covariance is projected onto the surface) and the log-variance feature equals its
+    floor log(1e-12) to FP64 rounding; on a barrel it is a real variance, far above the floor."""
+    wl = synth.workload("hi_occ")
+    g = oracle.Geometry(wl)
+    rng = np.random.default_rng(17)
+    C0 = np.diag([1e-4, 1e-4, 1e-2, 1e-4, 1e-4, 1e-4])
+    n_disk = n_barrel = 0
+    for _ in range(200):
+        th = rng.choice([rng.uniform(0.15, 0.5), rng.uniform(2.64, 2.99), rng.uniform(1.2, 1.9)])
+        p0 = np.array([0.0, 0.0, 0.0, rng.choice([-1, 1]) * rng.uniform(0.1, 1.0), rng.uniform(-np.pi, np.pi), th])
+        surf = (17 if th < 1.0 else 26) if abs(np.cos(th)) > 0.8 else 4
+        r = oracle.propagate(g, p0, C0, surf)
+        if r is None:
+            continue
+        p, C = r[0], r[1]
+        hit = (np.arctan2(p[1], p[0]) + 1e-3, (np.hypot(p[0], p[1]) if surf != 4 else p[2]) + 0.05)
+        f = oracle.pair_features(g, surf, p, C, hit)
+        if surf == 4:
+            n_barrel += 1
+            assert f[8] > np.log(1e-12) + 10
+        else:
+            n_disk += 1
+            assert abs(C[2, 2]) < 1e-15
+            assert abs(f[8] - np.log(1e-12)) < 1e-3
+        assert np.allclose(f[:6], p) and np.allclose(f[6:12], np.log(np.diag(C) + 1e-12))
+    assert n_disk > 50 and n_barrel > 20
