@@ -148,3 +148,79 @@ def test_disk_z_variance_feature_is_the_floor():
             assert abs(f[8] - np.log(1e-12)) < 1e-3
         assert np.allclose(f[:6], p) and np.allclose(f[6:12], np.log(np.diag(C) + 1e-12))
     assert n_disk > 50 and n_barrel > 20
+
+
+def _adam_steps(grads, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """Weight trajectory of the oracle's Adam under a sequence of gradient vectors."""
+    n = oracle.MLP_NPARAMS
+    w = np.zeros(n)
+    m, v = np.zeros(n), np.zeros(n)
+    out = []
+    for t, g in enumerate(grads, start=1):
+        before = w.copy()
+        oracle.adam(w, np.broadcast_to(g, (n,)).astype(np.float64).copy(), m, v, t, lr, b1, b2, eps)
+        out.append(w - before)
+    return out
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """Kingma and Ba: after bias correction the first moments are m_hat = g and v_hat = g^2, so
+    step 1 moves every weight by -lr g / (|g| + eps), i.e. lr against the sign of the gradient
+    whatever its size (swapped moments would move by |g|-proportional steps)."""
+    rng = np.random.default_rng(3)
+    g = rng.choice([-1, 1], oracle.MLP_NPARAMS) * 10.0 ** rng.uniform(-3, 2, oracle.MLP_NPARAMS)
+    (d,) = _adam_steps([g], lr=1e-3, eps=1e-8)
+    assert np.allclose(d, -1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(np.abs(d), 1e-3, rtol=1e-5)
+
+
+def test_adam_constant_gradient_keeps_a_step_of_lr():
+    """With a constant gradient both bias-corrected moments are exact at every step (m_hat = g,
+    v_hat = g^2), so the step stays lr: a correction by 1 - beta instead of 1 - beta^t would give
+    1.9 lr at step 2."""
+    g = np.full(oracle.MLP_NPARAMS, 0.37)
+    steps = _adam_steps([g] * 25, lr=2e-3)
+    for d in steps:
+        assert np.allclose(d, -2e-3 * 0.37 / (0.37 + 1e-8), rtol=1e-9, atol=0)
+
+
+def test_adam_two_steps_by_hand():
+    """g1 = +1 then g2 = -1 (beta1 = 0.9, beta2 = 0.999): m2 = 0.9 * 0.1 - 0.1 = -0.01,
+    1 - beta1^2 = 0.19, so m_hat = -1/19; v2 = 0.999 * 0.001 + 0.001 = 0.001999 = 1 - beta2^2,
+    so v_hat = 1. The second step is +lr/19 (up to eps)."""
+    d1, d2 = _adam_steps([1.0, -1.0], lr=1e-2, eps=1e-8)
+    assert np.allclose(d1, -1e-2, rtol=1e-7)
+    assert np.allclose(d2, 1e-2 / 19.0, rtol=1e-7)
+
+
+def test_pull_features_of_true_hits_have_unit_width():
+    """The last two features are the residuals over the square roots of the innovation variances
+    (pulls). Along the true hit sequence of scattering-free tracks (predicted state from the hits
+    before, as the fit makes it), the pulls of the next true hit have mean 0 and width 1: a
+    division by S instead of sqrt(S), or a swapped residual, would not. The first surface after
+    the seed is left out: the prior is centred on the seed made from hits 1-3, which changes the
+    spread there."""
+    wl = synth.workload("fit_small", n_events=1, tracks_lo=2500, tracks_hi=2500, seed=9)
+    b = synth.generate(wl)
+    g = oracle.Geometry(wl)
+    pulls = []
+    for t in range(b.n_tracks):
+        ids = b.track_hits[t]
+        ids = ids[ids >= 0]
+        st = oracle.seed(g, b.hits, b.hit_surface, ids[:3])
+        if st is None:
+            continue
+        p, C = st
+        for k, h in enumerate(ids):
+            surf = int(b.hit_surface[h])
+            if k > 0:
+                r = oracle.propagate(g, p, C, surf)
+                assert r is not None
+                p, C = r[0], r[1]
+                if k >= 4:
+                    pulls.append(oracle.pair_features(g, surf, p, C, b.hits[h])[12:])
+            p, C, _ = oracle.update(g, p, C, surf, b.hits[h])
+    x = np.array(pulls)
+    assert len(x) > 10000
+    assert np.all(np.abs(x.mean(0)) < 0.03), x.mean(0)
+    assert np.all(np.abs(x.std(0) - 1.0) < 0.03), x.std(0)
