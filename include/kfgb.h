@@ -329,7 +329,6 @@ int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_su
                     int n_tracks, int lmax, float* state_out, float* cov_out, float* chi2_out, int* ndof_out,
                     int* status_out, int* block_threads, float* best_ms, kf_stream_t stream);
 
-/* Human-readable name of a status code. */
 /* FP32 throughput probe (measurement only, not part of the path): launches `blocks` blocks of 256
  * threads, each running eight independent fused multiply-add chains for iters x 16 steps, on the
  * stream, and stores the launch's flop count (2 per FMA) in *flops. The caller times the launch
@@ -337,6 +336,7 @@ int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_su
  * [blocks] (practically never written). KF_ERR_ARG for non-positive sizes or null pointers. */
 int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_stream_t stream);
 
+/* Human-readable name of a status code. */
 const char* kf_status_string(int status);
 
 #ifdef __cplusplus

@@ -278,55 +278,83 @@ size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params) {
   return plan.ws_bytes;
 }
 
-int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
-                   const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
-                   int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
-                   int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream) {
-  DevGeom G;
-  int rc = pack_geometry(geom, &G);
+}  // extern "C"
+
+namespace kfgb {
+
+// Argument checks, geometry packing, launch plan and kernel arguments of a finder call, shared by
+// kf_find_tracks and kf_find_tracks_static (which differ only in where the scratch lives).
+// Returns KF_OK with *empty set when there is nothing to launch (no seeds).
+static int prepare_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                        const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
+                        int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
+                        int* status_out, int max_seeds, DevGeom* G, DevMat* M, FindPlan* plan, FindArgs* A,
+                        bool* empty) {
+  *empty = false;
+  int rc = pack_geometry(geom, G);
   if (rc != KF_OK) return rc;
   if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
-  rc = pack_steering(params->steering, &G);
+  rc = pack_steering(params->steering, G);
   if (rc != KF_OK) return rc;
-  DevMat M;
-  rc = pack_material(geom, &M);
+  rc = pack_material(geom, M);
   if (rc != KF_OK) return rc;
-  FindPlan plan;
-  rc = plan_find(n_seeds, params, sm_count(), find_features(G, M), &plan);
+  if (max_seeds >= 0 && n_seeds > max_seeds) return KF_ERR_CAPACITY;
+  rc = plan_find(n_seeds, params, sm_count(), find_features(*G, *M), plan);
   if (rc != KF_OK) return rc;
-  if (n_seeds == 0) return KF_OK;
-  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
+  if (n_seeds == 0) {
+    *empty = true;
+    return KF_OK;
+  }
+  if (index->n_bins != G->n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
       !index->sorted_rec || (reinterpret_cast<size_t>(index->sorted_rec) & 15) || !index->sub_off)
     return KF_ERR_ARG;
   if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
       !cov_out || !status_out)
     return KF_ERR_ARG;
-  if (!workspace || workspace_bytes < plan.ws_bytes || (reinterpret_cast<size_t>(workspace) & 255)) return KF_ERR_ARG;
+  A->bin_off = index->bin_off;
+  A->sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
+  A->sorted_ids = index->sorted_ids;
+  A->sorted_rec = reinterpret_cast<const float4*>(index->sorted_rec);
+  A->sub_off = index->sub_off;
+  A->hits = reinterpret_cast<const float2*>(hits);
+  A->hit_surface = hit_surface;
+  A->seed_hits = seed_hits;
+  A->seed_event = seed_event;
+  A->n_seeds = n_seeds;
+  A->n_events = index->n_events;
+  A->chi2_cut = params->chi2_cut;
+  A->k_max = params->k_max;
+  A->max_miss = params->max_miss;
+  A->lmax = params->lmax;
+  A->hits_out = hits_out;
+  A->nhits_out = nhits_out;
+  A->chi2_out = chi2_out;
+  A->state_out = state_out;
+  A->cov_out = cov_out;
+  A->status_out = status_out;
+  A->mlp = params->mlp;
+  A->top_n = params->mlp ? params->top_n : 0;
+  A->seed_keep = params->seed_keep;
+  return KF_OK;
+}
+
+}  // namespace kfgb
+
+extern "C" {
+
+int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
+                   const int* seed_hits, const int* seed_event, int n_seeds, const KfFindParams* params,
+                   int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
+                   int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream) {
+  DevGeom G;
+  DevMat M;
+  FindPlan plan;
   FindArgs A;
-  A.bin_off = index->bin_off;
-  A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
-  A.sorted_ids = index->sorted_ids;
-  A.sorted_rec = reinterpret_cast<const float4*>(index->sorted_rec);
-  A.sub_off = index->sub_off;
-  A.hits = reinterpret_cast<const float2*>(hits);
-  A.hit_surface = hit_surface;
-  A.seed_hits = seed_hits;
-  A.seed_event = seed_event;
-  A.n_seeds = n_seeds;
-  A.n_events = index->n_events;
-  A.chi2_cut = params->chi2_cut;
-  A.k_max = params->k_max;
-  A.max_miss = params->max_miss;
-  A.lmax = params->lmax;
-  A.hits_out = hits_out;
-  A.nhits_out = nhits_out;
-  A.chi2_out = chi2_out;
-  A.state_out = state_out;
-  A.cov_out = cov_out;
-  A.status_out = status_out;
-  A.mlp = params->mlp;
-  A.top_n = params->mlp ? params->top_n : 0;
-  A.seed_keep = params->seed_keep;
+  bool empty = false;
+  const int rc = prepare_find(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, params, hits_out,
+                              nhits_out, chi2_out, state_out, cov_out, status_out, -1, &G, &M, &plan, &A, &empty);
+  if (rc != KF_OK || empty) return rc;
+  if (!workspace || workspace_bytes < plan.ws_bytes || (reinterpret_cast<size_t>(workspace) & 255)) return KF_ERR_ARG;
   return launch_find(G, M, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -353,54 +381,18 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
                           const KfFindParams* params, int* hits_out, int* nhits_out, float* chi2_out,
                           float* state_out, float* cov_out, int* status_out, kf_stream_t stream) {
   DevGeom G;
-  int rc = pack_geometry(geom, &G);
-  if (rc != KF_OK) return rc;
-  if (!params || !index || n_seeds < 0) return KF_ERR_ARG;
-  rc = pack_steering(params->steering, &G);
-  if (rc != KF_OK) return rc;
   DevMat M;
-  rc = pack_material(geom, &M);
-  if (rc != KF_OK) return rc;
-  if (n_seeds > KF_STATIC_MAX_SEEDS) return KF_ERR_CAPACITY;
   FindPlan plan;
-  rc = plan_find(n_seeds, params, sm_count(), find_features(G, M), &plan);
+  FindArgs A;
+  bool empty = false;
+  int rc = prepare_find(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, params, hits_out, nhits_out,
+                        chi2_out, state_out, cov_out, status_out, KF_STATIC_MAX_SEEDS, &G, &M, &plan, &A, &empty);
   if (rc != KF_OK) return rc;
   if (plan.ws_bytes > KF_STATIC_SCRATCH_BYTES) return KF_ERR_CAPACITY;
-  if (n_seeds == 0) return KF_OK;
-  if (index->n_bins != G.n_bins || !index->bin_off || !index->sorted_hits || !index->sorted_ids ||
-      !index->sorted_rec || (reinterpret_cast<size_t>(index->sorted_rec) & 15) || !index->sub_off)
-    return KF_ERR_ARG;
-  if (!hits || !hit_surface || !seed_hits || !seed_event || !hits_out || !nhits_out || !chi2_out || !state_out ||
-      !cov_out || !status_out)
-    return KF_ERR_ARG;
+  if (empty) return KF_OK;
   void* scratch = nullptr;
   rc = static_scratch(&scratch);
   if (rc != KF_OK) return rc;
-  FindArgs A;
-  A.bin_off = index->bin_off;
-  A.sorted_hits = reinterpret_cast<const float2*>(index->sorted_hits);
-  A.sorted_ids = index->sorted_ids;
-  A.sorted_rec = reinterpret_cast<const float4*>(index->sorted_rec);
-  A.sub_off = index->sub_off;
-  A.hits = reinterpret_cast<const float2*>(hits);
-  A.hit_surface = hit_surface;
-  A.seed_hits = seed_hits;
-  A.seed_event = seed_event;
-  A.n_seeds = n_seeds;
-  A.n_events = index->n_events;
-  A.chi2_cut = params->chi2_cut;
-  A.k_max = params->k_max;
-  A.max_miss = params->max_miss;
-  A.lmax = params->lmax;
-  A.hits_out = hits_out;
-  A.nhits_out = nhits_out;
-  A.chi2_out = chi2_out;
-  A.state_out = state_out;
-  A.cov_out = cov_out;
-  A.status_out = status_out;
-  A.mlp = params->mlp;
-  A.top_n = params->mlp ? params->top_n : 0;
-  A.seed_keep = params->seed_keep;
   return launch_find(G, M, A, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
 
