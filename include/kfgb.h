@@ -336,6 +336,20 @@ int kf_autotune_fit(const KfGeometry* geom, const float* hits, const int* hit_su
  * [blocks] (practically never written). KF_ERR_ARG for non-positive sizes or null pointers. */
 int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_stream_t stream);
 
+/* Accuracy probe of the path's hand-written trigonometry (measurement only, not part of the path;
+ * the same code and compiler flags as the finder and the fit). For i < n (device arrays):
+ *   fn = KF_PROBE_SINCOS      o0 = sin a[i], o1 = cos a[i] (Cody-Waite reduction, Taylor series;
+ *                             for |a| <= 1e5, else NaN);
+ *   fn = KF_PROBE_ATAN_SMALL  o0 = atan(a[i] / b[i]) by its series, valid for b > 0, |a| < 0.05 b;
+ *   fn = KF_PROBE_HALF_ANGLE  o0 = sin(h)/h, o1 = sin h, o2 = cos h for h = a[i] / 2 (the helix
+ *                             step functions: series below |h| = 0.1, else the sincos above).
+ * b may be NULL except for KF_PROBE_ATAN_SMALL; o1 and o2 receive 0 where unused. KF_ERR_ARG for
+ * an unknown fn, n < 0 or a null pointer. */
+#define KF_PROBE_SINCOS 0
+#define KF_PROBE_ATAN_SMALL 1
+#define KF_PROBE_HALF_ANGLE 2
+int kf_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2, kf_stream_t stream);
+
 /* Human-readable name of a status code. */
 const char* kf_status_string(int status);
 

@@ -66,7 +66,7 @@ class KfFindParams(ctypes.Structure):
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
-           "kf_remove_duplicates", "kf_fp32_fma_probe")
+           "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
             lib.kf_remove_duplicates.argtypes = [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
             lib.kf_fp32_fma_probe.restype = I
             lib.kf_fp32_fma_probe.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_longlong), P]
+            lib.kf_math_probe.restype = I
+            lib.kf_math_probe.argtypes = [I, P, P, I, P, P, P, P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -331,6 +333,21 @@ def fp32_fma_rate(blocks: int = 0, iters: int = 4096, reps: int = 3, stream=None
         b.synchronize()
         best = max(best, flops.value / (a.elapsed_time(b) / 1000.0) / 1e12)
     return best
+
+
+PROBE_SINCOS, PROBE_ATAN_SMALL, PROBE_HALF_ANGLE = 0, 1, 2  # KF_PROBE_*
+
+
+def math_probe(fn: int, a, b=None, stream=None):
+    """kf_math_probe: the path's hand-written trigonometry on FP32 CUDA tensors a (and b for the
+    small-angle arctangent). Returns three tensors (o0, o1, o2) of a's shape."""
+    lib = load_library()
+    a = _cuda(a, torch.float32, "a").contiguous()
+    b = None if b is None else _cuda(b, torch.float32, "b").contiguous()
+    o = [torch.empty_like(a) for _ in range(3)]
+    _check(lib.kf_math_probe(int(fn), _ptr(a), _ptr(b), a.numel(), _ptr(o[0]), _ptr(o[1]), _ptr(o[2]), _stream(stream)),
+           "kf_math_probe")
+    return tuple(o)
 
 
 def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:

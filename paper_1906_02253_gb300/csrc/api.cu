@@ -24,6 +24,8 @@ int launch_clean_seeds(const DevGeom& G, const float2* hits, const int* hit_surf
                        const int* seed_event, int n, int n_hits, float dphi, float dtheta, int* keep, void* ws,
                        cudaStream_t st);
 int launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t st, long long* flops);
+int launch_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2,
+                      cudaStream_t st);
 int launch_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
                              const int* event, int n, int lmax, int n_hits, float dphi, float dtheta, int* keep,
                              void* ws, cudaStream_t st);
@@ -494,6 +496,13 @@ int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* c
 int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_stream_t stream) {
   if (!sink || !flops || blocks <= 0 || iters <= 0) return KF_ERR_ARG;
   return launch_fma_peak(sink, blocks, iters, reinterpret_cast<cudaStream_t>(stream), flops);
+}
+
+int kf_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2, kf_stream_t stream) {
+  if (fn < KF_PROBE_SINCOS || fn > KF_PROBE_HALF_ANGLE || n < 0) return KF_ERR_ARG;
+  if (n == 0) return KF_OK;
+  if (!a || !o0 || !o1 || !o2 || (fn == KF_PROBE_ATAN_SMALL && !b)) return KF_ERR_ARG;
+  return launch_math_probe(fn, a, b, n, o0, o1, o2, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char* kf_status_string(int status) {

@@ -185,12 +185,6 @@ __device__ __forceinline__ float cand_word(const WarpSmem<KC>& W, int w, int col
 // Full-range angle, out of line: only hits far from the prediction in azimuth need it.
 __device__ __noinline__ float atan2_cold(float a, float b) { return atan2f(a, b); }
 
-// atan(a / b) for b > 0 and |a| < 0.05 b: its series to t^7 (next term below 2e-11 relative).
-__device__ __forceinline__ float atan_small(float a, float b) {
-  const float t = a / b, t2 = t * t;
-  return t * (1.f + t2 * (-1.f / 3.f + t2 * (1.f / 5.f + t2 * (-1.f / 7.f))));
-}
-
 // Residual angle phi_hit - phi_pred from the hit direction (c, s) rotated into the frame of the
 // predicted position (x, y).
 __device__ __forceinline__ float resid_angle(float x, float y, float c, float s) {

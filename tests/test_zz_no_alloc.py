@@ -9,6 +9,7 @@ the same inputs; the second call must not see anything the first left in the sha
 file is collected last so that a failure here stops a run only after every other test ran.
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -70,6 +71,53 @@ def test_static_entry_point_matches_workspace_entry_point(kf, first, second):
         assert torch.allclose(out["chi2"][ok], ref["chi2"][ok], rtol=1e-3, atol=0)
         assert torch.allclose(out["state"][:, ok], ref["state"][:, ok], rtol=1e-4, atol=1e-6)
         assert torch.allclose(out["cov"][:, ok], ref["cov"][:, ok], rtol=1e-3, atol=1e-9)
+
+
+def _compare(out, ref):
+    for k in ("hits", "nhits", "status"):
+        assert torch.equal(out[k], ref[k]), k
+    ok = ref["status"] == 0
+    assert torch.allclose(out["chi2"][ok], ref["chi2"][ok], rtol=1e-3, atol=0)
+    assert torch.allclose(out["state"][:, ok], ref["state"][:, ok], rtol=1e-4, atol=1e-6)
+    assert torch.allclose(out["cov"][:, ok], ref["cov"][:, ok], rtol=1e-3, atol=1e-9)
+
+
+def test_static_entry_point_learned_proposal_between_plain_calls(kf):
+    """The learned proposal keeps a transposed copy of the network in the array, after the seed
+    states: plain, learned, plain again on the same events must each match kf_find_tracks."""
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", "mlp_learned.npz"))
+    buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device="cuda")
+    wl = synth.workload("learned", n_events=2, tracks_lo=1500, tracks_hi=3000, seed=35)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    for mlp, top_n in ((None, 0), (buf, 2), (None, 0), (buf, 1)):
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=mlp, top_n=top_n)
+        ref = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+        out = _outputs(dev["seed_hits"].shape[1], wl.lmax)
+        assert _static_call(kf, g, idx, dev, prm, out) == kf.KF_OK
+        torch.cuda.synchronize()
+        _compare(out, ref)
+
+
+def test_static_entry_point_at_its_seed_capacity(kf):
+    """Exactly KF_STATIC_MAX_SEEDS seeds (the largest call the array serves)."""
+    wl = synth.workload("find", n_events=14, seed=36)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    n = 65536
+    assert dev["seed_hits"].shape[1] >= n
+    dev["seed_hits"] = dev["seed_hits"][:, :n].contiguous()
+    dev["seed_event"] = dev["seed_event"][:n].contiguous()
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
+    ref = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    out = _outputs(n, wl.lmax)
+    assert _static_call(kf, g, idx, dev, prm, out) == kf.KF_OK
+    torch.cuda.synchronize()
+    _compare(out, ref)
 
 
 def test_static_entry_point_rejects_too_many_seeds(kf):
