@@ -294,6 +294,41 @@ class EventBatch:
     def n_surf(self) -> int:
         return len(self.wl.surfaces)
 
+    def select_events(self, events) -> "EventBatch":
+        """The sub-batch of the given events (ascending indices): their hits, tracks and truth,
+        with hit ids, track ids and event numbers renumbered in the sub-batch (a rank's share of a
+        fixed batch under strong scaling). Re-indexing only."""
+        events = np.asarray(events, dtype=np.int64)
+        if events.size > 1 and np.any(np.diff(events) <= 0):
+            raise ValueError("events must be ascending and distinct")
+        ns = self.n_surf
+        so = self.slab_offsets.astype(np.int64)
+        parts, new_so, base = [], [0], 0
+        for e in events:
+            a, b = so[e * ns], so[(e + 1) * ns]
+            parts.append(np.arange(a, b, dtype=np.int64))
+            new_so.extend((base + so[e * ns + 1:(e + 1) * ns + 1] - a).tolist())
+            base += b - a
+        hit_idx = np.concatenate(parts) if parts else np.zeros(0, np.int64)
+        new_hit = np.full(self.n_hits + 1, -1, np.int64)  # last entry maps the -1 padding
+        new_hit[hit_idx] = np.arange(hit_idx.size)
+        tsel = np.nonzero(np.isin(self.track_event, events))[0]
+        new_trk = np.full(self.n_tracks + 1, -1, np.int64)
+        new_trk[tsel] = np.arange(tsel.size)
+        th = self.track_hits[tsel]
+        sim = self.hit_sim[hit_idx]
+        wl = replace(self.wl, n_events=int(events.size))
+        pick = (lambda a: None if a is None else a[tsel])
+        return EventBatch(
+            wl=wl, hits=np.ascontiguousarray(self.hits[hit_idx]), hit_surface=self.hit_surface[hit_idx].copy(),
+            hit_sim=new_trk[np.where(sim >= 0, sim, self.n_tracks)].astype(np.int32),
+            slab_offsets=np.asarray(new_so, dtype=np.int64),
+            track_event=np.searchsorted(events, self.track_event[tsel]).astype(np.int32),
+            track_q=self.track_q[tsel].copy(), track_init=self.track_init[tsel].copy(),
+            track_nhits=self.track_nhits[tsel].copy(),
+            track_hits=new_hit[np.where(th >= 0, th, self.n_hits)].astype(np.int32),
+            track_surf=self.track_surf[tsel].copy(), truth_in=pick(self.truth_in), truth_out=pick(self.truth_out))
+
     def seeds(self, min_hits: int = 3, combinations: bool = None):
         """Seeds: (seed_hits [n,3], seed_track [n]). One per track from its first three true hits,
         or (combinations, the workload's default) one per combination of the track's hits on its
