@@ -49,13 +49,20 @@ WORKLOAD = "fit_batched"
 #   chi2 of one hit in a search window ...................................... 20
 #   seed from three hits ..................................................... 80
 FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20, 80
+# Learned proposal network 14 -> 64 -> 64 -> 1 per sample: forward 2 (14*64 + 64*64 + 64); backward
+# 2 (64*64 + 64*64 + 64*14 + 64) for the weight gradients and the hidden-layer back-propagation
+# (bias sums, ReLU masks and the sigmoid not counted).
+FLOP_MLP_FWD = 2 * (14 * 64 + 64 * 64 + 64)
+FLOP_MLP_BWD = 2 * (64 * 64 + 64 * 64 + 64 * 14 + 64)
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch on 30 events of the 100-event workload, per seed; profiles/step_kernels_fit_batched_100ev.md),
-# valid for that workload while the finder's sources and build flags are the ones profiled (SHA-1
-# over FIND_SOURCES); otherwise reported as null.
+# launch, per seed) on a smaller case of each workload (30 events of the 100-event workload, 40 of
+# the barrel + disk workload; profiles/k_find_tracks_*), valid while the finder's sources and build
+# flags are the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"workload": "fit_100ev_uneven_17layers_ms", "sources_sha1": "82e9fa34012c627d5b99d4e209ef75dc2e5a8e9c", "dram_bytes_per_seed": 160092160 / 302063}
+FIND_PROFILE = {"sources_sha1": "50c5dbfadcdb61f96ca2e45a03b5e42bcd425d47",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": 160558848 / 302063,
+                                        "find_200ev_barrel_disks_noise100": 174701568 / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
@@ -175,7 +182,7 @@ def run_reference(args, wl, batch):
     value = n / statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator)",
             "config": {"workload": wl.name, "sample": f"first {n} seeds of the batch (index, "
                        + ("seed cleaning, find, duplicate removal, fit)" if clean else "find, fit)")},
@@ -189,7 +196,12 @@ def run_reference(args, wl, batch):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
-def run_gpu(args, wl, batch):
+def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
+    """The step (index, seed states, find, fit; with seed cleaning and duplicate removal on
+    combinatorial seeds) on one workload: device-timed graph replays, per-part times, efficiency,
+    the learned proposal against plain finding and the rooflines. `full` adds the end-to-end
+    measurement through host buffers and the single-thread oracle figure. Returns the JSON object
+    (and, under "_ctx", the device state the further measurements reuse)."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -337,71 +349,77 @@ def run_gpu(args, wl, batch):
             kern[k].append(ev[i].elapsed_time(ev[i + 1]))
     kern_ms = {k: statistics.mean(v) for k, v in kern.items()}
 
-    # End to end through the public API with host buffers: H2D of the step's inputs from pinned
-    # memory, the calls, D2H of the step's result (found hit lists, fitted states, chi2). Serial:
-    # copy in, compute, copy out on one stream. Pipelined: copies on their own streams with two
-    # buffer sets, so the H2D of step i+1 and the D2H of step i-1 overlap the compute of step i
-    # (every step's copies stay inside the timed region).
-    pinned = {k: host[k].pin_memory() for k in ("hits", "hit_surface", "slab_offsets", "seed_hits", "seed_event")}
-    res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory(),
-                    state=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
-                    chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory())
-    h2d = sum(t.numel() * t.element_size() for t in pinned.values())
-    d2h = sum(t.numel() * t.element_size() for t in res_host.values())
+    res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory())
+    h2d = d2h = 0
+    ms_e2e = ms_e2e_serial = None
+    if full:
+        # End to end through the public API with host buffers: H2D of the step's inputs from pinned
+        # memory, the calls, D2H of the step's result (found hit lists, fitted states, chi2). Serial:
+        # copy in, compute, copy out on one stream. Pipelined: copies on their own streams with two
+        # buffer sets, so the H2D of step i+1 and the D2H of step i-1 overlap the compute of step i
+        # (every step's copies stay inside the timed region).
+        pinned = {k: host[k].pin_memory() for k in ("hits", "hit_surface", "slab_offsets", "seed_hits", "seed_event")}
+        res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory(),
+                        state=torch.empty((6, n_seeds), dtype=torch.float32).pin_memory(),
+                        chi2=torch.empty(n_seeds, dtype=torch.float32).pin_memory())
+        h2d = sum(t.numel() * t.element_size() for t in pinned.values())
+        d2h = sum(t.numel() * t.element_size() for t in res_host.values())
 
-    def copy_out(fo, fi):
-        res_host["hits"].copy_(fo["hits"], non_blocking=True)
-        res_host["state"].copy_(fi["state"], non_blocking=True)
-        res_host["chi2"].copy_(fi["chi2"], non_blocking=True)
+        def copy_out(fo, fi):
+            res_host["hits"].copy_(fo["hits"], non_blocking=True)
+            res_host["state"].copy_(fi["state"], non_blocking=True)
+            res_host["chi2"].copy_(fi["chi2"], non_blocking=True)
 
-    def e2e_step():
-        for k, t in pinned.items():
-            d[k].copy_(t, non_blocking=True)
-        step(stream)
-        copy_out(fout, fit_out)
+        def e2e_step():
+            for k, t in pinned.items():
+                d[k].copy_(t, non_blocking=True)
+            step(stream)
+            copy_out(fout, fit_out)
 
-    t_e2e = timed_steps(args.steps, e2e_step)
-    ms_e2e_serial = shard.max_over_ranks(statistics.mean(t_e2e), device=dev)
+        t_e2e = timed_steps(args.steps, e2e_step)
+        ms_e2e_serial = shard.max_over_ranks(statistics.mean(t_e2e), device=dev)
 
-    sets = [(d, fout, fit_out), ({k: torch.empty_like(d[k]) for k in pinned},
-                                 {k: torch.empty_like(v) for k, v in fout.items()},
-                                 {k: torch.empty_like(v) for k, v in fit_out.items()})]
-    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        sets = [(d, fout, fit_out), ({k: torch.empty_like(d[k]) for k in pinned},
+                                     {k: torch.empty_like(v) for k, v in fout.items()},
+                                     {k: torch.empty_like(v) for k, v in fit_out.items()})]
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
-    def e2e_pipeline(k):
-        k = max(1, k)
-        ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(k)] for _ in range(3))
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        s_in.wait_event(t0)
-        s_out.wait_event(t0)
-        for i in range(k):
-            dd, fo, fi = sets[i % 2]
-            with torch.cuda.stream(s_in):
+        def e2e_pipeline(k):
+            k = max(1, k)
+            ev_in, ev_c, ev_out = ([torch.cuda.Event() for _ in range(k)] for _ in range(3))
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            s_in.wait_event(t0)
+            s_out.wait_event(t0)
+            for i in range(k):
+                dd, fo, fi = sets[i % 2]
+                with torch.cuda.stream(s_in):
+                    if i >= 2:
+                        s_in.wait_event(ev_c[i - 2])  # step i-2 has read this input set
+                    for key, t in pinned.items():
+                        dd[key].copy_(t, non_blocking=True)
+                    ev_in[i].record(s_in)
+                stream.wait_event(ev_in[i])
                 if i >= 2:
-                    s_in.wait_event(ev_c[i - 2])  # step i-2 has read this input set
-                for key, t in pinned.items():
-                    dd[key].copy_(t, non_blocking=True)
-                ev_in[i].record(s_in)
-            stream.wait_event(ev_in[i])
-            if i >= 2:
-                stream.wait_event(ev_out[i - 2])  # step i-2's results in this output set are read back
-            step(stream, dd=dd, fo=fo, fi=fi)
-            ev_c[i].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_c[i])
-                copy_out(fo, fi)
-                ev_out[i].record(s_out)
-        stream.wait_event(ev_out[k - 1])
-        t1.record(stream)
-        torch.cuda.synchronize()
-        return t0.elapsed_time(t1) / k
+                    stream.wait_event(ev_out[i - 2])  # step i-2's results in this output set are read back
+                step(stream, dd=dd, fo=fo, fi=fi)
+                ev_c[i].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_c[i])
+                    copy_out(fo, fi)
+                    ev_out[i].record(s_out)
+            stream.wait_event(ev_out[k - 1])
+            t1.record(stream)
+            torch.cuda.synchronize()
+            return t0.elapsed_time(t1) / k
 
-    e2e_pipeline(min(args.warmup, 3))
-    ms_e2e = shard.max_over_ranks(e2e_pipeline(args.steps), device=dev)
+        e2e_pipeline(min(args.warmup, 3))
+        ms_e2e = shard.max_over_ranks(e2e_pipeline(args.steps), device=dev)
 
     # Result sanity on the last step (efficiency of the found tracks, host logic only).
     from paper_1906_02253_gb300 import metrics
+    if not full:
+        res_host["hits"].copy_(fout["hits"])
     eff, fake = metrics.efficiency(batch, host["seed_track"], res_host["hits"].numpy().T,
                                    fout["nhits"].cpu().numpy())
     dups = None
@@ -418,14 +436,15 @@ def run_gpu(args, wl, batch):
 
     learned = None
     if not args.no_learned:
-        learned = compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff, fake, kern_ms["find"])
+        learned = compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff, fake, kern_ms["find"],
+                                  mlp_name or args.workload)
 
     # whole job: the seeds of every rank (their events differ) over the slowest rank's time
     job_seeds = shard.sum_over_ranks(n_seeds, device=dev)
     value = job_seeds / (ms_step / 1000.0)
-    e2e_value = job_seeds / (ms_e2e / 1000.0)
+    e2e_value = job_seeds / (ms_e2e / 1000.0) if ms_e2e else None
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": args.scaling,
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator, no datasets)",
            "config": {"workload": wl.name, "events": batch.n_events, "seeds": n_seeds, "hits": n_hits,
                       "layers": len(wl.surfaces), "k_max": wl.k_max, "chi2_cut": wl.chi2_cut,
@@ -433,16 +452,20 @@ def run_gpu(args, wl, batch):
                                else "hit index + find + fit") + ", one CUDA graph",
                       "l2": "flushed between steps (256 MB write)",
                       "next_surface": "region steering (eta edges 0.4, 1.8)" if args.steering else "geometric rule",
-                      "parallelism": f"events sharded over {ws} GPU(s), no collective"},
+                      "parallelism": (f"one fixed batch split over {ws} GPU(s) by LPT on track counts"
+                                      if args.scaling == "strong" else f"every GPU its own events ({ws} GPU(s))")
+                                     + ", no collective"},
            "gpu_launches": launches_per_step * args.steps, "autotune": tuning,
            "kernel_ms": kern_ms, "efficiency": eff, "fake_rate": fake, "fit_ok_fraction": fit_ok,
            "fit_tracks_per_s": job_seeds / (kern_ms["fit"] / 1000.0),
            "find_seeds_per_s": job_seeds / (kern_ms["find"] / 1000.0),
-           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                   "ms_per_step": ms_e2e, "pipelined": "H2D of step i+1 and D2H of step i-1 on their own "
-                   "streams overlap step i (two buffer sets); L2: the H2D rewrites the inputs each step",
-                   "serial_ms_per_step": ms_e2e_serial,
-                   "serial_value": job_seeds / (ms_e2e_serial / 1000.0)}}
+           }
+    if full:
+        out["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "ms_per_step": ms_e2e, "pipelined": "H2D of step i+1 and D2H of step i-1 on their own "
+                      "streams overlap step i (two buffer sets); L2: the H2D rewrites the inputs each step",
+                      "serial_ms_per_step": ms_e2e_serial,
+                      "serial_value": job_seeds / (ms_e2e_serial / 1000.0)}
     out["clocks"] = clk.summary()
     if learned is not None:
         out["learned_vs_plain"] = learned
@@ -458,25 +481,30 @@ def run_gpu(args, wl, batch):
                                          + ("seed cleaning, find, duplicate removal, " if clean else "find, ")
                                          + f"fit of the found tracks (FP64, {dt:.1f} s)"}
         counters = np.asarray(counters, np.float64) / n
-        dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1)
-        out["cpu_baseline"]["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
-                                                "sample": f"first {n1} seeds ({dt1:.1f} s)"}
+        if full:
+            dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1)
+            out["cpu_baseline"]["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                                                    "sample": f"first {n1} seeds ({dt1:.1f} s)"}
     out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    out["_ctx"] = dict(kf=kf, g=g, d=d, host=host, idx=idx, prm=prm, fout=fout, fit_out=fit_out, stream=stream,
+                       flush=flush, n_seeds=n_seeds, batch=batch, wl=wl, learned=learned)
+    return out
 
 
 MLP_FILE = os.path.join(ROOT, "paper_1906_02253_gb300", "data", "mlp_learned.npz")
 
 
-def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff_plain, fake_plain, ms_plain):
+def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff_plain, fake_plain, ms_plain,
+                    mlp_name):
     """Learned proposal vs the plain finder on the same batch and K: finder seeds/s (CUDA events on
-    the launching stream, L2 flushed between runs), efficiency and fake rate, for several top_n."""
+    the launching stream, L2 flushed between runs), efficiency and fake rate, for several top_n.
+    Each learned configuration is autotuned on its own (block size and candidate capacity of the
+    learned instance) on the same calibration seeds as plain finding."""
     import numpy as np
     import torch
     from paper_1906_02253_gb300 import metrics
 
-    path = os.path.join(ROOT, "paper_1906_02253_gb300", "data", f"mlp_{args.workload}.npz")
+    path = os.path.join(ROOT, "paper_1906_02253_gb300", "data", f"mlp_{mlp_name}.npz")
     if not os.path.exists(path):
         path = MLP_FILE  # the barrel-geometry network
     if not os.path.exists(path):
@@ -485,15 +513,22 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device=d["hits"].device)
     n = host["seed_hits"].shape[1]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=d["hits"].device)
+    n_cal = int(np.searchsorted(host["seed_event"].numpy(), min(10, batch.n_events)))
+    cal_s = d["seed_hits"][:, :n_cal].contiguous()
+    cal_e = d["seed_event"][:n_cal].contiguous()
     res = {"network": json.loads(str(z["info"])), "network_file": os.path.basename(path), "k_max": prm.k_max,
-           "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain}}
+           "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain,
+                     "block_threads": prm.block_threads, "k_capacity": prm.k_capacity}}
     best = None
     for top_n in (1, 2, 4):
-        lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
-                            mlp=buf, top_n=top_n)
+        lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
         lp.seed_keep, lp._keep_ref = prm.seed_keep, getattr(prm, "_keep_ref", None)  # same seeds
         lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
+        if not args.no_autotune:
+            with torch.cuda.stream(stream):
+                lp, _ = kf.autotune_find(g, idx, d["hits"], d["hit_surface"], cal_s, cal_e, lp, stream=stream)
+            torch.cuda.synchronize()
         times = []
         for i in range(args.warmup + args.steps):
             with torch.cuda.stream(stream):
@@ -507,14 +542,229 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
             if i >= args.warmup:
                 times.append(a.elapsed_time(b))
         e, f = metrics.efficiency(batch, host["seed_track"], fout["hits"].cpu().numpy().T, fout["nhits"].cpu().numpy())
-        r = {"find_seeds_per_s": n / (statistics.mean(times) / 1000.0), "efficiency": e, "fake_rate": f,
-             "efficiency_loss": eff_plain - e}
+        r = {"find_seeds_per_s": n / (statistics.mean(times) / 1000.0), "find_ms": statistics.mean(times),
+             "efficiency": e, "fake_rate": f, "efficiency_loss": eff_plain - e,
+             "block_threads": lp.block_threads, "k_capacity": lp.k_capacity}
         r["speedup_vs_plain"] = r["find_seeds_per_s"] / res["plain"]["find_seeds_per_s"]
         res[f"top_n={top_n}"] = r
         if r["efficiency_loss"] <= 0.005 and (best is None or r["find_seeds_per_s"] > res[best]["find_seeds_per_s"]):
             best = f"top_n={top_n}"
     res["best_within_0.5pct_eff_loss"] = best
+    res["_mlp"] = (z["weights"], z["mean"], z["sd"])
     return res
+
+
+def learned_roofline(batch, wl, res, n_sample: int = 20000):
+    """Roofline of the learned finder (top_n = 2): the plain finder's algorithmic flops per seed with
+    the counts of learned finding, plus 10,112 flops per network evaluation, all counted by the
+    oracle's learned finding on the first seeds of the batch."""
+    import numpy as np
+    import oracle
+    import torch
+    w, mean, sd = res["_mlp"]
+    seeds, st = batch.seeds()
+    n = min(n_sample, len(st))
+    f = oracle.find(oracle.Geometry(wl), batch, seeds[:n], batch.track_event[st][:n],
+                    mlp=(np.asarray(w, np.float64), np.asarray(mean, np.float64), np.asarray(sd, np.float64)),
+                    top_n=2)
+    c = np.asarray(f["counters"], np.float64) / n
+    n_prop, n_pass, n_upd, n_scan, n_win, n_mlp = c
+    per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2 + n_mlp * FLOP_MLP_FWD
+    r = res["top_n=2"]
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    alu_peak = props.multi_processor_count * 128 * 2 * _peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = per_seed * r["find_seeds_per_s"] / 1e12
+    return {"kernel": "k_find_tracks (learned, top_n=2)", "bound": "alu", "achieved": ach, "peak": alu_peak,
+            "unit": "TFLOP/s", "frac": ach / alu_peak,
+            "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win, "network_evaluations": n_mlp,
+                              "flop": per_seed, "sample_seeds": n}}
+
+
+def _timed(args, stream, flush, fn, reps=None):
+    """Mean CUDA-event time (ms) of fn on `stream`, L2 flushed before each run, after warm-up."""
+    import torch
+    times = []
+    reps = args.steps if reps is None else reps
+    for i in range(args.warmup + reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(a.elapsed_time(b))
+    return statistics.mean(times)
+
+
+def _alu_peak():
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = _peaks().get("sm_max_mhz", 2070.0)
+    return props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def fit_line(args, kf, wl, batch, stream, flush, d=None):
+    """Fitting over the known hit sequences of a workload's generated tracks (the fitting configs):
+    every track of every event in one CUDA-graph launch of kf_fit_tracks with its autotuned block
+    size, L2 flushed between replays; tracks/s, the fit's roofline (FP32 ALU) and the FP64 oracle's
+    fit on the host cores."""
+    import numpy as np
+    import torch
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = kf.Geometry(wl)
+    if d is None:
+        d = {k: v.to(dev) for k, v in kf.to_device_event_batch(batch, device="cpu").items() if isinstance(v, torch.Tensor)}
+    th = d["track_hits"]
+    n = th.shape[1]
+    out = dict(state=torch.empty((6, n), dtype=torch.float32, device=dev),
+               cov=torch.empty((21, n), dtype=torch.float32, device=dev),
+               chi2=torch.empty(n, dtype=torch.float32, device=dev),
+               ndof=torch.empty(n, dtype=torch.int32, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev))
+    with torch.cuda.stream(stream):
+        blk, _ = kf.autotune_fit(g, d["hits"], d["hit_surface"], th, stream=stream)
+        for _ in range(args.warmup):
+            kf.fit_tracks(g, d["hits"], d["hit_surface"], th, out=out, block_threads=blk, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        kf.fit_tracks(g, d["hits"], d["hit_surface"], th, out=out, block_threads=blk, stream=stream)
+    torch.cuda.synchronize()
+    ms = _timed(args, stream, flush, graph.replay)
+    ok = out["status"] == 0
+    n_fit = int(ok.sum().item())
+    n_steps = float(((out["ndof"][ok].double() + 5.0) / 2.0 - 1.0).sum().item())
+    flops = n_fit * (FLOP_SEED + FLOP_UPDATE) + n_steps * (FLOP_PROP + FLOP_TRANSPORT + FLOP_UPDATE)
+    peak, mhz = _alu_peak()
+    ach = flops / (ms / 1000.0) / 1e12
+    res = {"workload": wl.name, "events": batch.n_events, "tracks": n, "layers": len(wl.surfaces),
+           "metric": "fitting tracks/s (known hit sequences, one CUDA graph launch)", "value": n / (ms / 1000.0),
+           "unit": "tracks/s", "ms": ms, "block_threads": blk, "fit_ok_fraction": n_fit / max(n, 1),
+           "roofline": {"kernel": "k_fit_tracks", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                        "frac": ach / peak, "peak_note": f"FP32 {mhz:.0f} MHz", "flop_per_track": flops / max(n_fit, 1)}}
+    if not args.no_cpu_baseline:
+        m = min(n, args.fit_cpu_tracks)
+        t0 = time.perf_counter()
+        oracle.fit(oracle.Geometry(wl), batch.hits, batch.hit_surface, batch.track_hits[:m])
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": m / dt, "unit": "tracks/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"first {m} tracks of the batch (FP64 fit, {dt:.2f} s)"}
+    return res
+
+
+def secondary_rooflines(args, kf, ctx, learned):
+    """Rooflines of the kernels besides index, finder and fit, each timed live with CUDA events on
+    its stream: the seed states (FP32 ALU), the network's forward and loss-gradient kernels on a
+    synthetic feature batch (FP32 ALU), seed cleaning and duplicate removal on the module-overlap
+    workload (HBM, their algorithmic bytes), and the learned finder."""
+    import numpy as np
+    import torch
+    import synth
+    peak, mhz = _alu_peak()
+    hbm = _peaks()["hbm_gbs"]
+    stream, flush, d, g, batch = ctx["stream"], ctx["flush"], ctx["d"], ctx["g"], ctx["batch"]
+    n = ctx["n_seeds"]
+    res = {}
+    st_out = (torch.empty((28, n), dtype=torch.float32, device=d["hits"].device),
+              torch.empty(n, dtype=torch.int32, device=d["hits"].device))
+    ms = _timed(args, stream, flush, lambda: kf.seed_states(g, d["hits"], d["hit_surface"], d["seed_hits"],
+                                                            d["seed_event"], batch.n_events, out=st_out, stream=stream))
+    per = FLOP_SEED + 2 * (FLOP_PROP + FLOP_TRANSPORT) + 3 * FLOP_UPDATE
+    ach = per * n / (ms / 1000.0) / 1e12
+    res["seed_states"] = {"kernel": "k_seed_states", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "ms": ms, "flop_per_seed": per, "seeds": n}
+    # network kernels on 2^20 synthetic feature rows
+    rows = 1 << 20
+    gen = torch.Generator(device=d["hits"].device).manual_seed(7)
+    feats = torch.randn((rows, 14), generator=gen, device=d["hits"].device)
+    labels = (torch.rand(rows, generator=gen, device=d["hits"].device) > 0.5).float()
+    params = kf.mlp_buffer(synth.mlp_init(5), np.zeros(14), np.ones(14), device=d["hits"].device)
+    logits = torch.empty(rows, device=d["hits"].device)
+    grad = torch.empty(kf.MLP_PARAMS, device=d["hits"].device)
+    loss = torch.empty(1, device=d["hits"].device)
+    ms = _timed(args, stream, flush, lambda: kf.mlp_forward(params, feats, out=logits, stream=stream))
+    ach = FLOP_MLP_FWD * rows / (ms / 1000.0) / 1e12
+    res["mlp_forward"] = {"kernel": "k_mlp_forward", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                          "frac": ach / peak, "ms": ms, "rows": rows, "flop_per_row": FLOP_MLP_FWD}
+    ms = _timed(args, stream, flush, lambda: kf.mlp_loss_grad(params, feats, labels, grad=grad, loss=loss, stream=stream))
+    ach = (FLOP_MLP_FWD + FLOP_MLP_BWD) * rows / (ms / 1000.0) / 1e12
+    res["mlp_loss_grad"] = {"kernel": "k_mlp_loss_grad", "bound": "alu", "achieved": ach, "peak": peak,
+                            "unit": "TFLOP/s", "frac": ach / peak, "ms": ms, "rows": rows,
+                            "flop_per_row": FLOP_MLP_FWD + FLOP_MLP_BWD}
+    # seed cleaning and duplicate removal on the module-overlap workload
+    wd = synth.workload("duplicates")
+    bd = synth.generate(wd)
+    hd = kf.to_device_event_batch(bd, device="cpu")
+    dd = {k: v.to(d["hits"].device) for k, v in hd.items() if isinstance(v, torch.Tensor)}
+    gd = kf.Geometry(wd)
+    nd = dd["seed_hits"].shape[1]
+    keep = torch.ones(nd, dtype=torch.int32, device=d["hits"].device)
+    dws = torch.empty(max(kf.dedup_workspace_size(nd, wd.lmax, bd.n_hits), 256), dtype=torch.uint8,
+                      device=d["hits"].device)
+    ms = _timed(args, stream, flush, lambda: kf.clean_seeds(gd, dd["hits"], dd["hit_surface"], dd["seed_hits"],
+                                                            dd["seed_event"], keep=keep, workspace=dws, stream=stream))
+    # bytes: seed hit ids and event (16), the three hits (24), keep (4), the inverted index (three
+    # references per seed, counted, filled and read: 3 x 12), its offsets (4 per hit, scanned twice)
+    nbytes = nd * (16 + 24 + 4 + 36) + bd.n_hits * 8
+    ach = nbytes / (ms / 1000.0) / 1e9
+    res["seed_cleaning"] = {"kernel": "k_count_users, scan, k_fill_users, k_seed_dirs, k_clean_seeds", "bound": "hbm",
+                            "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "ms": ms, "seeds": nd,
+                            "bytes": nbytes}
+    prm = kf.find_params(wd.chi2_cut, wd.k_max, wd.max_miss, wd.lmax, seed_keep=keep)
+    fo = kf.find_tracks(gd, kf.build_hit_index(gd, dd["hits"], dd["slab_offsets"], bd.n_events, hd["max_slab_hits"]),
+                        dd["hits"], dd["hit_surface"], dd["seed_hits"], dd["seed_event"], prm)
+    tkeep = torch.ones(nd, dtype=torch.int32, device=d["hits"].device)
+    ms = _timed(args, stream, flush, lambda: kf.remove_duplicates(fo["hits"], fo["nhits"], fo["chi2"], fo["state"],
+                                                                  dd["seed_event"], bd.n_hits, keep=tkeep,
+                                                                  workspace=dws, stream=stream))
+    # bytes: hit lists (lmax x 4), hits, chi2, direction, event, keep (24), the inverted index
+    # (lmax references per track, counted, filled and read: lmax x 12), offsets (8 per hit)
+    nbytes = nd * (wd.lmax * 16 + 24) + bd.n_hits * 8
+    ach = nbytes / (ms / 1000.0) / 1e9
+    res["duplicate_removal"] = {"kernel": "k_count_users, scan, k_fill_users, k_remove_duplicates", "bound": "hbm",
+                                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "ms": ms,
+                                "tracks": nd, "bytes": nbytes}
+    if learned is not None and "top_n=2" in learned and not args.no_cpu_baseline:
+        res["learned_find"] = learned_roofline(batch, ctx["wl"], learned)
+    return res
+
+
+def run_gpu(args, wl, batch):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    out = measure_workload(args, wl, batch, full=True)
+    ctx = out.pop("_ctx")
+    extras = ws == 1 and not args.no_extras
+    if extras:
+        import synth
+        kf = ctx["kf"]
+        # the largest configuration: barrel + disks, noise 100%, K = 8, plain and learned, autotuned
+        wh = synth.workload("hi_occ")
+        bh = synth.generate(wh)
+        hi = measure_workload(args, wh, bh, full=False, mlp_name="hi_occ")
+        hctx = hi.pop("_ctx")
+        for k in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline", "data"):
+            hi.pop(k, None)
+        out["hi_occ"] = hi
+        del hctx
+        torch.cuda.empty_cache()
+        # fitting over known hit sequences: the 1-event, 10-layer workload and the 100-event batch
+        out["fit_known_hits"] = {
+            "fit_small": fit_line(args, kf, synth.workload("fit_small"), synth.generate("fit_small"), ctx["stream"],
+                                  ctx["flush"]),
+            "fit_batched": fit_line(args, kf, wl, batch, ctx["stream"], ctx["flush"], d=ctx["d"]),
+        }
+        out["roofline"]["secondary"] = secondary_rooflines(args, kf, ctx, ctx["learned"])
+    for blk in (out, out.get("hi_occ", {})):
+        lv = blk.get("learned_vs_plain")
+        if isinstance(lv, dict):
+            lv.pop("_mlp", None)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def find_sources_sha1() -> str:
@@ -559,11 +809,12 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
                        "unit": "TFLOP/s", "frac": None, "traffic": None}
     else:
         # chi2 work: the hits of the windows the finder scans (limited to the phi sub-bins they touch)
-        n_prop, n_pass, n_upd, n_scan, n_win = counters
+        n_prop, n_pass, n_upd, n_scan, n_win = counters[:5]
         per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
         ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
-        profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and batch.wl.name == FIND_PROFILE["workload"]
-        traffic = FIND_PROFILE["dram_bytes_per_seed"] * n_seeds if profiled else None
+        bytes_seed = FIND_PROFILE["dram_bytes_per_seed"].get(batch.wl.name)
+        profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and bytes_seed is not None
+        traffic = bytes_seed * n_seeds if profiled else None
         per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak,
                        "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": traffic,
                        "traffic_unit": "bytes per launch (ncu, scaled by seeds)", "peak_note": f"FP32 {sm_mhz:.0f} MHz",
@@ -596,6 +847,11 @@ def main():
                     help="seed cleaning and duplicate-track removal in the step (on for combinatorial seeds)")
     ap.add_argument("--steering", action="store_true",
                     help="region steering lists (5 eta regions) instead of the geometric next-surface rule")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank its own events; strong: one fixed batch split over the ranks (LPT)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the main step (no high-occupancy block, fit lines or secondary rooflines)")
+    ap.add_argument("--fit-cpu-tracks", type=int, default=200000, help="oracle sample of the fit lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -607,10 +863,20 @@ def main():
         dist.init_process_group("nccl")
     import synth
     over = {"n_events": args.events} if args.events else {}
-    # weak scaling: every rank processes its own events (different seed), no data exchange
     from paper_1906_02253_gb300 import shard
-    wl = synth.workload(args.workload, seed=shard.rank_seed(synth.WORKLOADS[args.workload].seed, rank), **over)
-    batch = synth.generate(wl)
+    if args.scaling == "weak":
+        # every rank processes its own events (different seed), no data exchange
+        wl = synth.workload(args.workload, seed=shard.rank_seed(synth.WORKLOADS[args.workload].seed, rank), **over)
+        batch = synth.generate(wl)
+    else:
+        # one fixed batch; each rank takes its share of the events (greedy LPT on track counts)
+        import numpy as np
+        wl = synth.workload(args.workload, **over)
+        batch = synth.generate(wl)
+        if ws > 1 and args.impl != "reference":
+            counts = np.bincount(batch.track_event, minlength=batch.n_events)
+            batch = batch.select_events(shard.shard_events(counts, ws, rank))
+            wl = batch.wl
     if args.impl == "reference":
         run_reference(args, wl, batch)
         return

@@ -230,6 +230,21 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
                    int* hits_out, int* nhits_out, float* chi2_out, float* state_out, float* cov_out,
                    int* status_out, void* workspace, size_t workspace_bytes, kf_stream_t stream);
 
+/* Seed states alone (the first stage of kf_find_tracks; Sec. 2: each seed's track state from its
+ * three hits). Per seed: the circle through the three hits and the line through hits 1 and 3 give
+ * the state at hit 1 with the geometry's prior on hit 1's surface; the filter updates with hit 1,
+ * then propagates and updates through hits 2 and 3, as the fit does.
+ *   seed_hits, seed_event  as for kf_find_tracks; n_events: the batch's event count (a seed naming
+ *                          another event fails).
+ *   state_out  device float [28][n_seeds] (structure of arrays): p[6], packed C[21] at hit 3 and
+ *              chi2 (sum of the three predicted chi2); chi2 = -1 marks a seed that failed (invalid
+ *              hit id, event or surface, collinear hits, no crossing).
+ *   surf_out   device int [n_seeds]: surface of hit 3 (set for seeds that did not fail).
+ * Asynchronous on the stream; KF_ERR_ARG for a bad geometry, negative counts or null pointers. */
+int kf_seed_states(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* seed_hits,
+                   const int* seed_event, int n_seeds, int n_events, float* state_out, int* surf_out,
+                   kf_stream_t stream);
+
 /* Seed cleaning and duplicate-track removal. Seeds and tracks of one event that share a hit are
  * compared through an inverted index hit -> items built in the workspace; the decisions depend on
  * no processing order.

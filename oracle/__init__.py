@@ -277,7 +277,8 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     learned proposal keeps the top_n passing hits by score; ``steering`` (synth.steering_tables)
     replaces the geometric next-surface rule by the region lists. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
-    evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch)."""
+    evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch,
+    network evaluations of the learned proposal)."""
     lib = _load()
     wl = geom.wl
     prm = OrFindParams(wl.chi2_cut if chi2_cut is None else chi2_cut, wl.k_max if k_max is None else k_max,
@@ -291,7 +292,7 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     lmax = wl.lmax
     out = dict(hits=np.empty((n, lmax), np.int32), n_hits=np.empty(n, np.int32), chi2=np.empty(n),
                p=np.empty((n, 6)), cov=np.empty((n, 21)), status=np.empty(n, np.int32))
-    counters = np.zeros(5, np.int64)
+    counters = np.zeros(6, np.int64)
     lib.or_find(geom.ref, hits.ctypes.data, hs.ctypes.data, so.ctypes.data, batch.n_events, sh.ctypes.data,
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,

@@ -956,7 +956,7 @@ bool child_less(const Child& a, const Child& b) {
 }
 
 struct Counters {
-  long long n_prop = 0, n_chi2 = 0, n_upd = 0, n_scan = 0, n_win = 0;
+  long long n_prop = 0, n_chi2 = 0, n_upd = 0, n_scan = 0, n_win = 0, n_mlp = 0;
 };
 
 // Beam search for one seed. Returns false if the seed could not be formed.
@@ -1039,6 +1039,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
         for (const Found& fd : found) {
           pair_features(g, si, pred[ci], cx.hits[2 * fd.hit], cx.hits[2 * fd.hit + 1], f);
           sc.push_back({mlp_score(cx.mlp, f), fd.hit});
+          cnt.n_mlp++;
         }
         std::sort(sc.begin(), sc.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
           return a.first != b.first ? a.first > b.first : a.second < b.second;
@@ -1265,9 +1266,10 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 // that has more. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
 // status (0 ok, 1 seed failed). steering: region steering lists, or null for the geometric
-// next-surface rule. counters[5] += propagations, chi2 evaluations that passed the
+// next-surface rule. counters[6] += propagations, chi2 evaluations that passed the
 // cut, Kalman updates, hits whose chi2 was evaluated (whole bins of the windows), hits of the
-// windows limited to the phi sub-bins their phi range touches.
+// windows limited to the phi sub-bins their phi range touches, network evaluations of the learned
+// proposal.
 void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long long* slab_off, int n_events,
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
@@ -1278,7 +1280,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
   Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}, steering};
   cx.n_hits = slab_off[static_cast<long long>(n_events) * g->n_surf];
   cx.n_events = n_events;
-  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0);
+  std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0), c_mlp(0);
   parallel_for(n, n_threads, [&](long long i) {
     Cand best;
     Counters cnt;
@@ -1294,6 +1296,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     c_scan += cnt.n_scan;
     c_win += cnt.n_win;
     c_upd += cnt.n_upd;
+    c_mlp += cnt.n_mlp;
   });
   if (counters) {
     counters[0] += c_prop.load();
@@ -1301,6 +1304,7 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
     counters[2] += c_upd.load();
     counters[3] += c_scan.load();
     counters[4] += c_win.load();
+    counters[5] += c_mlp.load();
   }
 }
 

@@ -66,7 +66,7 @@ class KfFindParams(ctypes.Structure):
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
-           "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe")
+           "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe", "kf_seed_states")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
             lib.kf_remove_duplicates.argtypes = [P, P, P, P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]
             lib.kf_fp32_fma_probe.restype = I
             lib.kf_fp32_fma_probe.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_longlong), P]
+            lib.kf_seed_states.restype = I
+            lib.kf_seed_states.argtypes = [G, P, P, P, P, I, I, P, P, P]
             lib.kf_math_probe.restype = I
             lib.kf_math_probe.argtypes = [I, P, P, I, P, P, P, P]
             lib.kf_status_string.restype = ctypes.c_char_p
@@ -348,6 +350,22 @@ def math_probe(fn: int, a, b=None, stream=None):
     _check(lib.kf_math_probe(int(fn), _ptr(a), _ptr(b), a.numel(), _ptr(o[0]), _ptr(o[1]), _ptr(o[2]), _stream(stream)),
            "kf_math_probe")
     return tuple(o)
+
+
+def seed_states(geom: Geometry, hits, hit_surface, seed_hits, seed_event, n_events: int, out=None, stream=None):
+    """kf_seed_states: the fitted state of every seed at its third hit. Returns (state [28, n]
+    float32: p[6], packed C[21], chi2 (-1: failed seed), surface [n] int32 of hit 3)."""
+    for t, nm in ((hit_surface, "hit_surface"), (seed_hits, "seed_hits"), (seed_event, "seed_event")):
+        _cuda(t, torch.int32, nm)
+    _cuda(hits, torch.float32, "hits")
+    n = seed_hits.shape[1]
+    if out is None:
+        out = (torch.empty((28, n), dtype=torch.float32, device=hits.device),
+               torch.empty(n, dtype=torch.int32, device=hits.device))
+    _check(load_library().kf_seed_states(geom.ref, _ptr(hits), _ptr(hit_surface), _ptr(seed_hits), _ptr(seed_event),
+                                         n, int(n_events), _ptr(out[0]), _ptr(out[1]), _stream(stream)),
+           "kf_seed_states")
+    return out
 
 
 def find_workspace_size(n_seeds: int, params: KfFindParams) -> int:

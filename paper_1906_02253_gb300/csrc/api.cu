@@ -360,6 +360,32 @@ int kf_find_tracks(const KfGeometry* geom, const KfHitIndex* index, const float*
   return launch_find(G, M, A, plan, workspace, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int kf_seed_states(const KfGeometry* geom, const float* hits, const int* hit_surface, const int* seed_hits,
+                   const int* seed_event, int n_seeds, int n_events, float* state_out, int* surf_out,
+                   kf_stream_t stream) {
+  DevGeom G;
+  int rc = pack_geometry(geom, &G);
+  if (rc != KF_OK) return rc;
+  DevMat M;
+  rc = pack_material(geom, &M);
+  if (rc != KF_OK) return rc;
+  if (n_seeds < 0 || n_events < 0) return KF_ERR_ARG;
+  if (n_seeds == 0) return KF_OK;
+  if (!hits || !hit_surface || !seed_hits || !seed_event || !state_out || !surf_out) return KF_ERR_ARG;
+  FindArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.hits = reinterpret_cast<const float2*>(hits);
+  A.hit_surface = hit_surface;
+  A.seed_hits = seed_hits;
+  A.seed_event = seed_event;
+  A.n_seeds = n_seeds;
+  A.n_events = n_events;
+  A.lmax = 4;
+  A.seed_state = state_out;
+  A.seed_surf = surf_out;
+  return launch_seed_states(G, M, A, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream) {
   if (n < 0 || (n > 0 && (!params || !features || !logits))) return KF_ERR_ARG;
   return launch_mlp_forward(params, features, n, logits, reinterpret_cast<cudaStream_t>(stream));

@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(128) k_seed_states(DevGeom G, const __grid_con
     A.seed_surf[seed] = ss[2];
   } else {
     out[static_cast<size_t>(27) * n] = -1.f;
+    if (!A.hits_out) return;  // seed states alone (kf_seed_states): no track outputs
     const float nanf_ = __int_as_float(0x7fc00000);
     for (int k = 0; k < A.lmax; ++k) A.hits_out[static_cast<size_t>(k) * n + seed] = -1;
     A.nhits_out[seed] = 0;
@@ -1096,6 +1097,11 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   plan->off_mlp = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
   plan->ws_bytes = learned ? up(plan->off_mlp + static_cast<size_t>(kMlpParamsAll) * sizeof(float)) : plan->off_mlp;
   return KF_OK;
+}
+
+int launch_seed_states(const DevGeom& G, const DevMat& M, const FindArgs& A, cudaStream_t stream) {
+  k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, M, A);
+  return cudaGetLastError() == cudaSuccess ? KF_OK : KF_ERR_CUDA;
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -55,6 +55,8 @@ inline int find_features(const DevGeom& G, const DevMat& M) {
   return (G.steer != 0 ? 1 : 0) | ((M.map_on != 0 || M.eloss > 0.f) ? 2 : 0) | (G.field_on != 0 ? 4 : 0);
 }
 int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& plan, void* ws, cudaStream_t stream);
+// The seed-state kernel alone (A.hits_out null: failed seeds get chi2 = -1 only).
+int launch_seed_states(const DevGeom& G, const DevMat& M, const FindArgs& A, cudaStream_t stream);
 // Device address of the library's fixed finder scratch on the current device (looked up on the
 // first call per device; no allocation).
 int static_scratch(void** ptr);

@@ -158,7 +158,8 @@ def test_window_counters_are_ordered(wl_name):
     b = synth.generate(wl)
     sh, st = b.seeds()
     c = oracle.find(g, b, sh, b.track_event[st])["counters"]
-    n_prop, n_pass, n_upd, n_scan, n_win = (int(v) for v in c)
+    n_prop, n_pass, n_upd, n_scan, n_win, n_mlp = (int(v) for v in c)
+    assert n_mlp == 0  # plain finding evaluates no network
     n_window_pass = n_pass - 3 * len(st)  # the pass counter includes the three seed-hit updates
     assert 0 < n_window_pass <= n_win <= n_scan
     assert n_win < n_scan  # the sub-bins cut the scan on these windows

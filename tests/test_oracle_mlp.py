@@ -80,6 +80,7 @@ def test_learned_with_large_top_n_is_plain_finding():
     plain = oracle.find(g, b, sh, b.track_event[st])
     learned = oracle.find(g, b, sh, b.track_event[st], mlp=_mlp_for(F), top_n=1000)
     assert np.array_equal(plain["hits"], learned["hits"])
+    assert learned["counters"][5] == 0  # no window has more passing hits than top_n
 
 
 def test_learned_top1_matches_a_plain_loop():
@@ -118,6 +119,7 @@ def test_learned_top1_matches_a_plain_loop():
                 break
         assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
     assert pruned > 10
+    assert f["counters"][5] >= 2 * pruned  # every pruned window scores at least two hits
 
 
 def test_disk_z_variance_feature_is_the_floor():
