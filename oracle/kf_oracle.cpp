@@ -730,6 +730,7 @@ struct Mlp {
   const double* mean = nullptr;
   const double* sd = nullptr;
   int top_n = 0;               // 0: plain finding
+  double margin = 0.0;         // > 0: score margin rule (below)
 };
 
 double mlp_forward(const double* w, const double* xs, double* h1 = nullptr, double* h2 = nullptr) {
@@ -1032,8 +1033,11 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
           sink->labels.push_back(sink->hit_sim[fd.hit] == sink->seed_track ? 1.f : 0.f);
         }
       }
-      if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > cx.mlp.top_n) {
-        // Learned proposal: keep the top_n passing hits by MLP score (ties: lower hit id).
+      const bool margin_rule = cx.mlp.margin > 0.0;
+      if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > (margin_rule ? 1 : cx.mlp.top_n)) {
+        // Learned proposal: rank the passing hits by MLP score (ties: lower hit id) and keep the
+        // top_n; with a score margin, only those of them that score within the margin of the best
+        // (the best is always kept), so a window whose best hit stands out keeps one child.
         std::vector<std::pair<double, int>> sc;
         double f[kIn];
         for (const Found& fd : found) {
@@ -1045,9 +1049,11 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
           return a.first != b.first ? a.first > b.first : a.second < b.second;
         });
         std::vector<Found> kept;
-        for (int k = 0; k < cx.mlp.top_n; ++k)
+        for (int k = 0; k < cx.mlp.top_n && k < static_cast<int>(sc.size()); ++k) {
+          if (margin_rule && k > 0 && sc[k].first < sc[0].first - cx.mlp.margin) break;
           for (const Found& fd : found)
             if (fd.hit == sc[k].second) kept.push_back(fd);
+        }
         found.swap(kept);
       }
       if (!found.empty()) {
@@ -1263,7 +1269,8 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 
 // Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. With mlp_w set and
 // top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
-// that has more. Outputs per
+// that has more; with score_margin > 0, of each window with two or more passing hits, the hits
+// among its top_n that score within score_margin of its best. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
 // status (0 ok, 1 seed failed). steering: region steering lists, or null for the geometric
 // next-surface rule. counters[6] += propagations, chi2 evaluations that passed the
@@ -1274,10 +1281,11 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
              long long* counters, const double* mlp_w, const double* mlp_mean, const double* mlp_sd, int top_n,
-             const OrSteering* steering) {
+             const OrSteering* steering, double score_margin) {
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
-  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0}, steering};
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0, score_margin},
+         steering};
   cx.n_hits = slab_off[static_cast<long long>(n_events) * g->n_surf];
   cx.n_events = n_events;
   std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0), c_mlp(0);

@@ -226,3 +226,68 @@ def test_pull_features_of_true_hits_have_unit_width():
     assert len(x) > 10000
     assert np.all(np.abs(x.mean(0)) < 0.03), x.mean(0)
     assert np.all(np.abs(x.std(0) - 1.0) < 0.03), x.std(0)
+
+
+def test_score_margin_limits_reduce_to_the_top_n_rule():
+    """The score-margin rule at its limits: a margin larger than any score gap keeps the top_n of
+    every window (the top_n rule, though windows of 2..top_n passing hits are now scored too); a
+    vanishing margin keeps only the best-scoring hit (the top 1 rule, score ties having probability
+    zero)."""
+    wl = synth.workload("find", n_events=2, tracks_lo=400, tracks_hi=400, noise_frac=3.0, seed=43)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    top2 = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2)
+    wide = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, score_margin=1e9)
+    assert np.array_equal(top2["hits"], wide["hits"])
+    assert wide["counters"][5] > top2["counters"][5]  # windows of two passing hits are scored too
+    top1 = oracle.find(g, b, sh, ev, mlp=mlp, top_n=1)
+    narrow = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, score_margin=1e-12)
+    assert np.array_equal(top1["hits"], narrow["hits"])
+    assert not np.array_equal(top1["hits"], top2["hits"])
+
+
+def test_score_margin_matches_a_plain_loop():
+    """K = 1, top_n = 3, margin 0.7: at every step the kept hits are those among the three best
+    scoring passing hits that score within 0.7 of the best, and the surviving child is the kept hit
+    of lowest chi2."""
+    import test_oracle_find as tf
+    wl = synth.workload("find", n_events=2, tracks_lo=40, tracks_hi=40, noise_frac=80.0, seed=44)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    margin = 0.7
+    f = oracle.find(g, b, sh, ev, k_max=1, mlp=mlp, top_n=3, score_margin=margin)
+    multi = 0
+    for i in range(len(st)):
+        p, C, _ = tf._seed_fit(g, b, sh[i])
+        hits, n_miss = list(sh[i]), 0
+        while len(hits) < wl.lmax:
+            e = tf._expand(g, b, wl, ev[i], p, C)
+            if e is None:
+                break
+            surf, pp, CC, ids, c2 = e
+            if len(ids) > 1:
+                feats = np.array([oracle.pair_features(g, surf, pp, CC, b.hits[h]) for h in ids])
+                sc = oracle.mlp_forward(mlp[0], (feats - mlp[1]) / mlp[2])
+                order = sorted(range(len(ids)), key=lambda k: (-sc[k], ids[k]))[:3]
+                keep = [k for k in order if sc[k] >= sc[order[0]] - margin]
+                multi += len(keep) > 1
+                ids, c2 = ids[keep], c2[keep]
+            if len(ids):
+                best = sorted(range(len(ids)), key=lambda k: (c2[k], ids[k]))[0]
+                p, C, _ = oracle.update(g, pp, CC, surf, b.hits[ids[best]])
+                hits.append(int(ids[best]))
+            elif n_miss < wl.max_miss:
+                p, C, n_miss = pp, CC, n_miss + 1
+                hits.append(-1)
+            else:
+                break
+        assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
+    assert multi > 5  # the margin kept several hits in some windows
