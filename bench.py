@@ -520,8 +520,9 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
            "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain,
                      "block_threads": prm.block_threads, "k_capacity": prm.k_capacity}}
     best = None
-    for top_n in (1, 2, 4):
-        lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n)
+    for top_n, margin in ((1, 0.0), (2, 0.0), (4, 0.0), (2, 1.0), (2, 2.0), (3, 2.0)):
+        lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n,
+                            score_margin=margin)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
         lp.seed_keep, lp._keep_ref = prm.seed_keep, getattr(prm, "_keep_ref", None)  # same seeds
         lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
@@ -546,9 +547,10 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
              "efficiency": e, "fake_rate": f, "efficiency_loss": eff_plain - e,
              "block_threads": lp.block_threads, "k_capacity": lp.k_capacity}
         r["speedup_vs_plain"] = r["find_seeds_per_s"] / res["plain"]["find_seeds_per_s"]
-        res[f"top_n={top_n}"] = r
+        name = f"top_n={top_n}" + (f",margin={margin:g}" if margin > 0 else "")
+        res[name] = r
         if r["efficiency_loss"] <= 0.005 and (best is None or r["find_seeds_per_s"] > res[best]["find_seeds_per_s"]):
-            best = f"top_n={top_n}"
+            best = name
     res["best_within_0.5pct_eff_loss"] = best
     res["_mlp"] = (z["weights"], z["mean"], z["sd"])
     return res

@@ -161,6 +161,11 @@ typedef struct {
   /* Optional device int [n_seeds] (kf_clean_seeds' keep_out): seeds with 0 are not processed;
    * their outputs are empty (no hits, NaN state) with status 2. NULL: every seed. */
   const int* seed_keep;
+  /* Learned proposal with a score margin (> 0; 0 keeps the top_n rule above): of a window with two
+   * or more passing hits, only those among its top_n by score that score within score_margin (in
+   * logit units) of its best make children, the best always. A window whose best hit stands out then
+   * keeps one child. */
+  float score_margin;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,

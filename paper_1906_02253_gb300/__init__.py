@@ -60,7 +60,8 @@ class KfFindParams(ctypes.Structure):
     _fields_ = [("chi2_cut", ctypes.c_float), ("k_max", ctypes.c_int), ("max_miss", ctypes.c_int),
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int),
-                ("steering", ctypes.POINTER(KfSteering)), ("seed_keep", ctypes.c_void_p)]
+                ("steering", ctypes.POINTER(KfSteering)), ("seed_keep", ctypes.c_void_p),
+                ("score_margin", ctypes.c_float)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
@@ -251,10 +252,10 @@ def steering(tables: dict) -> KfSteering:
 
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
                 blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0,
-                steering_tables: dict = None, seed_keep=None) -> KfFindParams:
+                steering_tables: dict = None, seed_keep=None, score_margin: float = 0.0) -> KfFindParams:
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
     ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
-    next-surface rule."""
+    next-surface rule; ``score_margin`` > 0 switches the learned proposal to its score-margin rule."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
@@ -264,7 +265,8 @@ def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_thr
         _cuda(seed_keep, torch.int32, "seed_keep")
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
                        None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity),
-                       None if st is None else ctypes.pointer(st), None if seed_keep is None else seed_keep.data_ptr())
+                       None if st is None else ctypes.pointer(st), None if seed_keep is None else seed_keep.data_ptr(),
+                       float(score_margin))
     prm._mlp_ref = mlp  # keep the buffers alive with the parameters
     prm._steer_ref = st
     prm._keep_ref = seed_keep

@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
   const float* __restrict__ wmlp = A.mlp_t;  // transposed network parameters (L1/L2)
   const int keep = LEARNED ? A.top_n : A.k_max;  // capacity of a lane's list during the scan
+  const bool margin_on = LEARNED && A.score_margin > 0.f;
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
   const int gbase = in_grp ? grp * KC : lane;
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       }
       const int start = run - my_cnt;
       if (LEARNED) {
-        const bool need = !final_flush || scored || hl_n + my_cnt > keep;
+        const bool need = !final_flush || scored || hl_n + my_cnt > (margin_on ? 1 : keep);
         const unsigned needmask = __ballot_sync(kFull, need && my_cnt > 0);
         if (needmask) {
           // Every lane's raw candidate features (predicted state, log covariance diagonal) and the
@@ -846,7 +847,15 @@ __global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ 
       if (!more) break;
       __syncwarp();
     }
-    // With the learned proposal the kept hits are reordered by chi2 for the ranking below.
+    // With the learned proposal the kept hits are reordered by chi2 for the ranking below; with a
+    // score margin, the scored ones (kept in score order) are first cut to those within the margin
+    // of the best.
+    if (LEARNED && margin_on && scored) {
+      const float floor_sc = WL.hl_sc[0][lane] - A.score_margin;
+      int k = 1;
+      while (k < hl_n && !(WL.hl_sc[k][lane] < floor_sc)) ++k;
+      hl_n = min(hl_n, k);
+    }
     if (LEARNED && hl_n > 0) hl_sort_by_chi2(W, lane, hl_n, cap);
     // Outcome of each propagated candidate; keep the prediction for its children.
     if (kind == 1) {
@@ -1022,6 +1031,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   if (!(p->chi2_cut > 0.f)) return KF_ERR_ARG;
   const bool learned = p->mlp != nullptr && p->top_n > 0;
   if (p->top_n < 0 || p->top_n > KF_MAX_K) return KF_ERR_ARG;
+  if (!(p->score_margin >= 0.f) || !(p->score_margin < 3.4e38f)) return KF_ERR_ARG;
   if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32))
     return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;

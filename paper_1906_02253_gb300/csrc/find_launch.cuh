@@ -26,6 +26,7 @@ struct FindArgs {
   const float* mlp_t;  // their transposed copy in the workspace (set by launch_find)
   const int* seed_keep;  // seeds with 0 are skipped (status 2), or null
   int top_n;         // > 0 with mlp: keep the top_n passing hits by score
+  float score_margin;  // > 0: of those, only the ones within this margin of the window's best score
   int* hits_out;
   int* nhits_out;
   float* chi2_out;

@@ -79,11 +79,12 @@ def test_gpu_training_lowers_the_loss(kf, pairs):
     assert hist[-1] < 0.8 * first, (first, hist)
 
 
-def _find(kf, wl, b, buf, top_n, k, steering=None):
+def _find(kf, wl, b, buf, top_n, k, steering=None, margin=0.0):
     g = kf.Geometry(wl)
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
-    prm = kf.find_params(wl.chi2_cut, k, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, steering_tables=steering)
+    prm = kf.find_params(wl.chi2_cut, k, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, steering_tables=steering,
+                         score_margin=margin)
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
     torch.cuda.synchronize()
     return {kk: v.cpu().numpy() for kk, v in out.items() if kk != "workspace"}
@@ -139,6 +140,43 @@ def test_learned_finding_with_region_steering_and_material_matches_oracle(kf, pa
     assert np.array_equal(gpu["status"], ora["status"])
     plain = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], k_max=8, steering=tab)
     assert (plain["hits"] != ora["hits"]).any(axis=1).sum() > 0  # the pruning acted
+
+
+@pytest.mark.parametrize("name,net,margin,top_n,k", [
+    ("find", None, 0.7, 3, 6),
+    ("hi_occ", "mlp_hi_occ.npz", 1.0, 2, 8),
+    ("learned", "mlp_learned.npz", 2.0, 2, 6),
+])
+def test_learned_finding_with_score_margin_matches_oracle(kf, pairs, name, net, margin, top_n, k):
+    """The score-margin rule on the GPU against the oracle's: hit lists identical on >= 99.9% of the
+    seeds (scores compared in FP32 against FP64 at the margin's edge), with a random network on a
+    noisy barrel and with the trained networks on their workloads."""
+    import os
+    if net is None:
+        w, mean, sd = synth.mlp_init(12), pairs[2], pairs[3]
+        wl = synth.workload(name, n_events=2, tracks_lo=1500, tracks_hi=2500, noise_frac=2.0, seed=45)
+    else:
+        z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+        w, mean, sd = z["weights"], z["mean"], z["sd"]
+        wl = synth.workload(name, n_events=3, seed=46)
+    b = synth.generate(wl)
+    gpu = _find(kf, wl, b, kf.mlp_buffer(w, mean, sd), top_n, k, margin=margin)
+    sh, st = b.seeds()
+    mlp = (np.asarray(w, np.float64), np.asarray(mean, np.float64), np.asarray(sd, np.float64))
+    ora = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], k_max=k, mlp=mlp, top_n=top_n,
+                      score_margin=margin)
+    same = (gpu["hits"].T == ora["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    no_margin = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], k_max=k, mlp=mlp, top_n=top_n)
+    assert (no_margin["hits"] != ora["hits"]).any(axis=1).sum() > 20  # the margin pruned more
+
+
+def test_score_margin_wider_than_any_gap_is_the_top_n_rule_on_gpu(kf, pairs):
+    _, _, mean, sd = pairs
+    wl = synth.workload("find", n_events=2, tracks_lo=1000, tracks_hi=1500, noise_frac=2.0, seed=47)
+    b = synth.generate(wl)
+    buf = kf.mlp_buffer(synth.mlp_init(13), mean, sd)
+    assert np.array_equal(_find(kf, wl, b, buf, 2, 6)["hits"], _find(kf, wl, b, buf, 2, 6, margin=1e9)["hits"])
 
 
 @pytest.mark.parametrize("name,trained_file,events,min_gain", [
