@@ -60,9 +60,9 @@ FLOP_MLP_BWD = 2 * (64 * 64 + 64 * 64 + 64 * 14 + 64)
 # flags are the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "50c5dbfadcdb61f96ca2e45a03b5e42bcd425d47",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": 160558848 / 302063,
-                                        "find_200ev_barrel_disks_noise100": 174701568 / 211523}}
+FIND_PROFILE = {"sources_sha1": "e0da6a1efc949f6f8eaed8794666f4e2706a52cc",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": 160237312 / 302063,
+                                        "find_200ev_barrel_disks_noise100": 174745088 / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36

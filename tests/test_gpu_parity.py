@@ -301,10 +301,26 @@ def _assert_find_parity(b, gpu, ora, st):
     assert abs(e_g - e_o) <= 0.001
     # identical tracks carry the same fit
     ok = same & (ora["status"] == 0)
-    rel = _state_rel_err(gpu["state"].T[ok], ora["p"][ok])
-    assert np.quantile(rel.max(axis=1), 0.999) < 1e-4
-    c2r = np.abs(gpu["chi2"][ok] - ora["chi2"][ok]) / np.maximum(ora["chi2"][ok], 1.0)
-    assert np.quantile(c2r, 0.999) < 1e-3
+    _assert_track_state_parity(gpu["state"].T[ok], gpu["chi2"][ok], ora["p"][ok], ora["cov"][ok], ora["chi2"][ok])
+
+
+def _assert_track_state_parity(p_gpu, chi2_gpu, p_ora, cov_ora, chi2_ora):
+    """Tracks with identical hit lists carry the fit bars on every track: 1e-4 relative on the
+    state, 1e-3 on chi2 (measured maxima over the test workloads: 4e-5 and 2.3e-4); kappa, phi and
+    theta also within 1e-2 of their own standard deviations (measured: 2e-3)."""
+    rel = _state_rel_err(p_gpu, p_ora)
+    worst = rel.max(axis=1)
+    print(f"state: max {worst.max():.2e}, 99.9% {np.quantile(worst, 0.999):.2e}")
+    assert worst.max() < 1e-4, rel.max(axis=0)
+    sig = np.sqrt(np.diagonal(oracle.unpack_cov(cov_ora), axis1=1, axis2=2))[:, 3:]
+    dp = p_gpu[:, 3:].astype(np.float64) - p_ora[:, 3:]
+    dp[:, 1] = _wrap(dp[:, 1])
+    pulls = np.abs(dp) / sig
+    print(f"kappa, phi, theta in sigma: max {pulls.max(axis=0)}")
+    assert pulls.max() < 1e-2, pulls.max(axis=0)
+    c2r = np.abs(chi2_gpu - chi2_ora) / np.maximum(chi2_ora, 1.0)
+    print(f"chi2: max {c2r.max():.2e}, 99.9% {np.quantile(c2r, 0.999):.2e}")
+    assert c2r.max() < 1e-3, c2r.max()
 
 
 @pytest.mark.parametrize("wl_name,n_ev,nt,k", [("find", 2, 2500, 6), ("find", 2, 2500, 1), ("hi_occ", 2, 1500, 8),
