@@ -54,6 +54,14 @@ FLOP_PROP, FLOP_TRANSPORT, FLOP_UPDATE, FLOP_CHI2, FLOP_SEED = 150, 320, 260, 20
 # (bias sums, ReLU masks and the sigmoid not counted).
 FLOP_MLP_FWD = 2 * (14 * 64 + 64 * 64 + 64)
 FLOP_MLP_BWD = 2 * (64 * 64 + 64 * 64 + 64 * 14 + 64)
+# Both network kernels run their contractions on the tensor cores with every operand split into
+# three bf16 parts and six MMAs per product (FP32-faithful), so their roofline is the measured bf16
+# tensor peak / 6. MMA flops they issue per sample (M = 128 samples per tile, inputs padded to 16):
+# forward 6 x 2 (16 x 64 + 64 x 64); loss-gradient adds E2 W2 (6 x 2 x 64 x 64) and the weight-gradient
+# product [e2 | e1]^T [h1 | x | 1 | 0] (6 x 2 x 128 x 96).
+MLP_SPLIT_MMAS = 6
+MMA_MLP_FWD = MLP_SPLIT_MMAS * 2 * (16 * 64 + 64 * 64)
+MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch, per seed) on a smaller case of each workload (30 events of the 100-event workload, 40 of
 # the barrel + disk workload; profiles/k_find_tracks_*), valid while the finder's sources and build
@@ -660,7 +668,7 @@ def fit_line(args, kf, wl, batch, stream, flush, d=None):
 def secondary_rooflines(args, kf, ctx, learned):
     """Rooflines of the kernels besides index, finder and fit, each timed live with CUDA events on
     its stream: the seed states (FP32 ALU), the network's forward and loss-gradient kernels on a
-    synthetic feature batch (FP32 ALU), seed cleaning and duplicate removal on the module-overlap
+    synthetic feature batch (tensor cores), seed cleaning and duplicate removal on the module-overlap
     workload (HBM, their algorithmic bytes), and the learned finder."""
     import numpy as np
     import torch
@@ -687,15 +695,23 @@ def secondary_rooflines(args, kf, ctx, learned):
     logits = torch.empty(rows, device=d["hits"].device)
     grad = torch.empty(kf.MLP_PARAMS, device=d["hits"].device)
     loss = torch.empty(1, device=d["hits"].device)
-    ms = _timed(args, stream, flush, lambda: kf.mlp_forward(params, feats, out=logits, stream=stream))
-    ach = FLOP_MLP_FWD * rows / (ms / 1000.0) / 1e12
-    res["mlp_forward"] = {"kernel": "k_mlp_forward", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                          "frac": ach / peak, "ms": ms, "rows": rows, "flop_per_row": FLOP_MLP_FWD}
-    ms = _timed(args, stream, flush, lambda: kf.mlp_loss_grad(params, feats, labels, grad=grad, loss=loss, stream=stream))
-    ach = (FLOP_MLP_FWD + FLOP_MLP_BWD) * rows / (ms / 1000.0) / 1e12
-    res["mlp_loss_grad"] = {"kernel": "k_mlp_loss_grad", "bound": "alu", "achieved": ach, "peak": peak,
-                            "unit": "TFLOP/s", "frac": ach / peak, "ms": ms, "rows": rows,
-                            "flop_per_row": FLOP_MLP_FWD + FLOP_MLP_BWD}
+    pk = _peaks()
+    bf16 = pk.get("bf16_tflops") or 1900.0
+    split_peak = bf16 / MLP_SPLIT_MMAS
+    for key, kern, fn, alg, mma in (
+            ("mlp_forward", "k_mlp_forward", lambda: kf.mlp_forward(params, feats, out=logits, stream=stream),
+             FLOP_MLP_FWD, MMA_MLP_FWD),
+            ("mlp_loss_grad", "k_mlp_loss_grad",
+             lambda: kf.mlp_loss_grad(params, feats, labels, grad=grad, loss=loss, stream=stream),
+             FLOP_MLP_FWD + FLOP_MLP_BWD, MMA_MLP_GRAD)):
+        ms = _timed(args, stream, flush, fn)
+        ach = alg * rows / (ms / 1000.0) / 1e12
+        mma_t = mma * rows / (ms / 1000.0) / 1e12
+        res[key] = {"kernel": kern, "bound": "tensor", "achieved": ach, "peak": split_peak, "unit": "TFLOP/s",
+                    "frac": ach / split_peak, "ms": ms, "rows": rows, "flop_per_row": alg,
+                    "peak_basis": ("measured bf16 tensor peak / 6 (three-part bf16 split, six MMAs per product)"
+                                   if "bf16_tflops" in pk else "fallback bf16 peak / 6"),
+                    "mma_tflops": mma_t, "mma_frac_of_bf16_peak": mma_t / bf16, "mma_flop_per_row": mma}
     # seed cleaning and duplicate removal on the module-overlap workload
     wd = synth.workload("duplicates")
     bd = synth.generate(wd)

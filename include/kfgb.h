@@ -294,12 +294,18 @@ int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* c
 #define KF_MLP_PARAMS 5185
 #define KF_MLP_BUFFER 5213
 
-/* Logits of n feature rows (features float [n][14], raw, standardised inside). */
+/* Logits of n feature rows (features float [n][14], raw, standardised inside; 8-byte aligned, else
+ * KF_ERR_ARG). The two layers run on the tensor cores (tcgen05) with FP32-faithful products: each
+ * operand is split into two bf16 parts, hi = bf16(v) and lo = bf16(v - hi), and hi*hi + hi*lo +
+ * lo*hi is accumulated in FP32 (relative operand error <= 2^-18). A tile whose tensor-core wait
+ * gives up (one second) gets NaN logits. */
 int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream);
 
 /* Mean binary cross-entropy with logits over n samples (labels 0 or 1) and its gradient with
  * respect to the KF_MLP_PARAMS weights: grad float [KF_MLP_PARAMS] and loss float [1] are
- * overwritten. */
+ * overwritten. Features as for kf_mlp_forward (8-byte aligned). The forward layers, the
+ * back-propagation through W2 and the weight gradients of W1, b1, W2, b2 run on the tensor cores
+ * with the same FP32-faithful split; a tensor-core wait that gives up makes the loss NaN. */
 int kf_mlp_loss_grad(const float* params, const float* features, const float* labels, int n, float* grad,
                      float* loss, kf_stream_t stream);
 

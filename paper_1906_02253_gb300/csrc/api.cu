@@ -389,12 +389,14 @@ int kf_seed_states(const KfGeometry* geom, const float* hits, const int* hit_sur
 
 int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream) {
   if (n < 0 || (n > 0 && (!params || !features || !logits))) return KF_ERR_ARG;
+  if (reinterpret_cast<size_t>(features) & 7) return KF_ERR_ARG;  // rows are read as float pairs
   return launch_mlp_forward(params, features, n, logits, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int kf_mlp_loss_grad(const float* params, const float* features, const float* labels, int n, float* grad,
                      float* loss, kf_stream_t stream) {
   if (n < 0 || !params || !grad || !loss || (n > 0 && (!features || !labels))) return KF_ERR_ARG;
+  if (reinterpret_cast<size_t>(features) & 7) return KF_ERR_ARG;  // rows are read as float pairs
   return launch_mlp_loss_grad(params, features, labels, n, grad, loss, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -4,22 +4,213 @@
 //
 // Parameter buffer (FP32): W1[64][14], b1[64], W2[64][64], b2[64], W3[64], b3, then the feature
 // normaliser mean[14], sd[14] (KF_MLP_PARAMS weights + 28).
+#include <algorithm>
+
 #include "mlp.cuh"
+#include "tc.cuh"
 
 namespace kfgb {
 
-// Inference: one thread per sample, weights staged in shared memory.
-__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ params, const float* __restrict__ feats,
-                                                     int n, float* __restrict__ logits) {
-  __shared__ float w[kMlpParamsAll];
-  for (int i = threadIdx.x; i < kMlpParamsAll; i += blockDim.x) w[i] = params[i];
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  float x[kMlpIn];
+// Inference on the tensor cores (tcgen05): a persistent CTA of 128 threads takes tiles of 128
+// samples, one sample per thread. Per tile: standardised inputs -> X tile (128 x 16); D1 = X W1^T
+// in tensor memory; h1 = relu(D1 + b1) -> H tile (128 x 64); D2 = H W2^T; logit = b3 + sum_j W3[j]
+// relu(D2[j] + b2[j]) on the CUDA cores. Every operand is three bf16 tiles (hi, mid, lo; tc.cuh).
+// Shared memory (bytes): X, W1, W2 and H, then b1, b2, W3, mean, sd, b3, the mbarrier and the
+// tensor-memory base; 128 tensor-memory columns (D1 at 0, D2 at 64).
+namespace fwd {
+constexpr uint32_t X_T = 4096, W1_T = 2048, W2_T = 8192, H_T = 16384;  // bytes of one tile
+constexpr uint32_t X = 0, W1 = X + 3 * X_T, W2 = W1 + 3 * W1_T, H = W2 + 3 * W2_T, B1 = H + 3 * H_T, B2 = B1 + 256,
+                   W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, B3 = SD + 64, BAR = B3 + 8, TMEM = BAR + 8,
+                   BYTES = TMEM + 8;
+constexpr uint32_t kCols = 128;
+}  // namespace fwd
+constexpr int kTcM = 128;   // samples per tile (the MMA's M), one per thread
+constexpr int kTcK1 = 16;   // the 14 inputs padded to one MMA K step
+constexpr int kFwdCtasPerSm = 2;
+
+// Loads W1 (64 x 16, inputs 14 and 15 zero) and W2 (64 x 64) as the MMAs' B operands in the
+// K-major core-matrix layout, by all threads of the block.
+__device__ __forceinline__ void stage_weights_b(const float* __restrict__ params, unsigned char* w1, uint32_t w1_t,
+                                                unsigned char* w2, uint32_t w2_t) {
+  for (int item = threadIdx.x; item < kMlpHid * 2; item += blockDim.x) {
+    const int j = item >> 1, c = item & 1;
+    float v[8];
 #pragma unroll
-  for (int i = 0; i < kMlpIn; ++i) x[i] = feats[static_cast<size_t>(s) * kMlpIn + i];
-  logits[s] = mlp_logit(w, x);
+    for (int e = 0; e < 8; ++e) {
+      const int i = 8 * c + e;
+      v[e] = i < kMlpIn ? params[kMlpW1 + j * kMlpIn + i] : 0.f;
+    }
+    tc::store8_split(w1, w1_t, tc::kmajor_off(j, c, kTcK1), v);
+  }
+  for (int item = threadIdx.x; item < kMlpHid * 8; item += blockDim.x) {
+    const int o = item >> 3, c = item & 7;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = params[kMlpW2 + o * kMlpHid + 8 * c + e];
+    tc::store8_split(w2, w2_t, tc::kmajor_off(o, c, kMlpHid), v);
+  }
+}
+
+// Standardised inputs of sample r (zeros past n) into x[16] (inputs 14 and 15 zero).
+__device__ __forceinline__ void load_inputs(const float* __restrict__ feats, int r, int n, const float* mean,
+                                            const float* sd, float* x) {
+  if (r < n) {
+    const float2* f2 = reinterpret_cast<const float2*>(feats + static_cast<size_t>(r) * kMlpIn);
+#pragma unroll
+    for (int i = 0; i < kMlpIn / 2; ++i) {
+      const float2 f = __ldg(f2 + i);
+      x[2 * i] = (f.x - mean[2 * i]) / sd[2 * i];
+      x[2 * i + 1] = (f.y - mean[2 * i + 1]) / sd[2 * i + 1];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) x[i] = 0.f;
+  }
+  x[14] = 0.f;
+  x[15] = 0.f;
+}
+
+// One MMA operand in shared memory: the first of its three tiles (shared-window address), the
+// tile size, the descriptor's leading and stride byte offsets, and the byte advance per K = 16 step.
+struct Operand {
+  uint32_t base, tile, lbo, sbo, step;
+};
+
+// K-major operand (tc.cuh layout) of a tile with kt columns, starting at column block c0.
+__device__ __forceinline__ Operand kmajor(uint32_t base, uint32_t tile, int kt, int c0 = 0) {
+  return Operand{base + 128u * c0, tile, 128u, static_cast<uint32_t>(kt / 8 * 128), 256u};
+}
+
+// The same tile read MN-major (its rows become K, its columns M or N): 8-column blocks are 128 B
+// apart (stride byte offset), 8-row groups kt / 8 * 128 B apart (leading byte offset).
+__device__ __forceinline__ Operand mnmajor(uint32_t base, uint32_t tile, int kt) {
+  const uint32_t g = static_cast<uint32_t>(kt / 8 * 128);
+  return Operand{base, tile, g, 128u, 2u * g};
+}
+
+// D = A B^T over k_steps steps of K = 16 as the six products of the three-part split (hi*hi,
+// hi*mid, mid*hi, hi*lo, lo*hi, mid*mid); one thread issues, the mbarrier receives the
+// completion; the first product overwrites D unless accumulate is set.
+__device__ __forceinline__ void mma_split(uint32_t d, const Operand& A, const Operand& B, int k_steps, uint32_t idesc,
+                                          uint64_t* bar, bool accumulate = false) {
+  constexpr int kPa[6] = {0, 0, 1, 0, 2, 1}, kPb[6] = {0, 1, 0, 2, 0, 1};
+  tc::fence_after_sync();
+  for (int k = 0; k < k_steps; ++k) {
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const uint64_t ad = tc::smem_desc(A.base + A.tile * kPa[p] + A.step * k, A.lbo, A.sbo);
+      const uint64_t bd = tc::smem_desc(B.base + B.tile * kPb[p] + B.step * k, B.lbo, B.sbo);
+      tc::mma_bf16(d, ad, bd, idesc, (k > 0 || p > 0 || accumulate) ? 1u : 0u);
+    }
+  }
+  tc::mma_commit(bar);
+}
+
+__global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ params, const float* __restrict__ feats,
+                                                      int n, float* __restrict__ logits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* S = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
+  const uint32_t sb = tc::smem_u32(S);
+  float* b1 = reinterpret_cast<float*>(S + fwd::B1);
+  float* b2 = reinterpret_cast<float*>(S + fwd::B2);
+  float* w3 = reinterpret_cast<float*>(S + fwd::W3);
+  float* mean = reinterpret_cast<float*>(S + fwd::MEAN);
+  float* sd = reinterpret_cast<float*>(S + fwd::SD);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(S + fwd::BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(S + fwd::TMEM);
+  const int t = threadIdx.x, warp = t >> 5;
+
+  stage_weights_b(params, S + fwd::W1, fwd::W1_T, S + fwd::W2, fwd::W2_T);
+  for (int i = t; i < kMlpHid; i += blockDim.x) {
+    b1[i] = params[kMlpB1 + i];
+    b2[i] = params[kMlpB2 + i];
+    w3[i] = params[kMlpW3 + i];
+  }
+  if (t < kMlpIn) {
+    mean[t] = params[kMlpMean + t];
+    sd[t] = params[kMlpSd + t];
+  }
+  const float b3 = params[kMlpB3];
+  if (warp == 0) tc::tmem_alloc(tmem_slot, fwd::kCols);
+  if (t == 0) tc::mbar_init(bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kMlpHid);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int n_tiles = (n + kTcM - 1) / kTcM;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int r = tile * kTcM + t;
+    {
+      float x[kTcK1];
+      load_inputs(feats, r, n, mean, sd, x);
+      tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 0, kTcK1), x);
+      tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 1, kTcK1), x + 8);
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (t == 0)
+      mma_split(tmem, kmajor(sb + fwd::X, fwd::X_T, kTcK1), kmajor(sb + fwd::W1, fwd::W1_T, kTcK1), 1, idesc, bar);
+    bool ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[16 * q + i], 0.f);
+      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(t, 2 * q, kMlpHid), v);
+      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(t, 2 * q + 1, kMlpHid), v + 8);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (t == 0)
+      mma_split(tmem + 64, kmajor(sb + fwd::H, fwd::H_T, kMlpHid), kmajor(sb + fwd::W2, fwd::W2_T, kMlpHid), 4, idesc,
+                bar);
+    ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    float out = b3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + 64 + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) out = fmaf(w3[16 * q + i], fmaxf(v[i] + b2[16 * q + i], 0.f), out);
+    }
+    if (r < n) logits[r] = out;
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (failed) {
+    // A tensor-core wait gave up: this block's remaining samples get NaN logits; the MMA in
+    // flight gets one more bounded wait before the tensor memory is released.
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+      const int r = tile * kTcM + t;
+      if (r < n) logits[r] = __int_as_float(0x7fc00000);
+    }
+    tc::mbar_wait(bar, phase ^ 1u);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, fwd::kCols);
+  }
 }
 
 // Transposed copy for the finder (layout in mlp.cuh).
@@ -44,94 +235,237 @@ int launch_mlp_transpose(const float* params, float* wt, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// Loss and gradient summed over the samples of a block of kGradBlock threads (one sample each):
-// activations and their gradients in shared memory (rows padded to 65 words), then each thread
-// reduces a stripe of parameters over the block's samples and adds it to the global sums.
-constexpr int kGradBlock = 64;
-constexpr int kPad = kMlpHid + 1;
+// Loss and gradient on the tensor cores: a persistent CTA of 128 threads per SM takes tiles of 128
+// samples, one per thread, and runs per tile
+//   D1 = X W1^T -> h1 = relu(D1 + b1);  D2 = H1 W2^T -> z3 = b3 + W3 . relu(D2 + b2),
+//   g = sigmoid(z3) - y, e2 = g W3 [z2 > 0];  D3 = E2 W2 -> e1 = D3 [h1 > 0];
+//   Dg += [E2 | E1]^T [H1 | X | 1]   (accumulated in tensor memory over all the CTA's tiles),
+// so that Dg holds dW2 (rows 0-63, columns 0-63), dW1 (rows 64-127, columns 64-77), db2 and db1
+// (column 80). dW3, db3 and the loss are summed in registers. Shared memory (bytes; each operand
+// three tiles, hi, mid, lo): the sample x [e2 | e1] tile (128 x 128, K-major; read MN-major as the
+// A operand of the gradient MMA), the sample x [h1 | x | 1 | 0] tile (128 x 96: the A operand of
+// the first two MMAs, MN-major the B operand of the gradient MMA), W1 and W2 (W2 read MN-major is
+// W2^T for the third MMA); tensor memory: D1 then D3 at column 0, D2 at 64, Dg at 128.
+namespace grd {
+constexpr uint32_t E_T = 32768, XH_T = 24576, W1_T = 2048, W2_T = 8192;  // bytes of one tile
+constexpr uint32_t E = 0, XH = E + 3 * E_T, W1 = XH + 3 * XH_T, W2 = W1 + 3 * W1_T, B1 = W2 + 3 * W2_T,
+                   B2 = B1 + 256, W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, RED = SD + 64, B3 = RED + 272,
+                   BAR = B3 + 8, TMEM = BAR + 8, BYTES = TMEM + 8;
+// The allocation leaves room past W2's lo tile, so that no reading of the MN-major W2 operand's
+// offsets can leave the block's shared memory.
+constexpr uint32_t ALLOC = 208896;
+static_assert(BYTES <= ALLOC && W2 + 2 * W2_T + 13568 <= ALLOC, "shared-memory layout");
+constexpr uint32_t kCols = 256, kColD2 = 64, kColG = 128;
+constexpr int kXhK = 96, kEK = 128, kGN = 96;
+}  // namespace grd
 
-__global__ void __launch_bounds__(kGradBlock) k_mlp_loss_grad(const float* __restrict__ params,
-                                                              const float* __restrict__ feats,
-                                                              const float* __restrict__ labels, int n,
-                                                              float* __restrict__ grad, float* __restrict__ loss) {
-  extern __shared__ __align__(16) float sm[];
-  float* w = sm;                               // kMlpParamsAll
-  float* xs = w + kMlpParamsAll;               // [kGradBlock][kMlpIn]
-  float* h1 = xs + kGradBlock * kMlpIn;        // [kGradBlock][kPad]
-  float* h2 = h1 + kGradBlock * kPad;
-  float* d1 = h2 + kGradBlock * kPad;
-  float* d2 = d1 + kGradBlock * kPad;
-  float* dz = d2 + kGradBlock * kPad;          // [kGradBlock]
-  __shared__ float red[kGradBlock];
-  for (int i = threadIdx.x; i < kMlpParamsAll; i += blockDim.x) w[i] = params[i];
+// Instruction descriptor bits 15 and 16: A, B MN-major.
+constexpr uint32_t kAmn = 1u << 15, kBmn = 1u << 16;
+
+__global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict__ params,
+                                                        const float* __restrict__ feats,
+                                                        const float* __restrict__ labels, int n,
+                                                        float* __restrict__ grad, float* __restrict__ loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* S = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
+  const uint32_t sb = tc::smem_u32(S);
+  float* b1 = reinterpret_cast<float*>(S + grd::B1);
+  float* b2 = reinterpret_cast<float*>(S + grd::B2);
+  float* w3 = reinterpret_cast<float*>(S + grd::W3);
+  float* mean = reinterpret_cast<float*>(S + grd::MEAN);
+  float* sd = reinterpret_cast<float*>(S + grd::SD);
+  float* red = reinterpret_cast<float*>(S + grd::RED);  // dW3[64], db3, loss
+  uint64_t* bar = reinterpret_cast<uint64_t*>(S + grd::BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(S + grd::TMEM);
+  const int t = threadIdx.x, warp = t >> 5;
+
+  stage_weights_b(params, S + grd::W1, grd::W1_T, S + grd::W2, grd::W2_T);
+  for (int i = t; i < kMlpHid; i += blockDim.x) {
+    b1[i] = params[kMlpB1 + i];
+    b2[i] = params[kMlpB2 + i];
+    w3[i] = params[kMlpW3 + i];
+  }
+  if (t < kMlpIn) {
+    mean[t] = params[kMlpMean + t];
+    sd[t] = params[kMlpSd + t];
+  }
+  if (t < 66) red[t] = 0.f;
+  {  // constant columns of this thread's row of the [h1 | x | 1 | 0] tile: 80 (one) and 81-95 (zero)
+    float c[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 10, grd::kXhK), c);
+    c[0] = 0.f;
+    tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 11, grd::kXhK), c);
+  }
+  const float b3 = params[kMlpB3];
+  if (warp == 0) tc::tmem_alloc(tmem_slot, grd::kCols);
+  if (t == 0) tc::mbar_init(bar, 1);
+  tc::fence_before_sync();
   __syncthreads();
-  const int b = threadIdx.x;
-  const int s = blockIdx.x * kGradBlock + b;
-  const bool valid = s < n;
-  float lsum = 0.f;
-  {
-    float* x = xs + b * kMlpIn;
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  constexpr uint32_t id_kk = tc::idesc_bf16_f32(kTcM, kMlpHid);
+  constexpr uint32_t id_kmn = id_kk | kBmn;
+  constexpr uint32_t id_grad = tc::idesc_bf16_f32(kTcM, grd::kGN) | kAmn | kBmn;
+  uint32_t phase = 0;
+  bool failed = false;
+  float acc3[kMlpHid];
 #pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) {
-      const float f = valid ? feats[static_cast<size_t>(s) * kMlpIn + i] : 0.f;
-      x[i] = (f - w[kMlpMean + i]) / w[kMlpSd + i];
+  for (int j = 0; j < kMlpHid; ++j) acc3[j] = 0.f;
+  float gsum = 0.f, lsum = 0.f;
+
+  const int n_tiles = (n + kTcM - 1) / kTcM;
+  int done_tiles = 0;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++done_tiles) {
+    const int r = tile * kTcM + t;
+    const bool valid = r < n;
+    // inputs -> columns 64-79 of the [h1 | x | 1 | 0] tile
+    {
+      float x[kTcK1];
+      load_inputs(feats, r, n, mean, sd, x);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 8, grd::kXhK), x);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 9, grd::kXhK), x + 8);
     }
-    float* a1 = h1 + b * kPad;
-    for (int j = 0; j < kMlpHid; ++j) {
-      float z = w[kMlpB1 + j];
+    const float y = valid ? labels[r] : 0.f;
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (t == 0)
+      mma_split(tmem, kmajor(sb + grd::XH, grd::XH_T, grd::kXhK, 8), kmajor(sb + grd::W1, grd::W1_T, kTcK1), 1,
+                id_kk, bar);
+    bool ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    // h1 -> columns 0-63; mask1 = [h1 > 0]
+    unsigned long long mask1 = 0ull;
 #pragma unroll
-      for (int i = 0; i < kMlpIn; ++i) z += w[kMlpW1 + j * kMlpIn + i] * x[i];
-      a1[j] = fmaxf(z, 0.f);
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v[i] = fmaxf(v[i] + b1[16 * q + i], 0.f);
+        if (v[i] > 0.f) mask1 |= 1ull << (16 * q + i);
+      }
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 2 * q, grd::kXhK), v);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 2 * q + 1, grd::kXhK), v + 8);
     }
-    float* a2 = h2 + b * kPad;
-    float z3 = w[kMlpB3];
-    for (int j = 0; j < kMlpHid; ++j) {
-      float z = w[kMlpB2 + j];
-      for (int i = 0; i < kMlpHid; ++i) z += w[kMlpW2 + j * kMlpHid + i] * a1[i];
-      a2[j] = fmaxf(z, 0.f);
-      z3 += w[kMlpW3 + j] * a2[j];
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (t == 0)
+      mma_split(tmem + grd::kColD2, kmajor(sb + grd::XH, grd::XH_T, grd::kXhK),
+                kmajor(sb + grd::W2, grd::W2_T, kMlpHid), 4, id_kk, bar);
+    ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
     }
-    const float y = valid ? labels[s] : 0.f;
+    tc::fence_after_sync();
+    float z3 = b3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + grd::kColD2 + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z3 = fmaf(w3[16 * q + i], fmaxf(v[i] + b2[16 * q + i], 0.f), z3);
+    }
     const float g = valid ? 1.f / (1.f + expf(-z3)) - y : 0.f;
-    if (valid) lsum = fmaxf(z3, 0.f) - z3 * y + log1pf(expf(-fabsf(z3)));
-    dz[b] = g;
-    float* e2 = d2 + b * kPad;
-    for (int j = 0; j < kMlpHid; ++j) e2[j] = a2[j] > 0.f ? g * w[kMlpW3 + j] : 0.f;
-    float* e1 = d1 + b * kPad;
-    for (int i = 0; i < kMlpHid; ++i) {
-      float acc = 0.f;
-      for (int j = 0; j < kMlpHid; ++j) acc += e2[j] * w[kMlpW2 + j * kMlpHid + i];
-      e1[i] = a1[i] > 0.f ? acc : 0.f;
+    if (valid) lsum += fmaxf(z3, 0.f) - z3 * y + log1pf(expf(-fabsf(z3)));
+    gsum += g;
+    // e2 -> columns 0-63 of the [e2 | e1] tile; dW3 partial sums
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + grd::kColD2 + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float a2 = fmaxf(v[i] + b2[16 * q + i], 0.f);
+        acc3[16 * q + i] = fmaf(g, a2, acc3[16 * q + i]);
+        v[i] = a2 > 0.f ? g * w3[16 * q + i] : 0.f;
+      }
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 2 * q, grd::kEK), v);
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 2 * q + 1, grd::kEK), v + 8);
     }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // D3 = E2 W2: W2's K-major tile (rows o, columns i) read MN-major is W2^T (n = i, k = o).
+    if (t == 0)
+      mma_split(tmem, kmajor(sb + grd::E, grd::E_T, grd::kEK), mnmajor(sb + grd::W2, grd::W2_T, kMlpHid), 4, id_kmn,
+                bar);
+    ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    // e1 -> columns 64-127 of the [e2 | e1] tile
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float v[16];
+      tc::tmem_ld16(lane_base + 16 * q, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = (mask1 >> (16 * q + i)) & 1ull ? v[i] : 0.f;
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 8 + 2 * q, grd::kEK), v);
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 9 + 2 * q, grd::kEK), v + 8);
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    // Dg += [e2 | e1]^T [h1 | x | 1 | 0]: both tiles read MN-major, K = the tile's 128 samples.
+    if (t == 0)
+      mma_split(tmem + grd::kColG, mnmajor(sb + grd::E, grd::E_T, grd::kEK), mnmajor(sb + grd::XH, grd::XH_T, grd::kXhK),
+                kTcM / 16, id_grad, bar, done_tiles > 0);
+    ok = tc::mbar_wait(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
   }
-  red[b] = lsum;
-  __syncthreads();
-  for (int p = threadIdx.x; p < kMlpParams; p += blockDim.x) {
-    float acc = 0.f;
-    if (p < kMlpB1) {
-      const int j = p / kMlpIn, i = p % kMlpIn;
-      for (int k = 0; k < kGradBlock; ++k) acc += d1[k * kPad + j] * xs[k * kMlpIn + i];
-    } else if (p < kMlpW2) {
-      const int j = p - kMlpB1;
-      for (int k = 0; k < kGradBlock; ++k) acc += d1[k * kPad + j];
-    } else if (p < kMlpB2) {
-      const int j = (p - kMlpW2) / kMlpHid, i = (p - kMlpW2) % kMlpHid;
-      for (int k = 0; k < kGradBlock; ++k) acc += d2[k * kPad + j] * h1[k * kPad + i];
-    } else if (p < kMlpW3) {
-      const int j = p - kMlpB2;
-      for (int k = 0; k < kGradBlock; ++k) acc += d2[k * kPad + j];
-    } else if (p < kMlpB3) {
-      const int j = p - kMlpW3;
-      for (int k = 0; k < kGradBlock; ++k) acc += dz[k] * h2[k * kPad + j];
+  if (failed) {
+    // A tensor-core wait gave up: the loss becomes NaN and this block adds no gradient; the MMA in
+    // flight gets one more bounded wait before the tensor memory is released.
+    if (t == 0) atomicAdd(loss, __int_as_float(0x7fc00000));
+    tc::mbar_wait(bar, phase ^ 1u);
+  } else if (done_tiles > 0) {
+#pragma unroll
+    for (int j = 0; j < kMlpHid; ++j) atomicAdd(&red[j], acc3[j]);
+    atomicAdd(&red[64], gsum);
+    atomicAdd(&red[65], lsum);
+    // Dg row t: dW2 row j = t and db2[j] (t < 64), or dW1 row i = t - 64 and db1[i]
+    float v[16];
+    if (t < kMlpHid) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        tc::tmem_ld16(lane_base + grd::kColG + 16 * q, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) atomicAdd(grad + kMlpW2 + t * kMlpHid + 16 * q + i, v[i]);
+      }
     } else {
-      for (int k = 0; k < kGradBlock; ++k) acc += dz[k];
+      tc::tmem_ld16(lane_base + grd::kColG + 64, v);
+#pragma unroll
+      for (int k = 0; k < kMlpIn; ++k) atomicAdd(grad + kMlpW1 + (t - kMlpHid) * kMlpIn + k, v[k]);
     }
-    atomicAdd(grad + p, acc);
+    tc::tmem_ld16(lane_base + grd::kColG + 80, v);
+    atomicAdd(grad + (t < kMlpHid ? kMlpB2 + t : kMlpB1 + t - kMlpHid), v[0]);
+    __syncthreads();
+    if (t < kMlpHid) atomicAdd(grad + kMlpW3 + t, red[t]);
+    if (t == kMlpHid) atomicAdd(grad + kMlpB3, red[64]);
+    if (t == kMlpHid + 1) atomicAdd(loss, red[65]);
   }
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int k = 0; k < kGradBlock; ++k) t += red[k];
-    atomicAdd(loss, t);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, grd::kCols);
   }
 }
 
@@ -156,31 +490,42 @@ __global__ void k_mlp_adam(float* params, const float* grad, float* m, float* v,
   }
 }
 
-size_t mlp_grad_smem() {
-  return sizeof(float) * (kMlpParamsAll + kGradBlock * kMlpIn + 4 * kGradBlock * kPad + kGradBlock);
+// Number of SMs of the current device and, once per device, the kernel's shared-memory opt-in.
+static int tc_prepare(const void* kernel, int smem, int* sms) {
+  static int sm_count[64] = {0};
+  static int smem_set[2][64] = {{0}};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
+  if (!sm_count[dev] && cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -3;
+  const int which = kernel == reinterpret_cast<const void*>(k_mlp_forward) ? 0 : 1;
+  if (smem > smem_set[which][dev]) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -3;
+    smem_set[which][dev] = smem;
+  }
+  *sms = sm_count[dev];
+  return 0;
 }
 
 int launch_mlp_forward(const float* params, const float* feats, int n, float* logits, cudaStream_t st) {
   if (n == 0) return 0;
-  k_mlp_forward<<<(n + 127) / 128, 128, 0, st>>>(params, feats, n, logits);
+  const int smem = static_cast<int>(fwd::BYTES) + 1024;
+  int sms = 0;
+  if (tc_prepare(reinterpret_cast<const void*>(k_mlp_forward), smem, &sms) != 0) return -3;
+  const int tiles = (n + kTcM - 1) / kTcM;
+  k_mlp_forward<<<std::min(tiles, kFwdCtasPerSm * sms), kTcM, smem, st>>>(params, feats, n, logits);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 int launch_mlp_loss_grad(const float* params, const float* feats, const float* labels, int n, float* grad, float* loss,
                          cudaStream_t st) {
-  static int attr_set[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -3;
-  const size_t smem = mlp_grad_smem();
-  if (!attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_mlp_loss_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-        cudaSuccess)
-      return -3;
-    attr_set[dev] = 1;
-  }
+  const int smem = static_cast<int>(grd::ALLOC) + 1024;
+  int sms = 0;
+  if (tc_prepare(reinterpret_cast<const void*>(k_mlp_loss_grad), smem, &sms) != 0) return -3;
   if (cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st) != cudaSuccess) return -3;
   if (cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return -3;
-  if (n > 0) k_mlp_loss_grad<<<(n + kGradBlock - 1) / kGradBlock, kGradBlock, smem, st>>>(params, feats, labels, n, grad, loss);
+  const int tiles = (n + kTcM - 1) / kTcM;
+  if (n > 0) k_mlp_loss_grad<<<std::min(tiles, sms), kTcM, smem, st>>>(params, feats, labels, n, grad, loss);
   k_mlp_scale<<<8, 256, 0, st>>>(grad, loss, n > 0 ? 1.f / n : 0.f);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -18,29 +18,6 @@ constexpr int kMlpMean = kMlpParams;                // normaliser: mean[14], sd[
 constexpr int kMlpSd = kMlpMean + kMlpIn;
 constexpr int kMlpParamsAll = kMlpSd + kMlpIn;      // 5213 floats
 
-// Logit of raw features f (standardised here) with parameters w (shared or global memory).
-__device__ __forceinline__ float mlp_logit(const float* w, const float* f) {
-  float x[kMlpIn];
-#pragma unroll
-  for (int i = 0; i < kMlpIn; ++i) x[i] = (f[i] - w[kMlpMean + i]) / w[kMlpSd + i];
-  float h1[kMlpHid];
-#pragma unroll
-  for (int j = 0; j < kMlpHid; ++j) {
-    float z = w[kMlpB1 + j];
-#pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) z += w[kMlpW1 + j * kMlpIn + i] * x[i];
-    h1[j] = fmaxf(z, 0.f);
-  }
-  float out = w[kMlpB3];
-  for (int j = 0; j < kMlpHid; ++j) {
-    float z = w[kMlpB2 + j];
-#pragma unroll
-    for (int i = 0; i < kMlpHid; ++i) z += w[kMlpW2 + j * kMlpHid + i] * h1[i];
-    out += w[kMlpW3 + j] * fmaxf(z, 0.f);
-  }
-  return out;
-}
-
 // Transposed copy of the parameters for the finder's warp-level inference (same size and the same
 // offsets for b1, b2, W3, b3 and the normaliser): W1T[14][64] at kMlpW1 and W2T[64][64] at kMlpW2,
 // input-major, so that lane j reads hidden units 2j, 2j+1 of one input as one 8-byte word of a

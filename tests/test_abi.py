@@ -64,6 +64,10 @@ def test_host_side_argument_checks(kf):
     # finder parameters: k above the compiled maximum
     p = kf.find_params(30.0, kf.KF_MAX_K + 1, 1, 17)
     assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
+    # network kernels read feature rows as float pairs: an odd float offset is rejected
+    v = ctypes.c_void_p
+    assert lib.kf_mlp_forward(v(256), v(260), 1, v(512), None) == kf.KF_ERR_ARG
+    assert lib.kf_mlp_loss_grad(v(256), v(260), v(1024), 1, v(512), v(768), None) == kf.KF_ERR_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path):

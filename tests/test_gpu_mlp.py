@@ -71,6 +71,39 @@ def test_mlp_gradient_and_adam_match_oracle(kf, pairs):
     assert np.abs(got - w64).max() <= 1e-6
 
 
+_BLOCKS = {"W1": (0, 896), "b1": (896, 960), "W2": (960, 5056), "b2": (5056, 5120), "W3": (5120, 5184),
+           "b3": (5184, 5185)}
+
+
+@pytest.mark.parametrize("n", [0, 1, 127, 128, 129, 50001])
+def test_mlp_tensor_core_tiles_match_oracle(kf, pairs, n):
+    """The network's tensor-core kernels at the tile edges (128 samples per tile, ragged or empty
+    last tile) and over many tiles per block (50,001 samples: the gradient accumulates over about
+    three tiles per block in tensor memory); every parameter block against its own scale."""
+    F, L, mean, sd = pairs
+    w = synth.mlp_init(7)
+    buf = kf.mlp_buffer(w, mean, sd)
+    rng = np.random.default_rng(n)
+    idx = rng.integers(0, len(F), n)
+    x, y = np.ascontiguousarray(F[idx]), np.ascontiguousarray(L[idx])
+    xs = _std(x, mean, sd)
+    got = kf.mlp_forward(buf, torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    assert got.shape == (n,)
+    if n:
+        ref = oracle.mlp_forward(w.astype(np.float64), xs)
+        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    loss, grad = kf.mlp_loss_grad(buf, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    g = grad.cpu().numpy().astype(np.float64)
+    if n == 0:
+        assert float(loss.item()) == 0.0 and not g.any()
+        return
+    rl, rg = oracle.mlp_loss_grad(w.astype(np.float64), xs, y.astype(np.float64))
+    assert abs(float(loss.item()) - rl) <= 1e-5 * abs(rl)
+    for name, (a, b) in _BLOCKS.items():
+        scale = np.abs(rg[a:b]).max()
+        assert np.abs(g[a:b] - rg[a:b]).max() <= 1e-4 * scale + 1e-9, name
+
+
 def test_gpu_training_lowers_the_loss(kf, pairs):
     F, L, mean, sd = pairs
     buf = kf.mlp_buffer(synth.mlp_init(8), mean, sd)
