@@ -1,17 +1,19 @@
 // Hit index build: per (event, surface) slab, a counting sort of the hits by bin
-// (phi-bin * n_2nd + second-bin), ascending hit id within a bin. This is the binned hit
-// structure behind the per-layer search windows (paper Sec. 3.1) and the reuse of hit data by
+// (phi-bin * n_2nd + second-bin), ordered within a bin by (phi sub-bin, hit id). This is the binned
+// hit structure behind the per-layer search windows (paper Sec. 3.1) and the reuse of hit data by
 // nearby seeds (Sec. 3.2).
 //
 // One CTA per slab, everything staged in shared memory: the bin (u16) and phi sub-bin (u8) of each
 // hit, the bin histogram and its exclusive scan, then an unstable scatter of local hit numbers by
-// shared atomics, then a per-bin insertion sort by (sub-bin, id) (bins hold a handful of hits) and
-// the per-bin sub-bin offsets, then a coalesced gather-write of the sorted hits and ids and, when
-// asked for, of each
-// hit's 16-byte search record (cos phi, sin phi, second coordinate, id), so that the search reads
-// one aligned record per hit and computes residual angles without trig.
-// Global traffic per hit: one 8-byte read (plus an L2 re-read in the gather) and a 12-byte write
-// (28 bytes with search records).
+// shared atomics. Each bin's sub-bin counts give its sub-bin offsets; the output pass puts the hit
+// at unstable position p of bin [s, e) at s + its rank by (sub-bin, id) among the bin's hits (bins
+// hold a handful of hits) and writes the sorted hits, ids and, when asked for, each hit's 16-byte
+// search record (cos phi, sin phi, second coordinate, id), so that the search reads one aligned
+// record per hit and computes residual angles without trig. The ranks replace a per-bin insertion
+// sort, which took 43% of the kernel (one lane per bin, dependent shared loads, lanes diverging
+// with the bin sizes).
+// Global traffic per hit: one 8-byte read (plus an L2 re-read in the output pass) and a 12-byte
+// write (28 bytes with search records).
 #include "kf_math.cuh"
 
 namespace kfgb {
@@ -111,30 +113,20 @@ __global__ void __launch_bounds__(1024, 2) k_build_hit_index(DevGeom G, const fl
       order[pos] = static_cast<unsigned short>(i);
     }
     __syncthreads();
-    // Order each bin by (sub-bin, hit id) and write its sub-bin offsets.
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      unsigned long long c03 = 0, c47 = 0;  // 16-bit hit counts of sub-bins 0-3 and 4-7
-      if (b < nbs) {
-        const int e = hist[b];
-        const int s = b > 0 ? hist[b - 1] : 0;
-        for (int i = s + 1; i < e; ++i) {
-          const unsigned short v = order[i];
-          const unsigned kv = (static_cast<unsigned>(sub[v]) << 16) | v;
-          int j = i - 1;
-          while (j >= s && ((static_cast<unsigned>(sub[order[j]]) << 16) | order[j]) > kv) {
-            order[j + 1] = order[j];
-            --j;
+    // Sub-bin offsets of each bin (hit counts of its sub-bins, cumulated).
+    if (sout) {
+      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        unsigned long long c03 = 0, c47 = 0;  // 16-bit hit counts of sub-bins 0-3 and 4-7
+        if (b < nbs) {
+          const int e = hist[b];
+          const int s = b > 0 ? hist[b - 1] : 0;
+          for (int i = s; i < e; ++i) {
+            const unsigned sv = sub[order[i]];
+            const unsigned long long inc = 1ull << (16 * (sv & 3));
+            if (sv < 4) c03 += inc;
+            else c47 += inc;
           }
-          order[j + 1] = v;
         }
-        for (int i = s; i < e; ++i) {
-          const unsigned sv = sub[order[i]];
-          const unsigned long long inc = 1ull << (16 * (sv & 3));
-          if (sv < 4) c03 += inc;
-          else c47 += inc;
-        }
-      }
-      if (sout) {
         unsigned cum[kPhiSub];
         unsigned run = 0;
 #pragma unroll
@@ -146,15 +138,29 @@ __global__ void __launch_bounds__(1024, 2) k_build_hit_index(DevGeom G, const fl
                              cum[6] | (cum[7] << 16));
       }
     }
-    __syncthreads();
-    // Gather in sorted order, four per thread per iteration with their loads issued together.
+    // Gather: the hit at (unstable) position p of bin [s, e) goes to s + its rank by (sub-bin, id)
+    // among the bin's hits; four per thread per iteration with their loads issued together.
     for (int p0 = threadIdx.x; p0 < n; p0 += 4 * blockDim.x) {
-      int iv[4];
+      int iv[4], dv[4];
       float2 hv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int p = p0 + u * blockDim.x;
-        iv[u] = p < n ? order[p] : 0;
+        iv[u] = 0;
+        dv[u] = 0;
+        if (p < n) {
+          const int v = order[p];
+          const int b = bin[v];
+          const int s = b > 0 ? hist[b - 1] : 0, e = hist[b];
+          const unsigned kv = (static_cast<unsigned>(sub[v]) << 16) | static_cast<unsigned>(v);
+          int rank = 0;
+          for (int q = s; q < e; ++q) {
+            const unsigned w = order[q];
+            rank += ((static_cast<unsigned>(sub[w]) << 16) | w) < kv;
+          }
+          iv[u] = v;
+          dv[u] = s + rank;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) hv[u] = p0 + u * static_cast<int>(blockDim.x) < n ? __ldg(hits + h0 + iv[u]) : make_float2(0.f, 0.f);
@@ -162,12 +168,13 @@ __global__ void __launch_bounds__(1024, 2) k_build_hit_index(DevGeom G, const fl
       for (int u = 0; u < 4; ++u) {
         const int p = p0 + u * blockDim.x;
         if (p < n) {
-          sorted_hits[h0 + p] = hv[u];
-          sorted_ids[h0 + p] = h0 + iv[u];
+          const int d = h0 + dv[u];
+          sorted_hits[d] = hv[u];
+          sorted_ids[d] = h0 + iv[u];
           if (sorted_rec) {
             float s, c;
             sincosf(hv[u].x, &s, &c);
-            sorted_rec[h0 + p] = make_float4(c, s, hv[u].y, __int_as_float(h0 + iv[u]));
+            sorted_rec[d] = make_float4(c, s, hv[u].y, __int_as_float(h0 + iv[u]));
           }
         }
       }

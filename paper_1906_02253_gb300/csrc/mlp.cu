@@ -51,20 +51,20 @@ __device__ __forceinline__ void stage_weights_b(const float* __restrict__ params
   }
 }
 
-// Standardised inputs of sample r (zeros past n) into x[16] (inputs 14 and 15 zero).
-__device__ __forceinline__ void load_inputs(const float* __restrict__ feats, int r, int n, const float* mean,
-                                            const float* sd, float* x) {
-  if (r < n) {
-    const float2* f2 = reinterpret_cast<const float2*>(feats + static_cast<size_t>(r) * kMlpIn);
+// Raw features of sample r (zeros past n), loaded ahead of their tile.
+__device__ __forceinline__ void fetch_inputs(const float* __restrict__ feats, int r, int n, float2* f) {
+  const float2* f2 = reinterpret_cast<const float2*>(feats + static_cast<size_t>(r) * kMlpIn);
 #pragma unroll
-    for (int i = 0; i < kMlpIn / 2; ++i) {
-      const float2 f = __ldg(f2 + i);
-      x[2 * i] = (f.x - mean[2 * i]) / sd[2 * i];
-      x[2 * i + 1] = (f.y - mean[2 * i + 1]) / sd[2 * i + 1];
-    }
-  } else {
+  for (int i = 0; i < kMlpIn / 2; ++i) f[i] = r < n ? __ldg(f2 + i) : make_float2(0.f, 0.f);
+}
+
+// Standardised inputs x[16] from raw features (zeros past n; inputs 14 and 15 zero).
+__device__ __forceinline__ void standardise(const float2* f, bool valid, const float* mean, const float* sd,
+                                            float* x) {
 #pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) x[i] = 0.f;
+  for (int i = 0; i < kMlpIn / 2; ++i) {
+    x[2 * i] = valid ? (f[i].x - mean[2 * i]) / sd[2 * i] : 0.f;
+    x[2 * i + 1] = valid ? (f[i].y - mean[2 * i + 1]) / sd[2 * i + 1] : 0.f;
   }
   x[14] = 0.f;
   x[15] = 0.f;
@@ -143,11 +143,13 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
   bool failed = false;
 
   const int n_tiles = (n + kTcM - 1) / kTcM;
+  float2 fin[kMlpIn / 2];  // raw features of this thread's sample in the next tile
+  fetch_inputs(feats, blockIdx.x * kTcM + t, n, fin);
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int r = tile * kTcM + t;
     {
       float x[kTcK1];
-      load_inputs(feats, r, n, mean, sd, x);
+      standardise(fin, r < n, mean, sd, x);
       tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 0, kTcK1), x);
       tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 1, kTcK1), x + 8);
     }
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
     __syncthreads();
     if (t == 0)
       mma_split(tmem, kmajor(sb + fwd::X, fwd::X_T, kTcK1), kmajor(sb + fwd::W1, fwd::W1_T, kTcK1), 1, idesc, bar);
+    fetch_inputs(feats, (tile + gridDim.x) * kTcM + t, n, fin);  // in flight during this tile's MMAs
     bool ok = tc::mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -316,17 +319,25 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
 
   const int n_tiles = (n + kTcM - 1) / kTcM;
   int done_tiles = 0;
+  float2 fin[kMlpIn / 2];  // raw features and label of this thread's sample in the next tile
+  fetch_inputs(feats, blockIdx.x * kTcM + t, n, fin);
+  float yin = blockIdx.x * kTcM + t < n ? labels[blockIdx.x * kTcM + t] : 0.f;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++done_tiles) {
     const int r = tile * kTcM + t;
     const bool valid = r < n;
     // inputs -> columns 64-79 of the [h1 | x | 1 | 0] tile
     {
       float x[kTcK1];
-      load_inputs(feats, r, n, mean, sd, x);
+      standardise(fin, valid, mean, sd, x);
       tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 8, grd::kXhK), x);
       tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 9, grd::kXhK), x + 8);
     }
-    const float y = valid ? labels[r] : 0.f;
+    const float y = yin;
+    {
+      const int rn = (tile + gridDim.x) * kTcM + t;  // in flight during this tile's MMAs
+      fetch_inputs(feats, rn, n, fin);
+      yin = rn < n ? labels[rn] : 0.f;
+    }
     tc::fence_proxy_async();
     __syncthreads();
     if (t == 0)
