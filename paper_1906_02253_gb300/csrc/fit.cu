@@ -38,11 +38,28 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const __grid_cons
     if (!surf_ok || !seed_from_hits(G, xs, ys, zs, s1, p, C)) {
       status = 1;
     } else {
+      // Two-stage prefetch: entry k + 2 of the hit list and hit k + 1 (its coordinates and surface)
+      // are loaded while step k computes.
+      auto list_at = [&](int k) {
+        return k < 3 ? id[k] : (k < lmax ? track_hits[static_cast<size_t>(k) * n_tracks + t] : -1);
+      };
+      int hid = id[0];
+      float2 h = hits[hid];
+      int si = hit_surface[hid];
+      int hid_n = id[1];
+      int hid_nn = list_at(2);
       for (int k = 0; k < lmax; ++k) {
-        const int hid = k < 3 ? id[k] : track_hits[static_cast<size_t>(k) * n_tracks + t];
-        if (hid < 0) continue;
-        const float2 h = hits[hid];
-        const int si = hit_surface[hid];
+        float2 h_n = make_float2(0.f, 0.f);
+        int si_n = -1;
+        if (hid_n >= 0) {
+          h_n = hits[hid_n];
+          si_n = hit_surface[hid_n];
+        }
+        const int hid_3 = list_at(k + 3);
+        if (hid < 0) {
+          hid = hid_n, h = h_n, si = si_n, hid_n = hid_nn, hid_nn = hid_3;
+          continue;
+        }
         if (si < 0 || si >= G.n_surf) {
           status = 2;
           break;
@@ -66,6 +83,7 @@ __global__ void __launch_bounds__(256) k_fit_tracks(DevGeom G, const __grid_cons
         innovation(G, C, m, in);
         chi2 += kalman_update(p, C, in, m.r0, m.r1);
         ++nh;
+        hid = hid_n, h = h_n, si = si_n, hid_n = hid_nn, hid_nn = hid_3;
       }
     }
   }

@@ -83,6 +83,36 @@ def test_hit_index_edge_cases(kf):
     assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
 
 
+def test_hit_index_crowded_slab_at_capacity(kf):
+    """One slab of exactly the compiled capacity (KF_MAX_SLAB_HITS hits): a quarter of them in one
+    bin, 1,000 at identical coordinates (same bin and sub-bin, ordered by id alone), the rest
+    uniform; every other slab empty."""
+    wl = synth.workload("find", n_events=1, tracks_lo=3, tracks_hi=3)
+    b = synth.generate(wl)
+    s0 = wl.surfaces[0]
+    n = kf.KF_MAX_SLAB_HITS
+    rng = np.random.default_rng(11)
+    phi = rng.uniform(-np.pi, np.pi, n)
+    z = rng.uniform(s0.lo, s0.hi, n)
+    k = n // 4
+    phi[:k] = 0.01 + rng.uniform(0.0, 1e-3, k)
+    z[:k] = s0.lo + 1e-3
+    phi[k:k + 1000] = 0.02
+    z[k:k + 1000] = s0.lo + 0.5
+    perm = rng.permutation(n)
+    hits = np.stack([phi[perm], z[perm]], axis=1).astype(np.float32)
+    slab = np.full(b.n_events * b.n_surf + 1, n, np.int64)
+    slab[0] = 0
+    b.hits, b.slab_offsets = hits, slab
+    b.hit_surface = np.zeros(n, np.int32)
+    idx, (off, sh, si, sub), dev, _ = _index_both(kf, wl, b)
+    assert dev["max_slab_hits"] == n
+    assert np.array_equal(idx.bin_off.cpu().numpy(), off.astype(np.int32))
+    assert np.array_equal(idx.sub_off.cpu().numpy().view(np.uint16), sub)
+    assert np.array_equal(idx.sorted_ids.cpu().numpy(), si)
+    assert np.array_equal(idx.sorted_hits.cpu().numpy().view(np.uint32), sh.view(np.uint32))
+
+
 def test_hit_index_empty_event(kf):
     wl = synth.workload("find", n_events=1, tracks_lo=0, tracks_hi=0)
     b = synth.generate(wl)
