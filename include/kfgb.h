@@ -376,6 +376,14 @@ int kf_fp32_fma_probe(float* sink, int blocks, int iters, long long* flops, kf_s
 #define KF_PROBE_HALF_ANGLE 2
 int kf_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2, kf_stream_t stream);
 
+/* Probe of the bounded wait that the tensor-core kernels use for MMA completion (measurement only,
+ * not part of the path): one warp waits limit_us microseconds on a shared-memory mbarrier that
+ * receives no arrival, then, after the barrier's one expected arrival, waits on it again. out:
+ * device long long [3] = (1 if the first wait completed, 1 if the second completed, the first
+ * wait's duration in ns); expected (0, 1, about limit_us * 1000). KF_ERR_ARG for limit_us outside
+ * [1, 1000000] or a null pointer. */
+int kf_wait_probe(int limit_us, long long* out, kf_stream_t stream);
+
 /* Human-readable name of a status code. */
 const char* kf_status_string(int status);
 

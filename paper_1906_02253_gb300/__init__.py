@@ -67,7 +67,8 @@ class KfFindParams(ctypes.Structure):
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
-           "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe", "kf_seed_states")
+           "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe", "kf_seed_states",
+           "kf_wait_probe")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
@@ -119,6 +120,8 @@ def load_library(path: str = LIB_PATH):
             lib.kf_seed_states.argtypes = [G, P, P, P, P, I, I, P, P, P]
             lib.kf_math_probe.restype = I
             lib.kf_math_probe.argtypes = [I, P, P, I, P, P, P, P]
+            lib.kf_wait_probe.restype = I
+            lib.kf_wait_probe.argtypes = [I, P, P]
             lib.kf_status_string.restype = ctypes.c_char_p
             lib.kf_status_string.argtypes = [I]
             _lib = lib
@@ -340,6 +343,15 @@ def fp32_fma_rate(blocks: int = 0, iters: int = 4096, reps: int = 3, stream=None
 
 
 PROBE_SINCOS, PROBE_ATAN_SMALL, PROBE_HALF_ANGLE = 0, 1, 2  # KF_PROBE_*
+
+
+def wait_probe(limit_us: int, stream=None):
+    """kf_wait_probe: the tensor-core kernels' bounded mbarrier wait, once with no arrival (gives up
+    after limit_us) and once after the arrival. Returns (first completed, second completed, first
+    wait's ns) as an int64 CUDA tensor."""
+    out = torch.full((3,), -1, dtype=torch.int64, device="cuda")
+    _check(load_library().kf_wait_probe(int(limit_us), _ptr(out), _stream(stream)), "kf_wait_probe")
+    return out
 
 
 def math_probe(fn: int, a, b=None, stream=None):

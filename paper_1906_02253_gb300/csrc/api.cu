@@ -26,6 +26,7 @@ int launch_clean_seeds(const DevGeom& G, const float2* hits, const int* hit_surf
 int launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t st, long long* flops);
 int launch_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2,
                       cudaStream_t st);
+int launch_wait_probe(int limit_us, long long* out, cudaStream_t st);
 int launch_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
                              const int* event, int n, int lmax, int n_hits, float dphi, float dtheta, int* keep,
                              void* ws, cudaStream_t st);
@@ -532,6 +533,11 @@ int kf_math_probe(int fn, const float* a, const float* b, int n, float* o0, floa
   if (n == 0) return KF_OK;
   if (!a || !o0 || !o1 || !o2 || (fn == KF_PROBE_ATAN_SMALL && !b)) return KF_ERR_ARG;
   return launch_math_probe(fn, a, b, n, o0, o1, o2, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_wait_probe(int limit_us, long long* out, kf_stream_t stream) {
+  if (limit_us < 1 || limit_us > 1000000 || !out) return KF_ERR_ARG;
+  return launch_wait_probe(limit_us, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 const char* kf_status_string(int status) {

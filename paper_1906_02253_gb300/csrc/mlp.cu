@@ -11,8 +11,8 @@
 
 namespace kfgb {
 
-// Inference on the tensor cores (tcgen05): a persistent CTA of 128 threads takes tiles of 128
-// samples, one sample per thread. Per tile: standardised inputs -> X tile (128 x 16); D1 = X W1^T
+// Inference on the tensor cores (tcgen05): a persistent CTA of 256 threads takes tiles of 128
+// samples, two threads per sample (each half of the columns). Per tile: standardised inputs -> X tile (128 x 16); D1 = X W1^T
 // in tensor memory; h1 = relu(D1 + b1) -> H tile (128 x 64); D2 = H W2^T; logit = b3 + sum_j W3[j]
 // relu(D2[j] + b2[j]) on the CUDA cores. Every operand is three bf16 tiles (hi, mid, lo; tc.cuh).
 // Shared memory (bytes): X, W1, W2 and H, then b1, b2, W3, mean, sd, b3, the mbarrier and the
@@ -20,11 +20,11 @@ namespace kfgb {
 namespace fwd {
 constexpr uint32_t X_T = 4096, W1_T = 2048, W2_T = 8192, H_T = 16384;  // bytes of one tile
 constexpr uint32_t X = 0, W1 = X + 3 * X_T, W2 = W1 + 3 * W1_T, H = W2 + 3 * W2_T, B1 = H + 3 * H_T, B2 = B1 + 256,
-                   W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, B3 = SD + 64, BAR = B3 + 8, TMEM = BAR + 8,
-                   BYTES = TMEM + 8;
+                   W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, PART = SD + 64, B3 = PART + 1024, BAR = B3 + 8,
+                   TMEM = BAR + 8, BYTES = TMEM + 8;
 constexpr uint32_t kCols = 128;
 }  // namespace fwd
-constexpr int kTcM = 128;   // samples per tile (the MMA's M), one per thread
+constexpr int kTcM = 128;   // samples per tile (the MMA's M)
 constexpr int kTcK1 = 16;   // the 14 inputs padded to one MMA K step
 constexpr int kFwdCtasPerSm = 2;
 
@@ -51,23 +51,31 @@ __device__ __forceinline__ void stage_weights_b(const float* __restrict__ params
   }
 }
 
-// Raw features of sample r (zeros past n), loaded ahead of their tile.
-__device__ __forceinline__ void fetch_inputs(const float* __restrict__ feats, int r, int n, float2* f) {
+// Two threads per sample: thread t takes sample t % 128 of the tile and half h = t / 128 of its
+// columns. Warps w and w + 4 read the same tensor-memory lanes (32 (w % 4) ..), each its half of a
+// 64-column accumulator; every branch around a tensor-memory load is uniform within a warp.
+constexpr int kTcThreads = 2 * 128;
+
+// Raw features [8 h, 8 h + 8) of sample r (zeros past n and past the 14 inputs), loaded ahead of
+// their tile.
+__device__ __forceinline__ void fetch_half(const float* __restrict__ feats, int r, int n, int half, float2* f) {
   const float2* f2 = reinterpret_cast<const float2*>(feats + static_cast<size_t>(r) * kMlpIn);
 #pragma unroll
-  for (int i = 0; i < kMlpIn / 2; ++i) f[i] = r < n ? __ldg(f2 + i) : make_float2(0.f, 0.f);
+  for (int i = 0; i < 4; ++i) {
+    const int k = 4 * half + i;
+    f[i] = (r < n && k < kMlpIn / 2) ? __ldg(f2 + k) : make_float2(0.f, 0.f);
+  }
 }
 
-// Standardised inputs x[16] from raw features (zeros past n; inputs 14 and 15 zero).
-__device__ __forceinline__ void standardise(const float2* f, bool valid, const float* mean, const float* sd,
-                                            float* x) {
+// Standardised inputs [8 h, 8 h + 8) into x[8] (zero past n and for the padding inputs 14, 15).
+__device__ __forceinline__ void standardise_half(const float2* f, bool valid, int half, const float* mean,
+                                                 const float* sd, float* x) {
 #pragma unroll
-  for (int i = 0; i < kMlpIn / 2; ++i) {
-    x[2 * i] = valid ? (f[i].x - mean[2 * i]) / sd[2 * i] : 0.f;
-    x[2 * i + 1] = valid ? (f[i].y - mean[2 * i + 1]) / sd[2 * i + 1] : 0.f;
+  for (int i = 0; i < 4; ++i) {
+    const int k = 8 * half + 2 * i;
+    x[2 * i] = (valid && k < kMlpIn) ? (f[i].x - mean[k]) / sd[k] : 0.f;
+    x[2 * i + 1] = (valid && k + 1 < kMlpIn) ? (f[i].y - mean[k + 1]) / sd[k + 1] : 0.f;
   }
-  x[14] = 0.f;
-  x[15] = 0.f;
 }
 
 // One MMA operand in shared memory: the first of its three tiles (shared-window address), the
@@ -106,8 +114,9 @@ __device__ __forceinline__ void mma_split(uint32_t d, const Operand& A, const Op
   tc::mma_commit(bar);
 }
 
-__global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ params, const float* __restrict__ feats,
-                                                      int n, float* __restrict__ logits) {
+__global__ void __launch_bounds__(kTcThreads) k_mlp_forward(const float* __restrict__ params,
+                                                            const float* __restrict__ feats, int n,
+                                                            float* __restrict__ logits) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* S = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
   const uint32_t sb = tc::smem_u32(S);
@@ -116,9 +125,10 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
   float* w3 = reinterpret_cast<float*>(S + fwd::W3);
   float* mean = reinterpret_cast<float*>(S + fwd::MEAN);
   float* sd = reinterpret_cast<float*>(S + fwd::SD);
+  float* part = reinterpret_cast<float*>(S + fwd::PART);  // [2][128] output-layer partial sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(S + fwd::BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(S + fwd::TMEM);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, row = t & (kTcM - 1), half = t >> 7;
 
   stage_weights_b(params, S + fwd::W1, fwd::W1_T, S + fwd::W2, fwd::W2_T);
   for (int i = t; i < kMlpHid; i += blockDim.x) {
@@ -137,27 +147,26 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + 32u * half;
   constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, kMlpHid);
   uint32_t phase = 0;
   bool failed = false;
 
   const int n_tiles = (n + kTcM - 1) / kTcM;
-  float2 fin[kMlpIn / 2];  // raw features of this thread's sample in the next tile
-  fetch_inputs(feats, blockIdx.x * kTcM + t, n, fin);
+  float2 fin[4];  // this thread's half of the raw features of its sample in the next tile
+  fetch_half(feats, blockIdx.x * kTcM + row, n, half, fin);
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int r = tile * kTcM + t;
+    const int r = tile * kTcM + row;
     {
-      float x[kTcK1];
-      standardise(fin, r < n, mean, sd, x);
-      tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 0, kTcK1), x);
-      tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(t, 1, kTcK1), x + 8);
+      float x[8];
+      standardise_half(fin, r < n, half, mean, sd, x);
+      tc::store8_split(S + fwd::X, fwd::X_T, tc::kmajor_off(row, half, kTcK1), x);
     }
     tc::fence_proxy_async();
     __syncthreads();
     if (t == 0)
       mma_split(tmem, kmajor(sb + fwd::X, fwd::X_T, kTcK1), kmajor(sb + fwd::W1, fwd::W1_T, kTcK1), 1, idesc, bar);
-    fetch_inputs(feats, (tile + gridDim.x) * kTcM + t, n, fin);  // in flight during this tile's MMAs
+    fetch_half(feats, (tile + gridDim.x) * kTcM + row, n, half, fin);  // in flight during this tile's MMAs
     bool ok = tc::mbar_wait(bar, phase);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -165,14 +174,15 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
       break;
     }
     tc::fence_after_sync();
+    // h1 columns [32 h, 32 h + 32) -> the H tile
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float v[16];
       tc::tmem_ld16(lane_base + 16 * q, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[16 * q + i], 0.f);
-      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(t, 2 * q, kMlpHid), v);
-      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(t, 2 * q + 1, kMlpHid), v + 8);
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b1[32 * half + 16 * q + i], 0.f);
+      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(row, 4 * half + 2 * q, kMlpHid), v);
+      tc::store8_split(S + fwd::H, fwd::H_T, tc::kmajor_off(row, 4 * half + 2 * q + 1, kMlpHid), v + 8);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -187,24 +197,28 @@ __global__ void __launch_bounds__(kTcM) k_mlp_forward(const float* __restrict__ 
       break;
     }
     tc::fence_after_sync();
-    float out = b3;
+    float acc = 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float v[16];
       tc::tmem_ld16(lane_base + 64 + 16 * q, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) out = fmaf(w3[16 * q + i], fmaxf(v[i] + b2[16 * q + i], 0.f), out);
+      for (int i = 0; i < 16; ++i) {
+        const int j = 32 * half + 16 * q + i;
+        acc = fmaf(w3[j], fmaxf(v[i] + b2[j], 0.f), acc);
+      }
     }
-    if (r < n) logits[r] = out;
+    part[half * kTcM + row] = acc;
     tc::fence_before_sync();
     __syncthreads();
+    if (half == 0 && r < n) logits[r] = b3 + part[row] + part[kTcM + row];
   }
   if (failed) {
     // A tensor-core wait gave up: this block's remaining samples get NaN logits; the MMA in
     // flight gets one more bounded wait before the tensor memory is released.
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const int r = tile * kTcM + t;
-      if (r < n) logits[r] = __int_as_float(0x7fc00000);
+      const int r = tile * kTcM + row;
+      if (half == 0 && r < n) logits[r] = __int_as_float(0x7fc00000);
     }
     tc::mbar_wait(bar, phase ^ 1u);
   }
@@ -238,8 +252,8 @@ int launch_mlp_transpose(const float* params, float* wt, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// Loss and gradient on the tensor cores: a persistent CTA of 128 threads per SM takes tiles of 128
-// samples, one per thread, and runs per tile
+// Loss and gradient on the tensor cores: a persistent CTA of 256 threads per SM takes tiles of 128
+// samples, two threads per sample (each half of the columns), and runs per tile
 //   D1 = X W1^T -> h1 = relu(D1 + b1);  D2 = H1 W2^T -> z3 = b3 + W3 . relu(D2 + b2),
 //   g = sigmoid(z3) - y, e2 = g W3 [z2 > 0];  D3 = E2 W2 -> e1 = D3 [h1 > 0];
 //   Dg += [E2 | E1]^T [H1 | X | 1]   (accumulated in tensor memory over all the CTA's tiles),
@@ -252,8 +266,8 @@ int launch_mlp_transpose(const float* params, float* wt, cudaStream_t st) {
 namespace grd {
 constexpr uint32_t E_T = 32768, XH_T = 24576, W1_T = 2048, W2_T = 8192;  // bytes of one tile
 constexpr uint32_t E = 0, XH = E + 3 * E_T, W1 = XH + 3 * XH_T, W2 = W1 + 3 * W1_T, B1 = W2 + 3 * W2_T,
-                   B2 = B1 + 256, W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, RED = SD + 64, B3 = RED + 272,
-                   BAR = B3 + 8, TMEM = BAR + 8, BYTES = TMEM + 8;
+                   B2 = B1 + 256, W3 = B2 + 256, MEAN = W3 + 256, SD = MEAN + 64, RED = SD + 64, PART = RED + 272,
+                   B3 = PART + 1024, BAR = B3 + 8, TMEM = BAR + 8, BYTES = TMEM + 8;
 // The allocation leaves room past W2's lo tile, so that no reading of the MN-major W2 operand's
 // offsets can leave the block's shared memory.
 constexpr uint32_t ALLOC = 208896;
@@ -265,10 +279,10 @@ constexpr int kXhK = 96, kEK = 128, kGN = 96;
 // Instruction descriptor bits 15 and 16: A, B MN-major.
 constexpr uint32_t kAmn = 1u << 15, kBmn = 1u << 16;
 
-__global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict__ params,
-                                                        const float* __restrict__ feats,
-                                                        const float* __restrict__ labels, int n,
-                                                        float* __restrict__ grad, float* __restrict__ loss) {
+__global__ void __launch_bounds__(kTcThreads) k_mlp_loss_grad(const float* __restrict__ params,
+                                                              const float* __restrict__ feats,
+                                                              const float* __restrict__ labels, int n,
+                                                              float* __restrict__ grad, float* __restrict__ loss) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* S = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
   const uint32_t sb = tc::smem_u32(S);
@@ -277,10 +291,12 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
   float* w3 = reinterpret_cast<float*>(S + grd::W3);
   float* mean = reinterpret_cast<float*>(S + grd::MEAN);
   float* sd = reinterpret_cast<float*>(S + grd::SD);
-  float* red = reinterpret_cast<float*>(S + grd::RED);  // dW3[64], db3, loss
+  float* red = reinterpret_cast<float*>(S + grd::RED);    // dW3[64], db3, loss
+  float* part = reinterpret_cast<float*>(S + grd::PART);  // [2][128] output-layer partial sums
   uint64_t* bar = reinterpret_cast<uint64_t*>(S + grd::BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(S + grd::TMEM);
-  const int t = threadIdx.x, warp = t >> 5;
+  const int t = threadIdx.x, warp = t >> 5, row = t & (kTcM - 1), half = t >> 7;
+  const int hc = 32 * half;  // this thread's first column of a 64-column accumulator
 
   stage_weights_b(params, S + grd::W1, grd::W1_T, S + grd::W2, grd::W2_T);
   for (int i = t; i < kMlpHid; i += blockDim.x) {
@@ -293,11 +309,9 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
     sd[t] = params[kMlpSd + t];
   }
   if (t < 66) red[t] = 0.f;
-  {  // constant columns of this thread's row of the [h1 | x | 1 | 0] tile: 80 (one) and 81-95 (zero)
-    float c[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 10, grd::kXhK), c);
-    c[0] = 0.f;
-    tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 11, grd::kXhK), c);
+  {  // constant columns of this row of the [h1 | x | 1 | 0] tile: 80 (one) and 81-95 (zero)
+    float c[8] = {half == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(row, 10 + half, grd::kXhK), c);
   }
   const float b3 = params[kMlpB3];
   if (warp == 0) tc::tmem_alloc(tmem_slot, grd::kCols);
@@ -306,36 +320,34 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
   constexpr uint32_t id_kk = tc::idesc_bf16_f32(kTcM, kMlpHid);
   constexpr uint32_t id_kmn = id_kk | kBmn;
   constexpr uint32_t id_grad = tc::idesc_bf16_f32(kTcM, grd::kGN) | kAmn | kBmn;
   uint32_t phase = 0;
   bool failed = false;
-  float acc3[kMlpHid];
+  float acc3[32];  // dW3 partial sums of this thread's 32 hidden units
 #pragma unroll
-  for (int j = 0; j < kMlpHid; ++j) acc3[j] = 0.f;
+  for (int j = 0; j < 32; ++j) acc3[j] = 0.f;
   float gsum = 0.f, lsum = 0.f;
 
   const int n_tiles = (n + kTcM - 1) / kTcM;
   int done_tiles = 0;
-  float2 fin[kMlpIn / 2];  // raw features and label of this thread's sample in the next tile
-  fetch_inputs(feats, blockIdx.x * kTcM + t, n, fin);
-  float yin = blockIdx.x * kTcM + t < n ? labels[blockIdx.x * kTcM + t] : 0.f;
+  float2 fin[4];  // this thread's half of the raw features, and the label, of its sample in the next tile
+  fetch_half(feats, blockIdx.x * kTcM + row, n, half, fin);
+  float yin = blockIdx.x * kTcM + row < n ? labels[blockIdx.x * kTcM + row] : 0.f;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++done_tiles) {
-    const int r = tile * kTcM + t;
+    const int r = tile * kTcM + row;
     const bool valid = r < n;
-    // inputs -> columns 64-79 of the [h1 | x | 1 | 0] tile
-    {
-      float x[kTcK1];
-      standardise(fin, valid, mean, sd, x);
-      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 8, grd::kXhK), x);
-      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 9, grd::kXhK), x + 8);
+    {  // inputs -> columns 64-79 of the [h1 | x | 1 | 0] tile
+      float x[8];
+      standardise_half(fin, valid, half, mean, sd, x);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(row, 8 + half, grd::kXhK), x);
     }
     const float y = yin;
     {
-      const int rn = (tile + gridDim.x) * kTcM + t;  // in flight during this tile's MMAs
-      fetch_inputs(feats, rn, n, fin);
+      const int rn = (tile + gridDim.x) * kTcM + row;  // in flight during this tile's MMAs
+      fetch_half(feats, rn, n, half, fin);
       yin = rn < n ? labels[rn] : 0.f;
     }
     tc::fence_proxy_async();
@@ -350,19 +362,19 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
       break;
     }
     tc::fence_after_sync();
-    // h1 -> columns 0-63; mask1 = [h1 > 0]
-    unsigned long long mask1 = 0ull;
+    // h1 -> columns [hc, hc + 32) of the [h1 | x | 1 | 0] tile; mask1 = [h1 > 0]
+    unsigned mask1 = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float v[16];
-      tc::tmem_ld16(lane_base + 16 * q, v);
+      tc::tmem_ld16(lane_base + hc + 16 * q, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        v[i] = fmaxf(v[i] + b1[16 * q + i], 0.f);
-        if (v[i] > 0.f) mask1 |= 1ull << (16 * q + i);
+        v[i] = fmaxf(v[i] + b1[hc + 16 * q + i], 0.f);
+        if (v[i] > 0.f) mask1 |= 1u << (16 * q + i);
       }
-      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 2 * q, grd::kXhK), v);
-      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(t, 2 * q + 1, grd::kXhK), v + 8);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(row, 4 * half + 2 * q, grd::kXhK), v);
+      tc::store8_split(S + grd::XH, grd::XH_T, tc::kmajor_off(row, 4 * half + 2 * q + 1, grd::kXhK), v + 8);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -377,30 +389,40 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
       break;
     }
     tc::fence_after_sync();
-    float z3 = b3;
+    {  // logit from the two halves' partial sums
+      float acc = 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float v[16];
-      tc::tmem_ld16(lane_base + grd::kColD2 + 16 * q, v);
+      for (int q = 0; q < 2; ++q) {
+        float v[16];
+        tc::tmem_ld16(lane_base + grd::kColD2 + hc + 16 * q, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) z3 = fmaf(w3[16 * q + i], fmaxf(v[i] + b2[16 * q + i], 0.f), z3);
+        for (int i = 0; i < 16; ++i) {
+          const int j = hc + 16 * q + i;
+          acc = fmaf(w3[j], fmaxf(v[i] + b2[j], 0.f), acc);
+        }
+      }
+      part[half * kTcM + row] = acc;
     }
+    __syncthreads();
+    const float z3 = b3 + part[row] + part[kTcM + row];
     const float g = valid ? 1.f / (1.f + expf(-z3)) - y : 0.f;
-    if (valid) lsum += fmaxf(z3, 0.f) - z3 * y + log1pf(expf(-fabsf(z3)));
-    gsum += g;
-    // e2 -> columns 0-63 of the [e2 | e1] tile; dW3 partial sums
+    if (half == 0) {
+      if (valid) lsum += fmaxf(z3, 0.f) - z3 * y + log1pf(expf(-fabsf(z3)));
+      gsum += g;
+    }
+    // e2 -> columns [hc, hc + 32) of the [e2 | e1] tile; dW3 partial sums
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float v[16];
-      tc::tmem_ld16(lane_base + grd::kColD2 + 16 * q, v);
+      tc::tmem_ld16(lane_base + grd::kColD2 + hc + 16 * q, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const float a2 = fmaxf(v[i] + b2[16 * q + i], 0.f);
+        const float a2 = fmaxf(v[i] + b2[hc + 16 * q + i], 0.f);
         acc3[16 * q + i] = fmaf(g, a2, acc3[16 * q + i]);
-        v[i] = a2 > 0.f ? g * w3[16 * q + i] : 0.f;
+        v[i] = a2 > 0.f ? g * w3[hc + 16 * q + i] : 0.f;
       }
-      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 2 * q, grd::kEK), v);
-      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 2 * q + 1, grd::kEK), v + 8);
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(row, 4 * half + 2 * q, grd::kEK), v);
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(row, 4 * half + 2 * q + 1, grd::kEK), v + 8);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -416,15 +438,15 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
       break;
     }
     tc::fence_after_sync();
-    // e1 -> columns 64-127 of the [e2 | e1] tile
+    // e1 -> columns 64 + [hc, hc + 32) of the [e2 | e1] tile
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 2; ++q) {
       float v[16];
-      tc::tmem_ld16(lane_base + 16 * q, v);
+      tc::tmem_ld16(lane_base + hc + 16 * q, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = (mask1 >> (16 * q + i)) & 1ull ? v[i] : 0.f;
-      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 8 + 2 * q, grd::kEK), v);
-      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(t, 9 + 2 * q, grd::kEK), v + 8);
+      for (int i = 0; i < 16; ++i) v[i] = (mask1 >> (16 * q + i)) & 1u ? v[i] : 0.f;
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(row, 8 + 4 * half + 2 * q, grd::kEK), v);
+      tc::store8_split(S + grd::E, grd::E_T, tc::kmajor_off(row, 9 + 4 * half + 2 * q, grd::kEK), v + 8);
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -448,25 +470,33 @@ __global__ void __launch_bounds__(kTcM) k_mlp_loss_grad(const float* __restrict_
     tc::mbar_wait(bar, phase ^ 1u);
   } else if (done_tiles > 0) {
 #pragma unroll
-    for (int j = 0; j < kMlpHid; ++j) atomicAdd(&red[j], acc3[j]);
-    atomicAdd(&red[64], gsum);
-    atomicAdd(&red[65], lsum);
-    // Dg row t: dW2 row j = t and db2[j] (t < 64), or dW1 row i = t - 64 and db1[i]
+    for (int j = 0; j < 32; ++j) atomicAdd(&red[hc + j], acc3[j]);
+    if (half == 0) {
+      atomicAdd(&red[64], gsum);
+      atomicAdd(&red[65], lsum);
+    }
+    // Dg row `row` (warp-uniform branches): dW2 row j = row, columns [hc, hc + 32), and db2[j]
+    // (column 80, half 0); or dW1 row i = row - 64 (columns 64-77, half 0) and db1[i] (half 1).
     float v[16];
-    if (t < kMlpHid) {
+    if (row < kMlpHid) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        tc::tmem_ld16(lane_base + grd::kColG + 16 * q, v);
+      for (int q = 0; q < 2; ++q) {
+        tc::tmem_ld16(lane_base + grd::kColG + hc + 16 * q, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) atomicAdd(grad + kMlpW2 + t * kMlpHid + 16 * q + i, v[i]);
+        for (int i = 0; i < 16; ++i) atomicAdd(grad + kMlpW2 + row * kMlpHid + hc + 16 * q + i, v[i]);
       }
-    } else {
+      if (half == 0) {
+        tc::tmem_ld16(lane_base + grd::kColG + 80, v);
+        atomicAdd(grad + kMlpB2 + row, v[0]);
+      }
+    } else if (half == 0) {
       tc::tmem_ld16(lane_base + grd::kColG + 64, v);
 #pragma unroll
-      for (int k = 0; k < kMlpIn; ++k) atomicAdd(grad + kMlpW1 + (t - kMlpHid) * kMlpIn + k, v[k]);
+      for (int k = 0; k < kMlpIn; ++k) atomicAdd(grad + kMlpW1 + (row - kMlpHid) * kMlpIn + k, v[k]);
+    } else {
+      tc::tmem_ld16(lane_base + grd::kColG + 80, v);
+      atomicAdd(grad + kMlpB1 + row - kMlpHid, v[0]);
     }
-    tc::tmem_ld16(lane_base + grd::kColG + 80, v);
-    atomicAdd(grad + (t < kMlpHid ? kMlpB2 + t : kMlpB1 + t - kMlpHid), v[0]);
     __syncthreads();
     if (t < kMlpHid) atomicAdd(grad + kMlpW3 + t, red[t]);
     if (t == kMlpHid) atomicAdd(grad + kMlpB3, red[64]);
@@ -524,7 +554,7 @@ int launch_mlp_forward(const float* params, const float* feats, int n, float* lo
   int sms = 0;
   if (tc_prepare(reinterpret_cast<const void*>(k_mlp_forward), smem, &sms) != 0) return -3;
   const int tiles = (n + kTcM - 1) / kTcM;
-  k_mlp_forward<<<std::min(tiles, kFwdCtasPerSm * sms), kTcM, smem, st>>>(params, feats, n, logits);
+  k_mlp_forward<<<std::min(tiles, kFwdCtasPerSm * sms), kTcThreads, smem, st>>>(params, feats, n, logits);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -536,7 +566,7 @@ int launch_mlp_loss_grad(const float* params, const float* feats, const float* l
   if (cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, st) != cudaSuccess) return -3;
   if (cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess) return -3;
   const int tiles = (n + kTcM - 1) / kTcM;
-  if (n > 0) k_mlp_loss_grad<<<std::min(tiles, sms), kTcM, smem, st>>>(params, feats, labels, n, grad, loss);
+  if (n > 0) k_mlp_loss_grad<<<std::min(tiles, sms), kTcThreads, smem, st>>>(params, feats, labels, n, grad, loss);
   k_mlp_scale<<<8, 256, 0, st>>>(grad, loss, n > 0 ? 1.f / n : 0.f);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

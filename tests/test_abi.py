@@ -68,6 +68,10 @@ def test_host_side_argument_checks(kf):
     v = ctypes.c_void_p
     assert lib.kf_mlp_forward(v(256), v(260), 1, v(512), None) == kf.KF_ERR_ARG
     assert lib.kf_mlp_loss_grad(v(256), v(260), v(1024), 1, v(512), v(768), None) == kf.KF_ERR_ARG
+    # bounded-wait probe: limits outside [1 us, 1 s] and a null output are rejected
+    assert lib.kf_wait_probe(0, v(256), None) == kf.KF_ERR_ARG
+    assert lib.kf_wait_probe(2_000_000, v(256), None) == kf.KF_ERR_ARG
+    assert lib.kf_wait_probe(1000, None, None) == kf.KF_ERR_ARG
 
 
 def test_missing_library_fails_loudly(tmp_path):
