@@ -135,7 +135,7 @@ typedef struct {
  * kept per seed (<= KF_MAX_K); max_miss: surfaces a candidate may cross without a hit; lmax:
  * length of each output hit list (3 seed hits + at most lmax-3 steps; 4 <= lmax <= KF_MAX_LMAX);
  * block_threads: threads per block (0 = the size keeping most warps resident; a multiple of 32,
- * <= 256);
+ * <= 256; with the learned proposal <= 192, else KF_ERR_CAPACITY);
  * blocks_per_sm: resident blocks per SM for the persistent grid (0 = occupancy maximum). */
 typedef struct {
   float chi2_cut;

@@ -506,8 +506,12 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
 // uniform field are compiled in alone; each option left out keeps its code out of the kernel.
 constexpr int kFeatSteer = 1, kFeatMaterial = 2, kFeatField = 4, kFeatAll = 7;
 
+// Blocks of the learned instances hold at most 192 threads: at two blocks per SM that leaves them
+// 170 registers, which their scoring and score-ordered lists need (capped at 128, as the plain
+// instances are for 256-thread blocks, they spilled ~150 bytes per thread and ran 21-29% slower).
+constexpr int kFindMaxBlockLearned = 192;
 template <int KC, bool LEARNED, int FEAT>
-__global__ void __launch_bounds__(256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp,
+__global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_find_tracks(const __grid_constant__ DevGeom Gp,
                                                         const __grid_constant__ DevMat M, FindArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   {
@@ -1035,6 +1039,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32))
     return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;
+  if (learned && p->block_threads > kFindMaxBlockLearned) return KF_ERR_CAPACITY;
   if (p->k_capacity < 0 || p->k_capacity > KF_MAX_K) return KF_ERR_ARG;
   const int kc = pick_kc(std::max(learned ? std::max(p->k_max, p->top_n) : p->k_max, p->k_capacity));
   if (kc < 0) return KF_ERR_ARG;
@@ -1076,7 +1081,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
     if (rc != KF_OK) return rc;
   } else {
     int best_warps = 0;
-    for (int blk = 256; blk >= 64; blk -= 32) {
+    for (int blk = learned ? kFindMaxBlockLearned : 256; blk >= 64; blk -= 32) {
       size_t sm = 0;
       int o = 0;
       const int rc = occupancy(blk, &sm, &o);
