@@ -575,8 +575,10 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     }
     // One block-wide vote per step: the block's warps stay in step with each other, so the SM
     // fetches the code of one or two phases at a time (the kernel is larger than the instruction
-    // cache); the block ends when none of its warps has a seed.
-    if (!__syncthreads_or(seed >= 0)) break;
+    // cache); the block ends when none of its warps has a seed. The learned instances vote per
+    // warp: their network evaluations fall on a few warps of a step, and a block-wide vote made the
+    // block's other warps wait for them (9-14% of their time on the barrel workload).
+    if (LEARNED ? !__any_sync(kFull, seed >= 0) : !__syncthreads_or(seed >= 0)) break;
 
     // ---- a fresh group loads its seed state into slot 0 ------------------------------------
     int failed = 0;
