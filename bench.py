@@ -272,8 +272,10 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
             fit_block, ms_fit = kf.autotune_fit(g, d["hits"], d["hit_surface"], cal["hits"], stream=stream)
         torch.cuda.synchronize()
         tuning = {"calibration_seeds": n_cal, "find_block_threads": prm.block_threads,
-                  "find_k_capacity": prm.k_capacity, "find_ms": ms_find, "fit_block_threads": fit_block,
-                  "fit_ms": ms_fit}
+                  "find_k_capacity": prm.k_capacity, "find_adaptive_capacity": prm.adaptive_capacity,
+                  "find_ms": ms_find, "fit_block_threads": fit_block, "fit_ms": ms_fit}
+        # the tuned configuration's workspace (adaptive capacity adds its overflow list)
+        wsb = torch.empty(max(kf.find_workspace_size(n_seeds, prm), 256), dtype=torch.uint8, device=dev)
     parts = ["index"] + (["clean"] if clean else []) + ["find"] + (["dedup"] if clean else []) + ["fit"]
 
     def step(s, events=None, dd=None, fo=None, fi=None):
@@ -341,9 +343,10 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
         dist.barrier()
     from paper_1906_02253_gb300 import shard
     ms_step = shard.max_over_ranks(statistics.mean(t_steps), device=dev)
-    # index, seed states, find, fit kernels (plus one memset node); cleaning: count, 3 scan kernels,
-    # fill, seed directions, decision; duplicate removal: count, 3 scan kernels, fill, decision
-    launches_per_step = 4 + (7 + 6 if clean else 0)
+    # index, seed states, find, fit kernels (plus one memset node); adaptive capacity: a second find
+    # pass; cleaning: count, 3 scan kernels, fill, seed directions, decision; duplicate removal:
+    # count, 3 scan kernels, fill, decision
+    launches_per_step = 4 + (1 if prm.adaptive_capacity > 0 else 0) + (7 + 6 if clean else 0)
 
     # Per-part durations: the same launches eager, events on the launching stream.
     kern = {k: [] for k in parts}

@@ -166,6 +166,15 @@ typedef struct {
    * logit units) of its best make children, the best always. A window whose best hit stands out then
    * keeps one child. */
   float score_margin;
+  /* Adaptive capacity (plain finding only; 0 = off, the default): a first pass runs every seed with
+   * adaptive_capacity candidate slots (rounded up to a compiled capacity), more seeds per warp, and
+   * finishes the seeds whose children never outnumber those slots: keeping all of a step's children
+   * is what k_max does then, so their results are those of the single pass. The other seeds are
+   * listed in the workspace and found again, from their seed state, by a second pass at the full
+   * capacity. Ignored when no smaller compiled capacity exists; KF_ERR_ARG with the learned
+   * proposal or outside [0, KF_MAX_K]. Pays where most seeds carry few candidates (barrel + disk
+   * events with noise). */
+  int adaptive_capacity;
 } KfFindParams;
 
 /* Build the hit index (the binned hit structure behind the per-layer search windows, Sec. 3.1,
@@ -326,7 +335,8 @@ int kf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, 
  * the library of KF_STATIC_SCRATCH_BYTES (about 7.3 MiB),
  * held on every GPU that loads the library until the process exits. At most KF_STATIC_MAX_SEEDS
  * seeds per call: more returns KF_ERR_CAPACITY and launches nothing (split the seeds into
- * chunks). The call allocates nothing and calls no allocating routine.
+ * chunks). Adaptive capacity needs workspace for its overflow list: params->adaptive_capacity must
+ * be 0 here (else KF_ERR_ARG). The call allocates nothing and calls no allocating routine.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
  * that device current); make that first call before any stream capture. Every call uses the same
  * array and leaves its contents behind: calls whose kernels can overlap on the GPU (several
@@ -340,10 +350,13 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
 
 /* Autotuner for the persistent finder (not in the paper): runs kf_find_tracks on the given seeds
  * (a calibration subset of the workload) for every block size 64..256 (step 32) and for the
- * smallest and the next compiled candidate capacity, times each run with CUDA events (the stream
- * is synchronised: do not call it during a stream capture), and writes the fastest block size
- * and capacity into params->block_threads and params->k_capacity; *best_ms receives its time.
- * Every configuration gives the same results. Outputs and workspace as for kf_find_tracks. */
+ * smallest and the next compiled candidate capacity, and for plain finding with k_max > 4 with
+ * and without adaptive capacity 4, times each run with CUDA events (the stream is synchronised: do
+ * not call it during a stream capture), and writes the fastest block size, capacity and adaptive
+ * capacity into params->block_threads, params->k_capacity and params->adaptive_capacity; *best_ms
+ * receives its time. Every configuration gives the same results. Outputs as for kf_find_tracks; a
+ * configuration whose workspace is larger than workspace_bytes is passed over (size the workspace
+ * with adaptive_capacity = 4 to let it compete). */
 int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
                      const int* seed_hits, const int* seed_event, int n_seeds, KfFindParams* params, int* hits_out,
                      int* nhits_out, float* chi2_out, float* state_out, float* cov_out, int* status_out,

@@ -61,7 +61,7 @@ class KfFindParams(ctypes.Structure):
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int),
                 ("steering", ctypes.POINTER(KfSteering)), ("seed_keep", ctypes.c_void_p),
-                ("score_margin", ctypes.c_float)]
+                ("score_margin", ctypes.c_float), ("adaptive_capacity", ctypes.c_int)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
@@ -255,10 +255,12 @@ def steering(tables: dict) -> KfSteering:
 
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
                 blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0,
-                steering_tables: dict = None, seed_keep=None, score_margin: float = 0.0) -> KfFindParams:
+                steering_tables: dict = None, seed_keep=None, score_margin: float = 0.0,
+                adaptive_capacity: int = 0) -> KfFindParams:
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
     ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
-    next-surface rule; ``score_margin`` > 0 switches the learned proposal to its score-margin rule."""
+    next-surface rule; ``score_margin`` > 0 switches the learned proposal to its score-margin rule;
+    ``adaptive_capacity`` > 0 runs plain finding in two passes (see kfgb.h)."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
@@ -269,7 +271,7 @@ def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_thr
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
                        None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity),
                        None if st is None else ctypes.pointer(st), None if seed_keep is None else seed_keep.data_ptr(),
-                       float(score_margin))
+                       float(score_margin), int(adaptive_capacity))
     prm._mlp_ref = mlp  # keep the buffers alive with the parameters
     prm._steer_ref = st
     prm._keep_ref = seed_keep
@@ -512,10 +514,16 @@ def mlp_train(params, features, labels, epochs: int = 3, batch: int = 4096, lr: 
 
 def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits, seed_event, params: KfFindParams,
                   stream=None):
-    """Time every block size and candidate capacity on these seeds (a calibration subset) and
-    return (tuned params, best ms). Synchronises the stream."""
-    out = find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, params, stream=stream)
-    ws = out["workspace"]
+    """Time every block size, candidate capacity and (plain finding, k_max > 4) adaptive capacity on
+    these seeds (a calibration subset) and return (tuned params, best ms). Synchronises the stream."""
+    # Workspace for the largest configuration tried: adaptive capacity adds its overflow list.
+    wide = KfFindParams.from_buffer_copy(params)
+    if not (params.mlp and params.top_n > 0) and params.k_max > 4:
+        wide.adaptive_capacity = 4
+    n = seed_hits.shape[1]
+    ws = torch.empty(max(find_workspace_size(n, wide), find_workspace_size(n, params), 256), dtype=torch.uint8,
+                     device=seed_hits.device)
+    out = find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, params, workspace=ws, stream=stream)
     tuned = KfFindParams.from_buffer_copy(params)
     tuned._mlp_ref = getattr(params, "_mlp_ref", None)  # keep what the copied pointers point to alive
     tuned._steer_ref = getattr(params, "_steer_ref", None)

@@ -417,6 +417,7 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
   FindPlan plan;
   FindArgs A;
   bool empty = false;
+  if (params && params->adaptive_capacity != 0) return KF_ERR_ARG;  // the scratch holds no overflow list
   int rc = prepare_find(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, params, hits_out, nhits_out,
                         chi2_out, state_out, cov_out, status_out, KF_STATIC_MAX_SEEDS, &G, &M, &plan, &A, &empty);
   if (rc != KF_OK) return rc;
@@ -442,21 +443,29 @@ int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const floa
   int cap_opts[2] = {0, 0}, n_cap = 0;
   for (int c : caps)
     if (c >= need && n_cap < 2) cap_opts[n_cap++] = c;
+  // Plain finding with k_max > 4 also tries adaptive capacity 4 (a configuration whose workspace
+  // does not fit the caller's fails and is passed over).
+  const bool plain = !(params->mlp && params->top_n > 0);
+  const int ad_opts[2] = {0, 4};
+  const int n_ad = plain && params->k_max > 4 ? 2 : 1;
   KfFindParams best = *params;
   float best_t = -1.f;
   for (int ci2 = 0; ci2 < n_cap; ++ci2) {
     for (int blk = 64; blk <= 256; blk += 32) {
-      KfFindParams p = *params;
-      p.block_threads = blk;
-      p.k_capacity = cap_opts[ci2];
-      p.blocks_per_sm = 0;
-      const float t = time_config(st, [&]() {
-        return kf_find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, &p, hits_out, nhits_out,
-                              chi2_out, state_out, cov_out, status_out, workspace, workspace_bytes, stream);
-      });
-      if (t >= 0.f && (best_t < 0.f || t < best_t)) {
-        best_t = t;
-        best = p;
+      for (int ai = 0; ai < n_ad; ++ai) {
+        KfFindParams p = *params;
+        p.block_threads = blk;
+        p.k_capacity = cap_opts[ci2];
+        p.blocks_per_sm = 0;
+        p.adaptive_capacity = ad_opts[ai];
+        const float t = time_config(st, [&]() {
+          return kf_find_tracks(geom, index, hits, hit_surface, seed_hits, seed_event, n_seeds, &p, hits_out,
+                                nhits_out, chi2_out, state_out, cov_out, status_out, workspace, workspace_bytes, stream);
+        });
+        if (t >= 0.f && (best_t < 0.f || t < best_t)) {
+          best_t = t;
+          best = p;
+        }
       }
     }
   }

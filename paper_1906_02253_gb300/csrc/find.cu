@@ -534,7 +534,10 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
   WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
   const float* __restrict__ wmlp = A.mlp_t;  // transposed network parameters (L1/L2)
-  const int keep = LEARNED ? A.top_n : A.k_max;  // capacity of a lane's list during the scan
+  // Capacity of a lane's list during the scan; a first pass of adaptive capacity (detect) keeps at
+  // most its own slots (a lane with more passing hits makes its seed overflow anyway).
+  const int keep = LEARNED ? A.top_n : (A.detect ? min(A.k_max, KC) : A.k_max);
+  const bool detect = !LEARNED && A.detect != 0;
   const bool margin_on = LEARNED && A.score_margin > 0.f;
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
@@ -557,7 +560,9 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     // here rather than costing the group a step each.
     if (want && slot == 0) {
       s = atomicAdd(A.counter, 1);
-      if (A.seed_keep)
+      if (A.seed_list)  // second pass of adaptive capacity: the first pass's overflowing seeds
+        s = s < *A.seed_list_count ? A.seed_list[s] : n;
+      else if (A.seed_keep)
         while (s < n && A.seed_keep[s] == 0) s = atomicAdd(A.counter, 1);
     }
     s = __shfl_sync(kFull, s, gbase);
@@ -677,6 +682,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     const int nphi = si >= 0 ? G.n_phi[si] : 1, n2 = si >= 0 ? G.n_2nd[si] : 1;
     int np = 0;      // buffered pairs
     int my_cnt = 0;  // buffered pairs of this lane's window: one contiguous run of the buffer
+    int npass = 0;   // passing hits of this lane's window (a detecting pass counts beyond its list)
     // Buffered passing pairs go to their owner's list: the k_max best by (total chi2, hit id)
     // (plain), or, with the learned proposal, the top_n best by network score. A pair is scored
     // (by all lanes together) only when its owner has more passing hits than top_n; otherwise
@@ -751,6 +757,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
       } else {
         for (int k = start; k < start + my_cnt; ++k)
           hl_insert(W, lane, hl_n, keep, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
+        npass += my_cnt;
       }
       my_cnt = 0;
     };
@@ -879,7 +886,10 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     // over the group's heads (a segmented minimum by shuffles) give the seed's children in rank
     // order, and the child of rank j goes to the group's slot j. Keys of different lanes differ
     // (they carry the slot), so the order is the same total order as comparing all children.
-    const int nch = (on && kind != 3) ? (kind == 0 ? hl_n : 1) : 0;
+    // In a detecting pass a seed whose children outnumber the slots overflows: its group takes no
+    // part in the selection and the seed goes to the second pass (its children all fit otherwise,
+    // and keeping them all is what the full capacity does).
+    int nch = (on && kind != 3) ? (kind == 0 ? (detect ? npass : hl_n) : 1) : 0;
     // Rounds: the most children any group of the warp has, up to k_max.
     int tot = nch;
 #pragma unroll
@@ -887,7 +897,10 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
       const int v = __shfl_down_sync(kFull, tot, off);
       if (slot + off < KC) tot += v;
     }
-    const int rounds = min(cap, static_cast<int>(__reduce_max_sync(kFull, in_grp && slot == 0 ? tot : 0)));
+    const bool ovf = detect && __shfl_sync(kFull, tot, gbase) > KC;
+    if (ovf) nch = 0;
+    const int rounds =
+        min(cap, static_cast<int>(__reduce_max_sync(kFull, in_grp && slot == 0 && !ovf ? tot : 0)));
     unsigned long long mk = ~0ull, nk = ~0ull;  // this lane's head key and the one after it
     if (nch > 0) mk = kind == 0 ? pack_key(c.nh + 1, W.hl_tot[0][lane], slot << 2) : pack_key(c.nh, c.chi2, (slot << 2) | kind);
     if (nch > 1) nk = pack_key(c.nh + 1, W.hl_tot[1][lane], slot << 2);
@@ -956,9 +969,13 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     if (on) ++step;
     const unsigned live = __ballot_sync(kFull, on && won && !nc.stopped);
     const bool done = on && (((live & gmask) == 0u) || step >= max_steps);
-    if (done && slot == 0)
-      write_track(W, trace, gbase, step, seed, n, A.lmax, A.seed_hits, A.hits_out, A.nhits_out, A.chi2_out,
-                  A.state_out, A.cov_out, A.status_out);
+    if (done && slot == 0) {
+      if (ovf)
+        A.ovf_list[atomicAdd(A.ovf_count, 1)] = seed;
+      else
+        write_track(W, trace, gbase, step, seed, n, A.lmax, A.seed_hits, A.hits_out, A.nhits_out, A.chi2_out,
+                    A.state_out, A.cov_out, A.status_out);
+    }
     __syncwarp();
     if (done) {
       seed = -1;
@@ -1045,6 +1062,12 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   if (p->k_capacity < 0 || p->k_capacity > KF_MAX_K) return KF_ERR_ARG;
   const int kc = pick_kc(std::max(learned ? std::max(p->k_max, p->top_n) : p->k_max, p->k_capacity));
   if (kc < 0) return KF_ERR_ARG;
+  // Adaptive capacity (plain finding only): a first pass at the smallest compiled capacity >= the
+  // requested one, when that is below the full capacity.
+  const int ac = p->adaptive_capacity;
+  if (ac < 0 || ac > KF_MAX_K || (ac > 0 && learned)) return KF_ERR_ARG;
+  int kc1 = ac > 0 ? pick_kc(ac) : 0;
+  if (kc1 >= kc) kc1 = 0;
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
   const int feat = compiled_features(learned, features);
@@ -1052,10 +1075,10 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   static int occ_cache[16][6][2][5][8][32] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return KF_ERR_ARG;
-  const int ki = kc == 1 ? 0 : kc == 2 ? 1 : kc == 4 ? 2 : kc == 6 ? 3 : kc == 8 ? 4 : 5;
-  auto occupancy = [&](int blk, size_t* smem_out, int* occ_out) {
+  auto occupancy = [&](int kcx, int blk, size_t* smem_out, int* occ_out) {
+    const int ki = kcx == 1 ? 0 : kcx == 2 ? 1 : kcx == 4 ? 2 : kcx == 6 ? 3 : kcx == 8 ? 4 : 5;
     size_t sm = 0;
-    dispatch_find(kc, learned, feat, [&](auto k) {
+    dispatch_find(kcx, learned, feat, [&](auto k) {
       sm = kGeomBytes + warp_smem_bytes<decltype(k)::kc, decltype(k)::learned>(p->lmax) * (blk / 32);
       return KF_OK;
     });
@@ -1065,7 +1088,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
     int& cached = occ_cache[dev][ki][learned][fi][blk / 32 - 1][p->lmax];
     if (cached == 0) {
       int o = 0;
-      const int rc = dispatch_find(kc, learned, feat, [&](auto k) {
+      const int rc = dispatch_find(kcx, learned, feat, [&](auto k) {
         return kc_occupancy<decltype(k)::kc, decltype(k)::learned, decltype(k)::feat>(blk, sm, &o);
       });
       if (rc != KF_OK) return rc;
@@ -1074,45 +1097,62 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
     *occ_out = cached > 0 ? cached : 0;
     return KF_OK;
   };
-  // Block size: the caller's, or the one that keeps the most warps resident per SM.
-  int block = p->block_threads;
-  size_t smem = 0;
-  int occ = 0;
-  if (block != 0) {
-    const int rc = occupancy(block, &smem, &occ);
-    if (rc != KF_OK) return rc;
-  } else {
-    int best_warps = 0;
-    for (int blk = learned ? kFindMaxBlockLearned : 256; blk >= 64; blk -= 32) {
-      size_t sm = 0;
-      int o = 0;
-      const int rc = occupancy(blk, &sm, &o);
+  // Block size (the caller's, or the one that keeps the most warps resident per SM), persistent
+  // grid and shared memory of the instance with capacity kcx.
+  auto choose = [&](int kcx, int* block_out, int* grid_out, size_t* smem_out) {
+    int block = p->block_threads;
+    size_t smem = 0;
+    int occ = 0;
+    if (block != 0) {
+      const int rc = occupancy(kcx, block, &smem, &occ);
       if (rc != KF_OK) return rc;
-      if (o * blk / 32 > best_warps) {
-        best_warps = o * blk / 32;
-        block = blk;
-        smem = sm;
-        occ = o;
+    } else {
+      int best_warps = 0;
+      for (int blk = learned ? kFindMaxBlockLearned : 256; blk >= 64; blk -= 32) {
+        size_t sm = 0;
+        int o = 0;
+        const int rc = occupancy(kcx, blk, &sm, &o);
+        if (rc != KF_OK) return rc;
+        if (o * blk / 32 > best_warps) {
+          best_warps = o * blk / 32;
+          block = blk;
+          smem = sm;
+          occ = o;
+        }
       }
     }
+    if (occ < 1) return KF_ERR_CAPACITY;
+    int bps = p->blocks_per_sm;
+    if (bps == 0 || bps > occ) bps = occ;
+    const long long groups_per_block = static_cast<long long>(block / 32) * (32 / kcx);
+    const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
+    *block_out = block;
+    *grid_out = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
+    *smem_out = smem;
+    return KF_OK;
+  };
+  int rc = choose(kc, &plan->block, &plan->grid, &plan->smem);
+  if (rc != KF_OK) return rc;
+  plan->kc1 = kc1;
+  plan->block1 = plan->grid1 = 0;
+  plan->smem1 = 0;
+  if (kc1 > 0) {
+    rc = choose(kc1, &plan->block1, &plan->grid1, &plan->smem1);
+    if (rc != KF_OK) return rc;
   }
-  if (occ < 1) return KF_ERR_CAPACITY;
-  int bps = p->blocks_per_sm;
-  if (bps == 0 || bps > occ) bps = occ;
-  const int warps = block / 32;
-  const long long groups_per_block = static_cast<long long>(warps) * (32 / kc);
-  const long long want = (static_cast<long long>(n_seeds) + groups_per_block - 1) / groups_per_block;
   plan->kc = kc;
   plan->learned = learned;
   plan->feat = feat;
-  plan->block = block;
-  plan->grid = static_cast<int>(std::max(1LL, std::min<long long>(static_cast<long long>(sms) * bps, want)));
-  plan->smem = smem;
   auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-  plan->off_state = 256;  // after the work counter
+  plan->off_state = 256;  // after the work counters
   plan->off_surf = up(plan->off_state + static_cast<size_t>(kSeedWords) * n_seeds * sizeof(float));
   plan->off_mlp = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
   plan->ws_bytes = learned ? up(plan->off_mlp + static_cast<size_t>(kMlpParamsAll) * sizeof(float)) : plan->off_mlp;
+  plan->off_ovf = 0;
+  if (kc1 > 0) {
+    plan->off_ovf = plan->ws_bytes;
+    plan->ws_bytes = up(plan->off_ovf + static_cast<size_t>(n_seeds) * sizeof(int));
+  }
   return KF_OK;
 }
 
@@ -1161,8 +1201,26 @@ int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& 
     if (launch_mlp_transpose(A.mlp, wt, stream) != 0) return KF_ERR_CUDA;
     A.mlp_t = wt;
   }
-  if (cudaMemsetAsync(A.counter, 0, sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
+  // Work counters: [0] the (first) pass's seed queue, [1] the second pass's, [2] the overflow count.
+  if (cudaMemsetAsync(A.counter, 0, 3 * sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;
+  A.detect = 0;
+  A.ovf_list = A.ovf_count = nullptr;
+  A.seed_list = A.seed_list_count = nullptr;
   k_seed_states<<<(A.n_seeds + 127) / 128, 128, 0, stream>>>(G, M, A);
+  if (plan.kc1 > 0) {
+    // First pass at the smaller capacity; its overflowing seeds go to the second pass.
+    FindArgs A1 = A;
+    A1.detect = 1;
+    A1.ovf_list = reinterpret_cast<int*>(base + plan.off_ovf);
+    A1.ovf_count = A.counter + 2;
+    dispatch_find(plan.kc1, false, plan.feat, [&](auto k) {
+      k_find_tracks<decltype(k)::kc, false, decltype(k)::feat><<<plan.grid1, plan.block1, plan.smem1, stream>>>(G, M, A1);
+      return KF_OK;
+    });
+    A.counter = A.counter + 1;
+    A.seed_list = A1.ovf_list;
+    A.seed_list_count = A1.ovf_count;
+  }
   dispatch_find(plan.kc, plan.learned, plan.feat, [&](auto k) {
     k_find_tracks<decltype(k)::kc, decltype(k)::learned, decltype(k)::feat>
         <<<plan.grid, plan.block, plan.smem, stream>>>(G, M, A);

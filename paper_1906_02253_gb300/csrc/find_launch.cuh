@@ -37,6 +37,15 @@ struct FindArgs {
   int* counter;
   float* seed_state;  // [28][n_seeds]: p[6], C[21], chi2 (< 0: failed seed)
   int* seed_surf;     // [n_seeds]: surface of the third seed hit
+  // Adaptive capacity (plain finding): a first pass at a smaller capacity (detect = 1) finishes the
+  // seeds whose children never outnumber its slots, which then have exactly the results of the
+  // full capacity, and lists the others in ovf_list (*ovf_count of them) without writing their
+  // outputs; the second pass takes its seeds from that list (seed_list, *seed_list_count).
+  int detect;
+  int* ovf_list;
+  int* ovf_count;
+  const int* seed_list;
+  const int* seed_list_count;
 };
 
 // Candidate capacity kc (smallest compiled capacity >= k_max), persistent grid, shared memory,
@@ -47,6 +56,10 @@ struct FindPlan {
   int feat;  // options compiled into the instance: 1 steering, 2 material map and energy loss, 4 field
   size_t smem;
   size_t off_state, off_surf, off_mlp, ws_bytes;
+  // Adaptive capacity: the first pass's capacity (0 = a single pass), launch and shared memory,
+  // and the overflow list's place in the workspace.
+  int kc1, block1, grid1;
+  size_t smem1, off_ovf;
 };
 
 // general: the geometry or the parameters use region steering, the material map, energy loss or

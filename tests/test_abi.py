@@ -64,6 +64,11 @@ def test_host_side_argument_checks(kf):
     # finder parameters: k above the compiled maximum
     p = kf.find_params(30.0, kf.KF_MAX_K + 1, 1, 17)
     assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
+    # adaptive capacity: plain finding only, within [0, KF_MAX_K]
+    p = kf.find_params(30.0, 8, 1, 17, adaptive_capacity=-1)
+    assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
+    p = kf.find_params(30.0, 8, 1, 17, adaptive_capacity=kf.KF_MAX_K + 1)
+    assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
     # network kernels read feature rows as float pairs: an odd float offset is rejected
     v = ctypes.c_void_p
     assert lib.kf_mlp_forward(v(256), v(260), 1, v(512), None) == kf.KF_ERR_ARG

@@ -10,7 +10,10 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_graph_replay_equals_eager_calls():
+@pytest.mark.parametrize("adaptive", [0, 4])
+def test_graph_replay_equals_eager_calls(adaptive):
+    """With adaptive capacity the finder is two passes whose second takes its seeds (and their
+    number) from device memory written by the first: the graph needs no host synchronisation."""
     import __graft_entry__ as ge
     ge.build_library()
     import paper_1906_02253_gb300 as kf
@@ -24,7 +27,7 @@ def test_graph_replay_equals_eager_calls():
     keep = torch.ones(n, dtype=torch.int32, device=cuda)
     tkeep = torch.ones(n, dtype=torch.int32, device=cuda)
     dws = torch.empty(kf.dedup_workspace_size(n, lmax, nh), dtype=torch.uint8, device=cuda)
-    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, seed_keep=keep)
+    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, seed_keep=keep, adaptive_capacity=adaptive)
     fout = dict(hits=torch.empty((lmax, n), dtype=torch.int32, device=cuda),
                 nhits=torch.empty(n, dtype=torch.int32, device=cuda),
                 chi2=torch.empty(n, dtype=torch.float32, device=cuda),

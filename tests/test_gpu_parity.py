@@ -519,3 +519,49 @@ def test_autotuner_configurations_give_identical_results(kf):
     assert tuned.block_threads in range(64, 257, 32) and tuned.k_capacity in (6, 8) and ms > 0
     blk, ms = kf.autotune_fit(g, dev["hits"], dev["hit_surface"], dev["track_hits"])
     assert blk in range(64, 257, 32) and ms > 0
+
+
+def _find_gpu(kf, wl, b, **kw):
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    prm = kf.find_params(wl.chi2_cut, kw.get("k_max", wl.k_max), wl.max_miss, wl.lmax,
+                         steering_tables=kw.get("steering"), adaptive_capacity=kw.get("adaptive", 0),
+                         block_threads=kw.get("block", 0))
+    out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+    torch.cuda.synchronize()
+    # work counters at the head of the workspace: [2] = seeds the first pass left to the second
+    overflow = int(out["workspace"][8:12].view(torch.int32).item())
+    return {k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}, overflow
+
+
+@pytest.mark.parametrize("wl_name,n_ev,k,adaptive,opts", [
+    ("hi_occ", 3, 8, 4, {}), ("hi_occ", 3, 8, 2, {}), ("hi_occ", 3, 8, 4, {"block": 96}),
+    ("find", 3, 6, 4, {}), ("find", 3, 16, 4, {}), ("material", 3, 6, 4, {}), ("hi_occ", 3, 8, 4, {"steer": True})])
+def test_adaptive_capacity_gives_the_single_pass_results(kf, wl_name, n_ev, k, adaptive, opts):
+    """Two passes (a small capacity first, its overflowing seeds again at the full capacity) give
+    exactly the outputs of one pass at the full capacity, and both passes do work."""
+    wl = synth.workload(wl_name, n_events=n_ev)
+    b = synth.generate(wl)
+    kw = {"k_max": k, "block": opts.get("block", 0)}
+    if opts.get("steer"):
+        kw["steering"] = synth.steering_tables(wl, 0.4, 1.8, endcap_barrels=3)
+    one, ovf1 = _find_gpu(kf, wl, b, **kw)
+    two, ovf2 = _find_gpu(kf, wl, b, adaptive=adaptive, **kw)
+    assert ovf1 == 0
+    n = one["status"].shape[0]
+    assert 0 < ovf2 < n, (ovf2, n)
+    for key in ("hits", "nhits", "status"):
+        assert np.array_equal(one[key], two[key]), key
+    for key in ("chi2", "state", "cov"):
+        assert np.array_equal(one[key].view(np.uint32), two[key].view(np.uint32)), key
+
+
+def test_adaptive_capacity_parity_with_the_oracle(kf):
+    wl = synth.workload("hi_occ", n_events=3)
+    b = synth.generate(wl)
+    gpu, ovf = _find_gpu(kf, wl, b, adaptive=4)
+    assert ovf > 0
+    sh, st = b.seeds()
+    ora = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st])
+    _assert_find_parity(b, gpu, ora, st)
