@@ -166,14 +166,14 @@ typedef struct {
    * logit units) of its best make children, the best always. A window whose best hit stands out then
    * keeps one child. */
   float score_margin;
-  /* Adaptive capacity (plain finding only; 0 = off, the default): a first pass runs every seed with
-   * adaptive_capacity candidate slots (rounded up to a compiled capacity), more seeds per warp, and
-   * finishes the seeds whose children never outnumber those slots: keeping all of a step's children
-   * is what k_max does then, so their results are those of the single pass. The other seeds are
-   * listed in the workspace and found again, from their seed state, by a second pass at the full
-   * capacity. Ignored when no smaller compiled capacity exists; KF_ERR_ARG with the learned
-   * proposal or outside [0, KF_MAX_K]. Pays where most seeds carry few candidates (barrel + disk
-   * events with noise). */
+  /* Adaptive capacity (0 = off, the default): a first pass runs every seed with adaptive_capacity
+   * candidate slots (rounded up to a compiled capacity), more seeds per warp, and finishes the
+   * seeds whose children never outnumber those slots: keeping all of a step's children is what
+   * k_max does then, so their results are those of the single pass. The other seeds are listed in
+   * the workspace and found again, from their seed state, by a second pass at the full capacity.
+   * Ignored when no smaller compiled capacity exists or, with the learned proposal, when top_n
+   * exceeds the first pass's slots; KF_ERR_ARG outside [0, KF_MAX_K]. Pays where most seeds carry
+   * few candidates (barrel + disk events with noise; the learned proposal's pruning). */
   int adaptive_capacity;
 } KfFindParams;
 
@@ -350,11 +350,11 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
 
 /* Autotuner for the persistent finder (not in the paper): runs kf_find_tracks on the given seeds
  * (a calibration subset of the workload) for every block size 64..256 (step 32) and for the
- * smallest and the next compiled candidate capacity, and for plain finding with k_max > 4 with
- * and without adaptive capacity 4, times each run with CUDA events (the stream is synchronised: do
- * not call it during a stream capture), and writes the fastest block size, capacity and adaptive
- * capacity into params->block_threads, params->k_capacity and params->adaptive_capacity; *best_ms
- * receives its time. Every configuration gives the same results. Outputs as for kf_find_tracks; a
+ * smallest and the next compiled candidate capacity, and for k_max > 4 (the learned proposal:
+ * with top_n <= 4) with and without adaptive capacity 4, times each run with CUDA events (the
+ * stream is synchronised: do not call it during a stream capture), and writes the fastest block
+ * size, capacity and adaptive capacity into params->block_threads, params->k_capacity and
+ * params->adaptive_capacity; *best_ms receives its time. Every configuration gives the same results. Outputs as for kf_find_tracks; a
  * configuration whose workspace is larger than workspace_bytes is passed over (size the workspace
  * with adaptive_capacity = 4 to let it compete). */
 int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,

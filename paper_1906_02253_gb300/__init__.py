@@ -260,7 +260,7 @@ def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_thr
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
     ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
     next-surface rule; ``score_margin`` > 0 switches the learned proposal to its score-margin rule;
-    ``adaptive_capacity`` > 0 runs plain finding in two passes (see kfgb.h)."""
+    ``adaptive_capacity`` > 0 runs the finder in two passes (see kfgb.h)."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
@@ -514,11 +514,11 @@ def mlp_train(params, features, labels, epochs: int = 3, batch: int = 4096, lr: 
 
 def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits, seed_event, params: KfFindParams,
                   stream=None):
-    """Time every block size, candidate capacity and (plain finding, k_max > 4) adaptive capacity on
-    these seeds (a calibration subset) and return (tuned params, best ms). Synchronises the stream."""
+    """Time every block size, candidate capacity and (k_max > 4) adaptive capacity on these seeds (a
+    calibration subset) and return (tuned params, best ms). Synchronises the stream."""
     # Workspace for the largest configuration tried: adaptive capacity adds its overflow list.
     wide = KfFindParams.from_buffer_copy(params)
-    if not (params.mlp and params.top_n > 0) and params.k_max > 4:
+    if params.k_max > 4 and (not (params.mlp and params.top_n > 0) or params.top_n <= 4):
         wide.adaptive_capacity = 4
     n = seed_hits.shape[1]
     ws = torch.empty(max(find_workspace_size(n, wide), find_workspace_size(n, params), 256), dtype=torch.uint8,

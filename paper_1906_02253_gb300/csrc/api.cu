@@ -443,11 +443,11 @@ int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const floa
   int cap_opts[2] = {0, 0}, n_cap = 0;
   for (int c : caps)
     if (c >= need && n_cap < 2) cap_opts[n_cap++] = c;
-  // Plain finding with k_max > 4 also tries adaptive capacity 4 (a configuration whose workspace
-  // does not fit the caller's fails and is passed over).
-  const bool plain = !(params->mlp && params->top_n > 0);
+  // With k_max > 4 (and, for the learned proposal, top_n <= 4) adaptive capacity 4 is tried too
+  // (a configuration whose workspace does not fit the caller's fails and is passed over).
+  const bool learned = params->mlp && params->top_n > 0;
   const int ad_opts[2] = {0, 4};
-  const int n_ad = plain && params->k_max > 4 ? 2 : 1;
+  const int n_ad = params->k_max > 4 && (!learned || params->top_n <= 4) ? 2 : 1;
   KfFindParams best = *params;
   float best_t = -1.f;
   for (int ci2 = 0; ci2 < n_cap; ++ci2) {

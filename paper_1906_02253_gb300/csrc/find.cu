@@ -535,9 +535,11 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
   const float* __restrict__ wmlp = A.mlp_t;  // transposed network parameters (L1/L2)
   // Capacity of a lane's list during the scan; a first pass of adaptive capacity (detect) keeps at
-  // most its own slots (a lane with more passing hits makes its seed overflow anyway).
+  // most its own slots (a lane with more passing hits makes its seed overflow anyway). With the
+  // learned proposal a first pass runs only when top_n fits its slots, so a lane's list holds
+  // exactly its children.
   const int keep = LEARNED ? A.top_n : (A.detect ? min(A.k_max, KC) : A.k_max);
-  const bool detect = !LEARNED && A.detect != 0;
+  const bool detect = A.detect != 0;
   const bool margin_on = LEARNED && A.score_margin > 0.f;
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
@@ -889,7 +891,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     // In a detecting pass a seed whose children outnumber the slots overflows: its group takes no
     // part in the selection and the seed goes to the second pass (its children all fit otherwise,
     // and keeping them all is what the full capacity does).
-    int nch = (on && kind != 3) ? (kind == 0 ? (detect ? npass : hl_n) : 1) : 0;
+    int nch = (on && kind != 3) ? (kind == 0 ? (detect && !LEARNED ? npass : hl_n) : 1) : 0;
     // Rounds: the most children any group of the warp has, up to k_max.
     int tot = nch;
 #pragma unroll
@@ -1062,12 +1064,12 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   if (p->k_capacity < 0 || p->k_capacity > KF_MAX_K) return KF_ERR_ARG;
   const int kc = pick_kc(std::max(learned ? std::max(p->k_max, p->top_n) : p->k_max, p->k_capacity));
   if (kc < 0) return KF_ERR_ARG;
-  // Adaptive capacity (plain finding only): a first pass at the smallest compiled capacity >= the
-  // requested one, when that is below the full capacity.
+  // Adaptive capacity: a first pass at the smallest compiled capacity >= the requested one, when
+  // that is below the full capacity (and, with the learned proposal, holds top_n).
   const int ac = p->adaptive_capacity;
-  if (ac < 0 || ac > KF_MAX_K || (ac > 0 && learned)) return KF_ERR_ARG;
+  if (ac < 0 || ac > KF_MAX_K) return KF_ERR_ARG;
   int kc1 = ac > 0 ? pick_kc(ac) : 0;
-  if (kc1 >= kc) kc1 = 0;
+  if (kc1 >= kc || (learned && p->top_n > kc1)) kc1 = 0;
   // Resident blocks per SM for a block size (shared memory and registers), cached per (device,
   // capacity, mode, block size, lmax) so later calls, e.g. inside a stream capture, only launch.
   const int feat = compiled_features(learned, features);
@@ -1213,8 +1215,9 @@ int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& 
     A1.detect = 1;
     A1.ovf_list = reinterpret_cast<int*>(base + plan.off_ovf);
     A1.ovf_count = A.counter + 2;
-    dispatch_find(plan.kc1, false, plan.feat, [&](auto k) {
-      k_find_tracks<decltype(k)::kc, false, decltype(k)::feat><<<plan.grid1, plan.block1, plan.smem1, stream>>>(G, M, A1);
+    dispatch_find(plan.kc1, plan.learned, plan.feat, [&](auto k) {
+      k_find_tracks<decltype(k)::kc, decltype(k)::learned, decltype(k)::feat>
+          <<<plan.grid1, plan.block1, plan.smem1, stream>>>(G, M, A1);
       return KF_OK;
     });
     A.counter = A.counter + 1;

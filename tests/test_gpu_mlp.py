@@ -258,3 +258,31 @@ def test_training_module_learns_from_oracle_pairs(kf, pairs):
     assert hist[-1] < hist[0] and all(np.isfinite(hist))
     assert rec["held_out_auc"] > 0.7, rec["held_out_auc"]  # chance is 0.5
     assert w.shape == (kf.MLP_PARAMS,) and mean.shape == (14,) and sd.shape == (14,)
+
+
+@pytest.mark.parametrize("name,net,top_n,margin", [("hi_occ", "mlp_hi_occ.npz", 2, 0.0), ("hi_occ", "mlp_hi_occ.npz", 2, 2.0),
+                                                   ("learned", "mlp_learned.npz", 4, 0.0)])
+def test_learned_adaptive_capacity_gives_the_single_pass_results(kf, name, net, top_n, margin):
+    """The learned proposal in two passes (4 slots first) gives exactly its single-pass outputs."""
+    import os
+    wl = synth.workload(name, n_events=3)
+    b = synth.generate(wl)
+    g = kf.Geometry(wl)
+    dev = kf.to_device_event_batch(b)
+    idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+    buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"])
+    res = []
+    for ad in (0, 4):
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n,
+                             score_margin=margin, adaptive_capacity=ad)
+        out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
+        torch.cuda.synchronize()
+        ovf = int(out["workspace"][8:12].view(torch.int32).item())
+        res.append(({k: v.cpu().numpy() for k, v in out.items() if k != "workspace"}, ovf))
+    (one, o1), (two, o2) = res
+    assert o1 == 0 and 0 < o2 < one["status"].shape[0], (o1, o2)
+    for key in ("hits", "nhits", "status"):
+        assert np.array_equal(one[key], two[key]), key
+    for key in ("chi2", "state", "cov"):
+        assert np.array_equal(one[key].view(np.uint32), two[key].view(np.uint32)), key
