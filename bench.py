@@ -63,9 +63,10 @@ MLP_SPLIT_MMAS = 6
 MMA_MLP_FWD = MLP_SPLIT_MMAS * 2 * (16 * 64 + 64 * 64)
 MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch, per seed) on a smaller case of each workload (30 events of the 100-event workload, 40 of
-# the barrel + disk workload; profiles/k_find_tracks_*), valid while the finder's sources and build
-# flags are the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
+# launch, or of adaptive capacity's two passes, per seed) on a smaller case of each workload (30
+# events of the 100-event workload, 40 of the barrel + disk workload; profiles/k_find_tracks_*),
+# keyed by workload (and adaptive capacity), valid while the finder's sources and build flags are
+# the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
 FIND_PROFILE = {"sources_sha1": "e0da6a1efc949f6f8eaed8794666f4e2706a52cc",
@@ -238,7 +239,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
         dws = torch.empty(max(kf.dedup_workspace_size(n_seeds, lmax, n_hits), 256), dtype=torch.uint8,
                           device=dev)
     prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm,
-                         steering_tables=steer, seed_keep=seed_keep)
+                         steering_tables=steer, seed_keep=seed_keep, adaptive_capacity=args.adaptive)
     idx = kf.HitIndex(g, batch.n_events, n_hits, dev)
     fout = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32, device=dev),
                 nhits=torch.empty(n_seeds, dtype=torch.int32, device=dev),
@@ -496,7 +497,8 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
             dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1)
             out["cpu_baseline"]["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
                                                     "sample": f"first {n1} seeds ({dt1:.1f} s)"}
-    out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"])
+    out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"],
+                               adaptive=prm.adaptive_capacity)
     out["_ctx"] = dict(kf=kf, g=g, d=d, host=host, idx=idx, prm=prm, fout=fout, fit_out=fit_out, stream=stream,
                        flush=flush, n_seeds=n_seeds, batch=batch, wl=wl, learned=learned)
     return out
@@ -529,7 +531,8 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     cal_e = d["seed_event"][:n_cal].contiguous()
     res = {"network": json.loads(str(z["info"])), "network_file": os.path.basename(path), "k_max": prm.k_max,
            "plain": {"find_seeds_per_s": n / (ms_plain / 1000.0), "efficiency": eff_plain, "fake_rate": fake_plain,
-                     "block_threads": prm.block_threads, "k_capacity": prm.k_capacity}}
+                     "block_threads": prm.block_threads, "k_capacity": prm.k_capacity,
+                     "adaptive_capacity": prm.adaptive_capacity}}
     best = None
     for top_n, margin in ((1, 0.0), (2, 0.0), (4, 0.0), (2, 1.0), (2, 2.0), (3, 2.0)):
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n,
@@ -541,6 +544,8 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
             with torch.cuda.stream(stream):
                 lp, _ = kf.autotune_find(g, idx, d["hits"], d["hit_surface"], cal_s, cal_e, lp, stream=stream)
             torch.cuda.synchronize()
+            # the tuned configuration's workspace (adaptive capacity adds its overflow list)
+            lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
         times = []
         for i in range(args.warmup + args.steps):
             with torch.cuda.stream(stream):
@@ -556,7 +561,8 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
         e, f = metrics.efficiency(batch, host["seed_track"], fout["hits"].cpu().numpy().T, fout["nhits"].cpu().numpy())
         r = {"find_seeds_per_s": n / (statistics.mean(times) / 1000.0), "find_ms": statistics.mean(times),
              "efficiency": e, "fake_rate": f, "efficiency_loss": eff_plain - e,
-             "block_threads": lp.block_threads, "k_capacity": lp.k_capacity}
+             "block_threads": lp.block_threads, "k_capacity": lp.k_capacity,
+             "adaptive_capacity": lp.adaptive_capacity}
         r["speedup_vs_plain"] = r["find_seeds_per_s"] / res["plain"]["find_seeds_per_s"]
         name = f"top_n={top_n}" + (f",margin={margin:g}" if margin > 0 else "")
         res[name] = r
@@ -797,7 +803,7 @@ def find_sources_sha1() -> str:
     return h.hexdigest()
 
 
-def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
+def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks, adaptive=0):
     """Roofline of every step kernel, and of the dominant one at the top level. The finder and the
     fit are FP32-ALU bound (no dense contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM
     clock. The index is HBM bound."""
@@ -833,7 +839,8 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks):
         n_prop, n_pass, n_upd, n_scan, n_win = counters[:5]
         per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
         ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
-        bytes_seed = FIND_PROFILE["dram_bytes_per_seed"].get(batch.wl.name)
+        # profiled per configuration: one pass, or adaptive capacity's two passes together
+        bytes_seed = FIND_PROFILE["dram_bytes_per_seed"].get(batch.wl.name + (f"_adaptive{adaptive}" if adaptive else ""))
         profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and bytes_seed is not None
         traffic = bytes_seed * n_seeds if profiled else None
         per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak,
@@ -864,6 +871,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration")
+    ap.add_argument("--adaptive", type=int, default=0,
+                    help="with --no-autotune: the finder's adaptive capacity (first-pass slots; 0 = one pass)")
     ap.add_argument("--clean", action="store_true",
                     help="seed cleaning and duplicate-track removal in the step (on for combinatorial seeds)")
     ap.add_argument("--steering", action="store_true",

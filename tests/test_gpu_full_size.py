@@ -132,14 +132,12 @@ def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n):
     g = kf.Geometry(wl)
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
-    prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
-    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
-    prm, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"][:, :n_cal].contiguous(),
-                              dev["seed_event"][:n_cal].contiguous(), prm)
     z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"])
-    lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, prm.block_threads, prm.blocks_per_sm,
-                        mlp=buf, top_n=top_n)
+    lp = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n)
+    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
+    lp, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"][:, :n_cal].contiguous(),
+                             dev["seed_event"][:n_cal].contiguous(), lp)
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], lp)
     torch.cuda.synchronize()
     n = dev["seed_hits"].shape[1]
