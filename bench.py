@@ -69,9 +69,11 @@ MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 # the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "e0da6a1efc949f6f8eaed8794666f4e2706a52cc",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": 160237312 / 302063,
-                                        "find_200ev_barrel_disks_noise100": 174745088 / 211523}}
+FIND_PROFILE = {"sources_sha1": "08558b41e4e080588c76f579e2b395dc7fdf7374",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (124944128 + 35772672) / 302063,
+                                        "find_200ev_barrel_disks_noise100": (143625216 + 31266048) / 211523,
+                                        "find_200ev_barrel_disks_noise100_adaptive4":
+                                            (170581504 + 36413696 + 128902656 + 30736896) / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
@@ -146,6 +148,12 @@ def _peaks():
 # ------------------------------------------------------------------------------------------------
 # Oracle legs (host cores only)
 # ------------------------------------------------------------------------------------------------
+
+def calibration_events(n_events: int) -> int:
+    """Events whose seeds the autotuner times: a quarter of the batch, at least 10. Adaptive capacity
+    needs enough seeds in its second pass to fill the GPU before it can win on a subset."""
+    return min(n_events, max(10, n_events // 4))
+
 
 def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: int = 0):
     """Run the FP64 oracle (index + find + fit of the found tracks; with ``clean``, seed cleaning
@@ -255,8 +263,8 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
     wsb = torch.empty(max(kf.find_workspace_size(n_seeds, prm), 256), dtype=torch.uint8, device=dev)
     max_slab = host["max_slab_hits"]
     stream = torch.cuda.Stream(device=dev)
-    # Autotune (block size, candidate capacity) of the finder and the fit's block size on a
-    # calibration subset: the seeds of the first events (outside the timed region).
+    # Autotune (block size, candidate capacity, adaptive capacity) of the finder and the fit's block size on a
+    # calibration subset: the seeds of the first quarter of the events (outside the timed region).
     tuning = {}
     fit_block = 0
     if not args.no_autotune:
@@ -265,7 +273,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
             if clean:
                 kf.clean_seeds(g, d["hits"], d["hit_surface"], d["seed_hits"], d["seed_event"], keep=seed_keep,
                                workspace=dws, stream=stream)
-            n_cal = int(np.searchsorted(host["seed_event"].numpy(), min(10, batch.n_events)))
+            n_cal = int(np.searchsorted(host["seed_event"].numpy(), calibration_events(batch.n_events)))
             cal_s = d["seed_hits"][:, :n_cal].contiguous()
             cal_e = d["seed_event"][:n_cal].contiguous()
             prm, ms_find = kf.autotune_find(g, idx, d["hits"], d["hit_surface"], cal_s, cal_e, prm, stream=stream)
@@ -526,7 +534,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device=d["hits"].device)
     n = host["seed_hits"].shape[1]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=d["hits"].device)
-    n_cal = int(np.searchsorted(host["seed_event"].numpy(), min(10, batch.n_events)))
+    n_cal = int(np.searchsorted(host["seed_event"].numpy(), calibration_events(batch.n_events)))
     cal_s = d["seed_hits"][:, :n_cal].contiguous()
     cal_e = d["seed_event"][:n_cal].contiguous()
     res = {"network": json.loads(str(z["info"])), "network_file": os.path.basename(path), "k_max": prm.k_max,

@@ -2,8 +2,8 @@
 
 The GPU finds tracks for every seed of the full workloads (100 events; 200 events with disks and
 noise; 100 events with the material map; 20 events in the field map) with the
-autotuned block size and candidate capacity (calibrated on the first 10 events, as the benchmark
-does) and fits every simulated track; the FP64 oracle then computes a seeded random sample of 20,000
+autotuned block size, candidate capacity and adaptive capacity (calibrated on the first quarter of
+the events, as the benchmark does) and fits every simulated track; the FP64 oracle then computes a seeded random sample of 20,000
 seeds and 20,000 tracks one by one, and the sample is held to the parity bars: hit lists identical
 on >= 99.9% of seeds, efficiency within 0.1%, every track with an identical hit list
 carrying the same fitted state (1e-4) and chi2 (1e-3), fitted tracks within the fit bars.
@@ -14,6 +14,7 @@ import torch
 
 import oracle
 import synth
+from bench import calibration_events
 from test_gpu_parity import _assert_track_state_parity
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +40,7 @@ def test_full_size_parity_on_sampled_seeds_and_tracks(wl_name):
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
     prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax)
-    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
+    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), calibration_events(b.n_events)))
     cal_s = dev["seed_hits"][:, :n_cal].contiguous()
     cal_e = dev["seed_event"][:n_cal].contiguous()
     prm, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], cal_s, cal_e, prm)
@@ -135,7 +136,7 @@ def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n):
     z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"])
     lp = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n)
-    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), min(10, b.n_events)))
+    n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), calibration_events(b.n_events)))
     lp, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"][:, :n_cal].contiguous(),
                              dev["seed_event"][:n_cal].contiguous(), lp)
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], lp)
