@@ -69,6 +69,13 @@ def test_host_side_argument_checks(kf):
     assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
     p = kf.find_params(30.0, 8, 1, 17, adaptive_capacity=kf.KF_MAX_K + 1)
     assert lib.kf_find_workspace_size(100, ctypes.byref(p)) == 0
+    # the allocation-free entry point has no room for adaptive capacity's overflow list
+    p = kf.find_params(30.0, 8, 1, 17, adaptive_capacity=4)
+    idx = kf.KfHitIndex(1, g.n_bins, None, None, None, None)
+    v = ctypes.c_void_p
+    rc = lib.kf_find_tracks_static(g.ref, ctypes.byref(idx), v(256), v(256), v(256), v(256), 10, ctypes.byref(p),
+                                   v(256), v(256), v(256), v(256), v(256), v(256), None)
+    assert rc == kf.KF_ERR_ARG
     # network kernels read feature rows as float pairs: an odd float offset is rejected
     v = ctypes.c_void_p
     assert lib.kf_mlp_forward(v(256), v(260), 1, v(512), None) == kf.KF_ERR_ARG
