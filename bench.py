@@ -213,12 +213,13 @@ def run_reference(args, wl, batch):
 # GPU arm
 # ------------------------------------------------------------------------------------------------
 
-def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
+def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e2e: bool = None):
     """The step (index, seed states, find, fit; with seed cleaning and duplicate removal on
     combinatorial seeds) on one workload: device-timed graph replays, per-part times, efficiency,
-    the learned proposal against plain finding and the rooflines. `full` adds the end-to-end
-    measurement through host buffers and the single-thread oracle figure. Returns the JSON object
-    (and, under "_ctx", the device state the further measurements reuse)."""
+    the learned proposal against plain finding and the rooflines. `e2e` (default: `full`) adds the
+    end-to-end measurement through host buffers, `full` the single-thread oracle figure. Returns
+    the JSON object (and, under "_ctx", the device state the further measurements reuse)."""
+    e2e = full if e2e is None else e2e
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -372,7 +373,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
     res_host = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32).pin_memory())
     h2d = d2h = 0
     ms_e2e = ms_e2e_serial = None
-    if full:
+    if e2e:
         # End to end through the public API with host buffers: H2D of the step's inputs from pinned
         # memory, the calls, D2H of the step's result (found hit lists, fitted states, chi2). Serial:
         # copy in, compute, copy out on one stream. Pipelined: copies on their own streams with two
@@ -438,7 +439,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
 
     # Result sanity on the last step (efficiency of the found tracks, host logic only).
     from paper_1906_02253_gb300 import metrics
-    if not full:
+    if not e2e:
         res_host["hits"].copy_(fout["hits"])
     eff, fake = metrics.efficiency(batch, host["seed_track"], res_host["hits"].numpy().T,
                                    fout["nhits"].cpu().numpy())
@@ -480,7 +481,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None):
            "fit_tracks_per_s": job_seeds / (kern_ms["fit"] / 1000.0),
            "find_seeds_per_s": job_seeds / (kern_ms["find"] / 1000.0),
            }
-    if full:
+    if e2e:
         out["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "ms_per_step": ms_e2e, "pipelined": "H2D of step i+1 and D2H of step i-1 on their own "
                       "streams overlap step i (two buffer sets); L2: the H2D rewrites the inputs each step",
@@ -780,7 +781,7 @@ def run_gpu(args, wl, batch):
         # the largest configuration: barrel + disks, noise 100%, K = 8, plain and learned, autotuned
         wh = synth.workload("hi_occ")
         bh = synth.generate(wh)
-        hi = measure_workload(args, wh, bh, full=False, mlp_name="hi_occ")
+        hi = measure_workload(args, wh, bh, full=False, mlp_name="hi_occ", e2e=True)
         hctx = hi.pop("_ctx")
         for k in ("metric", "n_gpus", "steps", "warmup", "higher_is_better", "scaling", "vs_baseline", "data"):
             hi.pop(k, None)
