@@ -93,7 +93,8 @@ def _load():
             lib.or_next_surface.argtypes = [G, _P, _P]
             lib.or_find.argtypes = [G, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_longlong, ctypes.c_int,
                                     ctypes.POINTER(OrFindParams), ctypes.c_int, _P, _P, _P, _P, _P, _P, _P,
-                                    _P, _P, _P, ctypes.c_int, ctypes.POINTER(OrSteering), ctypes.c_double]
+                                    _P, _P, _P, ctypes.c_int, ctypes.POINTER(OrSteering), ctypes.c_double,
+                                    ctypes.c_int]
             lib.or_seed_params.argtypes = [G, _P, _P, _P, ctypes.c_longlong, _P]
             lib.or_clean_seeds.argtypes = [_P, _P, _P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, _P]
             lib.or_remove_duplicates.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_int,
@@ -273,10 +274,12 @@ def _steering(st):
 
 def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=None, max_miss=None,
          brute_force: bool = False, n_threads: int = 0, mlp=None, top_n: int = 0, steering=None,
-         score_margin: float = 0.0):
+         score_margin: float = 0.0, window: bool = False):
     """Combinatorial finding from seeds; with ``mlp`` = (weights, mean, sd) and top_n > 0 the
     learned proposal keeps the top_n passing hits by score (with ``score_margin`` > 0, of a window
-    with two or more passing hits, those of its top_n within the margin of its best score); ``steering`` (synth.steering_tables)
+    with two or more passing hits, those of its top_n within the margin of its best score; with
+    ``window``, instead, the top_n by score of every hit in the bounding box of the chi2 ellipse go
+    on to the chi2 cut when the box holds more than top_n hits); ``steering`` (synth.steering_tables)
     replaces the geometric next-surface rule by the region lists. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
     evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch,
@@ -299,7 +302,7 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
                 se.ctypes.data, n, lmax, ctypes.byref(prm), n_threads, out["hits"].ctypes.data,
                 out["n_hits"].ctypes.data, out["chi2"].ctypes.data, out["p"].ctypes.data, out["cov"].ctypes.data,
                 out["status"].ctypes.data, counters.ctypes.data, *_mlp_ptrs(mlp), int(top_n),
-                None if steering is None else ctypes.byref(_steering(steering)), float(score_margin))
+                None if steering is None else ctypes.byref(_steering(steering)), float(score_margin), int(bool(window)))
     out["counters"] = counters
     return out
 

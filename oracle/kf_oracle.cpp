@@ -731,6 +731,7 @@ struct Mlp {
   const double* sd = nullptr;
   int top_n = 0;               // 0: plain finding
   double margin = 0.0;         // > 0: score margin rule (below)
+  bool window = false;         // rank every hit of the window before the chi2 cut (below)
 };
 
 double mlp_forward(const double* w, const double* xs, double* h1 = nullptr, double* h2 = nullptr) {
@@ -866,10 +867,13 @@ int next_steered(const OrGeom& g, const OrSteering& sg, int region, int pos, con
 
 // All hits of surface si in event ev whose chi2 against the predicted state is below the cut.
 // Binned: the window is the bounding box of the chi2 ellipse, padded, turned into bin ranges by
-// the same FP32 rule as the index; brute force: every hit of the surface.
+// the same FP32 rule as the index; brute force: every hit of the surface. box (optional): the hits
+// inside the bounding box itself, |r_i| <= sqrt(cut S_ii) for both residuals, with their chi2 (a
+// superset of out).
 void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<Found>& out,
-                 long long* scanned = nullptr, long long* window_hits = nullptr) {
+                 long long* scanned = nullptr, long long* window_hits = nullptr, std::vector<Found>* box = nullptr) {
   out.clear();
+  if (box) box->clear();
   const OrGeom& g = *cx.g;
   const OrSurface& S = g.surf[si];
   const long long sl = static_cast<long long>(ev) * g.n_surf + si;
@@ -881,6 +885,8 @@ void search_hits(const Ctx& cx, int ev, int si, const State& pred, std::vector<F
     const double c2 = chi2_of(m, pred.C, Sm);
     if (scanned) ++*scanned;
     if (c2 < cut) out.push_back({id, c2});
+    if (box && std::fabs(m.r[0]) <= std::sqrt(cut * Sm[0][0]) && std::fabs(m.r[1]) <= std::sqrt(cut * Sm[1][1]))
+      box->push_back({id, c2});
   };
   if (cx.prm.brute_force) {
     for (long long h = cx.slab_off[sl]; h < cx.slab_off[sl + 1]; ++h) try_hit(cx.hits[2 * h], cx.hits[2 * h + 1], static_cast<int>(h));
@@ -998,7 +1004,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       if (cx.steer->surf[region][q] == c0.surf) c0.pos = q;
   }
   std::vector<Cand> cands{c0};
-  std::vector<Found> found;
+  std::vector<Found> found, box;
   std::vector<Child> pool;
   std::vector<State> pred;
   for (int step = 3; step < lmax; ++step) {
@@ -1023,7 +1029,7 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       cnt.n_prop++;
       pred_surf[ci] = si;
       pred_pos[ci] = np;
-      search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan, &cnt.n_win);
+      search_hits(cx, ev, si, pred[ci], found, &cnt.n_scan, &cnt.n_win, cx.mlp.top_n > 0 && cx.mlp.window ? &box : nullptr);
       cnt.n_chi2 += static_cast<long long>(found.size());
       if (sink) {  // training pairs: every passing (candidate, hit) pair, labelled by truth
         double f[kIn];
@@ -1034,7 +1040,28 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
         }
       }
       const bool margin_rule = cx.mlp.margin > 0.0;
-      if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > (margin_rule ? 1 : cx.mlp.top_n)) {
+      if (cx.mlp.top_n > 0 && cx.mlp.window) {
+        // Learned proposal ranking the window before the chi2 cut: when the window (the bounding
+        // box of the chi2 ellipse) holds more than top_n hits, only its top_n by MLP score (ties:
+        // lower hit id) go on to the cut; otherwise every passing hit makes a child.
+        if (static_cast<int>(box.size()) > cx.mlp.top_n) {
+          std::vector<std::pair<double, int>> sc;
+          double f[kIn];
+          for (const Found& fd : box) {
+            pair_features(g, si, pred[ci], cx.hits[2 * fd.hit], cx.hits[2 * fd.hit + 1], f);
+            sc.push_back({mlp_score(cx.mlp, f), fd.hit});
+            cnt.n_mlp++;
+          }
+          std::sort(sc.begin(), sc.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+            return a.first != b.first ? a.first > b.first : a.second < b.second;
+          });
+          std::vector<Found> kept;
+          for (int k = 0; k < cx.mlp.top_n; ++k)
+            for (const Found& fd : box)
+              if (fd.hit == sc[k].second && fd.chi2 < cx.prm.chi2_cut) kept.push_back(fd);
+          found.swap(kept);
+        }
+      } else if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > (margin_rule ? 1 : cx.mlp.top_n)) {
         // Learned proposal: rank the passing hits by MLP score (ties: lower hit id) and keep the
         // top_n; with a score margin, only those of them that score within the margin of the best
         // (the best is always kept), so a window whose best hit stands out keeps one child.
@@ -1270,7 +1297,9 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 // Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. With mlp_w set and
 // top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
 // that has more; with score_margin > 0, of each window with two or more passing hits, the hits
-// among its top_n that score within score_margin of its best. Outputs per
+// among its top_n that score within score_margin of its best; with window != 0 (and no margin),
+// the top_n by score of every hit in the window's box go on to the chi2 cut when the box holds
+// more than top_n hits. Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
 // status (0 ok, 1 seed failed). steering: region steering lists, or null for the geometric
 // next-surface rule. counters[6] += propagations, chi2 evaluations that passed the
@@ -1281,11 +1310,11 @@ void or_find(const OrGeom* g, const float* hits, const int* hsurf, const long lo
              const int* seeds, const int* seed_event, long long n, int lmax, const OrFindParams* prm, int n_threads,
              int* hits_out, int* nhits_out, double* chi2_out, double* p_out, double* C_out, int* status_out,
              long long* counters, const double* mlp_w, const double* mlp_mean, const double* mlp_sd, int top_n,
-             const OrSteering* steering, double score_margin) {
+             const OrSteering* steering, double score_margin, int window) {
   Index ix;
   if (!prm->brute_force) build_index(*g, hits, slab_off, n_events, ix);
-  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm, Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0, score_margin},
-         steering};
+  Ctx cx{g, hits, hsurf, slab_off, &ix, *prm,
+         Mlp{mlp_w, mlp_mean, mlp_sd, mlp_w ? top_n : 0, score_margin, window != 0}, steering};
   cx.n_hits = slab_off[static_cast<long long>(n_events) * g->n_surf];
   cx.n_events = n_events;
   std::atomic<long long> c_prop(0), c_chi2(0), c_upd(0), c_scan(0), c_win(0), c_mlp(0);

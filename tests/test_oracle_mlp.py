@@ -291,3 +291,75 @@ def test_score_margin_matches_a_plain_loop():
                 break
         assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
     assert multi > 5  # the margin kept several hits in some windows
+
+
+def test_window_ranking_with_a_top_n_above_every_window_is_plain_finding():
+    """Ranking the window before the chi2 cut keeps every hit of a window that holds at most top_n:
+    with top_n above any window's size the cut alone decides, as in plain finding."""
+    wl = synth.workload("find", n_events=2, tracks_lo=300, tracks_hi=300, noise_frac=3.0, seed=45)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    plain = oracle.find(g, b, sh, ev)
+    wide = oracle.find(g, b, sh, ev, mlp=mlp, top_n=100000, window=True)
+    assert np.array_equal(plain["hits"], wide["hits"])
+    assert wide["counters"][5] == 0
+    narrow = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, window=True)
+    assert narrow["counters"][5] > 0 and not np.array_equal(plain["hits"], narrow["hits"])
+
+
+def test_window_ranking_matches_a_plain_loop():
+    """K = 1, top_n = 2, window ranking: at every step the box of the chi2 ellipse (both pulls within
+    sqrt(cut)) is taken from every hit of the surface; when it holds more than two hits, only its two
+    best-scoring hits (ties: lower id) face the chi2 cut; the child is the kept passing hit of lowest
+    chi2."""
+    import test_oracle_find as tf
+    wl = synth.workload("find", n_events=2, tracks_lo=40, tracks_hi=40, noise_frac=80.0, seed=46)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    cut = wl.chi2_cut
+    f = oracle.find(g, b, sh, ev, k_max=1, mlp=mlp, top_n=2, window=True)
+    ranked = cut_after_ranking = 0
+    for i in range(len(st)):
+        p, C, _ = tf._seed_fit(g, b, sh[i])
+        hits, n_miss = list(sh[i]), 0
+        while len(hits) < wl.lmax:
+            surf, _ = oracle.next_surface(g, p)
+            if surf < 0:
+                break
+            r = oracle.propagate(g, p, C, surf)
+            if r is None:
+                break
+            pp, CC = r[0], r[1]
+            ids, c2 = oracle.search(g, b, pp, CC, ev[i], surf, 1e30, brute=True)  # every hit of the surface
+            feats = np.array([oracle.pair_features(g, surf, pp, CC, b.hits[h]) for h in ids]).reshape(-1, 14)
+            inbox = (np.abs(feats[:, 12]) <= np.sqrt(cut)) & (np.abs(feats[:, 13]) <= np.sqrt(cut))
+            bids, bc2, bf = ids[inbox], c2[inbox], feats[inbox]
+            if len(bids) > 2:
+                ranked += 1
+                sc = oracle.mlp_forward(mlp[0], (bf - mlp[1]) / mlp[2])
+                top = sorted(range(len(bids)), key=lambda k: (-sc[k], bids[k]))[:2]
+                keep = [k for k in top if bc2[k] < cut]
+                cut_after_ranking += len(keep) < len(top)
+                kids, kc2 = bids[keep], bc2[keep]
+            else:
+                kids, kc2 = bids[bc2 < cut], bc2[bc2 < cut]
+            if len(kids):
+                best = sorted(range(len(kids)), key=lambda k: (kc2[k], kids[k]))[0]
+                p, C, _ = oracle.update(g, pp, CC, surf, b.hits[kids[best]])
+                hits.append(int(kids[best]))
+            elif n_miss < wl.max_miss:
+                p, C, n_miss = pp, CC, n_miss + 1
+                hits.append(-1)
+            else:
+                break
+        assert f["hits"][i].tolist() == hits + [-1] * (wl.lmax - len(hits)), i
+    print("ranked windows", ranked, "with a ranked hit cut", cut_after_ranking)
+    assert ranked > 10 and cut_after_ranking >= 3  # the rule ranked windows, and the cut then removed ranked hits
