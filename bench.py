@@ -543,9 +543,12 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
                      "block_threads": prm.block_threads, "k_capacity": prm.k_capacity,
                      "adaptive_capacity": prm.adaptive_capacity}}
     best = None
-    for top_n, margin in ((1, 0.0), (2, 0.0), (4, 0.0), (2, 1.0), (2, 2.0), (3, 2.0)):
+    # top_n rule on the passing hits, score margins, and (window) the top_n of the whole window's box
+    # ranked before the chi2 cut
+    for top_n, margin, window in ((1, 0.0, False), (2, 0.0, False), (4, 0.0, False), (2, 1.0, False),
+                                  (2, 2.0, False), (3, 2.0, False), (2, 0.0, True), (4, 0.0, True)):
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n,
-                            score_margin=margin)
+                            score_margin=margin, window_ranking=window)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
         lp.seed_keep, lp._keep_ref = prm.seed_keep, getattr(prm, "_keep_ref", None)  # same seeds
         lw = torch.empty(max(kf.find_workspace_size(n, lp), 256), dtype=torch.uint8, device=d["hits"].device)
@@ -573,7 +576,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
              "block_threads": lp.block_threads, "k_capacity": lp.k_capacity,
              "adaptive_capacity": lp.adaptive_capacity}
         r["speedup_vs_plain"] = r["find_seeds_per_s"] / res["plain"]["find_seeds_per_s"]
-        name = f"top_n={top_n}" + (f",margin={margin:g}" if margin > 0 else "")
+        name = f"top_n={top_n}" + (f",margin={margin:g}" if margin > 0 else "") + (",window" if window else "")
         res[name] = r
         if r["efficiency_loss"] <= 0.005 and (best is None or r["find_seeds_per_s"] > res[best]["find_seeds_per_s"]):
             best = name

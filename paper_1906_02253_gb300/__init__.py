@@ -61,7 +61,7 @@ class KfFindParams(ctypes.Structure):
                 ("lmax", ctypes.c_int), ("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("mlp", ctypes.c_void_p), ("top_n", ctypes.c_int), ("k_capacity", ctypes.c_int),
                 ("steering", ctypes.POINTER(KfSteering)), ("seed_keep", ctypes.c_void_p),
-                ("score_margin", ctypes.c_float), ("adaptive_capacity", ctypes.c_int)]
+                ("score_margin", ctypes.c_float), ("adaptive_capacity", ctypes.c_int), ("window_ranking", ctypes.c_int)]
 
 
 EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_workspace_size", "kf_find_tracks",
@@ -256,11 +256,12 @@ def steering(tables: dict) -> KfSteering:
 def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_threads: int = 0,
                 blocks_per_sm: int = 0, mlp=None, top_n: int = 0, k_capacity: int = 0,
                 steering_tables: dict = None, seed_keep=None, score_margin: float = 0.0,
-                adaptive_capacity: int = 0) -> KfFindParams:
+                adaptive_capacity: int = 0, window_ranking: bool = False) -> KfFindParams:
     """Finder settings; ``mlp`` is a device tensor of MLP_BUFFER floats (learned proposal);
     ``steering_tables`` (dict of region lists) selects region steering instead of the geometric
     next-surface rule; ``score_margin`` > 0 switches the learned proposal to its score-margin rule;
-    ``adaptive_capacity`` > 0 runs the finder in two passes (see kfgb.h)."""
+    ``adaptive_capacity`` > 0 runs the finder in two passes; ``window_ranking`` ranks the learned
+    proposal's whole window before the chi2 cut (see kfgb.h)."""
     if mlp is not None:
         _cuda(mlp, torch.float32, "mlp")
         if mlp.numel() != MLP_BUFFER:
@@ -271,7 +272,7 @@ def find_params(chi2_cut: float, k_max: int, max_miss: int, lmax: int, block_thr
     prm = KfFindParams(chi2_cut, k_max, max_miss, lmax, block_threads, blocks_per_sm,
                        None if mlp is None else mlp.data_ptr(), int(top_n), int(k_capacity),
                        None if st is None else ctypes.pointer(st), None if seed_keep is None else seed_keep.data_ptr(),
-                       float(score_margin), int(adaptive_capacity))
+                       float(score_margin), int(adaptive_capacity), int(bool(window_ranking)))
     prm._mlp_ref = mlp  # keep the buffers alive with the parameters
     prm._steer_ref = st
     prm._keep_ref = seed_keep

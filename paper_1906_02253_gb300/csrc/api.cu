@@ -338,6 +338,7 @@ static int prepare_find(const KfGeometry* geom, const KfHitIndex* index, const f
   A->mlp = params->mlp;
   A->top_n = params->mlp ? params->top_n : 0;
   A->score_margin = params->mlp ? params->score_margin : 0.f;
+  A->window_rank = params->mlp ? params->window_ranking : 0;
   A->seed_keep = params->seed_keep;
   return KF_OK;
 }

@@ -69,6 +69,7 @@ constexpr float kLogFloor = -27.631021f;
 template <int KC>
 struct WarpLearned {
   float hl_sc[KC][32];
+  float2 box[32];  // window ranking: half-widths sqrt(cut S_00), sqrt(cut S_11) of each lane's window
 };
 
 template <int KC, bool LEARNED>
@@ -541,6 +542,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
   const int keep = LEARNED ? A.top_n : (A.detect ? min(A.k_max, KC) : A.k_max);
   const bool detect = A.detect != 0;
   const bool margin_on = LEARNED && A.score_margin > 0.f;
+  const bool window_rank = LEARNED && A.window_rank != 0;  // rank the window's box before the cut
   const int grp = lane / KC, slot = lane % KC;
   const bool in_grp = grp < NS;
   const int gbase = in_grp ? grp * KC : lane;
@@ -642,6 +644,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
             const float cz = barrel ? c.p[2] : rho;
             W.win_a[lane] = make_float4(c.p[0], c.p[1], cz, rref);
             W.win_b[lane] = make_float4(in.s11 * inv, -in.s01 * inv, in.s00 * inv, 1.002f * cut * in.s00 / (rref * rref));
+            if (LEARNED && window_rank) WL.box[lane] = make_float2(sqrtf(cut * in.s00), sqrtf(cut * in.s11));
             s00v = in.s00;
             s11v = in.s11;
             const float dphi = sqrtf(cut * in.s00) / rref * (1.f + 1e-4f) + 1e-5f;
@@ -744,14 +747,15 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
             const float x13 = (r1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
             const float sc = mlp_logit_warp(wmlp, base, x12, x13, lane);
             if (lane == o)
-              hl_insert_scored(W, WL, lane, hl_n, keep, sc, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k], W.u.pl.pos[k]);
+              hl_insert_scored(W, WL, lane, hl_n, keep, sc, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k],
+                               W.u.pl.c2[k] < cut ? W.u.pl.pos[k] : ~W.u.pl.pos[k]);
           }
         }
         if (!need) {  // kept unconditionally (at most top_n of them)
           for (int k = start; k < start + my_cnt; ++k) {
             W.hl_tot[hl_n][lane] = c.chi2 + W.u.pl.c2[k];
             W.hl_id[hl_n][lane] = W.u.pl.id[k];
-            W.hl_pos[hl_n][lane] = W.u.pl.pos[k];
+            W.hl_pos[hl_n][lane] = W.u.pl.c2[k] < cut ? W.u.pl.pos[k] : ~W.u.pl.pos[k];
             ++hl_n;
           }
         }
@@ -826,13 +830,20 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
           const int pos = o + adj;
           float c2v = __int_as_float(0x7f800000);
           int hid = 0;
+          bool inbox = false;
           if (q < total) {
             const float4 h = __ldg(A.sorted_rec + pos);
             float r0, r1;
             c2v = window_chi2(W.win_a[owner], W.win_b[owner], h, r0, r1);
             hid = __float_as_int(h.w);
+            // Window ranking buffers every hit of the box of the chi2 ellipse (a hit rejected by the
+            // angular pre-test, c2v infinite, lies outside it).
+            if (LEARNED && window_rank) {
+              const float2 bx = WL.box[owner];
+              inbox = c2v < __int_as_float(0x7f800000) && fabsf(r0) <= bx.x && fabsf(r1) <= bx.y;
+            }
           }
-          const bool pass = c2v < cut;
+          const bool pass = (LEARNED && window_rank) ? inbox : c2v < cut;
           const unsigned m = __ballot_sync(kFull, pass);
           // passing hits of this lane's own runs in this round
           const int lo = excl - q0, hi = incl - q0;
@@ -870,6 +881,19 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
       int k = 1;
       while (k < hl_n && !(WL.hl_sc[k][lane] < floor_sc)) ++k;
       hl_n = min(hl_n, k);
+    }
+    // Window ranking: of the kept hits of the box, those failing the chi2 cut (position stored
+    // inverted) make no child.
+    if (LEARNED && window_rank && hl_n > 0) {
+      int m = 0;
+      for (int k = 0; k < hl_n; ++k) {
+        if (W.hl_pos[k][lane] < 0) continue;
+        W.hl_tot[m][lane] = W.hl_tot[k][lane];
+        W.hl_id[m][lane] = W.hl_id[k][lane];
+        W.hl_pos[m][lane] = W.hl_pos[k][lane];
+        ++m;
+      }
+      hl_n = m;
     }
     if (LEARNED && hl_n > 0) hl_sort_by_chi2(W, lane, hl_n, cap);
     // Outcome of each propagated candidate; keep the prediction for its children.
@@ -1057,6 +1081,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   const bool learned = p->mlp != nullptr && p->top_n > 0;
   if (p->top_n < 0 || p->top_n > KF_MAX_K) return KF_ERR_ARG;
   if (!(p->score_margin >= 0.f) || !(p->score_margin < 3.4e38f)) return KF_ERR_ARG;
+  if (p->window_ranking != 0 && (p->window_ranking != 1 || p->score_margin > 0.f)) return KF_ERR_ARG;
   if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32))
     return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;

@@ -27,6 +27,7 @@ struct FindArgs {
   const int* seed_keep;  // seeds with 0 are skipped (status 2), or null
   int top_n;         // > 0 with mlp: keep the top_n passing hits by score
   float score_margin;  // > 0: of those, only the ones within this margin of the window's best score
+  int window_rank;     // 1: rank every hit of the window's box, then apply the chi2 cut to the top_n
   int* hits_out;
   int* nhits_out;
   float* chi2_out;

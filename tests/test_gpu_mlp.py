@@ -112,12 +112,12 @@ def test_gpu_training_lowers_the_loss(kf, pairs):
     assert hist[-1] < 0.8 * first, (first, hist)
 
 
-def _find(kf, wl, b, buf, top_n, k, steering=None, margin=0.0):
+def _find(kf, wl, b, buf, top_n, k, steering=None, margin=0.0, window=False, adaptive=0):
     g = kf.Geometry(wl)
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
     prm = kf.find_params(wl.chi2_cut, k, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, steering_tables=steering,
-                         score_margin=margin)
+                         score_margin=margin, window_ranking=window, adaptive_capacity=adaptive)
     out = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
     torch.cuda.synchronize()
     return {kk: v.cpu().numpy() for kk, v in out.items() if kk != "workspace"}
@@ -286,3 +286,34 @@ def test_learned_adaptive_capacity_gives_the_single_pass_results(kf, name, net, 
         assert np.array_equal(one[key], two[key]), key
     for key in ("chi2", "state", "cov"):
         assert np.array_equal(one[key].view(np.uint32), two[key].view(np.uint32)), key
+
+
+@pytest.mark.parametrize("name,net,top_n,adaptive", [("learned", "mlp_learned.npz", 2, 0), ("learned", "mlp_learned.npz", 4, 0),
+                                                     ("hi_occ", "mlp_hi_occ.npz", 2, 0), ("hi_occ", "mlp_hi_occ.npz", 2, 4)])
+def test_window_ranking_matches_oracle(kf, name, net, top_n, adaptive):
+    """Ranking the window's box before the chi2 cut, with the trained networks, against the FP64
+    oracle's same rule: hit lists identical on >= 99.9% of the seeds (box membership and scores are
+    FP32 on the GPU), efficiency within 0.1%; with adaptive capacity too."""
+    import os
+    wl = synth.workload(name, n_events=3)
+    b = synth.generate(wl)
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+    gpu = _find(kf, wl, b, kf.mlp_buffer(z["weights"], z["mean"], z["sd"]), top_n, wl.k_max, window=True,
+                adaptive=adaptive)
+    sh, st = b.seeds()
+    mlp = (z["weights"].astype(np.float64), z["mean"].astype(np.float64), z["sd"].astype(np.float64))
+    ora = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], mlp=mlp, top_n=top_n, window=True)
+    same = (gpu["hits"].T == ora["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    e_g = oracle.efficiency(b, st, gpu["hits"].T, gpu["nhits"])[0]
+    e_o = oracle.efficiency(b, st, ora["hits"], ora["n_hits"])[0]
+    assert abs(e_g - e_o) <= 0.001
+    top = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], mlp=mlp, top_n=top_n)
+    assert (top["hits"] != ora["hits"]).any(axis=1).sum() > 0  # the two readings differ (rarely on barrel + disks)
+
+
+def test_window_ranking_refuses_a_score_margin(kf, pairs):
+    _, _, mean, sd = pairs
+    buf = kf.mlp_buffer(synth.mlp_init(9), mean, sd)
+    p = kf.find_params(30.0, 6, 1, 17, mlp=buf, top_n=2, score_margin=1.0, window_ranking=True)
+    assert kf.load_library().kf_find_workspace_size(100, __import__("ctypes").byref(p)) == 0
