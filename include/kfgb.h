@@ -357,13 +357,14 @@ int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const
 
 /* Autotuner for the persistent finder (not in the paper): runs kf_find_tracks on the given seeds
  * (a calibration subset of the workload) for every block size 64..256 (step 32) and for the
- * smallest and the next compiled candidate capacity, and for k_max > 4 (the learned proposal:
- * with top_n <= 4) with and without adaptive capacity 4, times each run with CUDA events (the
+ * smallest and the next compiled candidate capacity, and for k_max > 4 with adaptive capacity 2,
+ * 4 (those holding top_n with the learned proposal) or none, times each run with CUDA events (the
  * stream is synchronised: do not call it during a stream capture), and writes the fastest block
  * size, capacity and adaptive capacity into params->block_threads, params->k_capacity and
  * params->adaptive_capacity; *best_ms receives its time. Every configuration gives the same results. Outputs as for kf_find_tracks; a
  * configuration whose workspace is larger than workspace_bytes is passed over (size the workspace
- * with adaptive_capacity = 4 to let it compete). */
+ * with an adaptive capacity set, which adds the same overflow list for 2 and 4, to let those
+ * compete). */
 int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const float* hits, const int* hit_surface,
                      const int* seed_hits, const int* seed_event, int n_seeds, KfFindParams* params, int* hits_out,
                      int* nhits_out, float* chi2_out, float* state_out, float* cov_out, int* status_out,

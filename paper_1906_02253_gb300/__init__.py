@@ -520,7 +520,7 @@ def autotune_find(geom: Geometry, index: HitIndex, hits, hit_surface, seed_hits,
     # Workspace for the largest configuration tried: adaptive capacity adds its overflow list.
     wide = KfFindParams.from_buffer_copy(params)
     if params.k_max > 4 and (not (params.mlp and params.top_n > 0) or params.top_n <= 4):
-        wide.adaptive_capacity = 4
+        wide.adaptive_capacity = 4  # the overflow list is as long for every first-pass capacity
     n = seed_hits.shape[1]
     ws = torch.empty(max(find_workspace_size(n, wide), find_workspace_size(n, params), 256), dtype=torch.uint8,
                      device=seed_hits.device)

@@ -444,11 +444,14 @@ int kf_autotune_find(const KfGeometry* geom, const KfHitIndex* index, const floa
   int cap_opts[2] = {0, 0}, n_cap = 0;
   for (int c : caps)
     if (c >= need && n_cap < 2) cap_opts[n_cap++] = c;
-  // With k_max > 4 (and, for the learned proposal, top_n <= 4) adaptive capacity 4 is tried too
-  // (a configuration whose workspace does not fit the caller's fails and is passed over).
+  // With k_max > 4 adaptive capacities 2 and 4 are tried too, those that hold top_n with the
+  // learned proposal (a configuration whose workspace does not fit the caller's fails and is
+  // passed over).
   const bool learned = params->mlp && params->top_n > 0;
-  const int ad_opts[2] = {0, 4};
-  const int n_ad = params->k_max > 4 && (!learned || params->top_n <= 4) ? 2 : 1;
+  int ad_opts[3] = {0, 0, 0}, n_ad = 1;
+  if (params->k_max > 4)
+    for (int a : {2, 4})
+      if (!learned || params->top_n <= a) ad_opts[n_ad++] = a;
   KfFindParams best = *params;
   float best_t = -1.f;
   for (int ci2 = 0; ci2 < n_cap; ++ci2) {
