@@ -338,7 +338,8 @@ int kf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, 
  * provide the workspace kf_find_tracks takes.
  *
  * Same arguments and results as kf_find_tracks, without workspace. The scratch (work counter, seed
- * states and, with the learned proposal, a transposed copy of the network) is a fixed array inside
+ * states and, with the learned proposal, the network's weights as tensor-core operands) is a fixed
+ * array inside
  * the library of KF_STATIC_SCRATCH_BYTES (about 7.3 MiB),
  * held on every GPU that loads the library until the process exits. At most KF_STATIC_MAX_SEEDS
  * seeds per call: more returns KF_ERR_CAPACITY and launches nothing (split the seeds into
@@ -349,7 +350,7 @@ int kf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, 
  * array and leaves its contents behind: calls whose kernels can overlap on the GPU (several
  * streams, several host threads) race and corrupt each other's results, so serialise them. */
 #define KF_STATIC_MAX_SEEDS 65536
-#define KF_STATIC_SCRATCH_BYTES 7623424
+#define KF_STATIC_SCRATCH_BYTES 7622912
 int kf_find_tracks_static(const KfGeometry* geom, const KfHitIndex* index, const float* hits,
                           const int* hit_surface, const int* seed_hits, const int* seed_event, int n_seeds,
                           const KfFindParams* params, int* hits_out, int* nhits_out, float* chi2_out,

@@ -70,12 +70,24 @@ template <int KC>
 struct WarpLearned {
   float hl_sc[KC][32];
   float2 box[32];  // window ranking: half-widths sqrt(cut S_00), sqrt(cut S_11) of each lane's window
+  float pl_sc[kPList];  // score of each buffered pair being ranked
 };
 
 template <int KC, bool LEARNED>
 __host__ __device__ size_t warp_smem_bytes(int lmax) {
   return (sizeof(WarpSmem<KC>) + static_cast<size_t>(lmax - 3) * 32 * sizeof(int) +
           (LEARNED ? sizeof(WarpLearned<KC>) : 0) + 15) / 16 * 16;
+}
+
+// The network's logits of 16 pairs, rows lane / 4 (a) and lane / 4 + 8 (b), from this lane's four
+// operand columns of each (mlp_logit16). Not inlined: its operands take ~70 registers, which the
+// finder has only between its phases; the call keeps them out of the finder's own allocation.
+static __device__ __forceinline__ float2 score16(const uint4* __restrict__ frag, const float* __restrict__ prm, float a0,
+                                              float a1, float a2, float a3, float b0, float b1, float b2, float b3) {
+  const float xa[4] = {a0, a1, a2, a3}, xb[4] = {b0, b1, b2, b3};
+  float la, lb;
+  mlp_logit16(frag, prm, xa, xb, static_cast<int>(threadIdx.x & 31), la, lb);
+  return make_float2(la, lb);
 }
 
 __device__ __forceinline__ bool before(float t, int id, float u, int uid) { return t < u || (t == u && id < uid); }
@@ -508,7 +520,7 @@ __device__ __forceinline__ unsigned long long pack_key(int nh, float c2, int pk)
 constexpr int kFeatSteer = 1, kFeatMaterial = 2, kFeatField = 4, kFeatAll = 7;
 
 // Blocks of the learned instances hold at most 192 threads: at two blocks per SM that leaves them
-// 170 registers, which their scoring and score-ordered lists need (capped at 128, as the plain
+// 168 registers, which their scoring and score-ordered lists need (capped at 128, as the plain
 // instances are for 256-thread blocks, they spilled ~150 bytes per thread and ran 21-29% slower).
 constexpr int kFindMaxBlockLearned = 192;
 template <int KC, bool LEARNED, int FEAT>
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
   int* trace = reinterpret_cast<int*>(wbase + sizeof(WarpSmem<KC>));  // [step][32]
   WarpLearned<KC>& WL = *reinterpret_cast<WarpLearned<KC>*>(wbase + sizeof(WarpSmem<KC>) +
                                                             static_cast<size_t>(A.lmax - 3) * 32 * sizeof(int));
-  const float* __restrict__ wmlp = A.mlp_t;  // transposed network parameters (L1/L2)
+  const float* __restrict__ wmlp = A.mlp;  // network parameters (biases, output layer, normaliser)
   // Capacity of a lane's list during the scan; a first pass of adaptive capacity (detect) keeps at
   // most its own slots (a lane with more passing hits makes its seed overflow anyway). With the
   // learned proposal a first pass runs only when top_n fits its slots, so a lane's list holds
@@ -584,10 +596,11 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     }
     // One block-wide vote per step: the block's warps stay in step with each other, so the SM
     // fetches the code of one or two phases at a time (the kernel is larger than the instruction
-    // cache); the block ends when none of its warps has a seed. The learned instances vote per
-    // warp: their network evaluations fall on a few warps of a step, and a block-wide vote made the
-    // block's other warps wait for them (9-14% of their time on the barrel workload).
-    if (LEARNED ? !__any_sync(kFull, seed >= 0) : !__syncthreads_or(seed >= 0)) break;
+    // cache); the block ends when none of its warps has a seed. This holds for the learned
+    // instances too: with warps voting on their own they drift apart, and the larger learned
+    // kernel then stalls on instruction fetch (twice as often per issued instruction), which costs
+    // more than the barrier's wait for a warp that is scoring.
+    if (!__syncthreads_or(seed >= 0)) break;
 
     // ---- a fresh group loads its seed state into slot 0 ------------------------------------
     int failed = 0;
@@ -690,9 +703,11 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     int npass = 0;   // passing hits of this lane's window (a detecting pass counts beyond its list)
     // Buffered passing pairs go to their owner's list: the k_max best by (total chi2, hit id)
     // (plain), or, with the learned proposal, the top_n best by network score. A pair is scored
-    // (by all lanes together) only when its owner has more passing hits than top_n; otherwise
-    // every hit is kept anyway. A flush in the middle of the scan (buffer full) scores all its
-    // pairs.
+    // only when its owner has more passing hits than top_n (with a score margin, two or more);
+    // otherwise every hit is kept anyway. A flush in the middle of the scan (buffer full) scores
+    // all its pairs. The pairs to score are evaluated by the warp on the tensor cores, 16 at a
+    // time; then each owner inserts its own (the kept list is ordered by (score, hit id), so the
+    // order of insertion does not matter).
     auto flush = [&](int count, bool final_flush) {
       int run = my_cnt;
 #pragma unroll
@@ -706,7 +721,8 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
         const unsigned needmask = __ballot_sync(kFull, need && my_cnt > 0);
         if (needmask) {
           // Every lane's raw candidate features (predicted state, log covariance diagonal) and the
-          // square roots of its innovation variances; an owner's reach the warp by shuffles.
+          // square roots of its innovation variances; an owner's reach the rows of its pairs by
+          // shuffles.
           float fe[kMlpIn];
 #pragma unroll
           for (int i = 0; i < 6; ++i) fe[i] = c.p[i];
@@ -722,34 +738,66 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
           fe[7] = fmaxf(fe[7], kLogFloor);
           fe[12] = sqrtf(s00v);
           fe[13] = sqrtf(s11v);
-          // The pairs of those owners in buffer order (owner by owner), each scored by the whole
-          // warp; the owner keeps its top_n by score as they come.
-          int prev = -1;
-          float2 base = make_float2(0.f, 0.f);
-          float d12 = 1.f, d13 = 1.f;
-          for (int k = 0; k < count; ++k) {
-            const int o = W.u.pl.own[k];
-            if (!((needmask >> o) & 1u)) continue;
-            if (o != prev) {
-              float x[12];
 #pragma unroll
-              for (int i = 0; i < 12; ++i)
-                x[i] = (__shfl_sync(kFull, fe[i], o) - __ldg(wmlp + kMlpMean + i)) / __ldg(wmlp + kMlpSd + i);
-              base = mlp_layer1_base(wmlp, x, lane);
-              d12 = __shfl_sync(kFull, fe[12], o);
-              d13 = __shfl_sync(kFull, fe[13], o);
-              prev = o;
-            }
-            const float4 h = __ldg(A.sorted_rec + W.u.pl.pos[k]);
-            float r0, r1;
-            window_chi2(W.win_a[o], W.win_b[o], h, r0, r1);
-            const float x12 = (r0 / d12 - __ldg(wmlp + kMlpMean + 12)) / __ldg(wmlp + kMlpSd + 12);
-            const float x13 = (r1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
-            const float sc = mlp_logit_warp(wmlp, base, x12, x13, lane);
-            if (lane == o)
-              hl_insert_scored(W, WL, lane, hl_n, keep, sc, c.chi2 + W.u.pl.c2[k], W.u.pl.id[k],
-                               W.u.pl.c2[k] < cut ? W.u.pl.pos[k] : ~W.u.pl.pos[k]);
+          for (int i = 0; i < 12; ++i) fe[i] = (fe[i] - __ldg(wmlp + kMlpMean + i)) / __ldg(wmlp + kMlpSd + i);
+          // The pairs to score: the runs of the owners in needmask, numbered owner by owner.
+          const int ncnt = ((needmask >> lane) & 1u) ? my_cnt : 0;
+          int ninc = ncnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(kFull, ninc, o);
+            if (lane >= o) ninc += v;
           }
+          const int nexc = ninc - ncnt;
+          const int total_sc = __shfl_sync(kFull, ninc, 31);
+          const int t4 = lane & 3;
+          for (int r0 = 0; r0 < total_sc; r0 += 16) {
+            // Rows lane / 4 and lane / 4 + 8 of this tile: their pairs' features in this lane's
+            // operand columns 2 t4, 2 t4 + 1, 2 t4 + 8, 2 t4 + 9.
+            float xr[2][4];
+            int kr[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int j = r0 + (lane >> 2) + 8 * h;
+              int o = 0;
+#pragma unroll
+              for (int bit = 16; bit > 0; bit >>= 1) {
+                const int v = __shfl_sync(kFull, ninc, o + bit - 1);
+                if (v <= j) o += bit;
+              }
+              o = min(o, 31);
+              const int k = __shfl_sync(kFull, start, o) + j - __shfl_sync(kFull, nexc, o);
+              float f[12];
+#pragma unroll
+              for (int i = 0; i < 12; ++i) f[i] = __shfl_sync(kFull, fe[i], o);
+              const float d12 = __shfl_sync(kFull, fe[12], o), d13 = __shfl_sync(kFull, fe[13], o);
+              const bool real = j < total_sc;
+              float x12 = 0.f, x13 = 0.f;
+              if (real && t4 == 2) {
+                const float4 hr = __ldg(A.sorted_rec + W.u.pl.pos[k]);
+                float q0, q1;
+                window_chi2(W.win_a[o], W.win_b[o], hr, q0, q1);
+                x12 = (q0 / d12 - __ldg(wmlp + kMlpMean + 12)) / __ldg(wmlp + kMlpSd + 12);
+                x13 = (q1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
+              }
+              xr[h][0] = !real ? 0.f : t4 == 0 ? f[0] : t4 == 1 ? f[2] : t4 == 2 ? f[4] : f[6];
+              xr[h][1] = !real ? 0.f : t4 == 0 ? f[1] : t4 == 1 ? f[3] : t4 == 2 ? f[5] : f[7];
+              xr[h][2] = !real ? 0.f : t4 == 0 ? f[8] : t4 == 1 ? f[10] : t4 == 2 ? x12 : 0.f;
+              xr[h][3] = !real ? 0.f : t4 == 0 ? f[9] : t4 == 1 ? f[11] : t4 == 2 ? x13 : 0.f;
+              kr[h] = real ? k : -1;
+            }
+            const float2 l2 = score16(A.mlp_frag, wmlp, xr[0][0], xr[0][1], xr[0][2], xr[0][3], xr[1][0],
+                                      xr[1][1], xr[1][2], xr[1][3]);
+            if (t4 == 0) {
+              if (kr[0] >= 0) WL.pl_sc[kr[0]] = l2.x;
+              if (kr[1] >= 0) WL.pl_sc[kr[1]] = l2.y;
+            }
+          }
+          __syncwarp();
+          if ((needmask >> lane) & 1u)
+            for (int k = start; k < start + my_cnt; ++k)
+              hl_insert_scored(W, WL, lane, hl_n, keep, WL.pl_sc[k], c.chi2 + W.u.pl.c2[k], W.u.pl.id[k],
+                               W.u.pl.c2[k] < cut ? W.u.pl.pos[k] : ~W.u.pl.pos[k]);
         }
         if (!need) {  // kept unconditionally (at most top_n of them)
           for (int k = start; k < start + my_cnt; ++k) {
@@ -1174,7 +1222,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   plan->off_state = 256;  // after the work counters
   plan->off_surf = up(plan->off_state + static_cast<size_t>(kSeedWords) * n_seeds * sizeof(float));
   plan->off_mlp = up(plan->off_surf + static_cast<size_t>(n_seeds) * sizeof(int));
-  plan->ws_bytes = learned ? up(plan->off_mlp + static_cast<size_t>(kMlpParamsAll) * sizeof(float)) : plan->off_mlp;
+  plan->ws_bytes = learned ? up(plan->off_mlp + static_cast<size_t>(kFragWords) * sizeof(uint4)) : plan->off_mlp;
   plan->off_ovf = 0;
   if (kc1 > 0) {
     plan->off_ovf = plan->ws_bytes;
@@ -1190,7 +1238,7 @@ int launch_seed_states(const DevGeom& G, const DevMat& M, const FindArgs& A, cud
 
 // ------------------------------------------------------------------------------------------------
 // Scratch of the allocation-free entry point (kf_find_tracks_static): the work counter, the seed
-// states for at most KF_STATIC_MAX_SEEDS seeds and the learned proposal's transposed parameters,
+// states for at most KF_STATIC_MAX_SEEDS seeds and the learned proposal's weight fragments,
 // laid out as plan_find lays out a caller's workspace. A fixed array in the library: every GPU that loads the library holds it until the
 // process exits. In host code g_find_scratch only names the array; its device address comes from
 // cudaGetSymbolAddress, looked up once per device.
@@ -1198,7 +1246,7 @@ constexpr size_t static_scratch_bytes() {
   return (((256 + static_cast<size_t>(kSeedWords) * KF_STATIC_MAX_SEEDS * sizeof(float) + 255) / 256 * 256 +
            static_cast<size_t>(KF_STATIC_MAX_SEEDS) * sizeof(int) + 255) /
               256 * 256 +
-          static_cast<size_t>(kMlpParamsAll) * sizeof(float) + 255) /
+          static_cast<size_t>(kFragWords) * sizeof(uint4) + 255) /
          256 * 256;
 }
 static_assert(static_scratch_bytes() == KF_STATIC_SCRATCH_BYTES, "header and library disagree on the scratch size");
@@ -1222,11 +1270,11 @@ int launch_find(const DevGeom& G, const DevMat& M, FindArgs& A, const FindPlan& 
   A.counter = reinterpret_cast<int*>(base);
   A.seed_state = reinterpret_cast<float*>(base + plan.off_state);
   A.seed_surf = reinterpret_cast<int*>(base + plan.off_surf);
-  A.mlp_t = nullptr;
+  A.mlp_frag = nullptr;
   if (plan.learned) {
-    float* wt = reinterpret_cast<float*>(base + plan.off_mlp);
-    if (launch_mlp_transpose(A.mlp, wt, stream) != 0) return KF_ERR_CUDA;
-    A.mlp_t = wt;
+    uint4* frag = reinterpret_cast<uint4*>(base + plan.off_mlp);
+    if (launch_mlp_fragments(A.mlp, frag, stream) != 0) return KF_ERR_CUDA;
+    A.mlp_frag = frag;
   }
   // Work counters: [0] the (first) pass's seed queue, [1] the second pass's, [2] the overflow count.
   if (cudaMemsetAsync(A.counter, 0, 3 * sizeof(int), stream) != cudaSuccess) return KF_ERR_CUDA;

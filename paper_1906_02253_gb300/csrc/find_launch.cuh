@@ -23,7 +23,7 @@ struct FindArgs {
   float chi2_cut;
   int k_max, max_miss, lmax;
   const float* mlp;    // learned proposal parameters (KF_MLP_BUFFER floats) or null
-  const float* mlp_t;  // their transposed copy in the workspace (set by launch_find)
+  const uint4* mlp_frag;  // their hidden layers as tensor-core fragments in the workspace (set by launch_find)
   const int* seed_keep;  // seeds with 0 are skipped (status 2), or null
   int top_n;         // > 0 with mlp: keep the top_n passing hits by score
   float score_margin;  // > 0: of those, only the ones within this margin of the window's best score

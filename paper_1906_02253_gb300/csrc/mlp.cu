@@ -230,25 +230,41 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward(const float* __restr
   }
 }
 
-// Transposed copy for the finder (layout in mlp.cuh).
-__global__ void k_mlp_transpose(const float* __restrict__ w, float* __restrict__ wt) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParamsAll; i += gridDim.x * blockDim.x) {
-    float v;
-    if (i < kMlpB1) {  // W1T[in][j] = W1[j][in]
-      const int in = i / kMlpHid, j = i % kMlpHid;
-      v = w[kMlpW1 + j * kMlpIn + in];
-    } else if (i >= kMlpW2 && i < kMlpB2) {  // W2T[in][o] = W2[o][in]
-      const int in = (i - kMlpW2) / kMlpHid, o = (i - kMlpW2) % kMlpHid;
-      v = w[kMlpW2 + o * kMlpHid + in];
+// The finder's B fragments of both hidden layers (layout in mlp.cuh): entry i holds, for hidden
+// unit n = 8 * tile + lane / 4, the weights of inputs 16 * step + 2 (lane % 4) + {0, 1, 8, 9} (zero
+// beyond the 14 inputs of the first layer), hi and scaled lo fp16 parts.
+__global__ void k_mlp_fragments(const float* __restrict__ w, uint4* __restrict__ frag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kFragWords; i += gridDim.x * blockDim.x) {
+    int step, tile, lane, ld;
+    const float* W;
+    if (i < kFragL2) {
+      step = 0;
+      tile = i / 32;
+      lane = i % 32;
+      W = w + kMlpW1;
+      ld = kMlpIn;
     } else {
-      v = w[i];
+      const int j = i - kFragL2;
+      step = j / 256;
+      tile = (j / 32) % 8;
+      lane = j % 32;
+      W = w + kMlpW2;
+      ld = kMlpHid;
     }
-    wt[i] = v;
+    const int n = 8 * tile + lane / 4, k0 = 16 * step + 2 * (lane % 4);
+    const int ks[4] = {k0, k0 + 1, k0 + 8, k0 + 9};
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = ks[q] < ld ? W[n * ld + ks[q]] : 0.f;
+    unsigned h01, l01, h23, l23;
+    split_f16x2(v[0], v[1], h01, l01);
+    split_f16x2(v[2], v[3], h23, l23);
+    frag[i] = make_uint4(h01, h23, l01, l23);
   }
 }
 
-int launch_mlp_transpose(const float* params, float* wt, cudaStream_t st) {
-  k_mlp_transpose<<<(kMlpParamsAll + 255) / 256, 256, 0, st>>>(params, wt);
+int launch_mlp_fragments(const float* params, uint4* frag, cudaStream_t st) {
+  k_mlp_fragments<<<(kFragWords + 255) / 256, 256, 0, st>>>(params, frag);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

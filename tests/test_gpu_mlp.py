@@ -177,6 +177,7 @@ def test_learned_finding_with_region_steering_and_material_matches_oracle(kf, pa
 
 @pytest.mark.parametrize("name,net,margin,top_n,k", [
     ("find", None, 0.7, 3, 6),
+    ("hi_occ", "mlp_hi_occ.npz", 0.7, 2, 8),
     ("hi_occ", "mlp_hi_occ.npz", 1.0, 2, 8),
     ("learned", "mlp_learned.npz", 2.0, 2, 6),
 ])
@@ -264,6 +265,7 @@ def test_training_module_learns_from_oracle_pairs(kf, pairs):
                                                          ("hi_occ", "mlp_hi_occ.npz", 2, 2.0, 4),
                                                          ("learned", "mlp_learned.npz", 4, 0.0, 4),
                                                          ("hi_occ", "mlp_hi_occ.npz", 2, 1.0, 2),
+                                                         ("hi_occ", "mlp_hi_occ.npz", 2, 0.7, 2),
                                                          ("learned", "mlp_learned.npz", 1, 0.0, 2)])
 def test_learned_adaptive_capacity_gives_the_single_pass_results(kf, name, net, top_n, margin, first):
     """The learned proposal in two passes (`first` slots first) gives exactly its single-pass
