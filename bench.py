@@ -65,15 +65,21 @@ MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 # DRAM traffic of the finder measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch, or of adaptive capacity's two passes, per seed) on a smaller case of each workload (30
 # events of the 100-event workload, 40 of the barrel + disk workload; profiles/k_find_tracks_*),
-# keyed by workload (and adaptive capacity), valid while the finder's sources and build flags are
-# the ones profiled (SHA-1 over FIND_SOURCES); otherwise reported as null.
+# keyed by workload (and adaptive capacity, and the learned proposal's top_n and score margin), valid
+# while the finder's sources and build flags are the ones profiled (SHA-1 over FIND_SOURCES);
+# otherwise reported as null.
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
-                "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "08558b41e4e080588c76f579e2b395dc7fdf7374",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (124944128 + 35772672) / 302063,
-                                        "find_200ev_barrel_disks_noise100": (143625216 + 31266048) / 211523,
+                "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/csrc/mlp.cuh",
+                "paper_1906_02253_gb300/build.py")
+FIND_PROFILE = {"sources_sha1": "ccbef5ca750ba9eb56828b4ef2f59d0823255756",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125849856 + 35077120) / 302063,
+                                        "find_200ev_barrel_disks_noise100": (144185344 + 30764544) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive4":
-                                            (170581504 + 36413696 + 128902656 + 30736896) / 211523}}
+                                            (170493440 + 36336640 + 128858112 + 27786240) / 211523,
+                                        "find_200ev_barrel_disks_noise100_adaptive2":
+                                            (168260352 + 38676480 + 159729664 + 35268864) / 211523,
+                                        "find_200ev_barrel_disks_noise100_adaptive2_learned2_0.7":
+                                            (161507840 + 33984512 + 47439104 + 4393728) / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
@@ -155,10 +161,11 @@ def calibration_events(n_events: int) -> int:
     return min(n_events, max(10, n_events // 4))
 
 
-def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: int = 0):
+def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: int = 0, learned=None):
     """Run the FP64 oracle (index + find + fit of the found tracks; with ``clean``, seed cleaning
     before finding and duplicate removal after it) on the first seeds of the batch, all host
-    cores. Returns (seconds, n_seeds, counters, threads)."""
+    cores; ``learned`` = (weights, mean, sd, top_n, score_margin) finds with the learned proposal.
+    Returns (seconds, n_seeds, counters, threads)."""
     import numpy as np
     import oracle
 
@@ -172,7 +179,12 @@ def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: i
     if clean:
         keep = oracle.clean_seeds(seeds[sub], ev[sub], oracle.seed_params(g, batch, seeds[sub]))
         sub = sub[keep != 0]
-    f = oracle.find(g, batch, seeds[sub], ev[sub], n_threads=n_threads)
+    lk = {}
+    if learned is not None:
+        w, mean, sd, top_n, margin = learned
+        lk = dict(mlp=(np.asarray(w, np.float64), np.asarray(mean, np.float64), np.asarray(sd, np.float64)),
+                  top_n=top_n, score_margin=margin)
+    f = oracle.find(g, batch, seeds[sub], ev[sub], n_threads=n_threads, **lk)
     if clean:
         oracle.remove_duplicates(f["hits"], f["n_hits"], f["chi2"], f["p"][:, 4], f["p"][:, 5], ev[sub])
     oracle.fit(g, batch.hits, batch.hit_surface, f["hits"], n_threads=n_threads)
@@ -183,6 +195,25 @@ def oracle_sample(wl, batch, n_seeds_max: int, clean: bool = False, n_threads: i
     return dt, len(sub), f["counters"], threads
 
 
+def network_file(name: str) -> str:
+    """The trained network of a workload (paper_1906_02253_gb300/data/mlp_<name>.npz), else the
+    barrel-geometry network."""
+    path = os.path.join(ROOT, "paper_1906_02253_gb300", "data", f"mlp_{name}.npz")
+    return path if os.path.exists(path) else MLP_FILE
+
+
+def learned_arg(args, name: str):
+    """--learned TOP_N[:MARGIN] as (weights, mean, sd, top_n, margin, file) with the workload's
+    network, or None."""
+    if not getattr(args, "learned", ""):
+        return None
+    import numpy as np
+    top_n, _, margin = args.learned.partition(":")
+    path = network_file(name)
+    z = np.load(path)
+    return z["weights"], z["mean"], z["sd"], int(top_n), float(margin or 0.0), os.path.basename(path)
+
+
 def run_reference(args, wl, batch):
     """The reference arm: the oracle as it stands, on the host cores, one bounded sample per step."""
     ws, rank, _ = _dist()
@@ -190,11 +221,13 @@ def run_reference(args, wl, batch):
         return
     per_step = args.ref_seeds
     clean = args.clean or getattr(wl, "combinatorial_seeds", False)
+    lrn = learned_arg(args, args.workload)
+    lrn = lrn[:5] if lrn else None
     for _ in range(args.warmup):
-        oracle_sample(wl, batch, min(per_step, 2000), clean)
+        oracle_sample(wl, batch, min(per_step, 2000), clean, learned=lrn)
     times, n = [], 0
     for _ in range(args.steps):
-        dt, n, _, cores = oracle_sample(wl, batch, per_step, clean)
+        dt, n, _, cores = oracle_sample(wl, batch, per_step, clean, learned=lrn)
         times.append(dt)
     value = n / statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -247,8 +280,12 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e
         track_keep = torch.ones(n_seeds, dtype=torch.int32, device=dev)
         dws = torch.empty(max(kf.dedup_workspace_size(n_seeds, lmax, n_hits), 256), dtype=torch.uint8,
                           device=dev)
+    # --learned: the step's finder runs the learned proposal with the workload's network
+    lrn = learned_arg(args, mlp_name or args.workload)
+    mlp_buf = kf.mlp_buffer(lrn[0], lrn[1], lrn[2], device=dev) if lrn else None
     prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, lmax, args.block, args.blocks_per_sm,
-                         steering_tables=steer, seed_keep=seed_keep, adaptive_capacity=args.adaptive)
+                         steering_tables=steer, seed_keep=seed_keep, adaptive_capacity=args.adaptive,
+                         mlp=mlp_buf, top_n=lrn[3] if lrn else 0, score_margin=lrn[4] if lrn else 0.0)
     idx = kf.HitIndex(g, batch.n_events, n_hits, dev)
     fout = dict(hits=torch.empty((lmax, n_seeds), dtype=torch.int32, device=dev),
                 nhits=torch.empty(n_seeds, dtype=torch.int32, device=dev),
@@ -356,7 +393,8 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e
     # index, seed states, find, fit kernels (plus one memset node); adaptive capacity: a second find
     # pass; cleaning: count, 3 scan kernels, fill, seed directions, decision; duplicate removal:
     # count, 3 scan kernels, fill, decision
-    launches_per_step = 4 + (1 if prm.adaptive_capacity > 0 else 0) + (7 + 6 if clean else 0)
+    # learned proposal: the weight-fragment kernel before the finder
+    launches_per_step = 4 + (1 if prm.adaptive_capacity > 0 else 0) + (7 + 6 if clean else 0) + (1 if lrn else 0)
 
     # Per-part durations: the same launches eager, events on the launching stream.
     kern = {k: [] for k in parts}
@@ -456,7 +494,7 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e
     fit_ok = float((fit_out["status"] == 0).float().mean().item())
 
     learned = None
-    if not args.no_learned:
+    if not args.no_learned and not lrn:  # (with --learned the step's finder is no longer plain)
         learned = compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, eff, fake, kern_ms["find"],
                                   mlp_name or args.workload)
 
@@ -473,6 +511,8 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e
                                else "hit index + find + fit") + ", one CUDA graph",
                       "l2": "flushed between steps (256 MB write)",
                       "next_surface": "region steering (eta edges 0.4, 1.8)" if args.steering else "geometric rule",
+                      "finder": (f"learned proposal, top_n {lrn[3]}, score margin {lrn[4]:g}, network {lrn[5]}"
+                                 if lrn else "plain (full window)"),
                       "parallelism": (f"one fixed batch split over {ws} GPU(s) by LPT on track counts"
                                       if args.scaling == "strong" else f"every GPU its own events ({ws} GPU(s))")
                                      + ", no collective"},
@@ -496,18 +536,19 @@ def measure_workload(args, wl, batch, full: bool = True, mlp_name: str = None, e
     # CPU baseline (oracle on a bounded sample) and the finder's algorithmic work per seed.
     counters = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, n, counters, cores = oracle_sample(wl, batch, args.cpu_seeds, clean)
+        dt, n, counters, cores = oracle_sample(wl, batch, args.cpu_seeds, clean, learned=lrn[:5] if lrn else None)
         out["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"first {n} seeds of the batch: index, "
                                          + ("seed cleaning, find, duplicate removal, " if clean else "find, ")
                                          + f"fit of the found tracks (FP64, {dt:.1f} s)"}
         counters = np.asarray(counters, np.float64) / n
         if full:
-            dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1)
+            dt1, n1, _, _ = oracle_sample(wl, batch, min(20000, n), clean, n_threads=1,
+                                          learned=lrn[:5] if lrn else None)
             out["cpu_baseline"]["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
                                                     "sample": f"first {n1} seeds ({dt1:.1f} s)"}
     out["roofline"] = roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, out["clocks"],
-                               adaptive=prm.adaptive_capacity)
+                               adaptive=prm.adaptive_capacity, learned=f"_learned{lrn[3]}_{lrn[4]:g}" if lrn else "")
     out["_ctx"] = dict(kf=kf, g=g, d=d, host=host, idx=idx, prm=prm, fout=fout, fit_out=fit_out, stream=stream,
                        flush=flush, n_seeds=n_seeds, batch=batch, wl=wl, learned=learned)
     return out
@@ -526,9 +567,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     import torch
     from paper_1906_02253_gb300 import metrics
 
-    path = os.path.join(ROOT, "paper_1906_02253_gb300", "data", f"mlp_{mlp_name}.npz")
-    if not os.path.exists(path):
-        path = MLP_FILE  # the barrel-geometry network
+    path = network_file(mlp_name)
     if not os.path.exists(path):
         return {"unavailable": "no trained network in paper_1906_02253_gb300/data"}
     z = np.load(path)
@@ -816,7 +855,7 @@ def find_sources_sha1() -> str:
     return h.hexdigest()
 
 
-def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks, adaptive=0):
+def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks, adaptive=0, learned=""):
     """Roofline of every step kernel, and of the dominant one at the top level. The finder and the
     fit are FP32-ALU bound (no dense contraction): peak = SMs x 128 FP32 lanes x 2 flop x max SM
     clock. The index is HBM bound."""
@@ -851,9 +890,12 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks, adaptiv
         # chi2 work: the hits of the windows the finder scans (limited to the phi sub-bins they touch)
         n_prop, n_pass, n_upd, n_scan, n_win = counters[:5]
         per_seed = FLOP_SEED + n_prop * (FLOP_PROP + FLOP_TRANSPORT) + n_upd * FLOP_UPDATE + n_win * FLOP_CHI2
+        n_mlp = counters[5] if learned and len(counters) > 5 else 0.0
+        per_seed += n_mlp * FLOP_MLP_FWD  # network evaluations (on the tensor cores, counted as FP32 flops)
         ach = per_seed * n_seeds / (kern_ms["find"] / 1000.0) / 1e12
         # profiled per configuration: one pass, or adaptive capacity's two passes together
-        bytes_seed = FIND_PROFILE["dram_bytes_per_seed"].get(batch.wl.name + (f"_adaptive{adaptive}" if adaptive else ""))
+        key = batch.wl.name + (f"_adaptive{adaptive}" if adaptive else "") + learned
+        bytes_seed = FIND_PROFILE["dram_bytes_per_seed"].get(key)
         profiled = find_sources_sha1() == FIND_PROFILE["sources_sha1"] and bytes_seed is not None
         traffic = bytes_seed * n_seeds if profiled else None
         per["find"] = {"kernel": "k_find_tracks", "bound": "alu", "achieved": ach, "peak": alu_peak,
@@ -861,7 +903,8 @@ def roofline(kern_ms, counters, n_seeds, n_hits, batch, fit_out, clocks, adaptiv
                        "traffic_unit": "bytes per launch (ncu, scaled by seeds)", "peak_note": f"FP32 {sm_mhz:.0f} MHz",
                        "fma_probe_tflops": fma_rate,
                        "work_per_seed": {"propagations": n_prop, "updates": n_upd, "chi2": n_win,
-                                         "chi2_whole_bins": n_scan, "flop": per_seed}}
+                                         "chi2_whole_bins": n_scan, "network_evaluations": n_mlp,
+                                         "flop": per_seed}}
     dom = max(("index", "find", "fit"), key=lambda k: kern_ms[k])
     out = dict(per[dom])
     out["per_kernel"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
@@ -883,6 +926,8 @@ def main():
     ap.add_argument("--ref-seeds", type=int, default=200000, help="oracle sample per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
+    ap.add_argument("--learned", default="", metavar="TOP_N[:MARGIN]",
+                    help="the step's finder with the learned proposal (the workload's trained network), e.g. 2:0.7")
     ap.add_argument("--no-autotune", action="store_true", help="default launch configuration")
     ap.add_argument("--adaptive", type=int, default=0,
                     help="with --no-autotune: the finder's adaptive capacity (first-pass slots; 0 = one pass)")
