@@ -79,17 +79,6 @@ __host__ __device__ size_t warp_smem_bytes(int lmax) {
           (LEARNED ? sizeof(WarpLearned<KC>) : 0) + 15) / 16 * 16;
 }
 
-// The network's logits of 16 pairs, rows lane / 4 (a) and lane / 4 + 8 (b), from this lane's four
-// operand columns of each (mlp_logit16). Not inlined: its operands take ~70 registers, which the
-// finder has only between its phases; the call keeps them out of the finder's own allocation.
-static __device__ __forceinline__ float2 score16(const uint4* __restrict__ frag, const float* __restrict__ prm, float a0,
-                                              float a1, float a2, float a3, float b0, float b1, float b2, float b3) {
-  const float xa[4] = {a0, a1, a2, a3}, xb[4] = {b0, b1, b2, b3};
-  float la, lb;
-  mlp_logit16(frag, prm, xa, xb, static_cast<int>(threadIdx.x & 31), la, lb);
-  return make_float2(la, lb);
-}
-
 __device__ __forceinline__ bool before(float t, int id, float u, int uid) { return t < u || (t == u && id < uid); }
 
 // Insert into a lane's kept list ordered by (score descending, hit id ascending), capacity cap.
@@ -705,7 +694,7 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     // (plain), or, with the learned proposal, the top_n best by network score. A pair is scored
     // only when its owner has more passing hits than top_n (with a score margin, two or more);
     // otherwise every hit is kept anyway. A flush in the middle of the scan (buffer full) scores
-    // all its pairs. The pairs to score are evaluated by the warp on the tensor cores, 16 at a
+    // all its pairs. The pairs to score are evaluated by the warp on the tensor cores, 8 at a
     // time; then each owner inserts its own (the kept list is ordered by (score, hit id), so the
     // order of insertion does not matter).
     auto flush = [&](int count, bool final_flush) {
@@ -751,46 +740,42 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
           const int nexc = ninc - ncnt;
           const int total_sc = __shfl_sync(kFull, ninc, 31);
           const int t4 = lane & 3;
-          for (int r0 = 0; r0 < total_sc; r0 += 16) {
-            // Rows lane / 4 and lane / 4 + 8 of this tile: their pairs' features in this lane's
-            // operand columns 2 t4, 2 t4 + 1, 2 t4 + 8, 2 t4 + 9.
-            float xr[2][4];
-            int kr[2];
+          for (int r0 = 0; r0 < total_sc; r0 += 8) {
+            // Pair lane / 4 of this tile: its features in this lane's operand columns 2 t4,
+            // 2 t4 + 1, 2 t4 + 8, 2 t4 + 9.
+            const int j = r0 + (lane >> 2);
+            int o = 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int j = r0 + (lane >> 2) + 8 * h;
-              int o = 0;
-#pragma unroll
-              for (int bit = 16; bit > 0; bit >>= 1) {
-                const int v = __shfl_sync(kFull, ninc, o + bit - 1);
-                if (v <= j) o += bit;
-              }
-              o = min(o, 31);
-              const int k = __shfl_sync(kFull, start, o) + j - __shfl_sync(kFull, nexc, o);
-              float f[12];
-#pragma unroll
-              for (int i = 0; i < 12; ++i) f[i] = __shfl_sync(kFull, fe[i], o);
-              const float d12 = __shfl_sync(kFull, fe[12], o), d13 = __shfl_sync(kFull, fe[13], o);
-              const bool real = j < total_sc;
-              float x12 = 0.f, x13 = 0.f;
-              if (real && t4 == 2) {
-                const float4 hr = __ldg(A.sorted_rec + W.u.pl.pos[k]);
-                float q0, q1;
-                window_chi2(W.win_a[o], W.win_b[o], hr, q0, q1);
-                x12 = (q0 / d12 - __ldg(wmlp + kMlpMean + 12)) / __ldg(wmlp + kMlpSd + 12);
-                x13 = (q1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
-              }
-              xr[h][0] = !real ? 0.f : t4 == 0 ? f[0] : t4 == 1 ? f[2] : t4 == 2 ? f[4] : f[6];
-              xr[h][1] = !real ? 0.f : t4 == 0 ? f[1] : t4 == 1 ? f[3] : t4 == 2 ? f[5] : f[7];
-              xr[h][2] = !real ? 0.f : t4 == 0 ? f[8] : t4 == 1 ? f[10] : t4 == 2 ? x12 : 0.f;
-              xr[h][3] = !real ? 0.f : t4 == 0 ? f[9] : t4 == 1 ? f[11] : t4 == 2 ? x13 : 0.f;
-              kr[h] = real ? k : -1;
+            for (int bit = 16; bit > 0; bit >>= 1) {
+              const int v = __shfl_sync(kFull, ninc, o + bit - 1);
+              if (v <= j) o += bit;
             }
-            const float2 l2 = score16(A.mlp_frag, wmlp, xr[0][0], xr[0][1], xr[0][2], xr[0][3], xr[1][0],
-                                      xr[1][1], xr[1][2], xr[1][3]);
-            if (t4 == 0) {
-              if (kr[0] >= 0) WL.pl_sc[kr[0]] = l2.x;
-              if (kr[1] >= 0) WL.pl_sc[kr[1]] = l2.y;
+            o = min(o, 31);
+            const int k = __shfl_sync(kFull, start, o) + j - __shfl_sync(kFull, nexc, o);
+            float f[12];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) f[i] = __shfl_sync(kFull, fe[i], o);
+            const float d12 = __shfl_sync(kFull, fe[12], o), d13 = __shfl_sync(kFull, fe[13], o);
+            const bool real = j < total_sc;
+            float x12 = 0.f, x13 = 0.f;
+            if (real && t4 == 2) {
+              const float4 hr = __ldg(A.sorted_rec + W.u.pl.pos[k]);
+              float q0, q1;
+              window_chi2(W.win_a[o], W.win_b[o], hr, q0, q1);
+              x12 = (q0 / d12 - __ldg(wmlp + kMlpMean + 12)) / __ldg(wmlp + kMlpSd + 12);
+              x13 = (q1 / d13 - __ldg(wmlp + kMlpMean + 13)) / __ldg(wmlp + kMlpSd + 13);
+            }
+            const float x[4] = {!real ? 0.f : t4 == 0 ? f[0] : t4 == 1 ? f[2] : t4 == 2 ? f[4] : f[6],
+                                !real ? 0.f : t4 == 0 ? f[1] : t4 == 1 ? f[3] : t4 == 2 ? f[5] : f[7],
+                                !real ? 0.f : t4 == 0 ? f[8] : t4 == 1 ? f[10] : t4 == 2 ? x12 : 0.f,
+                                !real ? 0.f : t4 == 0 ? f[9] : t4 == 1 ? f[11] : t4 == 2 ? x13 : 0.f};
+            const int kr = real ? k : -1;
+            const float2 l2 = mlp_logit8(A.mlp_frag, wmlp, x, lane);
+            // lanes 0-3 hold the logits of pairs 2 t4, 2 t4 + 1 of the tile (computed by lanes 8 t4, 8 t4 + 4)
+            const int k0 = __shfl_sync(kFull, kr, 8 * t4), k1 = __shfl_sync(kFull, kr, 8 * t4 + 4);
+            if (lane < 4) {
+              if (k0 >= 0) WL.pl_sc[k0] = l2.x;
+              if (k1 >= 0) WL.pl_sc[k1] = l2.y;
             }
           }
           __syncwarp();

@@ -230,36 +230,38 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward(const float* __restr
   }
 }
 
-// The finder's B fragments of both hidden layers (layout in mlp.cuh): entry i holds, for hidden
-// unit n = 8 * tile + lane / 4, the weights of inputs 16 * step + 2 (lane % 4) + {0, 1, 8, 9} (zero
-// beyond the 14 inputs of the first layer), hi and scaled lo fp16 parts.
+// The finder's A fragments of both hidden layers (layout in mlp.cuh): entry i holds, for row tile
+// m and K step s, lane l's four f16x2 words (rows 16 m + l / 4 and + 8, columns 16 s + 2 (l % 4)
+// and + 8; zero beyond the 14 inputs of the first layer), hi or scaled lo part.
 __global__ void k_mlp_fragments(const float* __restrict__ w, uint4* __restrict__ frag) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kFragWords; i += gridDim.x * blockDim.x) {
-    int step, tile, lane, ld;
+    const int part = i & 1, lane = (i >> 1) % 32;
+    int m, s, ld;
     const float* W;
     if (i < kFragL2) {
-      step = 0;
-      tile = i / 32;
-      lane = i % 32;
+      m = (i >> 1) / 32;
+      s = 0;
       W = w + kMlpW1;
       ld = kMlpIn;
     } else {
-      const int j = i - kFragL2;
-      step = j / 256;
-      tile = (j / 32) % 8;
-      lane = j % 32;
+      const int j = ((i - kFragL2) >> 1) / 32;
+      m = j / 4;
+      s = j % 4;
       W = w + kMlpW2;
       ld = kMlpHid;
     }
-    const int n = 8 * tile + lane / 4, k0 = 16 * step + 2 * (lane % 4);
-    const int ks[4] = {k0, k0 + 1, k0 + 8, k0 + 9};
-    float v[4];
+    const int r = 16 * m + lane / 4, c = 16 * s + 2 * (lane % 4);
+    const int rr[4] = {r, r + 8, r, r + 8}, cc[4] = {c, c, c + 8, c + 8};
+    unsigned word[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ks[q] < ld ? W[n * ld + ks[q]] : 0.f;
-    unsigned h01, l01, h23, l23;
-    split_f16x2(v[0], v[1], h01, l01);
-    split_f16x2(v[2], v[3], h23, l23);
-    frag[i] = make_uint4(h01, h23, l01, l23);
+    for (int q = 0; q < 4; ++q) {
+      const float v0 = cc[q] < ld ? W[rr[q] * ld + cc[q]] : 0.f;
+      const float v1 = cc[q] + 1 < ld ? W[rr[q] * ld + cc[q] + 1] : 0.f;
+      unsigned h, l;
+      split_f16x2(v0, v1, h, l);
+      word[q] = part ? l : h;
+    }
+    frag[i] = make_uint4(word[0], word[1], word[2], word[3]);
   }
 }
 

@@ -19,29 +19,30 @@ constexpr int kMlpMean = kMlpParams;                // normaliser: mean[14], sd[
 constexpr int kMlpSd = kMlpMean + kMlpIn;
 constexpr int kMlpParamsAll = kMlpSd + kMlpIn;      // 5213 floats
 
-// The finder scores its (candidate, hit) pairs on the tensor cores, 16 pairs at a time per warp,
-// with warp-level MMAs of shape m16n8k16 (fp16 operands, FP32 accumulation). A pair is a row of the
-// 16 x 16 input tile (14 features, two zero columns); the first layer is X W1^T (K = 16, eight
-// 8-column tiles of hidden units), the second H1 W2^T (K = 64 in four steps, eight column tiles),
-// and the output layer an FP32 dot product. Every operand is split into two fp16 parts, v = hi +
-// 2^-11 lo with hi = f16(v) and lo = f16(2^11 (v - hi)) (lo is scaled so that it stays a normal
-// fp16 number), which leaves |v - hi - 2^-11 lo| <= 2^-22 |v| for |v| >= 2^-14. Each product A B is
-// accumulated as hi hi in one FP32 accumulator and hi lo + lo hi in a second, combined as
-// D + 2^-11 E; the dropped 2^-22 lo lo and the two splits leave at most ~3 2^-22 of each product, a
-// few FP32 roundings. Operands must stay below the fp16 range (65504): the features are
-// standardised and the chi2 cut bounds the pulls, so they and the hidden units of a trained
-// network are far below it.
+// The finder scores its (candidate, hit) pairs on the tensor cores, 8 pairs at a time per warp,
+// with warp-level MMAs of shape m16n8k16 (fp16 operands, FP32 accumulation) in which the pairs are
+// the 8 columns and the network's weights the 16-row A operand: layer 1 is W1 X^T (four 16-row
+// tiles of hidden units, K = 16 inputs: 14 features and two zeros), layer 2 W2 H1 (four row tiles,
+// K = 64 in four steps), and the output layer an FP32 dot product. Layer 1's accumulator tiles
+// become layer 2's B operand by an 8 x 8 transpose in registers (movmatrix). Every operand is split
+// into two fp16 parts, v = hi + 2^-11 lo with hi = f16(v) and lo = f16(2^11 (v - hi)) (lo is scaled
+// so that it stays a normal fp16 number), which leaves |v - hi - 2^-11 lo| <= 2^-22 |v| for
+// |v| >= 2^-14. Each product A B is accumulated as hi hi in one FP32 accumulator and hi lo + lo hi
+// in a second, combined as D + 2^-11 E; the dropped 2^-22 lo lo and the two splits leave at most
+// ~3 2^-22 of each product, a few FP32 roundings. Operands must stay below the fp16 range (65504):
+// the features are standardised and the chi2 cut bounds the pulls, so they and the hidden units of
+// a trained network are far below it.
 //
-// The weights' parts are laid out once per launch as the B fragments of the MMA, so that each lane
-// loads both parts of one (K step, column tile) as one 16-byte word and a warp one contiguous
-// 512-byte run. Lane l (g = l / 4, t = l % 4) holds, for hidden unit n = 8 * tile + g, the weights
-// of inputs k = 16 * step + {2t, 2t + 1} (words x: hi, z: lo) and {2t + 8, 2t + 9} (words y: hi,
-// w: lo), two fp16 each, the lower input in the low half. Entries (uint4):
-//   layer 1: kFragL1 + tile * 32 + lane
-//   layer 2: kFragL2 + (step * 8 + tile) * 32 + lane
+// The weights' parts are laid out once per launch as the A fragments of the MMA: lane l (g = l / 4,
+// t = l % 4) of (row tile m, K step s) holds rows r = 16 m + g and r + 8, columns c = 16 s + 2t and
+// c + 8, as the words (W[r][c], W[r][c + 1]), (W[r + 8][c], ...), (W[r][c + 8], ...), (W[r + 8][c + 8],
+// ...) of two fp16 each (zero beyond the 14 inputs of the first layer), hi in one 16-byte entry and
+// lo in the next:
+//   layer 1: kFragL1 + (m * 32 + lane) * 2 + part
+//   layer 2: kFragL2 + ((m * 4 + s) * 32 + lane) * 2 + part
 constexpr int kFragL1 = 0;
-constexpr int kFragL2 = kFragL1 + 8 * 32;
-constexpr int kFragWords = kFragL2 + 4 * 8 * 32;  // 1280 entries, 20 KiB
+constexpr int kFragL2 = kFragL1 + 4 * 32 * 2;
+constexpr int kFragWords = kFragL2 + 16 * 32 * 2;  // 1280 entries, 20 KiB
 constexpr float kLoScale = 2048.f, kLoUnscale = 1.f / 2048.f;
 
 // Writes the fragments of params (KF_MLP_BUFFER floats) to frag (kFragWords entries).
@@ -56,77 +57,83 @@ __device__ __forceinline__ void split_f16x2(float x0, float x1, unsigned& hi, un
   lo = *reinterpret_cast<const unsigned*>(&l);
 }
 
-// D += A B for one m16n8k16 tile: A as four f16x2 words (rows g and g + 8, columns 2t, 2t + 1 and
-// 2t + 8, 2t + 9 in the order (g, lo), (g + 8, lo), (g, hi), (g + 8, hi)), B two words (inputs
-// 2t, 2t + 1 and 2t + 8, 2t + 9 of column g), D rows g (d[0], d[1]) and g + 8 (d[2], d[3]),
-// columns 2t, 2t + 1.
-__device__ __forceinline__ void mma_m16n8k16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+// D += A B for one m16n8k16 tile: A as the four f16x2 words of the layout above, B two words (lane
+// l: column g = l / 4, rows 2t, 2t + 1 and 2t + 8, 2t + 9), D rows g (d[0], d[1]) and g + 8 (d[2],
+// d[3]), columns 2t, 2t + 1.
+__device__ __forceinline__ void mma_m16n8k16(float (&d)[4], uint4 a, unsigned b0, unsigned b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
-// One K step of a split product: d += A_hi B_hi, e += A_hi B_lo + A_lo B_hi (b: the fragment).
-__device__ __forceinline__ void mma_split(float (&d)[4], float (&e)[4], const unsigned (&ahi)[4],
-                                          const unsigned (&alo)[4], uint4 b) {
-  mma_m16n8k16(e, alo, b.x, b.y);
-  mma_m16n8k16(e, ahi, b.z, b.w);
-  mma_m16n8k16(d, ahi, b.x, b.y);
+// One K step of a split product: d += A_hi B_hi, e += A_hi B_lo + A_lo B_hi.
+__device__ __forceinline__ void mma_split(float (&d)[4], float (&e)[4], uint4 ahi, uint4 alo, const unsigned (&bhi)[2],
+                                          const unsigned (&blo)[2]) {
+  mma_m16n8k16(e, alo, bhi[0], bhi[1]);
+  mma_m16n8k16(e, ahi, blo[0], blo[1]);
+  mma_m16n8k16(d, ahi, bhi[0], bhi[1]);
 }
 
-// Logits of 16 pairs evaluated together by the warp (every lane takes part). Lane l (g = l / 4,
-// t = l % 4) passes the normalised features of rows g (xa) and g + 8 (xb) in columns 2t, 2t + 1,
-// 2t + 8, 2t + 9 (zero beyond column 13) and receives their logits (la, lb). prm: the network's
-// FP32 parameters (biases, output layer), frag: the fragments of its hidden layers.
-__device__ __forceinline__ void mlp_logit16(const uint4* __restrict__ frag, const float* __restrict__ prm,
-                                            const float (&xa)[4], const float (&xb)[4], int lane, float& la,
-                                            float& lb) {
-  const int t = lane & 3;
-  unsigned a1h[4], a1l[4];
-  split_f16x2(xa[0], xa[1], a1h[0], a1l[0]);
-  split_f16x2(xb[0], xb[1], a1h[1], a1l[1]);
-  split_f16x2(xa[2], xa[3], a1h[2], a1l[2]);
-  split_f16x2(xb[2], xb[3], a1h[3], a1l[3]);
-  // First layer, column tiles 2s and 2s + 1 at a time: their ReLU outputs are the A operand of
-  // the second layer's K step s (the accumulator layout of two column tiles is the operand layout
-  // of one K step), split at once.
-  unsigned a2h[4][4], a2l[4][4];
+// Transpose of an 8 x 8 matrix of 16-bit values held as one word per lane (lane l: row l / 4,
+// columns 2 (l % 4), 2 (l % 4) + 1).
+__device__ __forceinline__ unsigned transpose8x8(unsigned v) {
+  unsigned r;
+  asm("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
+}
+
+// Logits of 8 pairs evaluated together by the warp (every lane takes part). Lane l (g = l / 4,
+// t = l % 4) passes the normalised features of pair g in columns 2t, 2t + 1, 2t + 8, 2t + 9 (zero
+// beyond column 13) and receives the logits of pairs 2t and 2t + 1. prm: the network's FP32
+// parameters (biases, output layer), frag: the fragments of its hidden layers.
+__device__ __forceinline__ float2 mlp_logit8(const uint4* __restrict__ frag, const float* __restrict__ prm,
+                                             const float (&x)[4], int lane) {
+  const int g = lane >> 2;
+  unsigned xh[2], xl[2];
+  split_f16x2(x[0], x[1], xh[0], xl[0]);
+  split_f16x2(x[2], x[3], xh[1], xl[1]);
+  // Layer 1, row tile m: its ReLU outputs (hidden units 16 m + g, + 8 of pairs 2t, 2t + 1),
+  // transposed, are layer 2's B operand of K step m.
+  unsigned hh[4][2], hl[4][2];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int nt = 2 * s + half;
-      const float b0 = __ldg(prm + kMlpB1 + 8 * nt + 2 * t), b1 = __ldg(prm + kMlpB1 + 8 * nt + 2 * t + 1);
-      float d[4] = {b0, b1, b0, b1}, e[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_split(d, e, a1h, a1l, __ldg(frag + kFragL1 + nt * 32 + lane));
-      split_f16x2(fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), fmaxf(fmaf(e[1], kLoUnscale, d[1]), 0.f),
-                  a2h[s][2 * half], a2l[s][2 * half]);
-      split_f16x2(fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), fmaxf(fmaf(e[3], kLoUnscale, d[3]), 0.f),
-                  a2h[s][2 * half + 1], a2l[s][2 * half + 1]);
-    }
+  for (int m = 0; m < 4; ++m) {
+    const float b0 = __ldg(prm + kMlpB1 + 16 * m + g), b1 = __ldg(prm + kMlpB1 + 16 * m + g + 8);
+    float d[4] = {b0, b0, b1, b1}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    const uint4* f = frag + kFragL1 + (m * 32 + lane) * 2;
+    mma_split(d, e, __ldg(f), __ldg(f + 1), xh, xl);
+    unsigned th, tl, uh, ul;
+    split_f16x2(fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), fmaxf(fmaf(e[1], kLoUnscale, d[1]), 0.f), th, tl);
+    split_f16x2(fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), fmaxf(fmaf(e[3], kLoUnscale, d[3]), 0.f), uh, ul);
+    hh[m][0] = transpose8x8(th);
+    hl[m][0] = transpose8x8(tl);
+    hh[m][1] = transpose8x8(uh);
+    hl[m][1] = transpose8x8(ul);
   }
-  // Second layer, one column tile at a time, folded into the output layer's sums of rows g, g + 8
-  // (not unrolled: the loads of one tile at a time stay in flight).
-  float sa = 0.f, sb = 0.f;
+  // Layer 2, row tile m, folded into the output layer's sums of pairs 2t, 2t + 1 (not unrolled:
+  // the loads of one tile at a time stay in flight).
+  float s0 = 0.f, s1 = 0.f;
 #pragma unroll 1
-  for (int nt = 0; nt < 8; ++nt) {
-    const float b0 = __ldg(prm + kMlpB2 + 8 * nt + 2 * t), b1 = __ldg(prm + kMlpB2 + 8 * nt + 2 * t + 1);
-    float d[4] = {b0, b1, b0, b1}, e[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < 4; ++m) {
+    const float b0 = __ldg(prm + kMlpB2 + 16 * m + g), b1 = __ldg(prm + kMlpB2 + 16 * m + g + 8);
+    float d[4] = {b0, b0, b1, b1}, e[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int s = 0; s < 4; ++s) mma_split(d, e, a2h[s], a2l[s], __ldg(frag + kFragL2 + (s * 8 + nt) * 32 + lane));
-    const float w0 = __ldg(prm + kMlpW3 + 8 * nt + 2 * t), w1 = __ldg(prm + kMlpW3 + 8 * nt + 2 * t + 1);
-    sa = fmaf(w1, fmaxf(fmaf(e[1], kLoUnscale, d[1]), 0.f), fmaf(w0, fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), sa));
-    sb = fmaf(w1, fmaxf(fmaf(e[3], kLoUnscale, d[3]), 0.f), fmaf(w0, fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), sb));
+    for (int k = 0; k < 4; ++k) {
+      const uint4* f = frag + kFragL2 + ((m * 4 + k) * 32 + lane) * 2;
+      mma_split(d, e, __ldg(f), __ldg(f + 1), hh[k], hl[k]);
+    }
+    const float w0 = __ldg(prm + kMlpW3 + 16 * m + g), w1 = __ldg(prm + kMlpW3 + 16 * m + g + 8);
+    s0 = fmaf(w1, fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), fmaf(w0, fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), s0));
+    s1 = fmaf(w1, fmaxf(fmaf(e[3], kLoUnscale, d[3]), 0.f), fmaf(w0, fmaxf(fmaf(e[1], kLoUnscale, d[1]), 0.f), s1));
   }
-  // The four lanes of a row hold its 64 terms.
-  sa += __shfl_xor_sync(0xffffffffu, sa, 1);
-  sb += __shfl_xor_sync(0xffffffffu, sb, 1);
-  sa += __shfl_xor_sync(0xffffffffu, sa, 2);
-  sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+  // The eight lanes of a column (t fixed) hold its 64 terms.
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
   const float b3 = __ldg(prm + kMlpB3);
-  la = b3 + sa;
-  lb = b3 + sb;
+  return make_float2(b3 + s0, b3 + s1);
 }
 
 int launch_mlp_forward(const float* params, const float* feats, int n, float* logits, cudaStream_t st);
