@@ -71,15 +71,15 @@ MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/csrc/mlp.cuh",
                 "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "ccbef5ca750ba9eb56828b4ef2f59d0823255756",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125849856 + 35077120) / 302063,
-                                        "find_200ev_barrel_disks_noise100": (144185344 + 30764544) / 211523,
+FIND_PROFILE = {"sources_sha1": "9a6a21a623845f162a59875f10f09a48f48eb6f6",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125417984 + 35355904) / 302063,
+                                        "find_200ev_barrel_disks_noise100": (143559424 + 31018240) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive4":
-                                            (170493440 + 36336640 + 128858112 + 27786240) / 211523,
+                                            (170629120 + 36768512 + 128814336 + 27837952) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2":
-                                            (168260352 + 38676480 + 159729664 + 35268864) / 211523,
+                                            (168325888 + 38745600 + 159756288 + 35380992) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2_learned2_0.7":
-                                            (161507840 + 33984512 + 47439104 + 4393728) / 211523}}
+                                            (154584320 + 32008704 + 41996288 + 3942912) / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
