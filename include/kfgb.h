@@ -145,9 +145,12 @@ typedef struct {
   int block_threads;
   int blocks_per_sm;
   /* Learned hit proposal (not in the paper): NULL for plain finding, else a device buffer of
-   * KF_MLP_BUFFER floats (see kf_mlp_forward). With top_n > 0, when more than top_n hits of a
-   * candidate's window pass the chi2 cut, only the top_n with the highest network score (ties:
-   * lower hit id) make children. */
+   * KF_MLP_BUFFER floats (see kf_mlp_forward), 4-byte aligned, unchanged while the call runs. With
+   * top_n > 0, when more than top_n hits of a candidate's window pass the chi2 cut, only the top_n
+   * with the highest network score (ties: lower hit id) make children. The finder evaluates the
+   * network on the tensor cores with FP32-faithful products (operands split into two fp16 parts;
+   * inputs and hidden units must stay within the fp16 range, as they do for standardised features
+   * and a trained network), 8 pairs at a time per warp. */
   const float* mlp;
   int top_n;
   /* Candidate capacity of the compiled kernel (one of 1, 2, 4, 6, 8, 16, >= k_max and top_n);

@@ -83,7 +83,7 @@ def _compare(out, ref):
 
 
 def test_static_entry_point_learned_proposal_between_plain_calls(kf):
-    """The learned proposal keeps a transposed copy of the network in the array, after the seed
+    """The learned proposal keeps its weight fragments in the array, after the seed
     states: plain, learned, plain again on the same events must each match kf_find_tracks."""
     z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", "mlp_learned.npz"))
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device="cuda")
