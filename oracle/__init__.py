@@ -279,7 +279,8 @@ def find(geom: Geometry, batch, seed_hits, seed_event, *, chi2_cut=None, k_max=N
     learned proposal keeps the top_n passing hits by score (with ``score_margin`` > 0, of a window
     with two or more passing hits, those of its top_n within the margin of its best score; with
     ``window``, instead, the top_n by score of every hit in the bounding box of the chi2 ellipse go
-    on to the chi2 cut when the box holds more than top_n hits); ``steering`` (synth.steering_tables)
+    on to the chi2 cut when the box holds more than top_n hits, with ``score_margin`` > 0 when it
+    holds two or more and only those within the margin of the best); ``steering`` (synth.steering_tables)
     replaces the geometric next-surface rule by the region lists. Returns dict with hits [n,lmax], n_hits, chi2, p, cov,
     status and counters (propagations, passing chi2 evaluations, updates, hits whose chi2 was
     evaluated in a window's bins, hits of the windows limited to the phi sub-bins they touch,

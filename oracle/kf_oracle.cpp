@@ -1042,9 +1042,11 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
       const bool margin_rule = cx.mlp.margin > 0.0;
       if (cx.mlp.top_n > 0 && cx.mlp.window) {
         // Learned proposal ranking the window before the chi2 cut: when the window (the bounding
-        // box of the chi2 ellipse) holds more than top_n hits, only its top_n by MLP score (ties:
-        // lower hit id) go on to the cut; otherwise every passing hit makes a child.
-        if (static_cast<int>(box.size()) > cx.mlp.top_n) {
+        // box of the chi2 ellipse) holds more than top_n hits (with a score margin, two or more),
+        // only its top_n by MLP score (ties: lower hit id) go on to the cut, with a margin only
+        // those of them that score within the margin of the best; otherwise every passing hit
+        // makes a child.
+        if (static_cast<int>(box.size()) > (margin_rule ? 1 : cx.mlp.top_n)) {
           std::vector<std::pair<double, int>> sc;
           double f[kIn];
           for (const Found& fd : box) {
@@ -1056,9 +1058,11 @@ bool find_one(const Ctx& cx, const int* seed_ids, int ev, int lmax, Cand& best, 
             return a.first != b.first ? a.first > b.first : a.second < b.second;
           });
           std::vector<Found> kept;
-          for (int k = 0; k < cx.mlp.top_n; ++k)
+          for (int k = 0; k < cx.mlp.top_n && k < static_cast<int>(sc.size()); ++k) {
+            if (margin_rule && k > 0 && sc[k].first < sc[0].first - cx.mlp.margin) break;
             for (const Found& fd : box)
               if (fd.hit == sc[k].second && fd.chi2 < cx.prm.chi2_cut) kept.push_back(fd);
+          }
           found.swap(kept);
         }
       } else if (cx.mlp.top_n > 0 && static_cast<int>(found.size()) > (margin_rule ? 1 : cx.mlp.top_n)) {
@@ -1297,9 +1301,10 @@ int or_next_surface(const OrGeom* g, const double* p, double* s_out) {
 // Combinatorial finding from seeds (3 hit ids each, [n][3]) with seed_event[n]. With mlp_w set and
 // top_n > 0, the learned proposal keeps only the top_n passing hits by MLP score of each window
 // that has more; with score_margin > 0, of each window with two or more passing hits, the hits
-// among its top_n that score within score_margin of its best; with window != 0 (and no margin),
-// the top_n by score of every hit in the window's box go on to the chi2 cut when the box holds
-// more than top_n hits. Outputs per
+// among its top_n that score within score_margin of its best; with window != 0, the top_n by score
+// of every hit in the window's box go on to the chi2 cut when the box holds more than top_n hits
+// (with score_margin > 0: two or more hits, and only those of the top_n within the margin of the
+// best). Outputs per
 // seed: hits_out[n][lmax] (path order, -1 = miss or none), n_hits, chi2 total, p[6], C[21],
 // status (0 ok, 1 seed failed). steering: region steering lists, or null for the geometric
 // next-surface rule. counters[6] += propagations, chi2 evaluations that passed the

@@ -311,10 +311,31 @@ def test_window_ranking_with_a_top_n_above_every_window_is_plain_finding():
     assert narrow["counters"][5] > 0 and not np.array_equal(plain["hits"], narrow["hits"])
 
 
-def test_window_ranking_matches_a_plain_loop():
+def test_window_ranking_with_a_margin_wider_than_any_gap_is_the_window_rule():
+    """With a score margin the box is ranked from two hits on and only the top_n within the margin of
+    the best face the cut: a margin wider than any score gap keeps all of the top_n, and a box of at
+    most top_n hits is then kept whole, which is the window rule without a margin."""
+    wl = synth.workload("find", n_events=2, tracks_lo=300, tracks_hi=300, noise_frac=3.0, seed=45)
+    g = oracle.Geometry(wl)
+    b = synth.generate(wl)
+    sh, st = b.seeds()
+    ev = b.track_event[st]
+    F, _ = oracle.find_pairs(g, b, sh, ev, st)
+    mlp = _mlp_for(F)
+    rule = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, window=True)
+    wide = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, window=True, score_margin=1e9)
+    assert np.array_equal(rule["hits"], wide["hits"])
+    assert wide["counters"][5] > rule["counters"][5]  # boxes of two hits are scored too
+    narrow = oracle.find(g, b, sh, ev, mlp=mlp, top_n=2, window=True, score_margin=0.5)
+    assert not np.array_equal(rule["hits"], narrow["hits"])
+
+
+@pytest.mark.parametrize("margin", [0.0, 1.0])
+def test_window_ranking_matches_a_plain_loop(margin):
     """K = 1, top_n = 2, window ranking: at every step the box of the chi2 ellipse (both pulls within
-    sqrt(cut)) is taken from every hit of the surface; when it holds more than two hits, only its two
-    best-scoring hits (ties: lower id) face the chi2 cut; the child is the kept passing hit of lowest
+    sqrt(cut)) is taken from every hit of the surface; when it holds more than two hits (with a score
+    margin: two or more), only its two best-scoring hits (ties: lower id), with a margin only those
+    scoring within it of the best, face the chi2 cut; the child is the kept passing hit of lowest
     chi2."""
     import test_oracle_find as tf
     wl = synth.workload("find", n_events=2, tracks_lo=40, tracks_hi=40, noise_frac=80.0, seed=46)
@@ -325,7 +346,7 @@ def test_window_ranking_matches_a_plain_loop():
     F, _ = oracle.find_pairs(g, b, sh, ev, st)
     mlp = _mlp_for(F)
     cut = wl.chi2_cut
-    f = oracle.find(g, b, sh, ev, k_max=1, mlp=mlp, top_n=2, window=True)
+    f = oracle.find(g, b, sh, ev, k_max=1, mlp=mlp, top_n=2, window=True, score_margin=margin)
     ranked = cut_after_ranking = 0
     for i in range(len(st)):
         p, C, _ = tf._seed_fit(g, b, sh[i])
@@ -342,10 +363,12 @@ def test_window_ranking_matches_a_plain_loop():
             feats = np.array([oracle.pair_features(g, surf, pp, CC, b.hits[h]) for h in ids]).reshape(-1, 14)
             inbox = (np.abs(feats[:, 12]) <= np.sqrt(cut)) & (np.abs(feats[:, 13]) <= np.sqrt(cut))
             bids, bc2, bf = ids[inbox], c2[inbox], feats[inbox]
-            if len(bids) > 2:
+            if len(bids) > (1 if margin > 0 else 2):
                 ranked += 1
                 sc = oracle.mlp_forward(mlp[0], (bf - mlp[1]) / mlp[2])
                 top = sorted(range(len(bids)), key=lambda k: (-sc[k], bids[k]))[:2]
+                if margin > 0:
+                    top = [k for k in top if sc[k] >= sc[top[0]] - margin]
                 keep = [k for k in top if bc2[k] < cut]
                 cut_after_ranking += len(keep) < len(top)
                 kids, kc2 = bids[keep], bc2[keep]
