@@ -586,7 +586,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     # ranked before the chi2 cut
     for top_n, margin, window in ((1, 0.0, False), (2, 0.0, False), (4, 0.0, False), (2, 0.5, False),
                                   (2, 0.7, False), (2, 1.0, False), (2, 2.0, False), (2, 0.0, True),
-                                  (4, 0.0, True)):
+                                  (4, 0.0, True), (2, 0.7, True), (2, 1.0, True)):
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n,
                             score_margin=margin, window_ranking=window)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule

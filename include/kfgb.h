@@ -178,12 +178,13 @@ typedef struct {
    * exceeds the first pass's slots; KF_ERR_ARG outside [0, KF_MAX_K]. Pays where most seeds carry
    * few candidates (barrel + disk events with noise; the learned proposal's pruning). */
   int adaptive_capacity;
-  /* Learned proposal ranking the window before the chi2 test (0 = off; 1 = on, not with a score
-   * margin): the window is the bounding box of the chi2 ellipse, |r_i| <= sqrt(chi2_cut S_ii) for
-   * both residuals; when it holds more than top_n hits, only its top_n by score (ties: lower hit
-   * id) face the chi2 cut, else every passing hit makes a child. Reading of "ranks and prunes each
-   * candidate's hit window before the exact chi2 and update" that scores failing hits too; with
-   * window_ranking = 0 the top_n rule applies to the passing hits. */
+  /* Learned proposal ranking the window before the chi2 test (0 = off; 1 = on): the window is the
+   * bounding box of the chi2 ellipse, |r_i| <= sqrt(chi2_cut S_ii) for both residuals; when it
+   * holds more than top_n hits, only its top_n by score (ties: lower hit id) face the chi2 cut, else
+   * every passing hit makes a child. With a score margin the box is ranked when it holds two or
+   * more hits, and only those of its top_n within the margin of its best score face the cut.
+   * Reading of "ranks and prunes each candidate's hit window before the exact chi2 and update" that
+   * scores failing hits too; with window_ranking = 0 the rules apply to the passing hits. */
   int window_ranking;
 } KfFindParams;
 

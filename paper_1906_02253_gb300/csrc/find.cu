@@ -1114,7 +1114,7 @@ int plan_find(int n_seeds, const KfFindParams* p, int sms, int features, FindPla
   const bool learned = p->mlp != nullptr && p->top_n > 0;
   if (p->top_n < 0 || p->top_n > KF_MAX_K) return KF_ERR_ARG;
   if (!(p->score_margin >= 0.f) || !(p->score_margin < 3.4e38f)) return KF_ERR_ARG;
-  if (p->window_ranking != 0 && (p->window_ranking != 1 || p->score_margin > 0.f)) return KF_ERR_ARG;
+  if (p->window_ranking != 0 && p->window_ranking != 1) return KF_ERR_ARG;
   if (p->block_threads != 0 && (p->block_threads < 32 || p->block_threads > 256 || p->block_threads % 32))
     return KF_ERR_ARG;
   if (p->blocks_per_sm < 0) return KF_ERR_ARG;

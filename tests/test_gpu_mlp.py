@@ -318,8 +318,28 @@ def test_window_ranking_matches_oracle(kf, name, net, top_n, adaptive):
     assert (top["hits"] != ora["hits"]).any(axis=1).sum() > 0  # the two readings differ (rarely on barrel + disks)
 
 
-def test_window_ranking_refuses_a_score_margin(kf, pairs):
-    _, _, mean, sd = pairs
-    buf = kf.mlp_buffer(synth.mlp_init(9), mean, sd)
-    p = kf.find_params(30.0, 6, 1, 17, mlp=buf, top_n=2, score_margin=1.0, window_ranking=True)
-    assert kf.load_library().kf_find_workspace_size(100, __import__("ctypes").byref(p)) == 0
+@pytest.mark.parametrize("name,net,margin,adaptive", [("hi_occ", "mlp_hi_occ.npz", 0.7, 0),
+                                                      ("hi_occ", "mlp_hi_occ.npz", 0.7, 2),
+                                                      ("learned", "mlp_learned.npz", 1.0, 0)])
+def test_window_ranking_with_score_margin_matches_oracle(kf, name, net, margin, adaptive):
+    """Ranking the window's box with a score margin (boxes of two or more hits scored, the top 2
+    within the margin of the best face the chi2 cut), trained networks, against the FP64 oracle's
+    same rule: hit lists identical on >= 99.9% of the seeds, efficiency within 0.1%; with adaptive
+    capacity too."""
+    import os
+    wl = synth.workload(name, n_events=3)
+    b = synth.generate(wl)
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+    gpu = _find(kf, wl, b, kf.mlp_buffer(z["weights"], z["mean"], z["sd"]), 2, wl.k_max, window=True,
+                margin=margin, adaptive=adaptive)
+    sh, st = b.seeds()
+    mlp = (z["weights"].astype(np.float64), z["mean"].astype(np.float64), z["sd"].astype(np.float64))
+    ora = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], mlp=mlp, top_n=2, window=True,
+                      score_margin=margin)
+    same = (gpu["hits"].T == ora["hits"]).all(axis=1)
+    assert same.mean() >= 0.999, same.mean()
+    e_g = oracle.efficiency(b, st, gpu["hits"].T, gpu["nhits"])[0]
+    e_o = oracle.efficiency(b, st, ora["hits"], ora["n_hits"])[0]
+    assert abs(e_g - e_o) <= 0.001
+    no_margin = oracle.find(oracle.Geometry(wl), b, sh, b.track_event[st], mlp=mlp, top_n=2, window=True)
+    assert (no_margin["hits"] != ora["hits"]).any(axis=1).sum() > 20  # the margin pruned more
