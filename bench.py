@@ -71,15 +71,15 @@ MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/csrc/mlp.cuh",
                 "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "9a6a21a623845f162a59875f10f09a48f48eb6f6",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125417984 + 35355904) / 302063,
-                                        "find_200ev_barrel_disks_noise100": (143559424 + 31018240) / 211523,
+FIND_PROFILE = {"sources_sha1": "435130e9ebfaf7d35ba59099a6f77555c7b7cfee",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125726976 + 35250176) / 302063,
+                                        "find_200ev_barrel_disks_noise100": (143526912 + 31075840) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive4":
-                                            (170629120 + 36768512 + 128814336 + 27837952) / 211523,
+                                            (170500864 + 36268800 + 128876544 + 27771392) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2":
-                                            (168325888 + 38745600 + 159756288 + 35380992) / 211523,
+                                            (168276736 + 39159040 + 159684096 + 35355904) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2_learned2_0.7":
-                                            (154584320 + 32008704 + 41996288 + 3942912) / 211523}}
+                                            (155214080 + 32209152 + 42020864 + 3977728) / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
@@ -586,7 +586,7 @@ def compare_learned(args, kf, g, idx, d, prm, fout, wsb, stream, batch, host, ef
     # ranked before the chi2 cut
     for top_n, margin, window in ((1, 0.0, False), (2, 0.0, False), (4, 0.0, False), (2, 0.5, False),
                                   (2, 0.7, False), (2, 1.0, False), (2, 2.0, False), (2, 0.0, True),
-                                  (4, 0.0, True), (2, 0.7, True), (2, 1.0, True)):
+                                  (4, 0.0, True), (2, 0.5, True), (2, 0.7, True)):
         lp = kf.find_params(prm.chi2_cut, prm.k_max, prm.max_miss, prm.lmax, 0, 0, mlp=buf, top_n=top_n,
                             score_margin=margin, window_ranking=window)
         lp.steering, lp._steer_ref = prm.steering, getattr(prm, "_steer_ref", None)  # same next-surface rule
