@@ -246,7 +246,10 @@ size_t kf_find_workspace_size(int n_seeds, const KfFindParams* params);
  *                      seed with a negative hit id, a hit on no surface of the geometry or an event
  *                      outside [0, index->n_events) fails (status 1); hit ids must be below the
  *                      number of hits.
- *   workspace          device memory of kf_find_workspace_size bytes, 256-byte aligned.
+ *   workspace          device memory of kf_find_workspace_size bytes, 256-byte aligned, owned
+ *                      by this call until its kernels finish: calls that can run at the same time
+ *                      (other streams, other host threads) need workspaces of their own (sharing
+ *                      one gives wrong results; the kernels keep their accesses in bounds).
  * Outputs (device): hits_out int [lmax][n_seeds] (best candidate's hit ids in path order, -1 for
  * a miss or no further step), nhits_out int, chi2_out float, state_out float [6][n_seeds],
  * cov_out float [21][n_seeds], status_out int (0 ok, 1 seed failed, 2 seed removed by seed_keep). */

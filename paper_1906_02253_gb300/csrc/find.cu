@@ -566,15 +566,15 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     if (want && slot == 0) {
       s = atomicAdd(A.counter, 1);
       if (A.seed_list)  // second pass of adaptive capacity: the first pass's overflowing seeds
-        s = s < *A.seed_list_count ? A.seed_list[s] : n;
+        s = s < min(*A.seed_list_count, n) ? A.seed_list[s] : n;
       else if (A.seed_keep)
         while (s < n && A.seed_keep[s] == 0) s = atomicAdd(A.counter, 1);
     }
     s = __shfl_sync(kFull, s, gbase);
     bool fresh = false;
     if (want) {
-      if (s >= n) {
-        exhausted = true;
+      if (s >= n || s < 0) {  // (a list entry outside the seeds, e.g. from a workspace shared by
+        exhausted = true;     // overlapping calls, ends the group instead of reading out of bounds)
       } else {
         seed = s;
         step = 0;
@@ -1029,9 +1029,10 @@ __global__ void __launch_bounds__(LEARNED ? kFindMaxBlockLearned : 256, 2) k_fin
     const unsigned live = __ballot_sync(kFull, on && won && !nc.stopped);
     const bool done = on && (((live & gmask) == 0u) || step >= max_steps);
     if (done && slot == 0) {
-      if (ovf)
-        A.ovf_list[atomicAdd(A.ovf_count, 1)] = seed;
-      else
+      if (ovf) {
+        const int at = atomicAdd(A.ovf_count, 1);
+        if (at < n) A.ovf_list[at] = seed;  // the list holds n entries (each seed appends once)
+      } else
         write_track(W, trace, gbase, step, seed, n, A.lmax, A.seed_hits, A.hits_out, A.nhits_out, A.chi2_out,
                     A.state_out, A.cov_out, A.status_out);
     }
