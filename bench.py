@@ -831,6 +831,18 @@ def run_gpu(args, wl, batch):
         out["hi_occ"] = hi
         del hctx
         torch.cuda.empty_cache()
+        # the same step with the learned finder (top 2, score margin 0.7), autotuned on its own
+        import copy
+        la = copy.copy(args)
+        la.learned, la.no_learned, la.cpu_seeds = "2:0.7", True, min(args.cpu_seeds, 50000)
+        hl = measure_workload(la, wh, bh, full=False, mlp_name="hi_occ", e2e=True)
+        hl.pop("_ctx")
+        out["hi_occ"]["learned_step"] = {k: hl[k] for k in ("value", "unit", "ms_per_step", "e2e", "efficiency", "fake_rate",
+                                                         "kernel_ms", "autotune", "gpu_launches", "roofline")
+                                         if k in hl}
+        out["hi_occ"]["learned_step"]["finder"] = hl["config"]["finder"]
+        out["hi_occ"]["learned_step"]["vs_plain_step"] = hl["value"] / hi["value"]
+        torch.cuda.empty_cache()
         # fitting over known hit sequences: the 1-event, 10-layer workload and the 100-event batch
         out["fit_known_hits"] = {
             "fit_small": fit_line(args, kf, synth.workload("fit_small"), synth.generate("fit_small"), ctx["stream"],
