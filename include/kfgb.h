@@ -148,9 +148,10 @@ typedef struct {
    * KF_MLP_BUFFER floats (see kf_mlp_forward), 4-byte aligned, unchanged while the call runs. With
    * top_n > 0, when more than top_n hits of a candidate's window pass the chi2 cut, only the top_n
    * with the highest network score (ties: lower hit id) make children. The finder evaluates the
-   * network on the tensor cores with FP32-faithful products (operands split into two fp16 parts;
-   * inputs and hidden units must stay within the fp16 range, as they do for standardised features
-   * and a trained network), 8 pairs at a time per warp. */
+   * network on the tensor cores, 8 pairs at a time per warp, with every operand split into two
+   * fp16 parts, which keeps all but 3 2^-22 of each product (inputs and hidden units must stay
+   * within the fp16 range, as they do for standardised features and a trained network); see
+   * kf_mlp_finder_scores. */
   const float* mlp;
   int top_n;
   /* Candidate capacity of the compiled kernel (one of 1, 2, 4, 6, 8, 16, >= k_max and top_n);
@@ -319,10 +320,23 @@ int kf_remove_duplicates(const int* track_hits, const int* nhits, const float* c
 
 /* Logits of n feature rows (features float [n][14], raw, standardised inside; 8-byte aligned, else
  * KF_ERR_ARG). The two layers run on the tensor cores (tcgen05) with FP32-faithful products: each
- * operand is split into two bf16 parts, hi = bf16(v) and lo = bf16(v - hi), and hi*hi + hi*lo +
- * lo*hi is accumulated in FP32 (relative operand error <= 2^-18). A tile whose tensor-core wait
- * gives up (one second) gets NaN logits. */
+ * operand is split into three bf16 parts, hi = bf16(v), mid = bf16(v - hi), lo = bf16(v - hi - mid),
+ * and the six products hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid are accumulated in FP32. A tile
+ * whose tensor-core wait gives up (one second) gets NaN logits. */
 int kf_mlp_forward(const float* params, const float* features, int n, float* logits, kf_stream_t stream);
+
+/* Logits of n feature rows evaluated exactly as the finder scores its (candidate, hit) pairs
+ * (measurement only, not part of the path): the features standardised in FP32, the hidden layers
+ * as warp-level tensor-core MMAs over 8 rows at a time with every operand split into two fp16
+ * parts (hi = f16(v), lo = f16(2^11 (v - hi))) and FP32 accumulation, the output layer in FP32:
+ * each product keeps all but 3 2^-22 of itself, and a logit lies within 2^-18 of the network
+ * evaluated on the absolute values of its weights and inputs (in practice about 1e-6 of logits of
+ * order 1). features float [n][14] (raw), logits float [n]; workspace: device memory of
+ * KF_MLP_FRAG_BYTES bytes, 16-byte aligned, which receives the weights' tensor-core operands.
+ * KF_ERR_ARG for n < 0, a null pointer or a misaligned workspace. */
+#define KF_MLP_FRAG_BYTES 20480
+int kf_mlp_finder_scores(const float* params, const float* features, int n, float* logits, void* workspace,
+                         kf_stream_t stream);
 
 /* Mean binary cross-entropy with logits over n samples (labels 0 or 1) and its gradient with
  * respect to the KF_MLP_PARAMS weights: grad float [KF_MLP_PARAMS] and loss float [1] are

@@ -68,8 +68,9 @@ EXPORTS = ("kf_build_hit_index", "kf_index_bins", "kf_fit_tracks", "kf_find_work
            "kf_find_tracks_static", "kf_mlp_forward", "kf_mlp_loss_grad", "kf_mlp_adam", "kf_autotune_find",
            "kf_autotune_fit", "kf_status_string", "kf_dedup_workspace_size", "kf_clean_seeds",
            "kf_remove_duplicates", "kf_fp32_fma_probe", "kf_math_probe", "kf_seed_states",
-           "kf_wait_probe")
+           "kf_wait_probe", "kf_mlp_finder_scores")
 MLP_PARAMS, MLP_BUFFER = 5185, 5213
+KF_MLP_FRAG_BYTES = 20480  # the finder's tensor-core operands of the network (kfgb.h)
 PHI_SUB = 8  # KF_PHI_SUB: phi sub-bins per phi bin of the hit index
 
 
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH):
                                            P, P, P, P, P, P, P, S, P]
             lib.kf_mlp_forward.restype = I
             lib.kf_mlp_forward.argtypes = [P, P, I, P, P]
+            lib.kf_mlp_finder_scores.restype = I
+            lib.kf_mlp_finder_scores.argtypes = [P, P, I, P, P, P]
             lib.kf_mlp_loss_grad.restype = I
             lib.kf_mlp_loss_grad.argtypes = [P, P, P, I, P, P, P]
             lib.kf_mlp_adam.restype = I
@@ -457,6 +460,19 @@ def mlp_forward(params, features, out=None, stream=None):
     n = features.shape[0]
     out = torch.empty(n, dtype=torch.float32, device=features.device) if out is None else out
     _check(load_library().kf_mlp_forward(_ptr(params), _ptr(features), n, _ptr(out), _stream(stream)), "kf_mlp_forward")
+    return out
+
+
+def mlp_finder_scores(params, features, out=None, stream=None):
+    """Logits of raw feature rows [n, 14] evaluated as the finder scores its pairs
+    (kf_mlp_finder_scores: warp-level tensor-core MMAs with the fp16 two-part split)."""
+    _cuda(params, torch.float32, "params")
+    features = _cuda(features, torch.float32, "features").contiguous()
+    n = features.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=features.device) if out is None else out
+    ws = torch.empty(KF_MLP_FRAG_BYTES, dtype=torch.uint8, device=features.device)
+    _check(load_library().kf_mlp_finder_scores(_ptr(params), _ptr(features), n, _ptr(out), _ptr(ws), _stream(stream)),
+           "kf_mlp_finder_scores")
     return out
 
 

@@ -27,6 +27,9 @@ int launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t st, long lo
 int launch_math_probe(int fn, const float* a, const float* b, int n, float* o0, float* o1, float* o2,
                       cudaStream_t st);
 int launch_wait_probe(int limit_us, long long* out, cudaStream_t st);
+int launch_mlp_finder_scores(const float* params, const float* feats, int n, float* logits, uint4* frag,
+                             cudaStream_t st);
+static_assert(KF_MLP_FRAG_BYTES == kFragWords * sizeof(uint4), "header and library disagree on the fragment size");
 int launch_remove_duplicates(const int* track_hits, const int* nhits, const float* chi2, const float* state,
                              const int* event, int n, int lmax, int n_hits, float dphi, float dtheta, int* keep,
                              void* ws, cudaStream_t st);
@@ -393,6 +396,16 @@ int kf_mlp_forward(const float* params, const float* features, int n, float* log
   if (n < 0 || (n > 0 && (!params || !features || !logits))) return KF_ERR_ARG;
   if (reinterpret_cast<size_t>(features) & 7) return KF_ERR_ARG;  // rows are read as float pairs
   return launch_mlp_forward(params, features, n, logits, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int kf_mlp_finder_scores(const float* params, const float* features, int n, float* logits, void* workspace,
+                         kf_stream_t stream) {
+  if (n < 0 || !params || !workspace || (n > 0 && (!features || !logits))) return KF_ERR_ARG;
+  if (reinterpret_cast<size_t>(workspace) & 15) return KF_ERR_ARG;  // fragments are 16-byte words
+  return launch_mlp_finder_scores(params, features, n, logits, static_cast<uint4*>(workspace),
+                                  reinterpret_cast<cudaStream_t>(stream)) == 0
+             ? KF_OK
+             : KF_ERR_CUDA;
 }
 
 int kf_mlp_loss_grad(const float* params, const float* features, const float* labels, int n, float* grad,

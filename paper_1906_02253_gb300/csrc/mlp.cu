@@ -270,6 +270,39 @@ int launch_mlp_fragments(const float* params, uint4* frag, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
+// The finder's scoring outside the finder: warp w of the grid takes rows 8w .. 8w + 7, lane l the
+// features of row 8w + l / 4 in its operand columns, standardised as the finder standardises its
+// candidate features and pulls; lanes 0-3 write the logits of rows 8w + 2l, 8w + 2l + 1.
+__global__ void k_mlp_finder_scores(const uint4* __restrict__ frag, const float* __restrict__ prm,
+                                    const float* __restrict__ feats, int n, float* __restrict__ logits) {
+  const int lane = threadIdx.x & 31;
+  const long long r0 = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) / 32 * 8;
+  if (r0 >= n) return;  // whole warps leave together (r0 is the same for the warp's lanes)
+  const long long row = r0 + (lane >> 2);
+  const int t = lane & 3;
+  const int cols[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+  float x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = cols[q];
+    x[q] = (row < n && c < kMlpIn) ? (feats[row * kMlpIn + c] - prm[kMlpMean + c]) / prm[kMlpSd + c] : 0.f;
+  }
+  const float2 l2 = mlp_logit8(frag, prm, x, lane);
+  if (lane < 4) {
+    if (r0 + 2 * lane < n) logits[r0 + 2 * lane] = l2.x;
+    if (r0 + 2 * lane + 1 < n) logits[r0 + 2 * lane + 1] = l2.y;
+  }
+}
+
+int launch_mlp_finder_scores(const float* params, const float* feats, int n, float* logits, uint4* frag,
+                             cudaStream_t st) {
+  if (launch_mlp_fragments(params, frag, st) != 0) return -3;
+  if (n == 0) return 0;
+  const long long warps = (static_cast<long long>(n) + 7) / 8;
+  k_mlp_finder_scores<<<static_cast<unsigned>((warps + 7) / 8), 256, 0, st>>>(frag, params, feats, n, logits);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 // Loss and gradient on the tensor cores: a persistent CTA of 256 threads per SM takes tiles of 128
 // samples, two threads per sample (each half of the columns), and runs per tile
 //   D1 = X W1^T -> h1 = relu(D1 + b1);  D2 = H1 W2^T -> z3 = b3 + W3 . relu(D2 + b2),

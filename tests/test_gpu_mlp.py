@@ -71,6 +71,37 @@ def test_mlp_gradient_and_adam_match_oracle(kf, pairs):
     assert np.abs(got - w64).max() <= 1e-6
 
 
+@pytest.mark.parametrize("net,n", [("mlp_hi_occ.npz", 50003), ("mlp_learned.npz", 50003), ("mlp_learned.npz", 7),
+                                   ("mlp_learned.npz", 0)])
+def test_finder_scores_match_oracle(kf, pairs, net, n):
+    """The finder's scoring of (candidate, hit) pairs (warp-level tensor-core MMAs over 8 rows, fp16
+    two-part split, FP32 accumulation; ragged last tile, empty call) with the trained networks
+    against the FP64 network, row by row within the split's error bound: each product keeps all
+    but 3 2^-22 of itself, the FP32 sums add a few 2^-24 of their terms, and the first layer's error
+    passes through the second, so a logit is within 2^-18 of the same network evaluated on the
+    absolute values of its weights and inputs."""
+    import os
+    z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
+    w, mean, sd = z["weights"], z["mean"], z["sd"]
+    F = pairs[0]
+    x = np.ascontiguousarray(F[np.random.default_rng(n).integers(0, len(F), n)])
+    got = kf.mlp_finder_scores(kf.mlp_buffer(w, mean, sd), torch.from_numpy(x).cuda()).cpu().numpy()
+    assert got.shape == (n,)
+    if n == 0:
+        return
+    xs = _std(x, mean, sd)
+    ref = oracle.mlp_forward(w.astype(np.float64), xs)
+    err = np.abs(got.astype(np.float64) - ref)
+    a = np.abs(w.astype(np.float64))
+    a1 = np.abs(xs) @ a[:896].reshape(64, 14).T + a[896:960]
+    a2 = a1 @ a[960:5056].reshape(64, 64).T + a[5056:5120]
+    bound = 2.0 ** -18 * (a2 @ a[5120:5184] + a[5184])
+    print(f"{net}: largest error {err.max():.2e}, median {np.median(err):.2e}, largest error / bound "
+          f"{float((err / bound).max()):.3f}")
+    assert np.all(np.isfinite(got)) and (err <= bound).all(), (err.max(), float((err / bound).max()))
+    assert np.median(err) <= 5e-6  # typical logits are as close as an FP32 evaluation's
+
+
 _BLOCKS = {"W1": (0, 896), "b1": (896, 960), "W2": (960, 5056), "b2": (5056, 5120), "W3": (5120, 5184),
            "b3": (5184, 5185)}
 
