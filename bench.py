@@ -235,7 +235,9 @@ def run_reference(args, wl, batch):
             "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator)",
             "config": {"workload": wl.name, "sample": f"first {n} seeds of the batch (index, "
-                       + ("seed cleaning, find, duplicate removal, fit)" if clean else "find, fit)")},
+                       + ("seed cleaning, find, duplicate removal, fit)" if clean else "find, fit)"),
+                       "finder": (f"learned proposal, top_n {lrn[3]}, score margin {lrn[4]:g}" if lrn
+                                  else "plain (full window)")},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} seeds per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

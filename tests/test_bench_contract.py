@@ -23,3 +23,14 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_reference_arm_with_the_learned_finder():
+    """--learned: the reference arm runs the oracle's learned finding with the workload's trained
+    network and says so in its config."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "hi_occ",
+                        "--events", "2", "--steps", "1", "--warmup", "3", "--ref-seeds", "300", "--learned", "2:0.7"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.strip().splitlines() if ln.startswith("{")][0])
+    assert d["value"] > 0 and d["config"]["finder"].startswith("learned proposal, top_n 2, score margin 0.7")
