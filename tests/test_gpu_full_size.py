@@ -118,15 +118,17 @@ def test_full_size_seed_cleaning_and_duplicate_removal_chain():
     assert abs(e_g - e_o) <= 0.001 and abs(d_g - d_o) <= 0.001
 
 
-@pytest.mark.parametrize("wl_name,net,top_n,margin", [("learned", "mlp_learned.npz", 1, 0.0),
-                                                      ("learned", "mlp_learned.npz", 4, 0.0),
-                                                      ("hi_occ", "mlp_hi_occ.npz", 2, 0.0),
-                                                      ("hi_occ", "mlp_hi_occ.npz", 4, 0.0),
-                                                      ("hi_occ", "mlp_hi_occ.npz", 2, 0.7)])
-def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n, margin):
+@pytest.mark.parametrize("wl_name,net,top_n,margin,window", [("learned", "mlp_learned.npz", 1, 0.0, False),
+                                                             ("learned", "mlp_learned.npz", 4, 0.0, False),
+                                                             ("hi_occ", "mlp_hi_occ.npz", 2, 0.0, False),
+                                                             ("hi_occ", "mlp_hi_occ.npz", 4, 0.0, False),
+                                                             ("hi_occ", "mlp_hi_occ.npz", 2, 0.7, False),
+                                                             ("hi_occ", "mlp_hi_occ.npz", 2, 0.5, True)])
+def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n, margin, window):
     """The learned proposal at full size, in the autotuned launch configuration the benchmark's
     learned-versus-plain comparison uses: hit lists identical to the FP64 oracle's (same network,
-    same top_n and score margin) on >= 99.9% of a 20,000-seed sample, efficiency within 0.1%."""
+    same top_n, score margin and window rule) on >= 99.9% of a 20,000-seed sample, efficiency within
+    0.1%."""
     import os
     import __graft_entry__ as ge
     ge.build_library()
@@ -138,7 +140,8 @@ def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n, margin)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
     z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", net))
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"])
-    lp = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, score_margin=margin)
+    lp = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=buf, top_n=top_n, score_margin=margin,
+                        window_ranking=window)
     n_cal = int(np.searchsorted(dev["seed_event"].cpu().numpy(), calibration_events(b.n_events)))
     lp, _ = kf.autotune_find(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"][:, :n_cal].contiguous(),
                              dev["seed_event"][:n_cal].contiguous(), lp)
@@ -148,7 +151,8 @@ def test_full_size_learned_finding_on_sampled_seeds(wl_name, net, top_n, margin)
     s = np.sort(np.random.default_rng(2253).choice(n, N_SAMPLE, replace=False))
     sh, st = b.seeds()
     w = (z["weights"].astype(np.float64), z["mean"].astype(np.float64), z["sd"].astype(np.float64))
-    r = oracle.find(oracle.Geometry(wl), b, sh[s], b.track_event[st][s], mlp=w, top_n=top_n, score_margin=margin)
+    r = oracle.find(oracle.Geometry(wl), b, sh[s], b.track_event[st][s], mlp=w, top_n=top_n, score_margin=margin,
+                    window=window)
     gh = out["hits"].cpu().numpy().T[s]
     same = (gh == r["hits"]).all(axis=1)
     assert same.mean() >= 0.999, same.mean()
