@@ -84,7 +84,8 @@ def _compare(out, ref):
 
 def test_static_entry_point_learned_proposal_between_plain_calls(kf):
     """The learned proposal keeps its weight fragments in the array, after the seed
-    states: plain, learned, plain again on the same events must each match kf_find_tracks."""
+    states: plain, learned (top_n rule, score margin, window ranking with a margin), plain again on
+    the same events must each match kf_find_tracks."""
     z = np.load(os.path.join(os.path.dirname(kf.__file__), "data", "mlp_learned.npz"))
     buf = kf.mlp_buffer(z["weights"], z["mean"], z["sd"], device="cuda")
     wl = synth.workload("learned", n_events=2, tracks_lo=1500, tracks_hi=3000, seed=35)
@@ -92,8 +93,10 @@ def test_static_entry_point_learned_proposal_between_plain_calls(kf):
     g = kf.Geometry(wl)
     dev = kf.to_device_event_batch(b)
     idx = kf.build_hit_index(g, dev["hits"], dev["slab_offsets"], b.n_events, dev["max_slab_hits"])
-    for mlp, top_n in ((None, 0), (buf, 2), (None, 0), (buf, 1)):
-        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=mlp, top_n=top_n)
+    for mlp, top_n, margin, window in ((None, 0, 0.0, False), (buf, 2, 0.0, False), (None, 0, 0.0, False),
+                                       (buf, 1, 0.0, False), (buf, 2, 0.7, False), (buf, 2, 0.7, True)):
+        prm = kf.find_params(wl.chi2_cut, wl.k_max, wl.max_miss, wl.lmax, mlp=mlp, top_n=top_n, score_margin=margin,
+                             window_ranking=window)
         ref = kf.find_tracks(g, idx, dev["hits"], dev["hit_surface"], dev["seed_hits"], dev["seed_event"], prm)
         out = _outputs(dev["seed_hits"].shape[1], wl.lmax)
         assert _static_call(kf, g, idx, dev, prm, out) == kf.KF_OK
