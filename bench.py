@@ -68,7 +68,8 @@ MMA_MLP_GRAD = MMA_MLP_FWD + MLP_SPLIT_MMAS * 2 * (64 * 64 + 128 * 96)
 # keyed by workload (and adaptive capacity, and the learned proposal's top_n and score margin), valid
 # while the finder's sources and build flags are the ones profiled (SHA-1 over FIND_SOURCES);
 # otherwise reported as null.
-FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
+FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/csrc/find_kernel.cuh",
+                "paper_1906_02253_gb300/csrc/find_learned.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/csrc/mlp.cuh",
                 "paper_1906_02253_gb300/build.py")
 FIND_PROFILE = {"sources_sha1": "7bc05405daa70957d38f5c39afb51827f5c768d4",

@@ -21,8 +21,10 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--compiler-options", "-fPIC", "-Xptx
 # the hardware log and exp, denormals flushed; its parity bars are 1e-4 on the state, 1e-3 on
 # chi2, and its values stay far above 1e-38); the hit binning, which must be bit-exact, uses
 # explicitly rounded intrinsics and lives in hitindex.cu, which keeps the IEEE defaults.
-# The math probe is compiled like the finder and the fit, whose trigonometry it measures.
-PER_FILE = {"fit.cu": ["-use_fast_math"], "find.cu": ["-use_fast_math"], "math_probe.cu": ["-use_fast_math"]}
+# The math probe is compiled like the finder (both of its units) and the fit, whose trigonometry it
+# measures.
+PER_FILE = {"fit.cu": ["-use_fast_math"], "find.cu": ["-use_fast_math"], "find_learned.cu": ["-use_fast_math"],
+            "math_probe.cu": ["-use_fast_math"]}
 
 
 def _nvcc() -> str:

@@ -86,7 +86,9 @@ __device__ __forceinline__ unsigned transpose8x8(unsigned v) {
 // Logits of 8 pairs evaluated together by the warp (every lane takes part). Lane l (g = l / 4,
 // t = l % 4) passes the normalised features of pair g in columns 2t, 2t + 1, 2t + 8, 2t + 9 (zero
 // beyond column 13) and receives the logits of pairs 2t and 2t + 1. prm: the network's FP32
-// parameters (biases, output layer), frag: the fragments of its hidden layers.
+// parameters (biases, output layer), frag: the fragments of its hidden layers, in global memory
+// (read through the read-only path) or, with SMEM, in shared memory.
+template <bool SMEM = false>
 __device__ __forceinline__ float2 mlp_logit8(const uint4* __restrict__ frag, const float* __restrict__ prm,
                                              const float (&x)[4], int lane) {
   const int g = lane >> 2;
@@ -101,7 +103,7 @@ __device__ __forceinline__ float2 mlp_logit8(const uint4* __restrict__ frag, con
     const float b0 = __ldg(prm + kMlpB1 + 16 * m + g), b1 = __ldg(prm + kMlpB1 + 16 * m + g + 8);
     float d[4] = {b0, b0, b1, b1}, e[4] = {0.f, 0.f, 0.f, 0.f};
     const uint4* f = frag + kFragL1 + (m * 32 + lane) * 2;
-    mma_split(d, e, __ldg(f), __ldg(f + 1), xh, xl);
+    mma_split(d, e, SMEM ? f[0] : __ldg(f), SMEM ? f[1] : __ldg(f + 1), xh, xl);
     unsigned th, tl, uh, ul;
     split_f16x2(fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), fmaxf(fmaf(e[1], kLoUnscale, d[1]), 0.f), th, tl);
     split_f16x2(fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), fmaxf(fmaf(e[3], kLoUnscale, d[3]), 0.f), uh, ul);
@@ -120,7 +122,7 @@ __device__ __forceinline__ float2 mlp_logit8(const uint4* __restrict__ frag, con
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint4* f = frag + kFragL2 + ((m * 4 + k) * 32 + lane) * 2;
-      mma_split(d, e, __ldg(f), __ldg(f + 1), hh[k], hl[k]);
+      mma_split(d, e, SMEM ? f[0] : __ldg(f), SMEM ? f[1] : __ldg(f + 1), hh[k], hl[k]);
     }
     const float w0 = __ldg(prm + kMlpW3 + 16 * m + g), w1 = __ldg(prm + kMlpW3 + 16 * m + g + 8);
     s0 = fmaf(w1, fmaxf(fmaf(e[2], kLoUnscale, d[2]), 0.f), fmaf(w0, fmaxf(fmaf(e[0], kLoUnscale, d[0]), 0.f), s0));
