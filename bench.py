@@ -72,15 +72,15 @@ FIND_SOURCES = ("paper_1906_02253_gb300/csrc/find.cu", "paper_1906_02253_gb300/c
                 "paper_1906_02253_gb300/csrc/find_learned.cu", "paper_1906_02253_gb300/csrc/kf_math.cuh",
                 "paper_1906_02253_gb300/csrc/find_launch.cuh", "paper_1906_02253_gb300/csrc/mlp.cuh",
                 "paper_1906_02253_gb300/build.py")
-FIND_PROFILE = {"sources_sha1": "7bc05405daa70957d38f5c39afb51827f5c768d4",
-                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125122560 + 35073792) / 302063,
-                                        "find_200ev_barrel_disks_noise100": (144009728 + 30782464) / 211523,
+FIND_PROFILE = {"sources_sha1": "37e3a4f5b5505e80f57304bd1472dadac3fc4110",
+                "dram_bytes_per_seed": {"fit_100ev_uneven_17layers_ms": (125605888 + 35233024) / 302063,
+                                        "find_200ev_barrel_disks_noise100": (144240128 + 31036672) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive4":
-                                            (170473472 + 36178944 + 128961792 + 27852800) / 211523,
+                                            (170531328 + 35969024 + 128829952 + 27841280) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2":
-                                            (168273920 + 38688512 + 159683328 + 35325696) / 211523,
+                                            (168316416 + 38796544 + 159785216 + 35333632) / 211523,
                                         "find_200ev_barrel_disks_noise100_adaptive2_learned2_0.7":
-                                            (155260160 + 31929088 + 42013696 + 3956992) / 211523}}
+                                            (154265088 + 31579648 + 42024960 + 3967232) / 211523}}
 # Hit index: algorithmic HBM bytes per hit (read 8 B of (phi, z); write 8 B sorted, 4 B id, 16 B search
 # record) plus, per (event, surface), the bin offsets (4 B per bin + 1) and the phi sub-bin offsets (16 B per bin).
 INDEX_BYTES_PER_HIT = 36
